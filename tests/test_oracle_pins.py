@@ -1,0 +1,419 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks a closed form, an
+invariant, a symmetry or a hand-worked value, chosen so that a dropped term, a
+wrong sign or index, or a transposed operand in the oracle fails at least one.
+CPU only.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ lattice
+def test_d3q19_isotropy(orc):
+    """D3Q19 weights are the unique ones giving lattice isotropy up to 4th order
+    with cs^2 = 1/3 (the paper names D3Q19 in Sec. 2.1 without its weights)."""
+    e, w, opp = orc.lattice()
+    e = e.astype(float)
+    assert len(w) == 19
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.allclose(np.einsum("k,ka->a", w, e), 0, atol=1e-16)
+    assert np.allclose(np.einsum("k,ka,kb->ab", w, e, e), np.eye(3) / 3.0, atol=1e-16)
+    assert np.allclose(np.einsum("k,ka,kb,kc->abc", w, e, e, e), 0, atol=1e-16)
+    d = np.eye(3)
+    iso4 = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+            + np.einsum("ad,bc->abcd", d, d)) / 9.0
+    assert np.allclose(np.einsum("k,ka,kb,kc,kd->abcd", w, e, e, e, e), iso4, atol=1e-16)
+    # 19 distinct velocities, the opposite of each is its negation
+    assert len({tuple(v) for v in e.astype(int)}) == 19
+    for k in range(19):
+        assert np.array_equal(e[opp[k]], -e[k])
+
+
+def test_equilibrium_moments(orc):
+    """Second-order equilibrium: sum f = rho, sum f e = rho u,
+    sum f e e = rho cs^2 I + rho u u (exact for the quadratic form)."""
+    e, _, _ = orc.lattice()
+    e = e.astype(float)
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        rho = rng.uniform(0.01, 3.0)
+        u = rng.uniform(-0.1, 0.1, 3)
+        feq = orc.equilibrium(rho, u)
+        assert abs(feq.sum() - rho) <= 1e-15 * 4 * rho
+        assert np.allclose(feq @ e, rho * u, rtol=0, atol=1e-15 * 4)
+        P = np.einsum("k,ka,kb->ab", feq, e, e)
+        assert np.allclose(P, rho * np.eye(3) / 3 + rho * np.outer(u, u), rtol=0, atol=1e-15 * 8)
+
+
+# ------------------------------------------------------------------- forces
+def _open_box(orc, shape, **kw):
+    cfg = orc.Config(shape=shape, **kw)
+    return cfg, np.zeros(shape, dtype=np.uint8)
+
+
+@pytest.mark.parametrize("kind", ["linear", "quadratic"])
+def test_force_is_discrete_gradient(orc, kind):
+    """Eq. 4 with psi = rho and weights w_k: for a linear or quadratic field,
+    sum_k w_k rho(x+e_k) e_k = cs^2 grad rho(x) exactly (odd moments vanish),
+    so with rho_w = 1 the cohesion force is F_w = -G/3 grad rho_nw."""
+    shape = (9, 10, 11)
+    G = 0.7
+    cfg, mask = _open_box(orc, shape, G=G, G_ads=(0.0, 0.0))
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    if kind == "linear":
+        rn = 1.0 + 0.01 * x - 0.02 * y + 0.03 * z
+        grad = np.stack([0.01 + 0 * x, -0.02 + 0 * x, 0.03 + 0 * x])
+    else:
+        rn = 1.0 + 0.001 * x * x + 0.002 * y * z - 0.0015 * z * z + 0.01 * x
+        grad = np.stack([0.002 * x + 0.01, 0.002 * z, 0.002 * y - 0.003 * z])
+    rho = np.stack([np.ones(shape), rn])
+    F = orc.force(cfg, mask, rho)
+    inner = (slice(1, -1),) * 3
+    expect = -G / 3.0 * grad
+    for d in range(3):
+        assert np.allclose(F[0, d][inner], expect[d][inner], rtol=0, atol=1e-14)
+
+
+def test_adhesion_flat_wall(orc):
+    """Adhesion next to a flat adhesive wall: sum_k w_k s(x+e_k) e_k has
+    y-component -(1/18 + 4/36) = -1/6 one cell above the wall, so
+    F_ads = (0, G_ads rho / 6, 0): attractive (towards the wall) for G_ads < 0."""
+    shape = (5, 6, 7)
+    cfg, mask = _open_box(orc, shape, G=0.0, G_ads=(-0.3, 0.25), periodic=(1, 0, 1))
+    mask[:, 0, :] = orc.M_SOLID | orc.M_ADHESIVE
+    rho = np.stack([np.full(shape, 1.7), np.full(shape, 0.4)])
+    F = orc.force(cfg, mask, rho)
+    assert np.allclose(F[0, 1, :, 1, :], -0.3 * 1.7 / 6.0, atol=1e-15)
+    assert np.allclose(F[1, 1, :, 1, :], 0.25 * 0.4 / 6.0, atol=1e-15)
+    assert np.allclose(F[:, 1, :, 2:-1, :], 0.0, atol=1e-15)  # beyond reach of the wall
+    assert np.allclose(F[:, 0], 0.0, atol=1e-15) and np.allclose(F[:, 2], 0.0, atol=1e-15)
+    # a neutral wall (solid without the adhesive bit) exerts nothing
+    mask[:, 0, :] = orc.M_SOLID
+    F = orc.force(cfg, mask, rho)
+    assert np.allclose(F[:, :, :, 1:, :], 0.0, atol=1e-15)
+
+
+def test_newton_third_law(orc):
+    """Periodic box, no walls: sum_x (F_w + F_nw) = 0 by the index shift
+    x -> x - e_k and e_kbar = -e_k."""
+    shape = (8, 9, 10)
+    cfg, mask = _open_box(orc, shape, G=0.9, G_ads=(0, 0), periodic=(1, 1, 1))
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(0.05, 2.0, (2,) + shape)
+    F = orc.force(cfg, mask, rho)
+    tot = F[0].sum(axis=(1, 2, 3)) + F[1].sum(axis=(1, 2, 3))
+    assert np.all(np.abs(tot) <= 1e-12 * np.abs(F).sum())
+    # and the force on one component alone does not vanish
+    assert np.abs(F[0].sum(axis=(1, 2, 3))).max() > 1e-3
+
+
+# -------------------------------------------------------------- conservation
+def _droplet_state(orc, shape, mask, center, radius, seed):
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=float) for n in shape], indexing="ij")
+    r = np.sqrt((x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2)
+    inside = r < radius
+    rng = np.random.default_rng(seed)
+    rho = np.stack([np.where(inside, 0.06, 2.0), np.where(inside, 2.0, 0.06)])
+    rho = rho * (1.0 + 1e-3 * rng.standard_normal(rho.shape))
+    return rho
+
+
+def test_mass_conserved_closed_box(orc):
+    """Closed walls, half-way bounce-back, no reservoirs: each component's mass
+    is invariant (pull + bounce-back permutes populations, BGK keeps rho)."""
+    shape = (14, 13, 12)
+    mask = orc.voxelise(shape, [(3.0, 3.0, 3.0, 2.5), (9.5, 8.0, 10.0, 3.2)])
+    cfg = orc.Config(shape=shape, G=0.9, G_ads=(-0.3, 0.3))
+    rho0 = _droplet_state(orc, shape, mask, (6, 6, 6), 4.0, seed=5)
+    f = orc.init(cfg, mask, rho0)
+    m0 = orc.measure(cfg, mask, f)["mass"]
+    orc.step(cfg, mask, f, 200)
+    m1 = orc.measure(cfg, mask, f)["mass"]
+    for s in range(2):
+        assert abs(m1[s] - m0[s]) <= 1e-12 * m0[s]
+    # the state did evolve
+    assert orc.measure(cfg, mask, f)["n_interface"] > 0
+
+
+def test_free_streaming_direction(orc):
+    """With no collision (tau -> infinity, so f* = f exactly) and no force,
+    pull streaming in a periodic box is the shift f_k(x, t+n) = f_k(x - n e_k, 0)."""
+    shape = (5, 6, 7)
+    cfg, mask = _open_box(orc, shape, tau=(1e300, 1e300), G=0.0, G_ads=(0, 0), periodic=(1, 1, 1))
+    rng = np.random.default_rng(8)
+    f = rng.uniform(0.01, 0.2, (2, 19) + shape)
+    f0 = f.copy()
+    orc.step(cfg, mask, f, 3)
+    e, _, _ = orc.lattice()
+    for k in range(19):
+        shifted = np.roll(f0[:, k], shift=(3 * e[k, 2], 3 * e[k, 1], 3 * e[k, 0]), axis=(1, 2, 3))
+        assert np.array_equal(f[:, k], shifted)
+
+
+def test_bounce_back_reverses_momentum(orc):
+    """One fluid cell enclosed by walls (a 1x1x1 box): with no force the
+    collision keeps each component's rho and the mixture's momentum (the common
+    velocity trades momentum between components only), and half-way bounce-back
+    sends every population back reversed, so rho is unchanged and the total j
+    flips sign each step."""
+    shape = (1, 1, 1)
+    cfg, mask = _open_box(orc, shape, tau=(0.8, 1.3), G=0.0, G_ads=(0, 0))
+    rng = np.random.default_rng(2)
+    f = rng.uniform(0.01, 0.2, (2, 19) + shape)
+    e, _, _ = orc.lattice()
+    rho0 = f.sum(axis=1)
+    j0 = np.einsum("skzyx,kd->d", f, e.astype(float))
+    orc.step(cfg, mask, f, 1)
+    assert np.allclose(f.sum(axis=1), rho0, rtol=1e-15)
+    assert np.allclose(np.einsum("skzyx,kd->d", f, e.astype(float)), -j0, atol=1e-15)
+    orc.step(cfg, mask, f, 1)
+    assert np.allclose(np.einsum("skzyx,kd->d", f, e.astype(float)), j0, atol=1e-15)
+
+
+def test_zero_coupling_reduces_to_single_component(orc):
+    """G = G_ads = 0 and equal tau: f^eq is linear in rho at fixed u and the
+    common velocity is the mixture's, so f_w + f_nw evolves exactly as a single
+    BGK fluid started from rho_w + rho_nw."""
+    shape = (7, 8, 9)
+    mask = orc.voxelise(shape, [(4.0, 4.0, 3.0, 2.2)])
+    cfg = orc.Config(shape=shape, tau=(0.8, 0.8), G=0.0, G_ads=(0, 0), periodic=(1, 0, 0),
+                     g=(1e-4, 0, 0))
+    rng = np.random.default_rng(4)
+    rho = rng.uniform(0.2, 1.5, (2,) + shape)
+    fa = orc.init(cfg, mask, rho)
+    fb = orc.init(cfg, mask, np.stack([rho[0] + rho[1], np.zeros(shape)]))
+    orc.step(cfg, mask, fa, 40)
+    orc.step(cfg, mask, fb, 40)
+    assert np.allclose(fa[0] + fa[1], fb[0], rtol=0, atol=1e-13)
+    # the components themselves did not stay proportional (they mixed)
+    assert not np.allclose(fa[0], fb[0] * 0.5, atol=1e-3)
+
+
+# ------------------------------------------------------------- channel flow
+@pytest.mark.parametrize("tau,tol", [(0.5 + math.sqrt(3.0 / 16.0), 1e-9), (1.0, 1e-2)])
+def test_poiseuille(orc, tau, tol):
+    """Body-force-driven flow between half-way bounce-back walls: steady
+    u(y) = g / (2 nu) (y - 1/2)(H + 1/2 - y), nu = (tau - 1/2)/3, walls half-way
+    between the solid and the first fluid layer.  With BGK and half-way
+    bounce-back the profile is exact at (tau - 1/2)^2 = 3/16; at tau = 1 it
+    carries a wall-slip error of order (16 (tau-1/2)^2 - 3) / H^2."""
+    H = 16
+    shape = (1, H + 2, 1)
+    g = 1e-6
+    cfg = orc.Config(shape=shape, tau=(tau, tau), G=0.0, G_ads=(0, 0), g=(g, 0, 0), periodic=(1, 0, 1))
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[:, 0, :] = orc.M_SOLID
+    mask[:, H + 1, :] = orc.M_SOLID
+    rho = np.zeros((2,) + shape)
+    rho[0] = 1.0
+    f = orc.init(cfg, mask, rho)
+    orc.step(cfg, mask, f, 40000)
+    u = orc.velocity(cfg, mask, f)[0, 0, 1:H + 1, 0]
+    y = np.arange(1, H + 1, dtype=float)
+    nu = (tau - 0.5) / 3.0
+    ua = g / (2 * nu) * (y - 0.5) * (H + 0.5 - y)
+    err = np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum())
+    assert err < tol, err
+
+
+# ----------------------------------------------------------- interfaces
+def _cylinder(orc, N, R, steps):
+    """Static cylindrical non-wetting drop, periodic N x N x 1 box."""
+    shape = (1, N, N)
+    cfg = orc.Config(shape=shape, periodic=(1, 1, 1), G_ads=(0, 0))
+    mask = np.zeros(shape, dtype=np.uint8)
+    y, x = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    inside = (np.sqrt((x - N / 2 + 0.5) ** 2 + (y - N / 2 + 0.5) ** 2) < R)[None]
+    rho0 = np.stack([np.where(inside, 0.06, 2.0), np.where(inside, 2.0, 0.06)])
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, steps)
+    rho = orc.density(cfg, mask, f)
+    p = orc.pressure(cfg, rho)
+    d_in, d_out = rho[1, 0, N // 2, N // 2], rho[1, 0, 0, 0]
+    area = ((rho[1] - d_out) / (d_in - d_out)).sum()
+    return math.sqrt(area / math.pi), p[0, N // 2, N // 2] - p[0, 0, 0]
+
+
+@pytest.mark.slow
+def test_laplace_law_one_surface_tension(orc):
+    """Laplace's law for cylindrical drops, dp = sigma / R: dp against 1/R is a
+    line through the origin for R = 6..14, which fixes one sigma."""
+    pts = [_cylinder(orc, 48, R, 6000) for R in (6, 8, 10, 12, 14)]
+    R = np.array([p[0] for p in pts])
+    dp = np.array([p[1] for p in pts])
+    A = np.vstack([1.0 / R, np.ones_like(R)]).T
+    (sigma, icpt), *_ = np.linalg.lstsq(A, dp, rcond=None)
+    pred = A @ np.array([sigma, icpt])
+    r2 = 1 - ((dp - pred) ** 2).sum() / ((dp - dp.mean()) ** 2).sum()
+    assert r2 >= 0.999, r2
+    assert abs(icpt) <= 0.02 * dp.max(), (icpt, dp.max())
+    assert sigma > 0
+
+
+def test_flat_interface_no_pressure_jump(orc):
+    """A planar interface (R -> infinity) carries no pressure jump at rest."""
+    shape = (32, 1, 1)
+    cfg = orc.Config(shape=shape, periodic=(1, 1, 1), G_ads=(0, 0))
+    mask = np.zeros(shape, dtype=np.uint8)
+    z = np.arange(32)[:, None, None]
+    layer = (z >= 8) & (z < 24)
+    rho0 = np.stack([np.where(layer, 2.0, 0.06), np.where(layer, 0.06, 2.0)]) * np.ones((2,) + shape)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 4000)
+    p = orc.pressure(cfg, orc.density(cfg, mask, f))
+    assert abs(p[16, 0, 0] - p[0, 0, 0]) <= 1e-6
+
+
+def _contact_angle(orc, g_w, g_nw, NX=48, NY=24, R0=9, steps=6000):
+    """Quasi-2D sessile drop of the wetting component on an adhesive wall at
+    y = 1/2; theta from a least-squares circle through the phi = 0 contour."""
+    shape = (1, NY, NX)
+    cfg = orc.Config(shape=shape, periodic=(1, 0, 1), G_ads=(g_w, g_nw))
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[0, 0, :] = orc.M_SOLID | orc.M_ADHESIVE
+    mask[0, NY - 1, :] = orc.M_SOLID | orc.M_ADHESIVE
+    y, x = np.meshgrid(np.arange(NY), np.arange(NX), indexing="ij")
+    inside = ((x - NX / 2) ** 2 + (y - 0.5) ** 2 < R0 ** 2)[None]
+    rho0 = np.stack([np.where(inside, 2.0, 0.06), np.where(inside, 0.06, 2.0)])
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, steps)
+    rho = orc.density(cfg, mask, f)[:, 0]
+    phi = (rho[0] - rho[1]) / (rho[0] + rho[1] + 1e-300)
+    pts = []
+    for yy in range(3, NY - 3):
+        row = phi[yy]
+        for xx in range(NX - 1):
+            a, b = row[xx], row[xx + 1]
+            if (a > 0) != (b > 0):
+                pts.append((xx + a / (a - b), yy))
+    for xx in range(NX):
+        col = phi[:, xx]
+        for yy in range(3, NY - 4):
+            a, b = col[yy], col[yy + 1]
+            if (a > 0) != (b > 0):
+                pts.append((xx, yy + a / (a - b)))
+    P = np.array(pts)
+    A = np.c_[P[:, 0], P[:, 1], np.ones(len(P))]
+    D, E, F = np.linalg.lstsq(A, -(P[:, 0] ** 2 + P[:, 1] ** 2), rcond=None)[0]
+    xc, yc = -D / 2, -E / 2
+    R = math.sqrt(xc * xc + yc * yc - F)
+    return math.degrees(math.acos(max(-1.0, min(1.0, -(yc - 0.5) / R))))
+
+
+@pytest.mark.slow
+def test_contact_angle_symmetries(orc):
+    """Wall adhesion: no adhesion -> 90 deg (component-swap symmetry);
+    swapping the adhesion signs gives the supplementary angle; the angle falls
+    monotonically as the wall attracts the wetting fluid more; and it follows
+    the estimate cos(theta) = (G_ads,nw - G_ads,w) / (G (rho_major - rho_minor)/2)
+    of Huang et al. (2007) to a few degrees."""
+    t0 = _contact_angle(orc, 0.0, 0.0)
+    assert abs(t0 - 90.0) <= 2.0, t0
+    ta = _contact_angle(orc, -0.2, 0.2)
+    tb = _contact_angle(orc, 0.2, -0.2)
+    assert abs(ta + tb - 180.0) <= 2.0, (ta, tb)
+    tc = _contact_angle(orc, -0.3, 0.3)
+    assert tc < ta < t0 < tb
+    for g, th in ((0.2, ta), (0.3, tc)):
+        est = math.degrees(math.acos(2 * g / (0.9 * (2.0 - 0.06) / 2)))
+        assert abs(th - est) <= 3.0, (g, th, est)
+
+
+# -------------------------------------------------------------- measurement
+def test_measure_hand_worked_column(orc):
+    gold = json.load(open(os.path.join(GOLDEN, "measure_column.json")))
+    shape = (6, 1, 1)
+    cfg = orc.Config(shape=shape, G=gold["G"])
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[0] = orc.M_INLET
+    mask[5] = orc.M_OUTLET
+    rho = np.stack([np.array(gold["rho_w"]), np.array(gold["rho_nw"])]).reshape((2,) + shape)
+    f = orc.init(cfg, mask, rho)
+    m = orc.measure(cfg, mask, f)
+    ex = gold["expected"]
+    for k in ("n_fluid", "n_w", "n_interface", "n_bulk_w", "n_bulk_nw"):
+        assert m[k] == ex[k], k
+    for k in ("S_w", "p_nw", "p_w", "p_c", "p_in", "p_out", "p_c_res"):
+        assert abs(m[k] - ex[k]) <= 1e-13, (k, m[k], ex[k])
+    assert np.allclose(m["mass"], ex["mass"], rtol=1e-14)
+    assert m["n_nonfinite"] == 0 and m["n_negative"] == 0
+
+
+def test_entry_pressure_rule(orc):
+    """p_c^e is the largest p_c up to the invasion increment; the first
+    maximiser wins ties; no invasion gives +inf."""
+    s = [0.1, 0.3, 0.5, 0.5, 0.2, 0.9]
+    assert orc.entry_pressure(s, 4) == (0.5, 2)
+    assert orc.entry_pressure(s, 1) == (0.3, 1)
+    assert orc.entry_pressure(s, 5) == (0.9, 5)
+    assert orc.entry_pressure(s, -1) == (math.inf, -1)
+    assert orc.entry_pressure([float("nan"), 0.2], 1) == (0.2, 1)
+
+
+# ----------------------------------------------------------------- geometry
+@pytest.mark.parametrize("r2,count", [(1, 7), (2, 19), (3, 27), (4, 33), (5, 57)])
+def test_voxelise_lattice_ball_counts(orc, r2, count):
+    """Cells with centre inside |x - c| <= r, c on a lattice point: the number of
+    integer points in a ball of radius^2 = 1..5 is 7, 19, 27, 33, 57."""
+    shape = (9, 9, 9)
+    # sqrt(r2)**2 can round just below r2, so the radius carries a 1e-9 margin
+    mask = orc.voxelise(shape, [(4.0, 4.0, 4.0, math.sqrt(r2 + 1e-9))])
+    assert int(((mask & orc.M_SOLID) > 0).sum()) == count
+
+
+def test_voxelise_sphere_volume(orc):
+    shape = (40, 40, 40)
+    r = 13.3
+    mask = orc.voxelise(shape, [(19.7, 20.2, 19.9, r)])
+    v = ((mask & orc.M_SOLID) > 0).sum()
+    assert abs(v - 4 / 3 * math.pi * r ** 3) < 0.01 * 4 / 3 * math.pi * r ** 3
+    assert np.all(mask[(mask & orc.M_SOLID) > 0] & orc.M_ADHESIVE)
+
+
+def test_prism_clip_and_reservoirs(orc):
+    """Sec. 2.2.2 throat domain: walls through pairs of centres, orthogonal to
+    the plane of the centres; inlet at z = 0, outlet at z = nz - 1."""
+    shape = (12, 20, 20)
+    sph = [(2.0, 2.0, 6.0, 1.0), (18.0, 2.0, 6.0, 1.0), (10.0, 17.0, 6.0, 1.0)]
+    mask = orc.voxelise(shape, sph, prism=True, reservoirs=True, membrane_layers=2)
+    # a point well inside the triangle is open in every layer
+    assert not (mask[:, 8, 10] & orc.M_SOLID).any()
+    # points outside the triangle are neutral solid in every layer
+    for (x, y) in ((0, 19), (19, 19), (10, 0)):
+        assert np.all(mask[:, y, x] == orc.M_SOLID), (x, y)
+    assert np.all(mask[0][(mask[0] & orc.M_SOLID) == 0] == orc.M_INLET)
+    assert np.all(mask[-1][(mask[-1] & orc.M_SOLID) == 0] == orc.M_OUTLET)
+    assert np.all(mask[-3:-1][(mask[-3:-1] & orc.M_SOLID) == 0] == orc.M_MEMBRANE)
+    # a point on an edge (y = 2 between the first two centres) counts as inside
+    assert mask[5, 2, 10] == 0
+
+
+def test_throat_frame(orc):
+    """Local frame of a throat: c0 at the origin, c1 on +x, c2 in the upper
+    half of the z = 0 plane; distances between the centres preserved."""
+    rng = np.random.default_rng(9)
+    for _ in range(10):
+        c = rng.uniform(0, 100, (3, 3))
+        r = rng.uniform(10, 14, 3)
+        sph = np.c_[c, r]
+        dims, org, loc = orc.throat_frame(sph)
+        assert np.allclose(loc[0, :3], 0, atol=1e-12)
+        assert abs(loc[1, 1]) < 1e-12 and abs(loc[1, 2]) < 1e-12 and loc[1, 0] > 0
+        assert abs(loc[2, 2]) < 1e-12 and loc[2, 1] > 0
+        for i in range(3):
+            for j in range(3):
+                dg = np.linalg.norm(c[i] - c[j])
+                dl = np.linalg.norm(loc[i, :3] - loc[j, :3])
+                assert abs(dg - dl) < 1e-9
+        assert np.allclose(loc[:, 3], r)
+        assert dims[2] == 2 * math.ceil(r.max()) + 1
+        mask = orc.voxelise_throat(sph)
+        assert mask.shape == (dims[2], dims[1], dims[0])
+        assert (mask == orc.M_INLET).any() and (mask == orc.M_OUTLET).any()
