@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused two-component Shan-Chen D3Q19 step.
+
+Workload (default): the fully resolved drainage sample, 192^3 lattice, 300
+non-overlapping spheres with radii U[10, 14] placed by seeded random
+sequential addition, inlet reservoir layer z = 0, three membrane layers and
+the outlet reservoir layer at the top, FP32 populations.  One bench step is
+one time step of the whole domain (one launch of the fused step kernel).
+
+Printed JSON line (rank 0):
+  value      fluid-cell updates per second (MLUPS) with the state resident in
+             HBM, CUDA events around exactly --steps launches, max over ranks;
+  roofline   the step kernel against HBM bandwidth: algorithmic bytes
+             (2 x 19 populations read + written per fluid cell) / mean launch time;
+  e2e        the same metric through the public C ABI from host data: domain
+             creation from the host sphere list, then per step
+             set_pressure_bc + 100 time steps + a measurement read back;
+  cpu_baseline  the FP64 oracle on a bounded crop of the same sample.
+--impl reference times that oracle alone (the method has no other reference
+implementation): rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 2-comp Shan-Chen MLUPS & % HBM peak; pore throats/s vs plain"
+FALLBACK_HBM_GBS = 6800.0
+E2E_SUBSTEPS = 100
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def sample_geometry():
+    import workloads as W
+    spheres = W.sample192_spheres()
+    return spheres, (192, 192, 192)
+
+
+def update_bytes(mask):
+    """Algorithmic bytes of one step: 19 populations x 4 B read + 4 B written
+    per component present at each non-solid cell (membrane cells carry only the
+    wetting component)."""
+    solid = (mask & 1) != 0
+    memb = (mask & 4) != 0
+    n_w = int((~solid).sum())
+    n_nw = int((~solid & ~memb).sum())
+    return n_w, n_w * 152 + n_nw * 152
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_gb_s"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_step.cu", "lbm_device.cuh", "lbm_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1906_04722_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "sc_step_sample192_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        if d.get("kernel_hash") == kernel_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+class OracleCrop:
+    """The FP64 oracle on a 64^3 crop of the 192^3 sample (same packing shifted
+    so that x, y in [64, 128) of the sample fill the crop, reservoir layer at the
+    inlet end, membrane and outlet at the other), timed on the host's cores."""
+
+    def __init__(self):
+        import oracle
+        import workloads as W
+        spheres, _ = sample_geometry()
+        self.shape = (64, 64, 64)
+        sh = spheres.copy()
+        sh[:, :3] -= np.array([64.0, 64.0, 0.0])
+        self.oracle = oracle
+        self.mask = oracle.voxelise(self.shape, sh, reservoirs=True, membrane_layers=3)
+        self.cfg = oracle.Config(shape=self.shape, tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS,
+                                 rho_in=(W.RHO_MINOR, W.RHO_MAJOR), rho_out=(W.RHO_MAJOR, W.RHO_MINOR))
+        self.f = oracle.init(self.cfg, self.mask, W.initial_densities(self.shape))
+        self.n_update = int(((self.mask & 1) == 0).sum())
+        self.cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def time_steps(self, n):
+        t0 = time.perf_counter()
+        self.oracle.step(self.cfg, self.mask, self.f, n)
+        return time.perf_counter() - t0
+
+    def sample_text(self, steps):
+        return (f"64^3 crop of the 192^3 sample (x, y in [64, 128)), {steps} FP64 oracle steps, "
+                f"{self.n_update} fluid cells per step")
+
+
+def cpu_baseline():
+    """About 15 s of oracle work on the crop."""
+    oc = OracleCrop()
+    oc.time_steps(1)
+    dt1 = oc.time_steps(2) / 2
+    steps = max(1, min(400, int(15.0 / max(dt1, 1e-3))))
+    dt = oc.time_steps(steps)
+    return {"value": oc.n_update * steps / dt / 1e6, "unit": "MLUPS", "cores": oc.cores, "kind": "oracle",
+            "sample": oc.sample_text(steps)}
+
+
+def run_reference(args, rank, world):
+    """The oracle itself as the reference arm, on the host cores, rank 0 only."""
+    if rank != 0:
+        return 0
+    oc = OracleCrop()
+    for _ in range(args.warmup):
+        oc.time_steps(1)
+    steps = max(1, args.steps)
+    t_all = sum(oc.time_steps(1) for _ in range(steps))
+    value = oc.n_update * steps / t_all / 1e6
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus, "steps": steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_all / steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": "sample192, 64^3 crop (FP64 oracle on host cores)", "global_batch": 1,
+                      "seq_len": 0, "parallelism": "host OpenMP threads"},
+           "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oc.cores, "kind": "oracle",
+                            "sample": oc.sample_text(steps)},
+           "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1906_04722_gb300 as lbm
+    import workloads as W
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device for --impl ours")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    spheres, box = sample_geometry()
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR, reservoirs=True, membrane_layers=3)
+    stream = torch.cuda.Stream()
+    dom = lbm.Domain(params, spheres, box, stream=ctypes.c_void_p(stream.cuda_stream))
+    mask = dom.mask()
+    n_upd, bytes_per_step = update_bytes(mask)
+    dom.set_pressure_bc(2.1, W.RHO_MAJOR)
+    dom.step(args.warmup)
+    torch.cuda.synchronize()
+
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        evs[0].record(stream)
+        for i in range(args.steps):
+            dom.step(1)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t = torch.tensor([total_ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * n_upd * args.steps / (total_ms / 1e3) / 1e6
+    mean_ms = float(np.mean(per))
+    peak, peak_kind = read_peaks()
+    achieved = bytes_per_step / (mean_ms / 1e3) / 1e9
+    m = dom.measure()
+    dom.close()
+
+    # end to end through the C ABI from host data
+    e2e_val = None
+    h2d = d2h = 0
+    if args.e2e_steps > 0:
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2 = lbm.Domain(params, spheres, box)
+        ladder = [W.RHO_MAJOR + 0.005 * i for i in range(args.e2e_steps)]
+        for rin in ladder:
+            d2.set_pressure_bc(rin, W.RHO_MAJOR)
+            d2.step(E2E_SUBSTEPS)
+            d2.measure()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d2.close()
+        N = box[0] * box[1] * box[2]
+        e2e_val = world * n_upd * E2E_SUBSTEPS * args.e2e_steps / dt / 1e6
+        h2d = int((N + 2 * N * 4 + spheres.nbytes) / args.e2e_steps) + 16
+        d2h = 16 * 8
+
+    clocks = clk.summary()
+    out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "sample192: 192^3, 300 RSA spheres r~U[10,14], reservoirs + 3 membrane layers, "
+                                  "FP32 populations, one fused step per launch",
+                      "fluid_cells": n_upd, "global_batch": world, "seq_len": 0,
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "inputs larger than L2 (2 x 1.08 GB population buffers)"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": read_traffic(), "peak_kind": peak_kind,
+                        "kernel": "sc_step_kernel<10>", "algorithmic_bytes_per_launch": bytes_per_step},
+           "gpu_launches": args.steps,
+           "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "step": f"set_pressure_bc + {E2E_SUBSTEPS} time steps + lbm_measure; domain creation "
+                           "from the host sphere list inside the timed region"},
+           "check": {"S_w": m["S_w"], "p_c_res": m["p_c_res"], "mass": m["mass"]}}
+    if clocks:
+        out["clocks"] = clocks
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * lbm.h -- C ABI of the GB300 two-component Shan-Chen D3Q19 library.
+ *
+ * The library implements the time step that the hybrid pore-network / lattice
+ * Boltzmann method of Montella, Yuan, Chareyre and Gens spends its time in:
+ * pull streaming with half-way bounce-back (Eq. 1, left-hand side), moments
+ * (Eqs. 2-3), the Shan-Chen inter-component force (Eq. 4, read with psi = rho
+ * and the lattice weights), wall adhesion, the velocity-shift BGK collision
+ * (Eq. 1, right-hand side) and reservoir layers whose densities are raised step
+ * by step to drive drainage (Sec. 2.2.2).  The measurements return the bulk
+ * phase pressures of the equation of state (Eq. 5), the capillary pressure and
+ * the saturation from which the entry pressure p_c^e (the largest p_c reached
+ * during invasion, Sec. 2.2.2) is read.
+ *
+ * Conventions shared by every call:
+ *  - Lattice units.  Cell (x, y, z) has its centre at (x, y, z); cell index
+ *    c = (z * ny + y) * nx + x.  N = nx * ny * nz.
+ *  - Component 0 is the wetting fluid, component 1 the non-wetting fluid.
+ *  - D3Q19 order of the populations: k = 0 rest; 1..6 = (+x, -x, +y, -y, +z, -z);
+ *    7..10 = (+x+y, -x-y, +x-y, -x+y); 11..14 = (+x+z, -x-z, +x-z, -x+z);
+ *    15..18 = (+y+z, -y-z, +y-z, -y+z).  Opposite pairs are (1,2), (3,4), ...
+ *  - Mask bytes: bit 0 solid, bit 1 adhesive (grain; meaningful with bit 0),
+ *    bit 2 membrane (solid for the non-wetting fluid only), bit 3 inlet
+ *    reservoir layer, bit 4 outlet reservoir layer.
+ *  - Cells beyond a non-periodic box edge are neutral (non-adhesive) walls.
+ *  - Every pointer argument is a HOST pointer unless stated otherwise; inputs
+ *    are copied during the call and stay owned by the caller.  Device memory is
+ *    allocated and owned by the library and released by lbm_destroy.
+ *  - Every int-returning call returns LBM_OK (0) or a negative LBM_ERR_* code
+ *    and then lbm_last_error() describes the failure (thread-local string).
+ *    No C++ exception crosses this boundary.
+ *  - A domain is not thread-safe; distinct domains may run on distinct streams.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, bad enum)   */
+#define LBM_ERR_OOM (-2)       /* device or host allocation failed                      */
+#define LBM_ERR_CUDA (-3)      /* a CUDA runtime call failed                            */
+#define LBM_ERR_TIMEOUT (-4)   /* a bounded wait for device work ran out                */
+#define LBM_ERR_NONFINITE (-5) /* a measurement met NaN/Inf or negative densities       */
+#define LBM_ERR_STATE (-6)     /* call not valid in the domain's current state          */
+
+#define LBM_MASK_SOLID 1
+#define LBM_MASK_ADHESIVE 2
+#define LBM_MASK_MEMBRANE 4
+#define LBM_MASK_INLET 8
+#define LBM_MASK_OUTLET 16
+
+typedef struct lbm_domain lbm_domain; /* opaque, library-owned */
+
+/* Model parameters (lattice units). */
+typedef struct {
+    double tau[2];        /* BGK relaxation time per component (> 0.5)                 */
+    double G;             /* Shan-Chen inter-component strength G_12 = G_21 (Eq. 4)     */
+    double G_ads[2];      /* wall adhesion strength per component (< 0 attracts)        */
+    double body_force[3]; /* acceleration g; the body force on component s is rho_s g   */
+    double rho_major;     /* density of the majority fluid of a phase (e.g. 2.0)        */
+    double rho_minor;     /* density of the dissolved other fluid (e.g. 0.06)           */
+    int precision;        /* storage of the populations: 0 = FP32 (only value so far)   */
+    int periodic[3];      /* 1 = periodic along x, y, z                                 */
+    int reservoirs;       /* 1 = inlet layer z = 0 (non-wetting reservoir) and outlet
+                             layer z = nz-1 (wetting reservoir)                          */
+    int membrane_layers;  /* fluid layers just above the outlet layer that let only the
+                             wetting fluid pass (porous plate); 0 = none                 */
+    int prism_clip;       /* 1 = cells outside the triangular prism of the first three
+                             spheres are neutral walls (throat domain, Sec. 2.2.2)       */
+} lbm_params;
+
+/* Observables of the state at the current time level (Eq. 5 for pressures).
+ *   interior fluid = not solid, not membrane, not a reservoir layer;
+ *   S_w = #(interior cells with rho_w > rho_nw) / #(interior cells);
+ *   interface cells: |phi| < 0.5 with phi = (rho_w - rho_nw)/(rho_w + rho_nw);
+ *   p_w, p_nw: mean Eq. 5 pressure over interior cells with phi > 0.9 / < -0.9;
+ *   p_c = p_nw - p_w (NaN when a phase has no bulk cell);
+ *   p_in, p_out: mean pressure over the inlet / outlet layers; p_c_res = p_in - p_out.
+ * Sums are accumulated in FP64 on the device. */
+typedef struct {
+    double mass[2];
+    double p_w, p_nw, p_c;
+    double p_in, p_out, p_c_res;
+    double S_w;
+    long long n_fluid, n_w, n_interface, n_bulk_w, n_bulk_nw, n_in, n_out;
+    long long n_nonfinite, n_negative;
+    int status_flags; /* bit 0: NaN/Inf density seen; bit 1: negative density seen */
+} lbm_measurement;
+
+/* lbm_create_domain -- voxelise spheres into a box and allocate a domain
+ * (Sec. 2.2.2 throat domain when prism_clip = 1; the fully resolved sample
+ * otherwise).
+ *   spheres   n_spheres x 4 doubles (cx, cy, cz, r), lattice units; a cell is
+ *             grain (solid + adhesive) when |centre - c| <= r.  May be NULL when
+ *             n_spheres = 0.
+ *   box       (nx, ny, nz), each >= 1.
+ *   stream    cudaStream_t the domain's work is queued on (NULL = legacy stream).
+ * The populations start at the rest equilibrium of rho_major wetting fluid
+ * (with rho_minor non-wetting) and, on the inlet layer, the reverse.
+ * Returns LBM_ERR_ARG for bad sizes or params, LBM_ERR_OOM when device memory
+ * runs out. */
+int lbm_create_domain(const lbm_params* params, const double* spheres, int n_spheres,
+                      const int box[3], void* stream, lbm_domain** out);
+
+/* lbm_create_domain_mask -- as lbm_create_domain, from an explicit mask
+ * (N bytes, layout above) instead of spheres; prism_clip, reservoirs and
+ * membrane_layers in params are ignored (the mask already carries them). */
+int lbm_create_domain_mask(const lbm_params* params, const unsigned char* mask, const int box[3],
+                           void* stream, lbm_domain** out);
+
+/* lbm_set_densities -- reset the populations to the rest equilibrium of the
+ * given densities: rho (2 x N doubles, component-major).  Values at cells where
+ * a component is not fluid are ignored.  Resets the step counter. */
+int lbm_set_densities(lbm_domain* d, const double* rho);
+
+/* lbm_set_pressure_bc -- densities imposed on the reservoir layers from the
+ * next step on: inlet (rho_minor, rho_in_nw), outlet (rho_out_w, rho_minor)
+ * (Sec. 2.2.2: the inlet/outlet densities are adjusted to raise p_c). */
+int lbm_set_pressure_bc(lbm_domain* d, double rho_in_nw, double rho_out_w);
+
+/* lbm_step -- queue n_steps fused time steps on the domain's stream
+ * (asynchronous; n_steps >= 0). */
+int lbm_step(lbm_domain* d, int n_steps);
+
+/* lbm_measure -- observables of the current state (synchronises the domain's
+ * stream, bounded by a 60 s wait: LBM_ERR_TIMEOUT).  Returns LBM_ERR_NONFINITE
+ * (with *out filled) when NaN/Inf or negative densities were found. */
+int lbm_measure(lbm_domain* d, lbm_measurement* out);
+
+/* lbm_get_density -- densities of the current state, 2 x N doubles
+ * (component-major), 0 where a component is not fluid. Synchronising. */
+int lbm_get_density(lbm_domain* d, double* rho_out);
+
+/* lbm_get_mask -- the domain's mask, N bytes. */
+int lbm_get_mask(const lbm_domain* d, unsigned char* mask_out);
+
+/* lbm_get_dims -- (nx, ny, nz) and the number of interior fluid cells. */
+int lbm_get_dims(const lbm_domain* d, int dims_out[3], long long* n_fluid_cells);
+
+/* lbm_get_state / lbm_set_state -- checkpoint: the stored populations,
+ * 2 x 19 x N floats (component, direction, cell), plus the step counter.  The
+ * stored values are the post-collision populations of the last step, which the
+ * next step pulls from (after lbm_set_densities, values whose pull yields the
+ * rest equilibrium).  Resuming from a saved state reproduces the uninterrupted
+ * run bit for bit. */
+int lbm_get_state(lbm_domain* d, float* f_out, long long* step_out);
+int lbm_set_state(lbm_domain* d, const float* f_in, long long step);
+
+/* lbm_destroy -- release the domain (NULL is ignored). */
+void lbm_destroy(lbm_domain* d);
+
+/* lbm_last_error -- description of the last failure on this thread. */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H_ */

@@ -1,0 +1,284 @@
+"""Python binding of liblbm.so, the GB300 two-component Shan-Chen D3Q19 library.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  The functions carry the C-ABI names of include/lbm.h; ``Domain`` is a
+small convenience wrapper over them.  Arrays are numpy (host) arrays in the
+ABI layouts: masks uint8[nz, ny, nx], densities float64[2, nz, ny, nx],
+stored populations float32[2, 19, nz, ny, nx].  If the compiled library is
+missing and cannot be built, loading raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK = 0
+LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_TIMEOUT, LBM_ERR_NONFINITE, LBM_ERR_STATE = -1, -2, -3, -4, -5, -6
+MASK_SOLID, MASK_ADHESIVE, MASK_MEMBRANE, MASK_INLET, MASK_OUTLET = 1, 2, 4, 8, 16
+Q = 19
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("G_ads", ctypes.c_double * 2),
+                ("body_force", ctypes.c_double * 3), ("rho_major", ctypes.c_double),
+                ("rho_minor", ctypes.c_double), ("precision", ctypes.c_int), ("periodic", ctypes.c_int * 3),
+                ("reservoirs", ctypes.c_int), ("membrane_layers", ctypes.c_int), ("prism_clip", ctypes.c_int)]
+
+
+class lbm_measurement(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double * 2),
+                ("p_w", ctypes.c_double), ("p_nw", ctypes.c_double), ("p_c", ctypes.c_double),
+                ("p_in", ctypes.c_double), ("p_out", ctypes.c_double), ("p_c_res", ctypes.c_double),
+                ("S_w", ctypes.c_double),
+                ("n_fluid", ctypes.c_longlong), ("n_w", ctypes.c_longlong), ("n_interface", ctypes.c_longlong),
+                ("n_bulk_w", ctypes.c_longlong), ("n_bulk_nw", ctypes.c_longlong), ("n_in", ctypes.c_longlong),
+                ("n_out", ctypes.c_longlong), ("n_nonfinite", ctypes.c_longlong),
+                ("n_negative", ctypes.c_longlong), ("status_flags", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if name == "mass" else v
+        return out
+
+
+# exported symbol -> (restype, argtypes)
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_FP = ctypes.POINTER(ctypes.c_float)
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+_IP = ctypes.POINTER(ctypes.c_int)
+_LLP = ctypes.POINTER(ctypes.c_longlong)
+SIGNATURES = {
+    "lbm_create_domain": (ctypes.c_int, [ctypes.POINTER(lbm_params), _DP, ctypes.c_int, _IP, _VP, ctypes.POINTER(_VP)]),
+    "lbm_create_domain_mask": (ctypes.c_int, [ctypes.POINTER(lbm_params), _U8P, _IP, _VP, ctypes.POINTER(_VP)]),
+    "lbm_set_densities": (ctypes.c_int, [_VP, _DP]),
+    "lbm_set_pressure_bc": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double]),
+    "lbm_step": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lbm_measure": (ctypes.c_int, [_VP, ctypes.POINTER(lbm_measurement)]),
+    "lbm_get_density": (ctypes.c_int, [_VP, _DP]),
+    "lbm_get_mask": (ctypes.c_int, [_VP, _U8P]),
+    "lbm_get_dims": (ctypes.c_int, [_VP, _IP, _LLP]),
+    "lbm_get_state": (ctypes.c_int, [_VP, _FP, _LLP]),
+    "lbm_set_state": (ctypes.c_int, [_VP, _FP, ctypes.c_longlong]),
+    "lbm_destroy": (None, [_VP]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblbm.so (building it first when its sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise ImportError(f"liblbm.so is missing at {_build.LIB}; run paper_1906_04722_gb300/build.py")
+            L = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != LBM_OK:
+        raise LbmError(rc, where, load().lbm_last_error().decode())
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def make_params(tau=(1.0, 1.0), G=0.9, G_ads=(-0.3, 0.3), body_force=(0.0, 0.0, 0.0), rho_major=2.0,
+                rho_minor=0.06, periodic=(0, 0, 0), reservoirs=False, membrane_layers=0, prism_clip=False,
+                precision=0) -> lbm_params:
+    p = lbm_params()
+    for s in range(2):
+        p.tau[s] = float(tau[s])
+        p.G_ads[s] = float(G_ads[s])
+    p.G = float(G)
+    for d in range(3):
+        p.body_force[d] = float(body_force[d])
+        p.periodic[d] = int(bool(periodic[d]))
+    p.rho_major = float(rho_major)
+    p.rho_minor = float(rho_minor)
+    p.precision = int(precision)
+    p.reservoirs = int(bool(reservoirs))
+    p.membrane_layers = int(membrane_layers)
+    p.prism_clip = int(bool(prism_clip))
+    return p
+
+
+# --------------------------------------------------------- C-ABI functions
+def lbm_create_domain(params: lbm_params, spheres, box, stream=None):
+    L = load()
+    sp = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4)) if spheres is not None else None
+    n = 0 if sp is None else sp.shape[0]
+    bx = (ctypes.c_int * 3)(*[int(v) for v in box])
+    h = ctypes.c_void_p()
+    rc = L.lbm_create_domain(ctypes.byref(params), sp.ctypes.data_as(_DP) if n else None, n, bx,
+                             stream if stream is not None else _torch_stream(), ctypes.byref(h))
+    _check(rc, "lbm_create_domain")
+    return h
+
+
+def lbm_create_domain_mask(params: lbm_params, mask: np.ndarray, stream=None):
+    L = load()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    nz, ny, nx = m.shape
+    bx = (ctypes.c_int * 3)(nx, ny, nz)
+    h = ctypes.c_void_p()
+    rc = L.lbm_create_domain_mask(ctypes.byref(params), m.ctypes.data_as(_U8P), bx,
+                                  stream if stream is not None else _torch_stream(), ctypes.byref(h))
+    _check(rc, "lbm_create_domain_mask")
+    return h
+
+
+def lbm_get_dims(h):
+    d = (ctypes.c_int * 3)()
+    nf = ctypes.c_longlong()
+    _check(load().lbm_get_dims(h, d, ctypes.byref(nf)), "lbm_get_dims")
+    return (d[0], d[1], d[2]), nf.value
+
+
+def lbm_set_densities(h, rho: np.ndarray):
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    _check(load().lbm_set_densities(h, r.ctypes.data_as(_DP)), "lbm_set_densities")
+
+
+def lbm_set_pressure_bc(h, rho_in_nw: float, rho_out_w: float):
+    _check(load().lbm_set_pressure_bc(h, float(rho_in_nw), float(rho_out_w)), "lbm_set_pressure_bc")
+
+
+def lbm_step(h, n_steps: int):
+    _check(load().lbm_step(h, int(n_steps)), "lbm_step")
+
+
+def lbm_measure(h, allow_nonfinite: bool = False) -> dict:
+    m = lbm_measurement()
+    rc = load().lbm_measure(h, ctypes.byref(m))
+    if not (allow_nonfinite and rc == LBM_ERR_NONFINITE):
+        _check(rc, "lbm_measure")
+    return m.as_dict()
+
+
+def lbm_get_density(h) -> np.ndarray:
+    (nx, ny, nz), _ = lbm_get_dims(h)
+    out = np.empty((2, nz, ny, nx), dtype=np.float64)
+    _check(load().lbm_get_density(h, out.ctypes.data_as(_DP)), "lbm_get_density")
+    return out
+
+
+def lbm_get_mask(h) -> np.ndarray:
+    (nx, ny, nz), _ = lbm_get_dims(h)
+    out = np.empty((nz, ny, nx), dtype=np.uint8)
+    _check(load().lbm_get_mask(h, out.ctypes.data_as(_U8P)), "lbm_get_mask")
+    return out
+
+
+def lbm_get_state(h):
+    (nx, ny, nz), _ = lbm_get_dims(h)
+    out = np.empty((2, Q, nz, ny, nx), dtype=np.float32)
+    st = ctypes.c_longlong()
+    _check(load().lbm_get_state(h, out.ctypes.data_as(_FP), ctypes.byref(st)), "lbm_get_state")
+    return out, st.value
+
+
+def lbm_set_state(h, f: np.ndarray, step: int):
+    a = np.ascontiguousarray(f, dtype=np.float32)
+    _check(load().lbm_set_state(h, a.ctypes.data_as(_FP), int(step)), "lbm_set_state")
+
+
+def lbm_destroy(h):
+    if h:
+        load().lbm_destroy(h)
+
+
+def lbm_last_error() -> str:
+    return load().lbm_last_error().decode()
+
+
+class Domain:
+    """Owning wrapper of one lbm_domain handle."""
+
+    def __init__(self, params: lbm_params, spheres=None, box=None, mask=None, stream=None):
+        if mask is not None:
+            self.h = lbm_create_domain_mask(params, mask, stream)
+        else:
+            self.h = lbm_create_domain(params, spheres, box, stream)
+        self.dims, self.n_fluid = lbm_get_dims(self.h)
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.dims
+        return (nz, ny, nx)
+
+    def set_densities(self, rho):
+        lbm_set_densities(self.h, rho)
+
+    def set_pressure_bc(self, rho_in_nw, rho_out_w):
+        lbm_set_pressure_bc(self.h, rho_in_nw, rho_out_w)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def measure(self, allow_nonfinite=False):
+        return lbm_measure(self.h, allow_nonfinite)
+
+    def density(self):
+        return lbm_get_density(self.h)
+
+    def mask(self):
+        return lbm_get_mask(self.h)
+
+    def state(self):
+        return lbm_get_state(self.h)
+
+    def set_state(self, f, step):
+        lbm_set_state(self.h, f, step)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,378 @@
+// lbm_api.cu -- the extern "C" entry points declared in include/lbm.h.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbmk {
+
+namespace {
+thread_local std::string g_error;
+
+// Rounds n up to a multiple of 32 floats so that every population plane starts
+// on a 128-byte boundary.
+long long plane_stride(long long n) { return (n + 31) / 32 * 32; }
+
+#define LBM_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                \
+            return e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;          \
+        }                                                                                 \
+    } while (0)
+
+int check_params(const lbm_params* p) {
+    if (!p) { set_error("params is NULL"); return LBM_ERR_ARG; }
+    for (int s = 0; s < 2; ++s)
+        if (!(p->tau[s] > 0.5) || !std::isfinite(p->tau[s])) { set_error("tau must be finite and > 0.5"); return LBM_ERR_ARG; }
+    if (!std::isfinite(p->G) || !std::isfinite(p->G_ads[0]) || !std::isfinite(p->G_ads[1])) {
+        set_error("G and G_ads must be finite");
+        return LBM_ERR_ARG;
+    }
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(p->body_force[d])) { set_error("body_force must be finite"); return LBM_ERR_ARG; }
+    if (!(p->rho_major > 0) || !(p->rho_minor >= 0) || !std::isfinite(p->rho_major) || !std::isfinite(p->rho_minor)) {
+        set_error("rho_major must be > 0 and rho_minor >= 0");
+        return LBM_ERR_ARG;
+    }
+    if (p->precision != 0) { set_error("only precision = 0 (FP32 populations) is available"); return LBM_ERR_ARG; }
+    if (p->membrane_layers < 0) { set_error("membrane_layers must be >= 0"); return LBM_ERR_ARG; }
+    return LBM_OK;
+}
+
+int check_box(const int box[3]) {
+    if (!box) { set_error("box is NULL"); return LBM_ERR_ARG; }
+    for (int d = 0; d < 3; ++d)
+        if (box[d] < 1 || box[d] > 4096) { set_error("box sizes must be in [1, 4096]"); return LBM_ERR_ARG; }
+    const long long N = (long long)box[0] * box[1] * box[2];
+    // population indices are 32-bit: 2 * 19 planes must stay below 2^31 entries
+    if (plane_stride(N) * 2 * Q >= (1LL << 31)) {
+        set_error("domain too large for one launch (at most ~56 million cells)");
+        return LBM_ERR_ARG;
+    }
+    return LBM_OK;
+}
+
+void fill_phys(lbm_domain* d, double rho_in_nw, double rho_out_w) {
+    const lbm_params& p = d->params;
+    Phys& ph = d->phys;
+    for (int s = 0; s < 2; ++s) {
+        ph.tau[s] = (float)p.tau[s];
+        ph.omega[s] = (float)(1.0 / p.tau[s]);
+        ph.Gads[s] = (float)p.G_ads[s];
+    }
+    ph.G = (float)p.G;
+    for (int k = 0; k < 3; ++k) ph.g[k] = (float)p.body_force[k];
+    ph.rho_in[0] = (float)p.rho_minor;
+    ph.rho_in[1] = (float)rho_in_nw;
+    ph.rho_out[0] = (float)rho_out_w;
+    ph.rho_out[1] = (float)p.rho_minor;
+}
+
+void free_domain(lbm_domain* d) {
+    if (!d) return;
+    cudaFree(d->f[0]);
+    cudaFree(d->f[1]);
+    cudaFree(d->d_mask);
+    cudaFree(d->d_nbr);
+    cudaFree(d->d_nbr_nw);
+    cudaFree(d->d_adh);
+    cudaFree(d->d_rho);
+    cudaFree(d->d_partials);
+    cudaFree(d->d_result);
+    if (d->h_result) cudaFreeHost(d->h_result);
+    if (d->done) cudaEventDestroy(d->done);
+    delete d;
+}
+
+// Bounded wait for the domain's queued work: polls an event for up to 60 s.
+int wait_domain(lbm_domain* d) {
+    LBM_CUDA(cudaEventRecord(d->done, d->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        cudaError_t e = cudaEventQuery(d->done);
+        if (e == cudaSuccess) return LBM_OK;
+        if (e != cudaErrorNotReady) {
+            set_error(std::string("device work failed: ") + cudaGetErrorString(e));
+            return LBM_ERR_CUDA;
+        }
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60)) {
+            set_error("device work did not finish within 60 s");
+            return LBM_ERR_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+// Upload rest-equilibrium densities (host doubles, 2 x N) and build the stored
+// populations from them.
+int upload_densities(lbm_domain* d, const double* rho) {
+    const long long N = d->N;
+    std::vector<float> tmp((size_t)(2 * N));
+    for (long long i = 0; i < 2 * N; ++i) tmp[(size_t)i] = (float)rho[i];
+    LBM_CUDA(cudaMemcpyAsync(d->d_rho, tmp.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, d->stream));
+    LBM_CUDA(launch_init(d->d_rho, d->f[0], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+    d->cur = 0;
+    d->step = 0;
+    return wait_domain(d);
+}
+
+int create_common(const lbm_params* params, const uint8_t* mask_host, const int box[3], void* stream,
+                  lbm_domain** out) {
+    lbm_domain* d = new (std::nothrow) lbm_domain();
+    if (!d) { set_error("host allocation failed"); return LBM_ERR_OOM; }
+    std::memset(d, 0, sizeof(*d));
+    d->params = *params;
+    d->stream = (cudaStream_t)stream;
+    Geom& g = d->geom;
+    g.nx = box[0];
+    g.ny = box[1];
+    g.nz = box[2];
+    g.nxy = box[0] * box[1];
+    d->N = (long long)g.nxy * g.nz;
+    g.plane = (int)plane_stride(d->N);
+    g.px = params->periodic[0] ? 1 : 0;
+    g.py = params->periodic[1] ? 1 : 0;
+    g.pz = params->periodic[2] ? 1 : 0;
+    d->tile = default_tile(g);
+    fill_phys(d, params->rho_major, params->rho_major);
+
+    auto fail = [&](int rc) { free_domain(d); return rc; };
+#define LBM_CUDA_D(call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);    \
+        }                                                                                 \
+    } while (0)
+    const size_t fbytes = sizeof(float) * (size_t)g.plane * 2 * Q;
+    LBM_CUDA_D(cudaEventCreateWithFlags(&d->done, cudaEventDisableTiming));
+    LBM_CUDA_D(cudaMalloc(&d->f[0], fbytes));
+    LBM_CUDA_D(cudaMalloc(&d->f[1], fbytes));
+    LBM_CUDA_D(cudaMalloc(&d->d_mask, (size_t)d->N));
+    LBM_CUDA_D(cudaMalloc(&d->d_nbr, sizeof(uint32_t) * (size_t)d->N));
+    LBM_CUDA_D(cudaMalloc(&d->d_nbr_nw, sizeof(uint32_t) * (size_t)d->N));
+    LBM_CUDA_D(cudaMalloc(&d->d_adh, sizeof(uint32_t) * (size_t)d->N));
+    LBM_CUDA_D(cudaMalloc(&d->d_rho, sizeof(float) * 2 * (size_t)d->N));
+    d->meas_blocks = measure_blocks(g);
+    LBM_CUDA_D(cudaMalloc(&d->d_partials, sizeof(double) * NMEAS * (size_t)d->meas_blocks));
+    LBM_CUDA_D(cudaMalloc(&d->d_result, sizeof(double) * NMEAS));
+    LBM_CUDA_D(cudaMallocHost(&d->h_result, sizeof(double) * NMEAS));
+    // the untouched planes between N and the plane stride stay zero
+    LBM_CUDA_D(cudaMemsetAsync(d->f[0], 0, fbytes, d->stream));
+    LBM_CUDA_D(cudaMemsetAsync(d->f[1], 0, fbytes, d->stream));
+    LBM_CUDA_D(cudaMemcpyAsync(d->d_mask, mask_host, (size_t)d->N, cudaMemcpyHostToDevice, d->stream));
+    LBM_CUDA_D(launch_geometry(d->d_mask, d->d_nbr, d->d_nbr_nw, d->d_adh, g, d->stream));
+#undef LBM_CUDA_D
+    long long nf = 0;
+    for (long long c = 0; c < d->N; ++c)
+        if (mask_host[c] == 0) ++nf;
+    d->n_fluid = nf;
+
+    // default initial state: wetting fluid everywhere, non-wetting reservoir on the inlet layer
+    std::vector<double> rho((size_t)(2 * d->N));
+    for (long long c = 0; c < d->N; ++c) {
+        const bool inlet = mask_host[c] & LBM_MASK_INLET;
+        rho[(size_t)c] = inlet ? params->rho_minor : params->rho_major;
+        rho[(size_t)(d->N + c)] = inlet ? params->rho_major : params->rho_minor;
+    }
+    int rc = upload_densities(d, rho.data());
+    if (rc != LBM_OK) return fail(rc);
+    *out = d;
+    return LBM_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+}  // namespace lbmk
+
+using namespace lbmk;
+
+extern "C" {
+
+int lbm_create_domain(const lbm_params* params, const double* spheres, int n_spheres, const int box[3],
+                      void* stream, lbm_domain** out) {
+    try {
+        int rc = check_params(params);
+        if (rc) return rc;
+        rc = check_box(box);
+        if (rc) return rc;
+        if (!out) { set_error("out is NULL"); return LBM_ERR_ARG; }
+        if (n_spheres < 0 || (n_spheres > 0 && !spheres)) { set_error("bad sphere list"); return LBM_ERR_ARG; }
+        for (int i = 0; i < n_spheres; ++i)
+            for (int k = 0; k < 4; ++k)
+                if (!std::isfinite(spheres[4 * i + k]) || (k == 3 && spheres[4 * i + k] < 0)) {
+                    set_error("sphere entries must be finite with r >= 0");
+                    return LBM_ERR_ARG;
+                }
+        if (params->prism_clip && n_spheres < 3) { set_error("prism_clip needs three spheres"); return LBM_ERR_ARG; }
+        const long long N = (long long)box[0] * box[1] * box[2];
+        std::vector<uint8_t> mask((size_t)N);
+        voxelise_box(box[0], box[1], box[2], spheres, n_spheres, params->prism_clip, params->reservoirs,
+                     params->membrane_layers, mask.data());
+        return create_common(params, mask.data(), box, stream, out);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected host exception");
+        return LBM_ERR_ARG;
+    }
+}
+
+int lbm_create_domain_mask(const lbm_params* params, const unsigned char* mask, const int box[3], void* stream,
+                           lbm_domain** out) {
+    try {
+        int rc = check_params(params);
+        if (rc) return rc;
+        rc = check_box(box);
+        if (rc) return rc;
+        if (!out || !mask) { set_error("mask or out is NULL"); return LBM_ERR_ARG; }
+        return create_common(params, mask, box, stream, out);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected host exception");
+        return LBM_ERR_ARG;
+    }
+}
+
+int lbm_set_densities(lbm_domain* d, const double* rho) {
+    if (!d || !rho) { set_error("domain or rho is NULL"); return LBM_ERR_ARG; }
+    try {
+        return upload_densities(d, rho);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    }
+}
+
+int lbm_set_pressure_bc(lbm_domain* d, double rho_in_nw, double rho_out_w) {
+    if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
+    if (!std::isfinite(rho_in_nw) || !std::isfinite(rho_out_w) || rho_in_nw < 0 || rho_out_w < 0) {
+        set_error("reservoir densities must be finite and >= 0");
+        return LBM_ERR_ARG;
+    }
+    fill_phys(d, rho_in_nw, rho_out_w);
+    return LBM_OK;
+}
+
+int lbm_step(lbm_domain* d, int n_steps) {
+    if (!d || n_steps < 0) { set_error("domain is NULL or n_steps < 0"); return LBM_ERR_ARG; }
+    for (int i = 0; i < n_steps; ++i) {
+        LBM_CUDA(launch_step(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys,
+                             d->tile, d->stream));
+        d->cur ^= 1;
+        ++d->step;
+    }
+    return LBM_OK;
+}
+
+int lbm_measure(lbm_domain* d, lbm_measurement* out) {
+    if (!d || !out) { set_error("domain or out is NULL"); return LBM_ERR_ARG; }
+    LBM_CUDA(launch_measure(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials,
+                            d->meas_blocks, d->d_result, d->stream));
+    LBM_CUDA(cudaMemcpyAsync(d->h_result, d->d_result, sizeof(double) * NMEAS, cudaMemcpyDeviceToHost, d->stream));
+    int rc = wait_domain(d);
+    if (rc) return rc;
+    const double* r = d->h_result;
+    std::memset(out, 0, sizeof(*out));
+    out->mass[0] = r[MS_MASS_W];
+    out->mass[1] = r[MS_MASS_NW];
+    out->n_fluid = (long long)r[MS_N_FLUID];
+    out->n_w = (long long)r[MS_N_W];
+    out->n_interface = (long long)r[MS_N_INTERFACE];
+    out->n_bulk_w = (long long)r[MS_N_BULK_W];
+    out->n_bulk_nw = (long long)r[MS_N_BULK_NW];
+    out->n_in = (long long)r[MS_N_IN];
+    out->n_out = (long long)r[MS_N_OUT];
+    out->n_nonfinite = (long long)r[MS_N_NONFINITE];
+    out->n_negative = (long long)r[MS_N_NEGATIVE];
+    out->p_w = out->n_bulk_w ? r[MS_PW] / (double)out->n_bulk_w : NAN;
+    out->p_nw = out->n_bulk_nw ? r[MS_PNW] / (double)out->n_bulk_nw : NAN;
+    out->p_c = out->p_nw - out->p_w;
+    out->p_in = out->n_in ? r[MS_PIN] / (double)out->n_in : NAN;
+    out->p_out = out->n_out ? r[MS_POUT] / (double)out->n_out : NAN;
+    out->p_c_res = out->p_in - out->p_out;
+    out->S_w = out->n_fluid ? (double)out->n_w / (double)out->n_fluid : NAN;
+    out->status_flags = (out->n_nonfinite ? 1 : 0) | (out->n_negative ? 2 : 0);
+    if (out->status_flags) {
+        set_error("non-finite or negative densities in the state");
+        return LBM_ERR_NONFINITE;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_density(lbm_domain* d, double* rho_out) {
+    if (!d || !rho_out) { set_error("domain or rho_out is NULL"); return LBM_ERR_ARG; }
+    try {
+        LBM_CUDA(launch_density(d->f[d->cur], d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        std::vector<float> tmp((size_t)(2 * d->N));
+        LBM_CUDA(cudaMemcpyAsync(tmp.data(), d->d_rho, sizeof(float) * 2 * d->N, cudaMemcpyDeviceToHost, d->stream));
+        int rc = wait_domain(d);
+        if (rc) return rc;
+        for (long long i = 0; i < 2 * d->N; ++i) rho_out[i] = tmp[(size_t)i];
+        return LBM_OK;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    }
+}
+
+int lbm_get_mask(const lbm_domain* d, unsigned char* mask_out) {
+    if (!d || !mask_out) { set_error("domain or mask_out is NULL"); return LBM_ERR_ARG; }
+    LBM_CUDA(cudaMemcpy(mask_out, d->d_mask, (size_t)d->N, cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+int lbm_get_dims(const lbm_domain* d, int dims_out[3], long long* n_fluid_cells) {
+    if (!d || !dims_out) { set_error("domain or dims_out is NULL"); return LBM_ERR_ARG; }
+    dims_out[0] = d->geom.nx;
+    dims_out[1] = d->geom.ny;
+    dims_out[2] = d->geom.nz;
+    if (n_fluid_cells) *n_fluid_cells = d->n_fluid;
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_domain* d, float* f_out, long long* step_out) {
+    if (!d || !f_out) { set_error("domain or f_out is NULL"); return LBM_ERR_ARG; }
+    const long long N = d->N;
+    for (int p = 0; p < 2 * Q; ++p)
+        LBM_CUDA(cudaMemcpyAsync(f_out + (size_t)p * N, d->f[d->cur] + (size_t)p * d->geom.plane, sizeof(float) * N,
+                                 cudaMemcpyDeviceToHost, d->stream));
+    int rc = wait_domain(d);
+    if (rc) return rc;
+    if (step_out) *step_out = d->step;
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_domain* d, const float* f_in, long long step) {
+    if (!d || !f_in || step < 0) { set_error("domain or f_in is NULL, or step < 0"); return LBM_ERR_ARG; }
+    const long long N = d->N;
+    for (int p = 0; p < 2 * Q; ++p)
+        LBM_CUDA(cudaMemcpyAsync(d->f[d->cur] + (size_t)p * d->geom.plane, f_in + (size_t)p * N, sizeof(float) * N,
+                                 cudaMemcpyHostToDevice, d->stream));
+    d->step = step;
+    return wait_domain(d);
+}
+
+void lbm_destroy(lbm_domain* d) {
+    if (!d) return;
+    if (d->done) wait_domain(d);
+    free_domain(d);
+}
+
+const char* lbm_last_error(void) { return g_error.c_str(); }
+
+}  // extern "C"

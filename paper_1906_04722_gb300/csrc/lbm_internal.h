@@ -1,0 +1,125 @@
+// lbm_internal.h -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "lbm.h"
+
+namespace lbmk {
+
+constexpr int Q = 19;
+
+// D3Q19 in the ABI order (rest, 6 faces, 12 edges); opposite pairs (1,2), (3,4), ...
+__host__ __device__ constexpr int EX(int k) {
+    constexpr int a[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return a[k];
+}
+__host__ __device__ constexpr int EY(int k) {
+    constexpr int a[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return a[k];
+}
+__host__ __device__ constexpr int EZ(int k) {
+    constexpr int a[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return a[k];
+}
+__host__ __device__ constexpr int OPP(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+// lattice weights: 1/3 rest, 1/18 faces, 1/36 edges (cs^2 = 1/3)
+__host__ __device__ constexpr float WK(int k) { return k == 0 ? (1.0f / 3.0f) : (k <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f)); }
+// 36 * w_k for k >= 1: 2 on faces, 1 on edges (adhesion vectors are stored in these units)
+__host__ __device__ constexpr int W36(int k) { return k == 0 ? 12 : (k <= 6 ? 2 : 1); }
+
+// Per-cell geometry word (uint32), built once per domain from the mask:
+//   bit k (1..18)  pulling direction k at this cell bounces back (x - e_k is not
+//                  fluid for the wetting component or lies beyond a closed edge)
+//   bits 19..21    cell class (below)
+//   bit 22         the non-wetting component bounces differently (membrane
+//                  nearby): its bits are in the second word array
+//   bit 23         an adhesive grain cell is among the 18 neighbours: the
+//                  adhesion vector sum_k 36 w_k s(x+e_k) e_k is in the third array
+//                  (three int8 in the low bytes)
+constexpr int CLS_SHIFT = 19;
+constexpr uint32_t CLS_MASK = 7u;
+enum : uint32_t { CLS_FLUID = 0, CLS_SOLID = 1, CLS_INLET = 2, CLS_OUTLET = 3, CLS_MEMBRANE = 4, CLS_OUTSIDE = 5 };
+constexpr uint32_t BIT_NW_DIFF = 1u << 22;
+constexpr uint32_t BIT_ADH = 1u << 23;
+
+struct Geom {
+    int nx, ny, nz;
+    int nxy;
+    int plane;  // stride between population planes (>= N, multiple of 32)
+    int px, py, pz;
+};
+
+struct Phys {
+    float tau[2];
+    float omega[2];
+    float G;
+    float Gads[2];
+    float g[3];
+    float rho_in[2];   // (w, nw) imposed on inlet cells
+    float rho_out[2];  // (w, nw) imposed on outlet cells
+};
+
+// Number of doubles in one measurement partial.
+constexpr int NMEAS = 16;
+enum {
+    MS_MASS_W = 0, MS_MASS_NW, MS_PW, MS_PNW, MS_PIN, MS_POUT,
+    MS_N_FLUID, MS_N_W, MS_N_INTERFACE, MS_N_BULK_W, MS_N_BULK_NW, MS_N_IN, MS_N_OUT,
+    MS_N_NONFINITE, MS_N_NEGATIVE, MS_SPARE
+};
+
+// ---------------------------------------------------------------- launchers
+struct StepTile {
+    int by;  // block rows including the two halo rows (6, 8, 10 or 12)
+    int lz;  // z-segment length per CTA
+};
+
+cudaError_t launch_geometry(const uint8_t* mask, uint32_t* nbr, uint32_t* nbr_nw, uint32_t* adh, const Geom& g,
+                            cudaStream_t s);
+cudaError_t launch_init(const float* rho0, float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g,
+                        cudaStream_t s);
+cudaError_t launch_step(const float* fin, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                        const uint32_t* adh, const Geom& g, const Phys& p, StepTile tile, cudaStream_t s);
+cudaError_t launch_density(const float* f, float* rho, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g,
+                           cudaStream_t s);
+int measure_blocks(const Geom& g);
+cudaError_t launch_measure(const float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, double G,
+                           double* partials, int nblocks, double* result, cudaStream_t s);
+StepTile default_tile(const Geom& g);
+bool tile_supported(int by);
+
+// host geometry (lbm_geometry.cpp)
+void voxelise_box(int nx, int ny, int nz, const double* spheres, int n_spheres, int prism_clip, int reservoirs,
+                  int membrane_layers, uint8_t* mask);
+
+// thread-local error text
+void set_error(const std::string& msg);
+
+}  // namespace lbmk
+
+// The opaque domain handle of the ABI.
+struct lbm_domain {
+    lbm_params params;
+    lbmk::Geom geom;
+    lbmk::Phys phys;
+    lbmk::StepTile tile;
+    long long N;
+    long long n_fluid;
+    float* f[2];
+    int cur;
+    long long step;
+    uint8_t* d_mask;
+    uint32_t* d_nbr;
+    uint32_t* d_nbr_nw;
+    uint32_t* d_adh;
+    float* d_rho;
+    double* d_partials;
+    double* d_result;
+    double* h_result;  // pinned
+    int meas_blocks;
+    cudaStream_t stream;
+    cudaEvent_t done;
+};

@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares; argument checks that fire before any device work.
+CPU only: no call here touches a GPU."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1906_04722_gb300 as lbm
+    return lbm
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("lbm_create_domain", "lbm_set_pressure_bc", "lbm_step", "lbm_measure", "lbm_destroy",
+              "lbm_last_error", "lbm_get_density"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    path = lib.library_path()
+    lib.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = declared_symbols() - exported
+    assert not missing, missing
+    # the binding knows every declared symbol too
+    assert declared_symbols() <= set(lib.SIGNATURES)
+
+
+def test_library_is_built_for_sm_103a(lib):
+    lib.load()
+    out = subprocess.run(["cuobjdump", "--list-elf", lib.library_path()], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+@pytest.mark.parametrize("field,value", [("tau", (0.5, 1.0)), ("precision", 3), ("membrane_layers", -1),
+                                         ("G", float("nan"))])
+def test_bad_params_rejected_before_device_work(lib, field, value):
+    p = lib.make_params()
+    if field == "tau":
+        p.tau[0], p.tau[1] = value
+    else:
+        setattr(p, field, value)
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_create_domain(p, None, (4, 4, 4), stream=ctypes.c_void_p(0))
+    assert e.value.code == lib.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("box", [(0, 4, 4), (4, -1, 4), (5000, 4, 4), (4096, 4096, 4)])
+def test_bad_boxes_rejected(lib, box):
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_create_domain(lib.make_params(), None, box, stream=ctypes.c_void_p(0))
+    assert e.value.code == lib.LBM_ERR_ARG
+
+
+def test_bad_spheres_rejected(lib):
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_create_domain(lib.make_params(), np.array([[1.0, 2.0, np.inf, 3.0]]), (8, 8, 8),
+                              stream=ctypes.c_void_p(0))
+    assert e.value.code == lib.LBM_ERR_ARG
+    with pytest.raises(lib.LbmError):
+        lib.lbm_create_domain(lib.make_params(prism_clip=True), np.array([[1.0, 2.0, 3.0, 1.0]]), (8, 8, 8),
+                              stream=ctypes.c_void_p(0))
+
+
+def test_null_domain_calls_rejected(lib):
+    L = lib.load()
+    assert L.lbm_step(None, 1) == lib.LBM_ERR_ARG
+    assert L.lbm_set_pressure_bc(None, 2.0, 2.0) == lib.LBM_ERR_ARG
+    assert "NULL" in lib.lbm_last_error()
+    L.lbm_destroy(None)  # ignored

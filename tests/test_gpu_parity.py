@@ -1,0 +1,243 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; each side builds its own mask from the same
+sphere list.  Bars: masks bit-exact; densities within max |drho|/rho <= 1e-5
+after up to 500 FP32 steps (per cell and component, relative to the oracle's
+local density); p_c, S_w within 0.5 %.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL_RHO = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04722_gb300 as m
+    m.load()
+    return m
+
+
+def _params(lbm, **kw):
+    base = dict(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR, rho_minor=W.RHO_MINOR)
+    base.update(kw)
+    return lbm.make_params(**base)
+
+
+def _cfg(orc, shape, **kw):
+    base = dict(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_in=(W.RHO_MINOR, W.RHO_MAJOR),
+                rho_out=(W.RHO_MAJOR, W.RHO_MINOR))
+    base.update(kw)
+    return orc.Config(shape=shape, **base)
+
+
+def _rel_err(rho_gpu, rho_orc, mask, orc):
+    err = 0.0
+    for s in range(2):
+        fl = (mask & orc.M_SOLID) == 0
+        if s == 1:
+            fl &= (mask & orc.M_MEMBRANE) == 0
+        d = np.abs(rho_gpu[s][fl] - rho_orc[s][fl]) / np.abs(rho_orc[s][fl])
+        err = max(err, float(d.max()))
+    return err
+
+
+def _run_pair(lbm, orc, shape, spheres, steps, rho0, pkw=None, ckw=None, flags=None):
+    flags = flags or {}
+    pkw = pkw or {}
+    ckw = ckw or {}
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm, **pkw, **flags), spheres, (nx, ny, nz))
+    mask_o = orc.voxelise(shape, spheres if spheres is not None else np.zeros((0, 4)),
+                          prism=flags.get("prism_clip", False), reservoirs=flags.get("reservoirs", False),
+                          membrane_layers=flags.get("membrane_layers", 0))
+    assert np.array_equal(dom.mask(), mask_o), "masks differ"
+    dom.set_densities(rho0)
+    cfg = _cfg(orc, shape, **ckw)
+    f = orc.init(cfg, mask_o, rho0)
+    dom.step(steps)
+    orc.step(cfg, mask_o, f, steps)
+    return dom, cfg, mask_o, f
+
+
+def test_periodic_droplet_8(lbm, orc):
+    shape = (8, 8, 8)
+    rho0 = W.droplet_densities(shape, (3.5, 4.0, 4.5), 2.5, seed=1)
+    dom, cfg, mask, f = _run_pair(lbm, orc, shape, None, 50, rho0, pkw=dict(periodic=(1, 1, 1)),
+                                  ckw=dict(periodic=(1, 1, 1)))
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+def test_ragged_closed_box_with_grains(lbm, orc):
+    """Several x/y tiles and z segments with ragged tails; grains with adhesion."""
+    shape = (23, 29, 67)
+    spheres = np.array([[10.0, 8.0, 6.0, 5.3], [40.2, 20.5, 15.0, 6.1], [60.0, 3.0, 20.0, 4.0]])
+    rho0 = W.droplet_densities(shape, (33, 14, 11), 7.0, seed=2)
+    dom, cfg, mask, f = _run_pair(lbm, orc, shape, spheres, 60, rho0)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+def test_mixed_periodicity_and_body_force(lbm, orc):
+    shape = (20, 13, 41)
+    spheres = np.array([[20.0, 6.0, 10.0, 4.5]])
+    rho0 = W.droplet_densities(shape, (8, 6, 9), 4.0, seed=3)
+    kw = dict(periodic=(1, 0, 1), tau=(0.8, 1.2))
+    dom, cfg, mask, f = _run_pair(lbm, orc, shape, spheres, 80, rho0, pkw=dict(kw, body_force=(1e-5, 0, -2e-5)),
+                                  ckw=dict(kw, g=(1e-5, 0, -2e-5)))
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+def test_reservoirs_and_membrane(lbm, orc):
+    shape = (30, 20, 24)
+    spheres = np.array([[12.0, 10.0, 14.0, 6.0], [3.0, 3.0, 8.0, 3.5]])
+    flags = dict(reservoirs=True, membrane_layers=3)
+    rho0 = W.initial_densities(shape, noise=1e-3, seed=4)
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm, **flags), spheres, (nx, ny, nz))
+    mask = orc.voxelise(shape, spheres, reservoirs=True, membrane_layers=3)
+    assert np.array_equal(dom.mask(), mask)
+    dom.set_densities(rho0)
+    cfg = _cfg(orc, shape, rho_in=(W.RHO_MINOR, 2.1), rho_out=(W.RHO_MAJOR, W.RHO_MINOR))
+    dom.set_pressure_bc(2.1, W.RHO_MAJOR)
+    f = orc.init(cfg, mask, rho0)
+    dom.step(120)
+    orc.step(cfg, mask, f, 120)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+    mg, mo = dom.measure(), orc.measure(cfg, mask, f)
+    for k in ("n_fluid", "n_in", "n_out"):
+        assert mg[k] == mo[k]
+    for k in ("p_in", "p_out", "S_w"):
+        assert abs(mg[k] - mo[k]) <= 5e-3 * abs(mo[k]), k
+
+
+def test_throat32_500_steps(lbm, orc):
+    """The single-throat workload: 32^3, three touching r = 10 spheres, prism
+    clip, reservoirs, inlet density raised by 0.01 every 25 steps, 500 steps."""
+    shape = (32, 32, 32)
+    spheres = W.throat32_spheres()
+    flags = dict(prism_clip=True, reservoirs=True)
+    rho0 = W.initial_densities(shape, noise=1e-3, seed=1)
+    dom = lbm.Domain(_params(lbm, **flags), spheres, (32, 32, 32))
+    mask = orc.voxelise(shape, spheres, prism=True, reservoirs=True)
+    assert np.array_equal(dom.mask(), mask)
+    dom.set_densities(rho0)
+    f = orc.init(_cfg(orc, shape), mask, rho0)
+    for i, rin in enumerate(W.throat32_ladder()):
+        cfg = _cfg(orc, shape, rho_in=(W.RHO_MINOR, rin))
+        dom.set_pressure_bc(rin, W.RHO_MAJOR)
+        dom.step(25)
+        orc.step(cfg, mask, f, 25)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+    mg, mo = dom.measure(), orc.measure(cfg, mask, f)
+    assert abs(mg["S_w"] - mo["S_w"]) <= 5e-3 * mo["S_w"]
+    assert abs(mg["p_c_res"] - mo["p_c_res"]) <= 5e-3 * abs(mo["p_c_res"])
+    for s in range(2):
+        assert abs(mg["mass"][s] - mo["mass"][s]) <= 1e-5 * mo["mass"][s]
+
+
+def test_mass_conserved_on_gpu(lbm, orc):
+    """Closed walls: per-component mass drift of the FP32 state, summed in FP64,
+    stays within 1e-6 over 500 steps."""
+    shape = (40, 36, 44)
+    spheres = np.array([[10.0, 10.0, 10.0, 6.0], [30.0, 25.0, 28.0, 7.5]])
+    rho0 = W.droplet_densities(shape, (22, 18, 20), 8.0, seed=6)
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm), spheres, (nx, ny, nz))
+    dom.set_densities(rho0)
+    m0 = dom.measure()["mass"]
+    dom.step(500)
+    m1 = dom.measure()["mass"]
+    for s in range(2):
+        assert abs(m1[s] - m0[s]) <= 1e-6 * m0[s]
+
+
+def test_measure_counts_match_oracle(lbm, orc):
+    """Rest state with densities on a discrete set kept away from every
+    threshold: counts exact, FP64 sums within FP32 rounding of the densities."""
+    shape = (17, 19, 45)
+    rng = np.random.default_rng(12)
+    choices = np.array([[2.0, 0.06], [0.06, 2.0], [1.0, 1.0], [1.6, 0.4], [0.3, 1.7], [1.2, 0.9]])
+    pick = rng.integers(0, len(choices), size=shape)
+    rho0 = np.moveaxis(choices[pick], -1, 0).copy()
+    spheres = np.array([[20.0, 9.0, 8.0, 4.0]])
+    flags = dict(reservoirs=True, membrane_layers=2)
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm, **flags), spheres, (nx, ny, nz))
+    mask = orc.voxelise(shape, spheres, reservoirs=True, membrane_layers=2)
+    dom.set_densities(rho0)
+    cfg = _cfg(orc, shape)
+    f = orc.init(cfg, mask, rho0)
+    mg, mo = dom.measure(), orc.measure(cfg, mask, f)
+    for k in ("n_fluid", "n_w", "n_interface", "n_bulk_w", "n_bulk_nw", "n_in", "n_out"):
+        assert mg[k] == mo[k], k
+    for k in ("p_w", "p_nw", "p_in", "p_out", "S_w"):
+        assert abs(mg[k] - mo[k]) <= 1e-6 * abs(mo[k]), k
+    for s in range(2):
+        assert abs(mg["mass"][s] - mo["mass"][s]) <= 1e-6 * mo["mass"][s]
+
+
+def test_checkpoint_resume_bitwise(lbm):
+    shape = (24, 20, 33)
+    spheres = np.array([[16.0, 10.0, 12.0, 5.0]])
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm, reservoirs=True), spheres, (nx, ny, nz))
+    dom.set_densities(W.initial_densities(shape, noise=1e-3, seed=7))
+    dom.set_pressure_bc(2.05, 2.0)
+    dom.step(7)
+    f, st = dom.state()
+    dom.step(13)
+    a, sa = dom.state()
+    dom.set_state(f, st)
+    dom.step(13)
+    b, sb = dom.state()
+    assert sa == sb == 20
+    assert np.array_equal(a, b)
+
+
+def test_sample192_full_size_sampled_cells(lbm, orc):
+    """The 192^3 drainage sample in the launch configuration the benchmark
+    times: two steps from a seeded noisy state, sampled cells against the
+    oracle run on a crop that holds their whole dependency cone (2 cells per
+    step), plus the bit-exact mask."""
+    shape = (192, 192, 192)
+    spheres = W.sample192_spheres()
+    flags = dict(reservoirs=True, membrane_layers=3)
+    dom = lbm.Domain(_params(lbm, **flags), spheres, (192, 192, 192))
+    mask = orc.voxelise(shape, spheres, reservoirs=True, membrane_layers=3)
+    assert np.array_equal(dom.mask(), mask)
+    rho0 = W.initial_densities(shape, noise=2e-2, seed=8)
+    dom.set_densities(rho0)
+    K = 2
+    dom.step(K)
+    rho_g = dom.density()
+    rng = np.random.default_rng(13)
+    R = 2 * K + 2
+    fluid = np.argwhere(mask == 0)
+    picks = fluid[rng.choice(len(fluid), 24, replace=False)]
+    edge = np.array([[0, 0, 0], [191, 191, 191], [1, 95, 0], [190, 100, 191]])
+    for z, y, x in list(picks) + [tuple(e) for e in edge]:
+        zs, ys, xs = [slice(max(0, v - R), min(192, v + R + 1)) for v in (z, y, x)]
+        sub = mask[zs, ys, xs].copy()
+        # crop edges that are not box edges must not act as walls on the
+        # centre: they are R > 2K cells away, beyond its dependency cone
+        cfg = _cfg(orc, sub.shape)
+        f = orc.init(cfg, sub, np.ascontiguousarray(rho0[:, zs, ys, xs]))
+        orc.step(cfg, sub, f, K)
+        ro = orc.density(cfg, sub, f)[:, z - zs.start, y - ys.start, x - xs.start]
+        rg = rho_g[:, z, y, x]
+        m = mask[z, y, x]
+        if m & orc.M_SOLID:
+            continue
+        for s in range(2):
+            if s == 1 and m & orc.M_MEMBRANE:
+                continue
+            assert abs(rg[s] - ro[s]) <= RTOL_RHO * abs(ro[s]), (z, y, x, s, rg[s], ro[s])
