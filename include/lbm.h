@@ -149,6 +149,30 @@ int lbm_get_dims(const lbm_domain* d, int dims_out[3], long long* n_fluid_cells)
 int lbm_get_state(lbm_domain* d, float* f_out, long long* step_out);
 int lbm_set_state(lbm_domain* d, const float* f_in, long long step);
 
+/* lbm_measure_state_noalloc -- the observables of lbm_measure for a state that
+ * lives in caller-owned device memory, computed without allocating any device
+ * memory.  The paper has no counterpart: this serves callers that cannot
+ * allocate, such as code running while a stream is captured, plug-ins whose
+ * host application owns all device memory through its own pool, or loops that
+ * cannot absorb the device synchronisation of cudaMalloc/cudaFree.
+ *   params    model parameters (only G and periodic are read).
+ *   box       (nx, ny, nz), each in [1, 4096], at most 56,000,000 cells in all;
+ *             larger states are rejected with LBM_ERR_ARG.
+ *   f_dev     DEVICE pointer to the stored populations in the lbm_get_state
+ *             layout: 2 x 19 x N floats, f[(s*19 + k) * N + cell].
+ *   mask_dev  DEVICE pointer to the N mask bytes (layout above).
+ *   stream    cudaStream_t to run on (NULL = legacy stream); the call waits for
+ *             it before returning.
+ *   out       HOST pointer, filled as by lbm_measure.
+ * The reduction scratch is a fixed device array inside the library (about
+ * 128 KiB, held by every GPU that loads the library until the process exits).
+ * All calls share it: calls whose device work overlaps in time race on it.
+ * The first call on each device looks up the array's device address; make that
+ * first call before any stream capture begins.  Returns LBM_ERR_NONFINITE like
+ * lbm_measure, LBM_ERR_CUDA when a CUDA call fails. */
+int lbm_measure_state_noalloc(const lbm_params* params, const int box[3], const float* f_dev,
+                              const unsigned char* mask_dev, void* stream, lbm_measurement* out);
+
 /* lbm_destroy -- release the domain (NULL is ignored). */
 void lbm_destroy(lbm_domain* d);
 

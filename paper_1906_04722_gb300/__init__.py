@@ -76,6 +76,8 @@ SIGNATURES = {
     "lbm_get_dims": (ctypes.c_int, [_VP, _IP, _LLP]),
     "lbm_get_state": (ctypes.c_int, [_VP, _FP, _LLP]),
     "lbm_set_state": (ctypes.c_int, [_VP, _FP, ctypes.c_longlong]),
+    "lbm_measure_state_noalloc": (ctypes.c_int, [ctypes.POINTER(lbm_params), _IP, _VP, _VP, _VP,
+                                                 ctypes.POINTER(lbm_measurement)]),
     "lbm_destroy": (None, [_VP]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -216,6 +218,20 @@ def lbm_get_state(h):
 def lbm_set_state(h, f: np.ndarray, step: int):
     a = np.ascontiguousarray(f, dtype=np.float32)
     _check(load().lbm_set_state(h, a.ctypes.data_as(_FP), int(step)), "lbm_set_state")
+
+
+def lbm_measure_state_noalloc(params: lbm_params, box, f_dev_ptr: int, mask_dev_ptr: int, stream=None,
+                              allow_nonfinite: bool = False) -> dict:
+    """Measurements of a state in caller-owned device memory (raw device
+    pointers, lbm_get_state / mask layouts) without any device allocation."""
+    m = lbm_measurement()
+    bx = (ctypes.c_int * 3)(*[int(v) for v in box])
+    rc = load().lbm_measure_state_noalloc(ctypes.byref(params), bx, ctypes.c_void_p(f_dev_ptr),
+                                          ctypes.c_void_p(mask_dev_ptr),
+                                          stream if stream is not None else _torch_stream(), ctypes.byref(m))
+    if not (allow_nonfinite and rc == LBM_ERR_NONFINITE):
+        _check(rc, "lbm_measure_state_noalloc")
+    return m.as_dict()
 
 
 def lbm_destroy(h):
