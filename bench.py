@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=192,
+                    help="box edge of the drainage sample (192 = the benchmark workload; smaller edges "
+                         "scale the sphere count with the volume, for profiling captures)")
     return ap.parse_args()
 
 
@@ -60,10 +63,9 @@ def dist_env():
     return rank, world, local
 
 
-def sample_geometry():
+def sample_geometry(edge: int = 192):
     import workloads as W
-    spheres = W.sample192_spheres()
-    return spheres, (192, 192, 192)
+    return W.sample_spheres(edge), (edge, edge, edge)
 
 
 def update_bytes(mask):
@@ -245,7 +247,7 @@ def run_ours(args, rank, world, local):
         if dist is not None:
             dist.barrier()
 
-    spheres, box = sample_geometry()
+    spheres, box = sample_geometry(args.size)
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
                              rho_minor=W.RHO_MINOR, reservoirs=True, membrane_layers=3)
     stream = torch.cuda.Stream()
@@ -304,14 +306,14 @@ def run_ours(args, rank, world, local):
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "sample192: 192^3, 300 RSA spheres r~U[10,14], reservoirs + 3 membrane layers, "
-                                  "FP32 populations, one fused step per launch",
+           "config": {"workload": f"sample{args.size}: {args.size}^3, {len(spheres)} RSA spheres r~U[10,14], "
+                                  "reservoirs + 3 membrane layers, FP32 populations, one fused step per launch",
                       "fluid_cells": n_upd, "global_batch": world, "seq_len": 0,
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "inputs larger than L2 (2 x 1.08 GB population buffers)"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": read_traffic(), "peak_kind": peak_kind,
-                        "kernel": "sc_step_kernel<10>", "algorithmic_bytes_per_launch": bytes_per_step},
+                        "kernel": "sc_step_kernel<6,2>", "algorithmic_bytes_per_launch": bytes_per_step},
            "gpu_launches": args.steps,
            "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "step": f"set_pressure_bc + {E2E_SUBSTEPS} time steps + lbm_measure; domain creation "

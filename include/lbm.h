@@ -173,6 +173,17 @@ int lbm_set_state(lbm_domain* d, const float* f_in, long long step);
 int lbm_measure_state_noalloc(const lbm_params* params, const int box[3], const float* f_dev,
                               const unsigned char* mask_dev, void* stream, lbm_measurement* out);
 
+/* lbm_set_tile / lbm_get_tile -- launch shape of the fused step kernel.
+ *   by    CTA rows including the two halo rows: 6, 8, 10 or 12 (the CTA owns
+ *         30 x (by - 2) columns of cells);
+ *   lz    planes per CTA z-segment, >= 1;
+ *   lead  planes queued ahead of the collided one: 2, 3 or 4 (lead 3 allows
+ *         by <= 10, lead 4 allows by <= 8).
+ * Results do not depend on the shape (bit for bit).  LBM_ERR_ARG for an
+ * unsupported combination. */
+int lbm_set_tile(lbm_domain* d, int by, int lz, int lead);
+int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
+
 /* lbm_destroy -- release the domain (NULL is ignored). */
 void lbm_destroy(lbm_domain* d);
 

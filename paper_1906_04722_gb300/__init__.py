@@ -78,6 +78,8 @@ SIGNATURES = {
     "lbm_set_state": (ctypes.c_int, [_VP, _FP, ctypes.c_longlong]),
     "lbm_measure_state_noalloc": (ctypes.c_int, [ctypes.POINTER(lbm_params), _IP, _VP, _VP, _VP,
                                                  ctypes.POINTER(lbm_measurement)]),
+    "lbm_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_get_tile": (ctypes.c_int, [_VP, _IP, _IP, _IP]),
     "lbm_destroy": (None, [_VP]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -234,6 +236,16 @@ def lbm_measure_state_noalloc(params: lbm_params, box, f_dev_ptr: int, mask_dev_
     return m.as_dict()
 
 
+def lbm_set_tile(h, by: int, lz: int, lead: int):
+    _check(load().lbm_set_tile(h, int(by), int(lz), int(lead)), "lbm_set_tile")
+
+
+def lbm_get_tile(h):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().lbm_get_tile(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "lbm_get_tile")
+    return a.value, b.value, c.value
+
+
 def lbm_destroy(h):
     if h:
         load().lbm_destroy(h)
@@ -281,6 +293,12 @@ class Domain:
 
     def set_state(self, f, step):
         lbm_set_state(self.h, f, step)
+
+    def set_tile(self, by, lz, lead):
+        lbm_set_tile(self.h, by, lz, lead)
+
+    def tile(self):
+        return lbm_get_tile(self.h)
 
     def close(self):
         if getattr(self, "h", None):

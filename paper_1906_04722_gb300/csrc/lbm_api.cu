@@ -141,6 +141,7 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     g.px = params->periodic[0] ? 1 : 0;
     g.py = params->periodic[1] ? 1 : 0;
     g.pz = params->periodic[2] ? 1 : 0;
+    fill_pull_offsets(g);
     d->tile = default_tile(g);
     fill_phys(d, params->rho_major, params->rho_major);
 
@@ -365,6 +366,26 @@ int lbm_set_state(lbm_domain* d, const float* f_in, long long step) {
                                  cudaMemcpyHostToDevice, d->stream));
     d->step = step;
     return wait_domain(d);
+}
+
+int lbm_set_tile(lbm_domain* d, int by, int lz, int lead) {
+    if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
+    if (lz < 1 || !tile_supported(by, lead)) {
+        set_error("unsupported tile: by in {6,8,10,12}, lz >= 1, lead in {2,3,4} (lead 3: by <= 10, lead 4: by <= 8)");
+        return LBM_ERR_ARG;
+    }
+    d->tile.by = by;
+    d->tile.lz = lz > d->geom.nz ? d->geom.nz : lz;
+    d->tile.lead = lead;
+    return LBM_OK;
+}
+
+int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead) {
+    if (!d || !by || !lz || !lead) { set_error("NULL argument"); return LBM_ERR_ARG; }
+    *by = d->tile.by;
+    *lz = d->tile.lz;
+    *lead = d->tile.lead;
+    return LBM_OK;
 }
 
 void lbm_destroy(lbm_domain* d) {

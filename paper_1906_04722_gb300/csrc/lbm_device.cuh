@@ -53,13 +53,61 @@ __device__ __forceinline__ Column make_column(int gx, int gy, const Geom& g) {
     return c;
 }
 
-// Pull the populations of cell (column, z) for both components:
+// Pull the populations of one cell whose geometry word w is known:
 //   f_k(x) = f*_k(x - e_k)   if x - e_k is fluid for the component,
 //   f_k(x) = f*_kbar(x)      otherwise (half-way bounce-back),
-// from the post-collision array fin[(s*19 + k) * plane + cell].  Returns the
-// cell's geometry word (class CLS_OUTSIDE for a cell beyond a closed edge) and
-// the component densities (0 where a component is not fluid).  With KEEP the
-// pulled values are left in f; otherwise only the sums are formed.
+// from the post-collision array fin[(s*19 + k) * plane + cell].  zz is the
+// cell's (wrapped) plane.  Returns the component densities (0 where a component
+// is not fluid): with ILP in four interleaved partial sums, otherwise in k order.
+// With KEEP the pulled values are left in f.
+template <bool KEEP, bool ILP = false>
+__device__ __forceinline__ void pull_known(const float* __restrict__ fin, const uint32_t* __restrict__ nbr_nw,
+                                           const Geom& g, const Column& c, int zz, int cell, uint32_t w,
+                                           float (&f)[2][Q], float& rw, float& rn) {
+    rw = 0.f;
+    rn = 0.f;
+    const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+    if (cls == CLS_SOLID || cls == CLS_OUTSIDE) return;
+    // away from periodic seams the source of direction k is cell - (ex + ey nx + ez nxy)
+    const bool seam = (g.px && (c.xo[1] == 0 || c.xo[1] == g.nx - 1)) ||
+                      (g.py && (c.yo[1] == 0 || c.yo[1] == (g.ny - 1) * g.nx)) ||
+                      (g.pz && (zz == 0 || zz == g.nz - 1));
+    int zo[3];
+    zo[0] = nb1(zz - 1, g.nz, g.pz) * g.nxy;
+    zo[1] = zz * g.nxy;
+    zo[2] = nb1(zz + 1, g.nz, g.pz) * g.nxy;
+    const uint32_t wn = (cls == CLS_MEMBRANE) ? 0u : ((w & BIT_NW_DIFF) ? __ldg(nbr_nw + cell) : w);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (s == 1 && cls == CLS_MEMBRANE) {
+            if (KEEP) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k) f[1][k] = 0.f;
+            }
+            break;
+        }
+        const uint32_t bits = s == 0 ? w : wn;
+        const float* fs = fin + (size_t)s * Q * g.plane;
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            int src;
+            if (!seam) src = cell - (EX(k) + EY(k) * g.nx + EZ(k) * g.nxy);
+            else src = zo[1 - EZ(k)] + c.yo[1 - EY(k)] + c.xo[1 - EX(k)];
+            const int idx = ((bits >> k) & 1u) ? (OPP(k) * g.plane + cell) : (k * g.plane + src);
+            const float v = __ldg(fs + idx);
+            if (KEEP) f[s][k] = v;
+            if (ILP) a[k & 3] += v;
+            else a[0] += v;
+        }
+        const float r = ILP ? (a[0] + a[1]) + (a[2] + a[3]) : a[0];
+        if (s == 0) rw = r;
+        else rn = r;
+    }
+}
+
+// Pull cell (column, z): loads the geometry word, then as pull_known.  Returns
+// the word (class CLS_OUTSIDE for a cell beyond a closed edge).
 template <bool KEEP>
 __device__ __forceinline__ uint32_t pull_cell(const float* __restrict__ fin, const uint32_t* __restrict__ nbr,
                                               const uint32_t* __restrict__ nbr_nw, const Geom& g,
@@ -69,42 +117,12 @@ __device__ __forceinline__ uint32_t pull_cell(const float* __restrict__ fin, con
     rn = 0.f;
     cell_out = 0;
     bool ok = c.ok;
-    int zz = wrap1(z, g.nz, g.pz, ok);
+    const int zz = wrap1(z, g.nz, g.pz, ok);
     if (!ok) return CLS_OUTSIDE << CLS_SHIFT;
-    int zo[3];
-    zo[0] = nb1(zz - 1, g.nz, g.pz) * g.nxy;
-    zo[1] = zz * g.nxy;
-    zo[2] = nb1(zz + 1, g.nz, g.pz) * g.nxy;
-    const int cell = zo[1] + c.yo[1] + c.xo[1];
+    const int cell = zz * g.nxy + c.yo[1] + c.xo[1];
     cell_out = cell;
     const uint32_t w = __ldg(nbr + cell);
-    const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
-    if (cls == CLS_SOLID) return w;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const int src = zo[1 - EZ(k)] + c.yo[1 - EY(k)] + c.xo[1 - EX(k)];
-        const bool bb = (w >> k) & 1u;
-        const int idx = bb ? (OPP(k) * g.plane + cell) : (k * g.plane + src);
-        const float v = __ldg(fin + idx);
-        if (KEEP) f[0][k] = v;
-        rw += v;
-    }
-    if (cls != CLS_MEMBRANE) {
-        const uint32_t wn = (w & BIT_NW_DIFF) ? __ldg(nbr_nw + cell) : w;
-        const float* fin1 = fin + (size_t)Q * g.plane;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const int src = zo[1 - EZ(k)] + c.yo[1 - EY(k)] + c.xo[1 - EX(k)];
-            const bool bb = (wn >> k) & 1u;
-            const int idx = bb ? (OPP(k) * g.plane + cell) : (k * g.plane + src);
-            const float v = __ldg(fin1 + idx);
-            if (KEEP) f[1][k] = v;
-            rn += v;
-        }
-    } else if (KEEP) {
-#pragma unroll
-        for (int k = 0; k < Q; ++k) f[1][k] = 0.f;
-    }
+    pull_known<KEEP>(fin, nbr_nw, g, c, zz, cell, w, f, rw, rn);
     return w;
 }
 

@@ -51,7 +51,15 @@ struct Geom {
     int nxy;
     int plane;  // stride between population planes (>= N, multiple of 32)
     int px, py, pz;
+    // poff[k] = k * plane - (ex_k + ey_k nx + ez_k nxy): from a cell's index to
+    // its pull source of direction k in population plane k (kernel parameters
+    // live in the constant bank, so these cost no registers)
+    int poff[Q];
 };
+
+inline void fill_pull_offsets(Geom& g) {
+    for (int k = 0; k < Q; ++k) g.poff[k] = k * g.plane - (EX(k) + EY(k) * g.nx + EZ(k) * g.nxy);
+}
 
 struct Phys {
     float tau[2];
@@ -73,8 +81,9 @@ enum {
 
 // ---------------------------------------------------------------- launchers
 struct StepTile {
-    int by;  // block rows including the two halo rows (6, 8, 10 or 12)
-    int lz;  // z-segment length per CTA
+    int by;    // block rows including the two halo rows (6, 8, 10 or 12)
+    int lz;    // z-segment length per CTA
+    int lead;  // planes queued ahead of the collided plane (2, 3 or 4)
 };
 
 cudaError_t launch_geometry(const uint8_t* mask, uint32_t* nbr, uint32_t* nbr_nw, uint32_t* adh, const Geom& g,
@@ -89,7 +98,7 @@ int measure_blocks(const Geom& g);
 cudaError_t launch_measure(const float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, double G,
                            double* partials, int nblocks, double* result, cudaStream_t s);
 StepTile default_tile(const Geom& g);
-bool tile_supported(int by);
+bool tile_supported(int by, int lead);
 
 // host geometry (lbm_geometry.cpp)
 void voxelise_box(int nx, int ny, int nz, const double* spheres, int n_spheres, int prism_clip, int reservoirs,

@@ -186,6 +186,7 @@ extern "C" int lbm_measure_state_noalloc(const lbm_params* params, const int box
     g.px = params->periodic[0] ? 1 : 0;
     g.py = params->periodic[1] ? 1 : 0;
     g.pz = params->periodic[2] ? 1 : 0;
+    fill_pull_offsets(g);
     long long nb = (N + NA_THREADS * 8 - 1) / (NA_THREADS * 8);
     if (nb > NA_MAX_BLOCKS) nb = NA_MAX_BLOCKS;
     if (nb < 1) nb = 1;

@@ -35,8 +35,6 @@ namespace lbmk {
 
 namespace {
 
-constexpr int STAGES = 3;
-
 __device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
@@ -47,43 +45,47 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Queue the pull of this thread's cell on plane z into its private stage slots
-// st[(s*19 + k) * NT + tid].  Returns the geometry word (CLS_OUTSIDE beyond a
-// closed edge) and the cell index.
+// Cell index of this thread's column on plane z (periodic wrap); ok is cleared
+// for a plane beyond a closed z edge.
+__device__ __forceinline__ int plane_cell(const Geom& g, const Column& c, int z, int& zz, bool& ok) {
+    ok = c.ok;
+    zz = wrap1(z, g.nz, g.pz, ok);
+    return zz * g.nxy + c.yo[1] + c.xo[1];
+}
+
+// Queue the pull of this thread's cell (index cell, geometry word w, plane zz)
+// into its private stage slots st[(s*19 + k) * NT + tid].  Away from periodic
+// seams the source of direction k is cell + poff[k] (a kernel-parameter offset);
+// on a seam the wrapped neighbour offsets are used.  Bounce-back is decided per
+// copy from the geometry word.
 template <int NT>
-__device__ __forceinline__ uint32_t issue_pull(const float* __restrict__ fin, const uint32_t* __restrict__ nbr,
-                                               const uint32_t* __restrict__ nbr_nw, const Geom& g,
-                                               const Column& c, int z, float* st, int tid, int& cell_out) {
-    cell_out = 0;
-    bool ok = c.ok;
-    const int zz = wrap1(z, g.nz, g.pz, ok);
-    if (!ok) return CLS_OUTSIDE << CLS_SHIFT;
+__device__ __forceinline__ void issue_pull(const float* __restrict__ fin, const uint32_t* __restrict__ nbr_nw,
+                                          const Geom& g, const Column& c, int zz, int cell, uint32_t w, float* st,
+                                          int tid) {
+    const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+    if (cls == CLS_SOLID || cls == CLS_OUTSIDE) return;
+    const bool seam = (g.px && (c.xo[1] == 0 || c.xo[1] == g.nx - 1)) ||
+                      (g.py && (c.yo[1] == 0 || c.yo[1] == (g.ny - 1) * g.nx)) ||
+                      (g.pz && (zz == 0 || zz == g.nz - 1));
     int zo[3];
     zo[0] = nb1(zz - 1, g.nz, g.pz) * g.nxy;
     zo[1] = zz * g.nxy;
     zo[2] = nb1(zz + 1, g.nz, g.pz) * g.nxy;
-    const int cell = zo[1] + c.yo[1] + c.xo[1];
-    cell_out = cell;
-    const uint32_t w = __ldg(nbr + cell);
-    const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
-    if (cls == CLS_SOLID) return w;
+    const uint32_t wn = (cls == CLS_MEMBRANE) ? 0u : ((w & BIT_NW_DIFF) ? __ldg(nbr_nw + cell) : w);
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const int src = zo[1 - EZ(k)] + c.yo[1 - EY(k)] + c.xo[1 - EX(k)];
-        const int idx = ((w >> k) & 1u) ? (OPP(k) * g.plane + cell) : (k * g.plane + src);
-        cp_async4(st + k * NT + tid, fin + idx);
-    }
-    if (cls != CLS_MEMBRANE) {
-        const uint32_t wn = (w & BIT_NW_DIFF) ? __ldg(nbr_nw + cell) : w;
-        const float* fin1 = fin + (size_t)Q * g.plane;
+    for (int s = 0; s < 2; ++s) {
+        if (s == 1 && cls == CLS_MEMBRANE) break;
+        const uint32_t bits = s == 0 ? w : wn;
+        const float* fs = fin + (size_t)s * Q * g.plane;
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            const int src = zo[1 - EZ(k)] + c.yo[1 - EY(k)] + c.xo[1 - EX(k)];
-            const int idx = ((wn >> k) & 1u) ? (OPP(k) * g.plane + cell) : (k * g.plane + src);
-            cp_async4(st + (Q + k) * NT + tid, fin1 + idx);
+            int idx;
+            if (!seam) idx = cell + g.poff[k];
+            else idx = k * g.plane + zo[1 - EZ(k)] + c.yo[1 - EY(k)] + c.xo[1 - EX(k)];
+            if ((bits >> k) & 1u) idx = OPP(k) * g.plane + cell;
+            cp_async4(st + (s * Q + k) * NT + tid, fs + idx);
         }
     }
-    return w;
 }
 
 // Densities of a landed plane (0 where a component is not fluid), summed in k order.
@@ -93,25 +95,34 @@ __device__ __forceinline__ void plane_density(uint32_t w, const float* st, int t
     rn = 0.f;
     const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
     if (cls == CLS_SOLID || cls == CLS_OUTSIDE) return;
+    // four interleaved partial sums keep the adds independent
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < Q; ++k) rw += st[k * NT + tid];
+    for (int k = 0; k < Q; ++k) a[k & 3] += st[k * NT + tid];
+    rw = (a[0] + a[1]) + (a[2] + a[3]);
     if (cls != CLS_MEMBRANE) {
+        float b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < Q; ++k) rn += st[(Q + k) * NT + tid];
+        for (int k = 0; k < Q; ++k) b[k & 3] += st[(Q + k) * NT + tid];
+        rn = (b[0] + b[1]) + (b[2] + b[3]);
     }
 }
 
-// Collide one interior fluid cell of plane z and store its post-collision values.
+// Collide one interior fluid cell of plane z (pulled populations f) and store
+// its post-collision values.  ring holds (rho_w, rho_nw) of planes z-1..z+1 for
+// the CTA's 32 x BY cells: ring[slot * 32*BY + row*32 + lane].  Directions come
+// in opposite pairs (k, k+1) with e_{k+1} = -e_k, which halves the arithmetic of
+// the moments, the force sums and the equilibria (the symmetric and the
+// antisymmetric part of f^eq are shared by a pair).
 template <int BY>
-__device__ __forceinline__ void collide_store(const float* st, const float* ring, uint32_t w, int cell, int z,
-                                              int row, int lane, const uint32_t* __restrict__ adh, const Phys& P,
-                                              const Geom& g, float* __restrict__ fout) {
+__device__ __forceinline__ void collide_cell(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
+                                             int cell, int z, int row, int lane, const Phys& P, const Geom& g,
+                                             float* __restrict__ fout) {
     constexpr int NT = 32 * BY;
-    const int tid = row * 32 + lane;
     const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
     const bool has_nw = cls != CLS_MEMBRANE;
-    float* __restrict__ out0 = fout;
-    float* __restrict__ out1 = fout + (size_t)Q * g.plane;
+    float* __restrict__ out0 = fout + cell;
+    float* __restrict__ out1 = fout + (size_t)Q * g.plane + cell;
 
     if (cls == CLS_INLET || cls == CLS_OUTLET) {
         const float r0 = cls == CLS_INLET ? P.rho_in[0] : P.rho_out[0];
@@ -119,60 +130,54 @@ __device__ __forceinline__ void collide_store(const float* st, const float* ring
         float s0 = 0.f, s1 = 0.f;
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
-            const float a = WK(k) * r0, b = WK(k) * r1;
-            s0 += a;
-            s1 += b;
-            out0[k * g.plane + cell] = a;
-            out1[k * g.plane + cell] = b;
+            const float va = WK(k) * r0, vb = WK(k) * r1;
+            s0 += va;
+            s1 += vb;
+            out0[(size_t)k * g.plane] = va;
+            out1[(size_t)k * g.plane] = vb;
         }
-        out0[cell] = r0 - s0;
-        out1[cell] = r1 - s1;
+        out0[0] = r0 - s0;
+        out1[0] = r1 - s1;
         return;
     }
 
-    // ring[(slot*2 + comp) * NT + row*32 + lane]
-    auto rho_at = [&](int k, int comp) {
-        const int slot = (z + EZ(k)) & 3;
-        return ring[(slot * 2 + comp) * NT + (row + EY(k)) * 32 + (lane + EX(k))];
+    auto rho_at = [&](int k) {
+        return ring[((z + EZ(k)) & 3) * NT + (row + EY(k)) * 32 + (lane + EX(k))];
     };
-    const float rw = rho_at(0, 0);
-    const float rn = rho_at(0, 1);
+    const float2 r00 = rho_at(0);
+    const float rw = r00.x;
+    const float rn = r00.y;
 
-    // neighbour density sums: cw = sum_k w_k rho_nw(x+e_k) e_k (acts on w),
-    // cn = sum_k w_k rho_w(x+e_k) e_k (acts on nw)
+    // neighbour density sums over opposite pairs:
+    // cw = sum_k w_k rho_nw(x+e_k) e_k (acts on w), cn = sum_k w_k rho_w(x+e_k) e_k
     float cw[3] = {0.f, 0.f, 0.f}, cn[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int k = 1; k < Q; ++k) {
-        const float nrw = rho_at(k, 0);
-        const float nrn = rho_at(k, 1);
-        const float wk = WK(k);
-        if (EX(k)) { cw[0] += wk * nrn * (float)EX(k); cn[0] += wk * nrw * (float)EX(k); }
-        if (EY(k)) { cw[1] += wk * nrn * (float)EY(k); cn[1] += wk * nrw * (float)EY(k); }
-        if (EZ(k)) { cw[2] += wk * nrn * (float)EZ(k); cn[2] += wk * nrw * (float)EZ(k); }
+    for (int k = 1; k < Q; k += 2) {
+        const float2 p = rho_at(k), m = rho_at(k + 1);
+        const float dn = WK(k) * (p.y - m.y);
+        const float dw = WK(k) * (p.x - m.x);
+        if (EX(k)) { cw[0] += EX(k) > 0 ? dn : -dn; cn[0] += EX(k) > 0 ? dw : -dw; }
+        if (EY(k)) { cw[1] += EY(k) > 0 ? dn : -dn; cn[1] += EY(k) > 0 ? dw : -dw; }
+        if (EZ(k)) { cw[2] += EZ(k) > 0 ? dn : -dn; cn[2] += EZ(k) > 0 ? dw : -dw; }
     }
     float ad[3] = {0.f, 0.f, 0.f};
     if (w & BIT_ADH) {
-        const uint32_t a = __ldg(adh + cell);
         ad[0] = (float)(int8_t)(a & 0xffu) * (1.0f / 36.0f);
         ad[1] = (float)(int8_t)((a >> 8) & 0xffu) * (1.0f / 36.0f);
         ad[2] = (float)(int8_t)((a >> 16) & 0xffu) * (1.0f / 36.0f);
     }
 
-    float f[2][Q];
+    // momenta (Eq. 3) over opposite pairs
+    float j[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        f[0][k] = st[k * NT + tid];
-        f[1][k] = has_nw ? st[(Q + k) * NT + tid] : 0.f;
-    }
-
-    // momenta (Eq. 3)
-    float j0[3] = {0.f, 0.f, 0.f}, j1[3] = {0.f, 0.f, 0.f};
+    for (int s = 0; s < 2; ++s)
 #pragma unroll
-    for (int k = 1; k < Q; ++k) {
-        if (EX(k)) { j0[0] += EX(k) > 0 ? f[0][k] : -f[0][k]; j1[0] += EX(k) > 0 ? f[1][k] : -f[1][k]; }
-        if (EY(k)) { j0[1] += EY(k) > 0 ? f[0][k] : -f[0][k]; j1[1] += EY(k) > 0 ? f[1][k] : -f[1][k]; }
-        if (EZ(k)) { j0[2] += EZ(k) > 0 ? f[0][k] : -f[0][k]; j1[2] += EZ(k) > 0 ? f[1][k] : -f[1][k]; }
-    }
+        for (int k = 1; k < Q; k += 2) {
+            const float d = f[s][k] - f[s][k + 1];
+            if (EX(k)) j[s][0] += EX(k) > 0 ? d : -d;
+            if (EY(k)) j[s][1] += EY(k) > 0 ? d : -d;
+            if (EZ(k)) j[s][2] += EZ(k) > 0 ? d : -d;
+        }
 
     // common velocity u' = (j_w/tau_w + j_nw/tau_nw) / (rho_w/tau_w + rho_nw/tau_nw)
     float up[3];
@@ -180,7 +185,7 @@ __device__ __forceinline__ void collide_store(const float* st, const float* ring
         const float den = rw * P.omega[0] + (has_nw ? rn * P.omega[1] : 0.f);
         const float inv = den != 0.f ? 1.0f / den : 0.f;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) up[d] = (j0[d] * P.omega[0] + (has_nw ? j1[d] * P.omega[1] : 0.f)) * inv;
+        for (int d = 0; d < 3; ++d) up[d] = (j[0][d] * P.omega[0] + (has_nw ? j[1][d] * P.omega[1] : 0.f)) * inv;
     }
 
 #pragma unroll
@@ -196,31 +201,47 @@ __device__ __forceinline__ void collide_store(const float* st, const float* ring
         }
         const float uu = ueq[0] * ueq[0] + ueq[1] * ueq[1] + ueq[2] * ueq[2];
         const float om = P.omega[s];
+        const float keep = 1.0f - om;
+        const float base = rs * (1.0f - 1.5f * uu);
+        const float r45 = 4.5f * rs;
+        const float r3 = 3.0f * rs;
         float* __restrict__ out = s == 0 ? out0 : out1;
-        float sum = 0.f;
+        float part[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
+        for (int k = 1; k < Q; k += 2) {
             const float eu = (float)EX(k) * ueq[0] + (float)EY(k) * ueq[1] + (float)EZ(k) * ueq[2];
-            const float feq = WK(k) * rs * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-            const float v = f[s][k] - om * (f[s][k] - feq);
-            sum += v;
-            out[k * g.plane + cell] = v;
+            // f^eq_k = w rho (1 + 3 eu + 4.5 eu^2 - 1.5 uu), f^eq_{k+1} with -eu
+            const float sym = WK(k) * (base + r45 * eu * eu);
+            const float asym = WK(k) * (r3 * eu);
+            const float v0 = keep * f[s][k] + om * (sym + asym);
+            const float v1 = keep * f[s][k + 1] + om * (sym - asym);
+            part[(k >> 1) % 3] += v0 + v1;
+            out[(size_t)k * g.plane] = v0;
+            out[(size_t)(k + 1) * g.plane] = v1;
         }
-        out[cell] = rs - sum;  // rest population: the collision keeps rho_s
+        out[0] = rs - ((part[0] + part[1]) + part[2]);  // rest population: the collision keeps rho_s
     }
 }
 
-template <int BY>
-__global__ void __launch_bounds__(32 * BY, 1) sc_step_kernel(const float* __restrict__ fin, float* __restrict__ fout,
+// Pipeline: plane p is queued LEAD iterations before it is collided; plane z+1
+// must have landed when plane z is collided (its densities feed the force), so
+// LEAD + 1 planes of populations sit in each thread's private stage slots.
+// The geometry word of a plane is fetched one iteration before its pull is
+// queued, so the queueing never waits on memory.
+template <int BY, int LEAD>
+__global__ void __launch_bounds__(32 * BY, (BY <= 6 && LEAD <= 2) ? 2 : 1) sc_step_kernel(const float* __restrict__ fin, float* __restrict__ fout,
                                                              const uint32_t* __restrict__ nbr,
                                                              const uint32_t* __restrict__ nbr_nw,
                                                              const uint32_t* __restrict__ adh, Geom g, Phys P,
                                                              int lz) {
     constexpr int TY = BY - 2;
     constexpr int NT = 32 * BY;
+    constexpr int NS = LEAD + 1;  // stages
     extern __shared__ float smem[];
-    float* stage = smem;                         // [STAGES][2*Q][NT], each thread its own column
-    float* ring = smem + STAGES * 2 * Q * NT;    // [4][2][NT]
+    float* stage = smem;                          // [NS][2*Q][NT], each thread its own column
+    float2* ring = reinterpret_cast<float2*>(smem + NS * 2 * Q * NT);  // [4][NT] (rho_w, rho_nw)
+    uint32_t* words = reinterpret_cast<uint32_t*>(ring + 4 * NT);       // [NS][NT]
+    uint32_t* adhw = words + NS * NT;                                   // [NS][NT]
     const int lane = threadIdx.x;
     const int row = threadIdx.y;
     const int tid = row * 32 + lane;
@@ -232,99 +253,240 @@ __global__ void __launch_bounds__(32 * BY, 1) sc_step_kernel(const float* __rest
     // columns beyond the last halo column are not needed by anyone
     const bool needed = gx <= g.nx && gy <= g.ny;
     const bool interior = lane >= 1 && lane <= 30 && row >= 1 && row <= TY && gx < g.nx && gy < g.ny;
-    auto st_of = [&](int p) { return stage + ((p + STAGES) % STAGES) * (2 * Q * NT); };
-    auto issue = [&](int p, int& cell) -> uint32_t {
-        if (!needed || p > z1) { cell = 0; return CLS_OUTSIDE << CLS_SHIFT; }
-        return issue_pull<NT>(fin, nbr, nbr_nw, g, col, p, st_of(p), tid, cell);
+    auto slot = [&](int p) { return (p - z0 + 1) % NS; };  // p >= z0 - 1
+    auto st_of = [&](int p) { return stage + slot(p) * (2 * Q * NT); };
+    // geometry word of plane p (CLS_OUTSIDE when not needed or beyond a closed edge)
+    auto fetch_word = [&](int p) -> uint32_t {
+        if (!needed || p > z1) return CLS_OUTSIDE << CLS_SHIFT;
+        int zz;
+        bool ok;
+        const int cell = plane_cell(g, col, p, zz, ok);
+        return ok ? __ldg(nbr + cell) : (CLS_OUTSIDE << CLS_SHIFT);
     };
-    auto publish = [&](int p, uint32_t w) {
+    auto issue = [&](int p, uint32_t w) {
+        words[slot(p) * NT + tid] = w;
+        if (!needed || p > z1) return;
+        int zz;
+        bool ok;
+        const int cell = plane_cell(g, col, p, zz, ok);
+        if (!ok) return;
+        issue_pull<NT>(fin, nbr_nw, g, col, zz, cell, w, st_of(p), tid);
+        if (w & BIT_ADH)
+            cp_async4(reinterpret_cast<float*>(adhw + slot(p) * NT + tid), reinterpret_cast<const float*>(adh + cell));
+    };
+    auto publish = [&](int p) {
         float rw, rn;
-        plane_density<NT>(w, st_of(p), tid, rw, rn);
-        ring[((p & 3) * 2 + 0) * NT + tid] = rw;
-        ring[((p & 3) * 2 + 1) * NT + tid] = rn;
+        plane_density<NT>(words[slot(p) * NT + tid], st_of(p), tid, rw, rn);
+        ring[(p & 3) * NT + tid] = make_float2(rw, rn);
     };
 
-    int cm, c0, c1;
-    const uint32_t wm = issue(z0 - 1, cm);
-    cp_async_commit();
-    uint32_t w0 = issue(z0, c0);
-    cp_async_commit();
-    uint32_t w1 = issue(z0 + 1, c1);
-    cp_async_commit();
-    cp_async_wait<1>();
-    publish(z0 - 1, wm);
-    publish(z0, w0);
-    for (int z = z0; z < z1; ++z) {
-        int c2;
-        const uint32_t w2 = issue(z + 2, c2);
+    // prologue: planes z0-1 .. z0+LEAD-1 queued, z0-1 and z0 published
+    uint32_t wnext = fetch_word(z0 - 1);
+#pragma unroll
+    for (int i = 0; i <= LEAD; ++i) {
+        const int p = z0 - 1 + i;
+        const uint32_t w = wnext;
+        wnext = fetch_word(p + 1);
+        issue(p, w);
         cp_async_commit();
-        cp_async_wait<1>();
-        publish(z + 1, w1);
+    }
+    // groups queued: planes z0-1 .. z0+LEAD-1 (LEAD+1 groups); planes z0-1, z0 done
+    cp_async_wait<LEAD - 1>();
+    publish(z0 - 1);
+    publish(z0);
+    for (int z = z0; z < z1; ++z) {
+        {
+            const int p = z + LEAD;
+            const uint32_t w = wnext;
+            wnext = fetch_word(p + 1);
+            issue(p, w);
+            cp_async_commit();
+        }
+        cp_async_wait<LEAD - 1>();  // plane z+1 has landed
+        publish(z + 1);
         __syncthreads();
+        const uint32_t w0 = words[slot(z) * NT + tid];
         const uint32_t cls = (w0 >> CLS_SHIFT) & CLS_MASK;
-        if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE)
-            collide_store<BY>(st_of(z), ring, w0, c0, z, row, lane, adh, P, g, fout);
-        w0 = w1;
-        c0 = c1;
-        w1 = w2;
-        c1 = c2;
+        if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE) {
+            int zz;
+            bool ok;
+            const int cell = plane_cell(g, col, z, zz, ok);
+            const float* st = st_of(z);
+            const bool has_nw = cls != CLS_MEMBRANE;
+            float f[2][Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                f[0][k] = st[k * NT + tid];
+                f[1][k] = has_nw ? st[(Q + k) * NT + tid] : 0.f;
+            }
+            collide_cell<BY>(f, ring, w0, adhw[slot(z) * NT + tid], cell, z, row, lane, P, g, fout);
+        }
     }
     cp_async_wait<0>();
 }
 
-template <int BY>
-size_t smem_bytes() {
-    return sizeof(float) * (size_t)(STAGES * 2 * Q + 4 * 2) * 32 * BY;
+// Double-pull variant: no staging buffers.  Each iteration first pulls plane
+// z+1 into registers only to sum its densities into the shared ring (all 32 x BY
+// threads), then, after the barrier, the interior threads pull plane z again --
+// the same addresses the previous iteration summed, normally still in L1 -- and
+// collide it.  Twice the load instructions, a tenth of the shared memory, so
+// two to three CTAs share an SM.
+template <int BY, int MINB>
+__global__ void __launch_bounds__(32 * BY, MINB) sc_step_dp_kernel(const float* __restrict__ fin,
+                                                                  float* __restrict__ fout,
+                                                                  const uint32_t* __restrict__ nbr,
+                                                                  const uint32_t* __restrict__ nbr_nw,
+                                                                  const uint32_t* __restrict__ adh, Geom g, Phys P,
+                                                                  int lz) {
+    constexpr int TY = BY - 2;
+    constexpr int NT = 32 * BY;
+    __shared__ float2 ring[4 * NT];
+    const int lane = threadIdx.x;
+    const int row = threadIdx.y;
+    const int tid = row * 32 + lane;
+    const int gx = blockIdx.x * 30 - 1 + lane;
+    const int gy = blockIdx.y * TY - 1 + row;
+    const int z0 = blockIdx.z * lz;
+    const int z1 = min(z0 + lz, g.nz);
+    const Column col = make_column(gx, gy, g);
+    const bool needed = gx <= g.nx && gy <= g.ny;
+    const bool interior = lane >= 1 && lane <= 30 && row >= 1 && row <= TY && gx < g.nx && gy < g.ny;
+    auto word_of = [&](int p) -> uint32_t {
+        if (!needed || p > z1) return CLS_OUTSIDE << CLS_SHIFT;
+        int zz;
+        bool ok;
+        const int cell = plane_cell(g, col, p, zz, ok);
+        return ok ? __ldg(nbr + cell) : (CLS_OUTSIDE << CLS_SHIFT);
+    };
+    auto publish = [&](int p, uint32_t w) {
+        float rw = 0.f, rn = 0.f;
+        int zz;
+        bool ok;
+        const int cell = plane_cell(g, col, p, zz, ok);
+        float dummy[2][Q];
+        if (needed && ok) pull_known<false, true>(fin, nbr_nw, g, col, zz, cell, w, dummy, rw, rn);
+        ring[(p & 3) * NT + tid] = make_float2(rw, rn);
+    };
+    uint32_t wm = word_of(z0 - 1);
+    uint32_t w0 = word_of(z0);
+    uint32_t w1 = word_of(z0 + 1);
+    publish(z0 - 1, wm);
+    publish(z0, w0);
+    for (int z = z0; z < z1; ++z) {
+        const uint32_t w2 = word_of(z + 2);  // prefetched for the next iteration
+        publish(z + 1, w1);
+        __syncthreads();
+        const uint32_t cls = (w0 >> CLS_SHIFT) & CLS_MASK;
+        if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE) {
+            int zz;
+            bool ok;
+            const int cell = plane_cell(g, col, z, zz, ok);
+            const uint32_t a = (w0 & BIT_ADH) ? __ldg(adh + cell) : 0u;
+            float f[2][Q];
+            float rw, rn;
+            pull_known<true, true>(fin, nbr_nw, g, col, zz, cell, w0, f, rw, rn);
+            collide_cell<BY>(f, ring, w0, a, cell, z, row, lane, P, g, fout);
+        }
+        w0 = w1;
+        w1 = w2;
+    }
 }
 
-template <int BY>
+template <int BY, int LEAD>
+size_t smem_bytes() {
+    return sizeof(float) * (size_t)((LEAD + 1) * 2 * Q + 4 * 2 + 2 * (LEAD + 1)) * 32 * BY;
+}
+
+template <int BY, int LEAD>
 cudaError_t launch_by(const float* fin, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw, const uint32_t* adh,
                       const Geom& g, const Phys& p, int lz, cudaStream_t s) {
     constexpr int TY = BY - 2;
     static unsigned long long configured = 0;  // one bit per device: the attribute is per device
-    const size_t sm = smem_bytes<BY>();
+    const size_t sm = smem_bytes<BY, LEAD>();
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured & bit)) {
-        e = cudaFuncSetAttribute(sc_step_kernel<BY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(sc_step_kernel<BY, LEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         configured |= bit;
     }
     dim3 grid((g.nx + 29) / 30, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
     dim3 block(32, BY);
-    sc_step_kernel<BY><<<grid, block, sm, s>>>(fin, fout, nbr, nbr_nw, adh, g, p, lz);
+    sc_step_kernel<BY, LEAD><<<grid, block, sm, s>>>(fin, fout, nbr, nbr_nw, adh, g, p, lz);
+    return cudaGetLastError();
+}
+
+template <int BY, int MINB>
+cudaError_t launch_dp(const float* fin, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw, const uint32_t* adh,
+                      const Geom& g, const Phys& p, int lz, cudaStream_t s) {
+    constexpr int TY = BY - 2;
+    static unsigned long long configured = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured & bit)) {
+        // most of the unified L1/shared storage goes to L1: the second pull reads from it
+        e = cudaFuncSetAttribute(sc_step_dp_kernel<BY, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, 10);
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    dim3 grid((g.nx + 29) / 30, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
+    dim3 block(32, BY);
+    sc_step_dp_kernel<BY, MINB><<<grid, block, 0, s>>>(fin, fout, nbr, nbr_nw, adh, g, p, lz);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 StepTile default_tile(const Geom& g) {
+    // 32 x 6 threads per CTA (30 x 4 interior columns), two planes queued ahead:
+    // two CTAs per SM.  z segments sized for about eight waves on 152 SMs.
     StepTile t;
-    t.by = 10;
-    // z segments: about 4 waves of one CTA per SM on 152 SMs, segments of >= 8 planes
+    t.by = 6;
+    t.lead = 2;
     const long long tiles_xy = (long long)((g.nx + 29) / 30) * ((g.ny + (t.by - 2) - 1) / (t.by - 2));
-    const long long want_segments = (4LL * 152 + tiles_xy - 1) / tiles_xy;
+    const long long want_segments = (4LL * 2 * 152 + tiles_xy - 1) / tiles_xy;
     int lz = (int)((g.nz + want_segments - 1) / want_segments);
-    if (lz < 8) lz = 8;
+    if (lz < 16) lz = 16;
     if (lz > g.nz) lz = g.nz;
     t.lz = lz;
     return t;
 }
 
-bool tile_supported(int by) { return by == 6 || by == 8 || by == 10 || by == 12; }
+bool tile_supported(int by, int lead) {
+    switch (lead) {
+        case 0: return by == 6 || by == 8 || by == 10;  // double-pull kernel
+        case 1: return by == 6 || by == 8 || by == 10;  // double-pull kernel, one more CTA per SM
+        case 2: return by == 6 || by == 8 || by == 10 || by == 12;
+        case 3: return by == 6 || by == 8 || by == 10;
+        case 4: return by == 6 || by == 8;
+        default: return false;
+    }
+}
 
 cudaError_t launch_step(const float* fin, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
                         const uint32_t* adh, const Geom& g, const Phys& p, StepTile tile, cudaStream_t s) {
-    if (tile.lz < 1) return cudaErrorInvalidValue;
-    switch (tile.by) {
-        case 6: return launch_by<6>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
-        case 8: return launch_by<8>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
-        case 10: return launch_by<10>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
-        case 12: return launch_by<12>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
-        default: return cudaErrorInvalidValue;
+    if (tile.lz < 1 || !tile_supported(tile.by, tile.lead)) return cudaErrorInvalidValue;
+#define LBM_TILE(BY, LEAD) \
+    if (tile.by == BY && tile.lead == LEAD) return launch_by<BY, LEAD>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
+    LBM_TILE(6, 2) LBM_TILE(8, 2) LBM_TILE(10, 2) LBM_TILE(12, 2)
+    LBM_TILE(6, 3) LBM_TILE(8, 3) LBM_TILE(10, 3)
+    LBM_TILE(6, 4) LBM_TILE(8, 4)
+#undef LBM_TILE
+    if (tile.lead == 0) {
+        if (tile.by == 6) return launch_dp<6, 3>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
+        if (tile.by == 8) return launch_dp<8, 2>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
+        if (tile.by == 10) return launch_dp<10, 2>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
     }
+    if (tile.lead == 1) {
+        if (tile.by == 6) return launch_dp<6, 4>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
+        if (tile.by == 8) return launch_dp<8, 3>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
+        if (tile.by == 10) return launch_dp<10, 3>(fin, fout, nbr, nbr_nw, adh, g, p, tile.lz, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lbmk

@@ -128,6 +128,15 @@ def sample192_spheres(seed: int = 2) -> np.ndarray:
     return rsa_packing(300, (192, 192, 192), 10.0, 14.0, seed, z_margin=(2.0, 5.0))
 
 
+def sample_spheres(edge: int, seed: int = 2) -> np.ndarray:
+    """The drainage-sample recipe at another box edge: the sphere count scales
+    with the box volume (300 at 192^3), same radii, same margins."""
+    if edge == 192:
+        return sample192_spheres(seed)
+    n = max(1, int(round(300 * (edge / 192.0) ** 3)))
+    return rsa_packing(n, (edge, edge, edge), 10.0, 14.0, seed, z_margin=(2.0, 5.0))
+
+
 def delaunay_throats(spheres: np.ndarray, n: int, seed: int, max_edge: float = 64.0):
     """Throats as sphere triples: the triangular facets of a Delaunay
     tetrahedralisation of the centres that two tetrahedra share, whose longest
