@@ -201,7 +201,7 @@ def cpu_baseline():
     oc = OracleCrop()
     oc.time_steps(1)
     dt1 = oc.time_steps(2) / 2
-    steps = max(1, min(400, int(15.0 / max(dt1, 1e-3))))
+    steps = max(1, min(4000, int(15.0 / max(dt1, 1e-3))))
     dt = oc.time_steps(steps)
     return {"value": oc.n_update * steps / dt / 1e6, "unit": "MLUPS", "cores": oc.cores, "kind": "oracle",
             "sample": oc.sample_text(steps)}
