@@ -122,13 +122,85 @@ int lbm_set_densities(lbm_domain* d, const double* rho);
 int lbm_set_pressure_bc(lbm_domain* d, double rho_in_nw, double rho_out_w);
 
 /* lbm_step -- queue n_steps fused time steps on the domain's stream
- * (asynchronous; n_steps >= 0). */
+ * (asynchronous; n_steps >= 0).  Whole chunks of 64 steps replay a CUDA graph
+ * captured on first use (one per starting buffer, recaptured after
+ * lbm_set_tile); the remainder is launched step by step.  Results are the same
+ * either way, bit for bit. */
 int lbm_step(lbm_domain* d, int n_steps);
 
 /* lbm_measure -- observables of the current state (synchronises the domain's
  * stream, bounded by a 60 s wait: LBM_ERR_TIMEOUT).  Returns LBM_ERR_NONFINITE
  * (with *out filled) when NaN/Inf or negative densities were found. */
 int lbm_measure(lbm_domain* d, lbm_measurement* out);
+
+/* lbm_get_density_at -- (rho_w, rho_nw) of one cell of the current state
+ * (synchronising); LBM_ERR_ARG outside the box. */
+int lbm_get_density_at(lbm_domain* d, int x, int y, int z, double rho_out[2]);
+
+/* One pressure increment of a drainage ladder. */
+typedef struct {
+    double rho_in_nw;      /* inlet non-wetting density of the increment              */
+    double p_c, p_c_res;   /* bulk-phase and reservoir capillary pressure (lbm_measure) */
+    double S_w, p_w, p_nw;
+    double phi_probe;      /* (rho_w - rho_nw)/(rho_w + rho_nw) at the probe cell       */
+    long long n_interface;
+} lbm_increment;
+
+/* lbm_run_drainage -- the pressure ladder of Sec. 2.2.2: for increment i the
+ * inlet reservoir is set to (rho_minor, rho_in_nw[i]) and the outlet to
+ * (rho_out_w, rho_minor), n_steps time steps run (replayed CUDA graphs of 64
+ * steps), and the domain is measured into rows[i].  The throat counts as
+ * invaded at the first increment after which phi < 0 at the probe cell (x, y, z);
+ * p_c^e is the largest p_c (bulk-phase) up to and including that increment --
+ * the maximum capillary pressure reached during invasion -- the first maximiser
+ * winning ties; *p_ce = +inf and *invaded_at = -1 when the probe never turned
+ * non-wetting.  rows holds n_incr entries (caller-owned).  Synchronising. */
+int lbm_run_drainage(lbm_domain* d, const double* rho_in_nw, int n_incr, int n_steps, double rho_out_w,
+                     const int probe[3], lbm_increment* rows, double* p_ce, int* invaded_at);
+
+/* Pressure ladder shared by every throat of a batch. */
+typedef struct {
+    int n_incr;               /* number of increments (>= 1)                          */
+    int n_steps;              /* time steps per increment (>= 0)                      */
+    const double* rho_in_nw;  /* n_incr inlet non-wetting densities (host, caller's)  */
+    double rho_out_w;         /* outlet wetting density                               */
+} lbm_schedule;
+
+/* Per-throat outcome of a batch. */
+typedef struct {
+    double p_ce;         /* entry capillary pressure (rule of lbm_run_drainage); +inf if not invaded */
+    int invaded_at;      /* increment of invasion, -1 if none                                      */
+    int dims[3];         /* throat box (nx, ny, nz)                                                */
+    int probe[3];        /* probe cell, -1s if the probe plane holds no fluid                      */
+    long long n_fluid;   /* interior fluid cells                                                   */
+} lbm_throat_result;
+
+/* lbm_throat_geometry -- the throat domain of Sec. 2.2.2 for three spheres
+ * (spheres3: 3 x (cx, cy, cz, r), any frame): a box in the frame of the three
+ * centres (x along c1 - c0, z along the normal of their plane; cell (i, j, k)
+ * at local (x0 + i, y0 + j, -ceil(rmax) + k) with x0, y0 the floors of the
+ * centres' local minima), grain inside the spheres, neutral walls outside the
+ * triangular prism whose walls pass through pairs of centres orthogonally to
+ * their plane, inlet layer k = 0 and outlet layer k = nz - 1.  Fills dims_out;
+ * when mask_out is not NULL also the nx*ny*nz mask bytes and probe_out (the
+ * fluid cell of plane nz - 3 farthest from the sphere surfaces, where invasion
+ * is detected).  LBM_ERR_ARG for collinear centres or boxes beyond 512. */
+int lbm_throat_geometry(const double* spheres3, int dims_out[3], unsigned char* mask_out, int probe_out[3]);
+
+/* lbm_run_throat_batch -- the per-throat simulations of the hybrid method
+ * (Sec. 2.2.2: one LBM run per pore throat, p_c^e from its drainage ladder) for
+ * n throats at once: each throat's box (lbm_throat_geometry) starts filled with
+ * wetting fluid, then runs the schedule's ladder exactly as lbm_run_drainage
+ * would on that box alone.  All throats share one device arena; one persistent
+ * launch per increment processes them largest first, one CTA per throat.
+ *   throats   n x 3 x 4 doubles (host)
+ *   params    tau, G, G_ads, body_force, rho_major, rho_minor are used
+ *   results   n entries (host, caller-owned)
+ *   rows      n x n_incr increments, throat-major (host, caller-owned)
+ *   stream    cudaStream_t (NULL = legacy stream); the call synchronises it.
+ * Device memory is allocated for the call and released before it returns. */
+int lbm_run_throat_batch(const double* throats, int n, const lbm_params* params, const lbm_schedule* sched,
+                         lbm_throat_result* results, lbm_increment* rows, void* stream);
 
 /* lbm_get_density -- densities of the current state, 2 x N doubles
  * (component-major), 0 where a component is not fluid. Synchronising. */

@@ -189,6 +189,34 @@ def voxelise_throat(spheres3) -> np.ndarray:
     return mask
 
 
+def throat_probe(spheres3, mask):
+    """Probe cell of a throat box: the fluid cell of plane nz - 3 farthest from
+    every sphere surface (max over cells of min_s |p - c_s| - r_s, the first in
+    cell order on ties); (-1, -1, -1) when that plane holds no fluid."""
+    dims, org, loc = throat_frame(spheres3)
+    nx, ny, nz = dims
+    k = nz - 3
+    best, probe = -1e300, (-1, -1, -1)
+    if k < 0:
+        return probe
+    for j in range(ny):
+        for i in range(nx):
+            if mask[k, j, i] & M_SOLID:
+                continue
+            p = (org[0] + float(i), org[1] + float(j), org[2] + float(k))
+            dmin = 1e300
+            for s in range(3):
+                dx = p[0] - loc[s, 0]
+                dy = p[1] - loc[s, 1]
+                dz = p[2] - loc[s, 2]
+                d = math.sqrt(dx * dx + dy * dy + dz * dz) - loc[s, 3]
+                if d < dmin:
+                    dmin = d
+            if dmin > best:
+                best, probe = dmin, (i, j, k)
+    return probe
+
+
 # -------------------------------------------------------------------- state
 def init(cfg: Config, mask: np.ndarray, rho0: np.ndarray) -> np.ndarray:
     """Rest equilibrium of the initial densities rho0[2, nz, ny, nx]."""

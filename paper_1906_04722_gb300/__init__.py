@@ -57,6 +57,29 @@ class lbm_measurement(ctypes.Structure):
         return out
 
 
+class lbm_increment(ctypes.Structure):
+    _fields_ = [("rho_in_nw", ctypes.c_double), ("p_c", ctypes.c_double), ("p_c_res", ctypes.c_double),
+                ("S_w", ctypes.c_double), ("p_w", ctypes.c_double), ("p_nw", ctypes.c_double),
+                ("phi_probe", ctypes.c_double), ("n_interface", ctypes.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class lbm_schedule(ctypes.Structure):
+    _fields_ = [("n_incr", ctypes.c_int), ("n_steps", ctypes.c_int),
+                ("rho_in_nw", ctypes.POINTER(ctypes.c_double)), ("rho_out_w", ctypes.c_double)]
+
+
+class lbm_throat_result(ctypes.Structure):
+    _fields_ = [("p_ce", ctypes.c_double), ("invaded_at", ctypes.c_int), ("dims", ctypes.c_int * 3),
+                ("probe", ctypes.c_int * 3), ("n_fluid", ctypes.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {"p_ce": self.p_ce, "invaded_at": self.invaded_at, "dims": tuple(self.dims),
+                "probe": tuple(self.probe), "n_fluid": self.n_fluid}
+
+
 # exported symbol -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -72,6 +95,9 @@ SIGNATURES = {
     "lbm_step": (ctypes.c_int, [_VP, ctypes.c_int]),
     "lbm_measure": (ctypes.c_int, [_VP, ctypes.POINTER(lbm_measurement)]),
     "lbm_get_density": (ctypes.c_int, [_VP, _DP]),
+    "lbm_get_density_at": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP]),
+    "lbm_run_drainage": (ctypes.c_int, [_VP, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_double, _IP,
+                                        ctypes.POINTER(lbm_increment), _DP, _IP]),
     "lbm_get_mask": (ctypes.c_int, [_VP, _U8P]),
     "lbm_get_dims": (ctypes.c_int, [_VP, _IP, _LLP]),
     "lbm_get_state": (ctypes.c_int, [_VP, _FP, _LLP]),
@@ -80,6 +106,10 @@ SIGNATURES = {
                                                  ctypes.POINTER(lbm_measurement)]),
     "lbm_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_get_tile": (ctypes.c_int, [_VP, _IP, _IP, _IP]),
+    "lbm_throat_geometry": (ctypes.c_int, [_DP, _IP, _U8P, _IP]),
+    "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
+                                            ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
+                                            ctypes.POINTER(lbm_increment), _VP]),
     "lbm_destroy": (None, [_VP]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -202,6 +232,25 @@ def lbm_get_density(h) -> np.ndarray:
     return out
 
 
+def lbm_get_density_at(h, x: int, y: int, z: int):
+    out = (ctypes.c_double * 2)()
+    _check(load().lbm_get_density_at(h, int(x), int(y), int(z), out), "lbm_get_density_at")
+    return out[0], out[1]
+
+
+def lbm_run_drainage(h, rho_in_nw, n_steps: int, rho_out_w: float, probe):
+    """Pressure ladder; returns {'rows': [...], 'p_ce': float, 'invaded_at': int}."""
+    lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
+    n = lad.shape[0]
+    rows = (lbm_increment * n)()
+    pr = (ctypes.c_int * 3)(*[int(v) for v in probe])
+    pce = ctypes.c_double()
+    inv = ctypes.c_int()
+    _check(load().lbm_run_drainage(h, lad.ctypes.data_as(_DP), n, int(n_steps), float(rho_out_w), pr, rows,
+                                   ctypes.byref(pce), ctypes.byref(inv)), "lbm_run_drainage")
+    return {"rows": [r.as_dict() for r in rows], "p_ce": pce.value, "invaded_at": inv.value}
+
+
 def lbm_get_mask(h) -> np.ndarray:
     (nx, ny, nz), _ = lbm_get_dims(h)
     out = np.empty((nz, ny, nx), dtype=np.uint8)
@@ -246,6 +295,37 @@ def lbm_get_tile(h):
     return a.value, b.value, c.value
 
 
+def lbm_throat_geometry(spheres3):
+    """(mask uint8[nz, ny, nx], probe (x, y, z)) of the throat box of three spheres."""
+    sp = np.ascontiguousarray(np.asarray(spheres3, dtype=np.float64).reshape(3, 4))
+    dims = (ctypes.c_int * 3)()
+    _check(load().lbm_throat_geometry(sp.ctypes.data_as(_DP), dims, None, None), "lbm_throat_geometry")
+    nx, ny, nz = dims
+    mask = np.empty((nz, ny, nx), dtype=np.uint8)
+    probe = (ctypes.c_int * 3)()
+    _check(load().lbm_throat_geometry(sp.ctypes.data_as(_DP), dims, mask.ctypes.data_as(_U8P), probe),
+           "lbm_throat_geometry")
+    return mask, tuple(probe)
+
+
+def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None):
+    """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict)."""
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
+    n = th.shape[0]
+    lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
+    sch = lbm_schedule()
+    sch.n_incr = lad.shape[0]
+    sch.n_steps = int(n_steps)
+    sch.rho_in_nw = lad.ctypes.data_as(_DP)
+    sch.rho_out_w = float(rho_out_w)
+    res = (lbm_throat_result * n)()
+    rows = (lbm_increment * (n * sch.n_incr))()
+    _check(load().lbm_run_throat_batch(th.ctypes.data_as(_DP), n, ctypes.byref(params), ctypes.byref(sch), res, rows,
+                                       stream if stream is not None else _torch_stream()), "lbm_run_throat_batch")
+    I = sch.n_incr
+    return [r.as_dict() for r in res], [[rows[t * I + i].as_dict() for i in range(I)] for t in range(n)]
+
+
 def lbm_destroy(h):
     if h:
         load().lbm_destroy(h)
@@ -287,6 +367,12 @@ class Domain:
 
     def mask(self):
         return lbm_get_mask(self.h)
+
+    def density_at(self, x, y, z):
+        return lbm_get_density_at(self.h, x, y, z)
+
+    def drainage(self, rho_in_nw, n_steps, rho_out_w, probe):
+        return lbm_run_drainage(self.h, rho_in_nw, n_steps, rho_out_w, probe)
 
     def state(self):
         return lbm_get_state(self.h)

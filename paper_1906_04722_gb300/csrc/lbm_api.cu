@@ -60,7 +60,7 @@ int check_box(const int box[3]) {
     return LBM_OK;
 }
 
-void fill_phys(lbm_domain* d, double rho_in_nw, double rho_out_w) {
+void fill_phys(lbm_domain* d) {
     const lbm_params& p = d->params;
     Phys& ph = d->phys;
     for (int s = 0; s < 2; ++s) {
@@ -70,10 +70,78 @@ void fill_phys(lbm_domain* d, double rho_in_nw, double rho_out_w) {
     }
     ph.G = (float)p.G;
     for (int k = 0; k < 3; ++k) ph.g[k] = (float)p.body_force[k];
-    ph.rho_in[0] = (float)p.rho_minor;
-    ph.rho_in[1] = (float)rho_in_nw;
-    ph.rho_out[0] = (float)rho_out_w;
-    ph.rho_out[1] = (float)p.rho_minor;
+    ph.bc = d->d_bc;
+}
+
+// Queue the reservoir densities (inlet: rho_minor / rho_in_nw, outlet:
+// rho_out_w / rho_minor) on the domain's stream.
+int set_bc(lbm_domain* d, double rho_in_nw, double rho_out_w) {
+    d->bc_host[0] = d->params.rho_minor;
+    d->bc_host[1] = rho_in_nw;
+    d->bc_host[2] = rho_out_w;
+    d->bc_host[3] = d->params.rho_minor;
+    LBM_CUDA(launch_set_bc(d->d_bc, (float)d->bc_host[0], (float)d->bc_host[1], (float)d->bc_host[2],
+                           (float)d->bc_host[3], d->stream));
+    return LBM_OK;
+}
+
+void drop_graphs(lbm_domain* d) {
+    for (int i = 0; i < 2; ++i)
+        if (d->graph[i]) {
+            cudaGraphExecDestroy(d->graph[i]);
+            d->graph[i] = nullptr;
+        }
+}
+
+// Capture GRAPH_STEPS step launches that start from buffer `parity` on the
+// domain's private capture stream; the graph is launched on the domain's stream.
+int capture_graph(lbm_domain* d, int parity) {
+    LBM_CUDA(prepare_step(d->tile));
+    if (!d->capture_stream) LBM_CUDA(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
+    LBM_CUDA(cudaStreamBeginCapture(d->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int cur = parity;
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < GRAPH_STEPS && err == cudaSuccess; ++i) {
+        err = launch_step(d->f[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys, d->tile,
+                          d->capture_stream);
+        cur ^= 1;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t end = cudaStreamEndCapture(d->capture_stream, &graph);
+    if (err != cudaSuccess || end != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        set_error(std::string("graph capture of the step failed: ") +
+                  cudaGetErrorString(err != cudaSuccess ? err : end));
+        return LBM_ERR_CUDA;
+    }
+    cudaError_t inst = cudaGraphInstantiate(&d->graph[parity], graph, 0);
+    cudaGraphDestroy(graph);
+    if (inst != cudaSuccess) {
+        d->graph[parity] = nullptr;
+        set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(inst));
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+// n steps: whole chunks replay a captured graph, the remainder is launched one by one.
+int run_steps(lbm_domain* d, int n) {
+    while (n >= GRAPH_STEPS) {
+        if (!d->graph[d->cur]) {
+            int rc = capture_graph(d, d->cur);
+            if (rc) return rc;
+        }
+        LBM_CUDA(cudaGraphLaunch(d->graph[d->cur], d->stream));
+        d->step += GRAPH_STEPS;
+        n -= GRAPH_STEPS;
+    }
+    for (int i = 0; i < n; ++i) {
+        LBM_CUDA(launch_step(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys,
+                             d->tile, d->stream));
+        d->cur ^= 1;
+        ++d->step;
+    }
+    return LBM_OK;
 }
 
 void free_domain(lbm_domain* d) {
@@ -87,6 +155,10 @@ void free_domain(lbm_domain* d) {
     cudaFree(d->d_rho);
     cudaFree(d->d_partials);
     cudaFree(d->d_result);
+    cudaFree(d->d_bc);
+    cudaFree(d->d_probe);
+    drop_graphs(d);
+    if (d->capture_stream) cudaStreamDestroy(d->capture_stream);
     if (d->h_result) cudaFreeHost(d->h_result);
     if (d->done) cudaEventDestroy(d->done);
     delete d;
@@ -143,7 +215,6 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     g.pz = params->periodic[2] ? 1 : 0;
     fill_pull_offsets(g);
     d->tile = default_tile(g);
-    fill_phys(d, params->rho_major, params->rho_major);
 
     auto fail = [&](int rc) { free_domain(d); return rc; };
 #define LBM_CUDA_D(call)                                                                  \
@@ -167,6 +238,10 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     LBM_CUDA_D(cudaMalloc(&d->d_partials, sizeof(double) * NMEAS * (size_t)d->meas_blocks));
     LBM_CUDA_D(cudaMalloc(&d->d_result, sizeof(double) * NMEAS));
     LBM_CUDA_D(cudaMallocHost(&d->h_result, sizeof(double) * NMEAS));
+    LBM_CUDA_D(cudaMalloc(&d->d_bc, sizeof(float) * 4));
+    LBM_CUDA_D(cudaMalloc(&d->d_probe, sizeof(float) * 2));
+    fill_phys(d);
+    if (int rc = set_bc(d, params->rho_major, params->rho_major)) return fail(rc);
     // the untouched planes between N and the plane stride stay zero
     LBM_CUDA_D(cudaMemsetAsync(d->f[0], 0, fbytes, d->stream));
     LBM_CUDA_D(cudaMemsetAsync(d->f[1], 0, fbytes, d->stream));
@@ -265,17 +340,69 @@ int lbm_set_pressure_bc(lbm_domain* d, double rho_in_nw, double rho_out_w) {
         set_error("reservoir densities must be finite and >= 0");
         return LBM_ERR_ARG;
     }
-    fill_phys(d, rho_in_nw, rho_out_w);
-    return LBM_OK;
+    return set_bc(d, rho_in_nw, rho_out_w);
 }
 
 int lbm_step(lbm_domain* d, int n_steps) {
     if (!d || n_steps < 0) { set_error("domain is NULL or n_steps < 0"); return LBM_ERR_ARG; }
-    for (int i = 0; i < n_steps; ++i) {
-        LBM_CUDA(launch_step(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys,
-                             d->tile, d->stream));
-        d->cur ^= 1;
-        ++d->step;
+    return run_steps(d, n_steps);
+}
+
+int lbm_get_density_at(lbm_domain* d, int x, int y, int z, double rho_out[2]) {
+    if (!d || !rho_out) { set_error("domain or rho_out is NULL"); return LBM_ERR_ARG; }
+    if (x < 0 || y < 0 || z < 0 || x >= d->geom.nx || y >= d->geom.ny || z >= d->geom.nz) {
+        set_error("probe cell outside the box");
+        return LBM_ERR_ARG;
+    }
+    LBM_CUDA(launch_probe(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
+    LBM_CUDA(cudaMemcpyAsync(d->h_result, d->d_probe, sizeof(float) * 2, cudaMemcpyDeviceToHost, d->stream));
+    int rc = wait_domain(d);
+    if (rc) return rc;
+    const float* r = reinterpret_cast<const float*>(d->h_result);
+    rho_out[0] = r[0];
+    rho_out[1] = r[1];
+    return LBM_OK;
+}
+
+int lbm_run_drainage(lbm_domain* d, const double* rho_in_nw, int n_incr, int n_steps, double rho_out_w,
+                     const int probe[3], lbm_increment* rows, double* p_ce, int* invaded_at) {
+    if (!d || !rho_in_nw || !probe || !rows || !p_ce || !invaded_at || n_incr < 1 || n_steps < 0) {
+        set_error("lbm_run_drainage: NULL argument, n_incr < 1 or n_steps < 0");
+        return LBM_ERR_ARG;
+    }
+    *invaded_at = -1;
+    for (int i = 0; i < n_incr; ++i) {
+        int rc = lbm_set_pressure_bc(d, rho_in_nw[i], rho_out_w);
+        if (rc) return rc;
+        rc = run_steps(d, n_steps);
+        if (rc) return rc;
+        lbm_measurement m;
+        rc = lbm_measure(d, &m);
+        if (rc && rc != LBM_ERR_NONFINITE) return rc;
+        double pr[2];
+        int rp = lbm_get_density_at(d, probe[0], probe[1], probe[2], pr);
+        if (rp) return rp;
+        lbm_increment& r = rows[i];
+        r.rho_in_nw = rho_in_nw[i];
+        r.p_c = m.p_c;
+        r.p_c_res = m.p_c_res;
+        r.S_w = m.S_w;
+        r.p_w = m.p_w;
+        r.p_nw = m.p_nw;
+        r.n_interface = m.n_interface;
+        r.phi_probe = (pr[0] + pr[1]) != 0.0 ? (pr[0] - pr[1]) / (pr[0] + pr[1]) : 0.0;
+        if (*invaded_at < 0 && r.phi_probe < 0.0) *invaded_at = i;
+        if (rc == LBM_ERR_NONFINITE) return rc;
+    }
+    // p_c^e: the largest p_c up to and including the invasion increment (the
+    // maximum p_c reached during invasion, Sec. 2.2.2); first maximiser on ties
+    if (*invaded_at < 0) {
+        *p_ce = INFINITY;
+    } else {
+        double best = -INFINITY;
+        for (int i = 0; i <= *invaded_at; ++i)
+            if (rows[i].p_c == rows[i].p_c && rows[i].p_c > best) best = rows[i].p_c;
+        *p_ce = best;
     }
     return LBM_OK;
 }
@@ -377,6 +504,7 @@ int lbm_set_tile(lbm_domain* d, int by, int lz, int lead) {
     d->tile.by = by;
     d->tile.lz = lz > d->geom.nz ? d->geom.nz : lz;
     d->tile.lead = lead;
+    drop_graphs(d);  // captured with the old shape
     return LBM_OK;
 }
 

@@ -1,0 +1,439 @@
+// lbm_batch.cu -- many pore throats in one persistent launch per pressure increment.
+//
+// The hybrid method runs one small LBM simulation per pore throat (Sec. 2.2.2)
+// and the paper assigns one throat per CPU core (Sec. 4).  Here all throats of
+// a batch live in one device arena (each with its own box, plane stride and
+// geometry words, found through a record table) and a persistent grid of CTAs
+// pulls throats off a work counter, largest first.  A CTA owns its throat for a
+// whole increment: it runs the increment's time steps on the throat box tile by
+// tile (step_column, the same fused step as the single-domain kernel), with a
+// CTA barrier between steps as the only synchronisation, then measures the throat
+// (FP64 CTA reduction) and reads the probe cell.  One launch per increment; the
+// launches of all increments are captured in one CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "lbm_step_core.cuh"
+
+namespace lbmk {
+
+namespace {
+
+struct ThroatRec {
+    Geom g;
+    long long f_off;  // offset of the throat's populations in each population arena (floats)
+    long long c_off;  // offset of its cells in the per-cell arenas
+    int probe;        // probe cell index in the box, -1 if none
+};
+
+constexpr int BATCH_BY = 6;
+constexpr int BATCH_LEAD = 2;
+constexpr int BATCH_THREADS = 32 * BATCH_BY;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < BATCH_THREADS / 32; ++w) s += red[w];
+    return s;  // valid in thread 0
+}
+
+// Measurements of one throat box (definitions of lbm_measure), into row.
+__device__ void measure_throat(const float* __restrict__ f, const uint32_t* __restrict__ nbr,
+                               const uint32_t* __restrict__ nbr_nw, const Geom& g, double G, int probe,
+                               double rho_in_nw, double* red, lbm_increment* row) {
+    double acc[NMEAS];
+#pragma unroll
+    for (int i = 0; i < NMEAS; ++i) acc[i] = 0.0;
+    const int N = g.nxy * g.nz;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int c = tid; c < N; c += BATCH_THREADS) {
+        const int x = c % g.nx;
+        const int y = (c / g.nx) % g.ny;
+        const int z = c / g.nxy;
+        const Column col = make_column(x, y, g);
+        float dummy[2][Q];
+        float rwf, rnf;
+        int cell;
+        const uint32_t w = pull_cell<false>(f, nbr, nbr_nw, g, col, z, dummy, rwf, rnf, cell);
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        if (cls == CLS_SOLID) continue;
+        const double rw = rwf, rn = rnf;
+        acc[MS_MASS_W] += rw;
+        acc[MS_MASS_NW] += rn;
+        if (!isfinite(rw) || !isfinite(rn)) acc[MS_N_NONFINITE] += 1.0;
+        const double p = (rw + rn) / 3.0 + G * rw * rn / 3.0;  // Eq. 5
+        if (cls == CLS_INLET) { acc[MS_PIN] += p; acc[MS_N_IN] += 1.0; continue; }
+        if (cls == CLS_OUTLET) { acc[MS_POUT] += p; acc[MS_N_OUT] += 1.0; continue; }
+        acc[MS_N_FLUID] += 1.0;
+        if (rw > rn) acc[MS_N_W] += 1.0;
+        const double phi = (rw - rn) / (rw + rn);
+        if (fabs(phi) < 0.5) acc[MS_N_INTERFACE] += 1.0;
+        if (phi > 0.9) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
+        if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
+    }
+    double tot[NMEAS];
+#pragma unroll
+    for (int i = 0; i < NMEAS; ++i) tot[i] = block_sum(acc[i], red);
+    float pr[2] = {0.f, 0.f};
+    if (tid == 0 && probe >= 0) {
+        const int x = probe % g.nx, y = (probe / g.nx) % g.ny, z = probe / g.nxy;
+        const Column col = make_column(x, y, g);
+        float dummy[2][Q];
+        int cell;
+        pull_cell<false>(f, nbr, nbr_nw, g, col, z, dummy, pr[0], pr[1], cell);
+    }
+    if (tid == 0) {
+        lbm_increment r;
+        r.rho_in_nw = rho_in_nw;
+        r.p_w = tot[MS_N_BULK_W] > 0 ? tot[MS_PW] / tot[MS_N_BULK_W] : NAN;
+        r.p_nw = tot[MS_N_BULK_NW] > 0 ? tot[MS_PNW] / tot[MS_N_BULK_NW] : NAN;
+        r.p_c = r.p_nw - r.p_w;
+        const double pin = tot[MS_N_IN] > 0 ? tot[MS_PIN] / tot[MS_N_IN] : NAN;
+        const double pout = tot[MS_N_OUT] > 0 ? tot[MS_POUT] / tot[MS_N_OUT] : NAN;
+        r.p_c_res = pin - pout;
+        r.S_w = tot[MS_N_FLUID] > 0 ? tot[MS_N_W] / tot[MS_N_FLUID] : NAN;
+        const double a = pr[0], b = pr[1];
+        r.phi_probe = probe >= 0 && (a + b) != 0.0 ? (a - b) / (a + b) : 0.0;
+        r.n_interface = (long long)tot[MS_N_INTERFACE];
+        *row = r;
+    }
+}
+
+template <int BY, int LEAD>
+__global__ void __launch_bounds__(32 * BY, 2)
+    throat_batch_kernel(const ThroatRec* __restrict__ recs, const int* __restrict__ order, int n,
+                        int* __restrict__ counter, float* arena0, float* arena1, const uint32_t* __restrict__ nbr,
+                        const uint32_t* __restrict__ nbr_nw, const uint32_t* __restrict__ adh, Phys P, int n_steps,
+                        int parity, double G, double rho_in_nw, lbm_increment* __restrict__ rows, int incr,
+                        int n_incr) {
+    extern __shared__ float smem[];
+    __shared__ int s_t;
+    __shared__ double red[32];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    while (true) {
+        if (tid == 0) s_t = atomicAdd(counter, 1);
+        __syncthreads();
+        const int t = s_t;
+        __syncthreads();
+        if (t >= n) break;
+        const int id = order[t];
+        const Geom g = recs[id].g;
+        const long long f_off = recs[id].f_off, c_off = recs[id].c_off;
+        const int probe = recs[id].probe;
+        float* buf[2] = {arena0 + f_off, arena1 + f_off};
+        const uint32_t* tn = nbr + c_off;
+        const uint32_t* tnn = nbr_nw + c_off;
+        const uint32_t* ta = adh + c_off;
+        const int tiles_x = (g.nx + 29) / 30, tiles_y = (g.ny + BY - 3) / (BY - 2);
+        int cur = parity;
+        for (int s = 0; s < n_steps; ++s) {
+            for (int ty = 0; ty < tiles_y; ++ty)
+                for (int tx = 0; tx < tiles_x; ++tx) {
+                    step_column<BY, LEAD>(buf[cur], buf[cur ^ 1], tn, tnn, ta, g, P, tx, ty, 0, g.nz, smem);
+                    __syncthreads();
+                }
+            cur ^= 1;
+        }
+        measure_throat(buf[cur], tn, tnn, g, G, probe, rho_in_nw, red, rows + (size_t)id * n_incr + incr);
+        __syncthreads();
+    }
+}
+
+// Rest-equilibrium start of every throat: wetting fluid (rho_major, rho_minor)
+// everywhere, (rho_minor, rho_major) on the inlet layer; stored so that the first
+// pull yields exactly that (as init_kernel).
+__global__ void throat_init_kernel(const ThroatRec* __restrict__ recs, int n, float* arena,
+                                   const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
+                                   float rho_major, float rho_minor) {
+    const int id = blockIdx.x;
+    if (id >= n) return;
+    const Geom g = recs[id].g;
+    float* f = arena + recs[id].f_off;
+    const uint32_t* tn = nbr + recs[id].c_off;
+    const uint32_t* tnn = nbr_nw + recs[id].c_off;
+    const int N = g.nxy * g.nz;
+    auto rho_of = [&](int c, int s) {
+        const uint32_t cls = (tn[c] >> CLS_SHIFT) & CLS_MASK;
+        const bool inlet = cls == CLS_INLET;
+        return s == 0 ? (inlet ? rho_minor : rho_major) : (inlet ? rho_major : rho_minor);
+    };
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        const int x = c % g.nx, y = (c / g.nx) % g.ny, z = c / g.nxy;
+        const uint32_t w = tn[c];
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        for (int s = 0; s < 2; ++s) {
+            const bool fl = cls != CLS_SOLID && !(s == 1 && cls == CLS_MEMBRANE);
+            const uint32_t bits = s == 0 ? w : tnn[c];
+            float* fs = f + (size_t)s * Q * g.plane;
+            const float r = fl ? rho_of(c, s) : 0.f;
+            float sum = 0.f;
+            for (int i = 1; i < Q; ++i) sum += WK(i) * r;
+            for (int j = 0; j < Q; ++j) {
+                float v = 0.f;
+                if (fl && j == 0) {
+                    v = r - sum;
+                } else if (fl) {
+                    if ((bits >> OPP(j)) & 1u) {
+                        v = WK(j) * r;
+                    } else {
+                        bool ok = true;
+                        const int tx = wrap1(x + EX(j), g.nx, g.px, ok);
+                        const int ty = wrap1(y + EY(j), g.ny, g.py, ok);
+                        const int tz = wrap1(z + EZ(j), g.nz, g.pz, ok);
+                        v = WK(j) * rho_of(tz * g.nxy + ty * g.nx + tx, s);
+                    }
+                }
+                fs[(size_t)j * g.plane + c] = v;
+            }
+        }
+    }
+}
+
+size_t batch_smem() {
+    return sizeof(float) * (size_t)((BATCH_LEAD + 1) * 2 * Q + 4 * 2 + 2 * (BATCH_LEAD + 1)) * BATCH_THREADS;
+}
+
+int fail_cuda(cudaError_t e, const char* what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+}  // namespace
+
+}  // namespace lbmk
+
+using namespace lbmk;
+
+extern "C" int lbm_throat_geometry(const double* spheres3, int dims_out[3], unsigned char* mask_out,
+                                   int probe_out[3]) {
+    if (!spheres3 || !dims_out) {
+        set_error("lbm_throat_geometry: NULL argument");
+        return LBM_ERR_ARG;
+    }
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(spheres3[i])) {
+            set_error("lbm_throat_geometry: non-finite sphere entry");
+            return LBM_ERR_ARG;
+        }
+    double a[3], b[3], n[3];
+    for (int d = 0; d < 3; ++d) {
+        a[d] = spheres3[4 + d] - spheres3[d];
+        b[d] = spheres3[8 + d] - spheres3[d];
+    }
+    n[0] = a[1] * b[2] - a[2] * b[1];
+    n[1] = a[2] * b[0] - a[0] * b[2];
+    n[2] = a[0] * b[1] - a[1] * b[0];
+    if (n[0] * n[0] + n[1] * n[1] + n[2] * n[2] <= 1e-12) {
+        set_error("lbm_throat_geometry: the three centres are collinear");
+        return LBM_ERR_ARG;
+    }
+    double org[3], loc[12];
+    throat_frame(spheres3, dims_out, org, loc);
+    if (dims_out[0] > 512 || dims_out[1] > 512 || dims_out[2] > 512) {
+        set_error("lbm_throat_geometry: throat box larger than 512 cells along an axis");
+        return LBM_ERR_ARG;
+    }
+    if (mask_out) {
+        int probe[3];
+        voxelise_throat(spheres3, mask_out, probe);
+        if (probe_out) std::memcpy(probe_out, probe, sizeof(probe));
+    }
+    return LBM_OK;
+}
+
+extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_params* params,
+                                    const lbm_schedule* sched, lbm_throat_result* results, lbm_increment* rows,
+                                    void* stream_ptr) {
+    if (!throats || n < 1 || !params || !sched || !results || !rows || !sched->rho_in_nw || sched->n_incr < 1 ||
+        sched->n_steps < 0) {
+        set_error("lbm_run_throat_batch: NULL argument or empty batch/schedule");
+        return LBM_ERR_ARG;
+    }
+    for (int s = 0; s < 2; ++s)
+        if (!(params->tau[s] > 0.5)) {
+            set_error("lbm_run_throat_batch: tau must be > 0.5");
+            return LBM_ERR_ARG;
+        }
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    const int I = sched->n_incr;
+    try {
+        // host geometry: frames, masks, probes
+        std::vector<ThroatRec> recs((size_t)n);
+        std::vector<std::vector<uint8_t>> masks((size_t)n);
+        long long f_tot = 0, c_tot = 0;
+        for (int t = 0; t < n; ++t) {
+            int dims[3], probe[3];
+            int rc = lbm_throat_geometry(throats + 12 * t, dims, nullptr, nullptr);
+            if (rc) return rc;
+            const long long N = (long long)dims[0] * dims[1] * dims[2];
+            masks[t].resize((size_t)N);
+            lbm_throat_geometry(throats + 12 * t, dims, masks[t].data(), probe);
+            Geom& g = recs[t].g;
+            std::memset(&g, 0, sizeof(g));
+            g.nx = dims[0];
+            g.ny = dims[1];
+            g.nz = dims[2];
+            g.nxy = dims[0] * dims[1];
+            g.plane = (int)((N + 31) / 32 * 32);
+            fill_pull_offsets(g);
+            recs[t].f_off = f_tot;
+            recs[t].c_off = c_tot;
+            recs[t].probe = probe[0] < 0 ? -1 : (probe[2] * dims[1] + probe[1]) * dims[0] + probe[0];
+            f_tot += (long long)g.plane * 2 * Q;
+            c_tot += N;
+            lbm_throat_result& r = results[t];
+            r.dims[0] = dims[0];
+            r.dims[1] = dims[1];
+            r.dims[2] = dims[2];
+            std::memcpy(r.probe, probe, sizeof(probe));
+            long long nf = 0;
+            for (uint8_t m : masks[t]) nf += m == 0;
+            r.n_fluid = nf;
+        }
+        // largest boxes first
+        std::vector<int> order((size_t)n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (long long)recs[a].g.nxy * recs[a].g.nz > (long long)recs[b].g.nxy * recs[b].g.nz;
+        });
+
+        float *a0 = nullptr, *a1 = nullptr, *d_bc = nullptr;
+        uint8_t* d_mask = nullptr;
+        uint32_t *d_nbr = nullptr, *d_nbr_nw = nullptr, *d_adh = nullptr;
+        ThroatRec* d_recs = nullptr;
+        int *d_order = nullptr, *d_counter = nullptr;
+        lbm_increment* d_rows = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t cap = nullptr;
+        auto cleanup = [&]() {
+            cudaFree(a0); cudaFree(a1); cudaFree(d_bc); cudaFree(d_mask); cudaFree(d_nbr); cudaFree(d_nbr_nw);
+            cudaFree(d_adh); cudaFree(d_recs); cudaFree(d_order); cudaFree(d_counter); cudaFree(d_rows);
+            if (exec) cudaGraphExecDestroy(exec);
+            if (cap) cudaStreamDestroy(cap);
+        };
+#define BATCH_CUDA(call)                               \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) {                       \
+            cleanup();                                 \
+            return fail_cuda(e_, #call);               \
+        }                                              \
+    } while (0)
+        BATCH_CUDA(cudaMalloc(&a0, sizeof(float) * (size_t)f_tot));
+        BATCH_CUDA(cudaMalloc(&a1, sizeof(float) * (size_t)f_tot));
+        BATCH_CUDA(cudaMalloc(&d_mask, (size_t)c_tot));
+        BATCH_CUDA(cudaMalloc(&d_nbr, sizeof(uint32_t) * (size_t)c_tot));
+        BATCH_CUDA(cudaMalloc(&d_nbr_nw, sizeof(uint32_t) * (size_t)c_tot));
+        BATCH_CUDA(cudaMalloc(&d_adh, sizeof(uint32_t) * (size_t)c_tot));
+        BATCH_CUDA(cudaMalloc(&d_recs, sizeof(ThroatRec) * (size_t)n));
+        BATCH_CUDA(cudaMalloc(&d_order, sizeof(int) * (size_t)n));
+        BATCH_CUDA(cudaMalloc(&d_counter, sizeof(int) * (size_t)I));
+        BATCH_CUDA(cudaMalloc(&d_rows, sizeof(lbm_increment) * (size_t)n * I));
+        BATCH_CUDA(cudaMalloc(&d_bc, sizeof(float) * 4 * (size_t)I));
+        BATCH_CUDA(cudaMemsetAsync(a0, 0, sizeof(float) * (size_t)f_tot, stream));
+        BATCH_CUDA(cudaMemsetAsync(a1, 0, sizeof(float) * (size_t)f_tot, stream));
+        {
+            std::vector<uint8_t> all((size_t)c_tot);
+            for (int t = 0; t < n; ++t) std::memcpy(all.data() + recs[t].c_off, masks[t].data(), masks[t].size());
+            BATCH_CUDA(cudaMemcpyAsync(d_mask, all.data(), (size_t)c_tot, cudaMemcpyHostToDevice, stream));
+            for (int t = 0; t < n; ++t)
+                BATCH_CUDA(launch_geometry(d_mask + recs[t].c_off, d_nbr + recs[t].c_off, d_nbr_nw + recs[t].c_off,
+                                           d_adh + recs[t].c_off, recs[t].g, stream));
+            BATCH_CUDA(cudaMemcpyAsync(d_recs, recs.data(), sizeof(ThroatRec) * (size_t)n, cudaMemcpyHostToDevice,
+                                       stream));
+            BATCH_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, stream));
+            std::vector<float> bc((size_t)4 * I);
+            for (int i = 0; i < I; ++i) {
+                bc[4 * i + 0] = (float)params->rho_minor;
+                bc[4 * i + 1] = (float)sched->rho_in_nw[i];
+                bc[4 * i + 2] = (float)sched->rho_out_w;
+                bc[4 * i + 3] = (float)params->rho_minor;
+            }
+            BATCH_CUDA(cudaMemcpyAsync(d_bc, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice, stream));
+            throat_init_kernel<<<n, 256, 0, stream>>>(d_recs, n, a0, d_nbr, d_nbr_nw, (float)params->rho_major,
+                                                      (float)params->rho_minor);
+            BATCH_CUDA(cudaGetLastError());
+            BATCH_CUDA(cudaStreamSynchronize(stream));  // host staging buffers go out of scope
+        }
+        Phys P;
+        for (int s = 0; s < 2; ++s) {
+            P.tau[s] = (float)params->tau[s];
+            P.omega[s] = (float)(1.0 / params->tau[s]);
+            P.Gads[s] = (float)params->G_ads[s];
+        }
+        P.G = (float)params->G;
+        for (int d = 0; d < 3; ++d) P.g[d] = (float)params->body_force[d];
+
+        auto kern = throat_batch_kernel<BATCH_BY, BATCH_LEAD>;
+        const size_t smem = batch_smem();
+        BATCH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0, dev = 0, sms = 0;
+        BATCH_CUDA(cudaGetDevice(&dev));
+        BATCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem));
+        const int grid = std::max(1, std::min(n, sms * std::max(1, per_sm)));
+
+        // one launch per increment, all captured in one graph
+        BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        BATCH_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t cerr = cudaMemsetAsync(d_counter, 0, sizeof(int) * (size_t)I, cap);
+        for (int i = 0; i < I && cerr == cudaSuccess; ++i) {
+            Phys Pi = P;
+            Pi.bc = d_bc + 4 * i;
+            const int parity = (int)(((long long)i * sched->n_steps) & 1);
+            kern<<<grid, dim3(32, BATCH_BY), smem, cap>>>(d_recs, d_order, n, d_counter + i, a0, a1, d_nbr, d_nbr_nw,
+                                                          d_adh, Pi, sched->n_steps, parity, params->G,
+                                                          sched->rho_in_nw[i], d_rows, i, I);
+            cerr = cudaGetLastError();
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t eend = cudaStreamEndCapture(cap, &graph);
+        if (cerr != cudaSuccess || eend != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cleanup();
+            return fail_cuda(cerr != cudaSuccess ? cerr : eend, "capture of the throat batch");
+        }
+        cudaError_t einst = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (einst != cudaSuccess) {
+            exec = nullptr;
+            cleanup();
+            return fail_cuda(einst, "cudaGraphInstantiate");
+        }
+        BATCH_CUDA(cudaGraphLaunch(exec, stream));
+        BATCH_CUDA(cudaMemcpyAsync(rows, d_rows, sizeof(lbm_increment) * (size_t)n * I, cudaMemcpyDeviceToHost,
+                                   stream));
+        BATCH_CUDA(cudaStreamSynchronize(stream));
+        cleanup();
+#undef BATCH_CUDA
+        // invasion and p_c^e per throat (the rule of lbm_run_drainage)
+        for (int t = 0; t < n; ++t) {
+            const lbm_increment* r = rows + (size_t)t * I;
+            int inv = -1;
+            for (int i = 0; i < I; ++i)
+                if (r[i].phi_probe < 0.0) { inv = i; break; }
+            double best = INFINITY;
+            if (inv >= 0) {
+                best = -INFINITY;
+                for (int i = 0; i <= inv; ++i)
+                    if (r[i].p_c == r[i].p_c && r[i].p_c > best) best = r[i].p_c;
+            }
+            results[t].invaded_at = inv;
+            results[t].p_ce = best;
+        }
+        return LBM_OK;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    }
+}

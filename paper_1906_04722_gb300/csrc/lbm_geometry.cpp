@@ -109,4 +109,98 @@ void voxelise_box(int nx, int ny, int nz, const double* spheres, int n_spheres, 
             }
 }
 
+// Throat frame of Sec. 2.2.2 for centres c0, c1, c2: e1 along c1 - c0, e3 the
+// unit normal (c1 - c0) x (c2 - c0), e2 = e3 x e1; the local coordinates of a
+// point q are ((q - c0).e1, (q - c0).e2, (q - c0).e3).  The box spans the
+// integer bounding box of the centres' local x and y and z in [-ceil(H),
+// ceil(H)], H the largest radius; cell (i, j, k) sits at local
+// (x0 + i, y0 + j, -ceil(H) + k).
+void throat_frame(const double* sph, int dims[3], double origin[3], double local[12]) {
+    const double* c0 = sph;
+    const double* c1 = sph + 4;
+    const double* c2 = sph + 8;
+    double a[3], b[3], e1[3], e2[3], e3[3], n3[3];
+    sub3(c1, c0, a);
+    sub3(c2, c0, b);
+    const double la = std::sqrt(dot3(a, a));
+    for (int d = 0; d < 3; ++d) e1[d] = a[d] / la;
+    cross3(a, b, n3);
+    const double ln = std::sqrt(dot3(n3, n3));
+    for (int d = 0; d < 3; ++d) e3[d] = n3[d] / ln;
+    cross3(e3, e1, e2);
+    double H = 0.0, lx[3], ly[3];
+    for (int i = 0; i < 3; ++i) {
+        const double* ci = sph + 4 * i;
+        double rel[3];
+        sub3(ci, c0, rel);
+        lx[i] = dot3(rel, e1);
+        ly[i] = dot3(rel, e2);
+        local[4 * i + 0] = lx[i];
+        local[4 * i + 1] = ly[i];
+        local[4 * i + 2] = dot3(rel, e3);
+        local[4 * i + 3] = ci[3];
+        if (ci[3] > H) H = ci[3];
+    }
+    const double xmin = std::min(lx[0], std::min(lx[1], lx[2])), xmax = std::max(lx[0], std::max(lx[1], lx[2]));
+    const double ymin = std::min(ly[0], std::min(ly[1], ly[2])), ymax = std::max(ly[0], std::max(ly[1], ly[2]));
+    const double x0 = std::floor(xmin), y0 = std::floor(ymin), hz = std::ceil(H);
+    dims[0] = (int)(std::ceil(xmax) - x0) + 1;
+    dims[1] = (int)(std::ceil(ymax) - y0) + 1;
+    dims[2] = 2 * (int)hz + 1;
+    origin[0] = x0;
+    origin[1] = y0;
+    origin[2] = -hz;
+}
+
+// Throat box mask: grain inside the spheres, neutral wall outside the prism,
+// inlet layer k = 0, outlet layer k = nz - 1.  probe = the fluid cell of plane
+// nz - 3 farthest from every sphere surface (max of min_s |p - c_s| - r_s; the
+// first in cell order on ties), or (-1, -1, -1) when that plane has no fluid.
+void voxelise_throat(const double* sph, uint8_t* mask, int probe[3]) {
+    int dims[3];
+    double org[3], loc[12];
+    throat_frame(sph, dims, org, loc);
+    const Prism prism(loc, loc + 4, loc + 8);
+    for (int k = 0; k < dims[2]; ++k)
+        for (int j = 0; j < dims[1]; ++j)
+            for (int i = 0; i < dims[0]; ++i) {
+                const long long c = ((long long)k * dims[1] + j) * dims[0] + i;
+                const double p[3] = {org[0] + (double)i, org[1] + (double)j, org[2] + (double)k};
+                uint8_t m = 0;
+                for (int s = 0; s < 3; ++s)
+                    if (ball_contains(p[0], p[1], p[2], loc + 4 * s)) { m = LBM_MASK_SOLID | LBM_MASK_ADHESIVE; break; }
+                if (!m && !prism.contains(p)) m = LBM_MASK_SOLID;
+                if (!m) {
+                    if (k == 0) m = LBM_MASK_INLET;
+                    else if (k == dims[2] - 1) m = LBM_MASK_OUTLET;
+                }
+                mask[c] = m;
+            }
+    probe[0] = probe[1] = probe[2] = -1;
+    const int k = dims[2] - 3;
+    if (k < 0) return;
+    double best = -1e300;
+    for (int j = 0; j < dims[1]; ++j)
+        for (int i = 0; i < dims[0]; ++i) {
+            const long long c = ((long long)k * dims[1] + j) * dims[0] + i;
+            if (mask[c] & LBM_MASK_SOLID) continue;
+            const double p[3] = {org[0] + (double)i, org[1] + (double)j, org[2] + (double)k};
+            double dmin = 1e300;
+            for (int s = 0; s < 3; ++s) {
+                const double* q = loc + 4 * s;
+                const double dx = p[0] - q[0];
+                const double dy = p[1] - q[1];
+                const double dz = p[2] - q[2];
+                const double d = std::sqrt(dx * dx + dy * dy + dz * dz) - q[3];
+                if (d < dmin) dmin = d;
+            }
+            if (dmin > best) {
+                best = dmin;
+                probe[0] = i;
+                probe[1] = j;
+                probe[2] = k;
+            }
+        }
+}
+
 }  // namespace lbmk

@@ -67,8 +67,10 @@ struct Phys {
     float G;
     float Gads[2];
     float g[3];
-    float rho_in[2];   // (w, nw) imposed on inlet cells
-    float rho_out[2];  // (w, nw) imposed on outlet cells
+    // device pointer to the reservoir densities (inlet w, inlet nw, outlet w,
+    // outlet nw): kept in device memory so that a captured graph of steps stays
+    // valid when the pressure ladder moves on
+    const float* bc;
 };
 
 // Number of doubles in one measurement partial.
@@ -97,12 +99,19 @@ cudaError_t launch_density(const float* f, float* rho, const uint32_t* nbr, cons
 int measure_blocks(const Geom& g);
 cudaError_t launch_measure(const float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, double G,
                            double* partials, int nblocks, double* result, cudaStream_t s);
+cudaError_t prepare_step(const StepTile& tile);
+cudaError_t launch_set_bc(float* bc, float in_w, float in_nw, float out_w, float out_nw, cudaStream_t s);
+cudaError_t launch_probe(const float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, int x, int y,
+                         int z, float* out, cudaStream_t s);
 StepTile default_tile(const Geom& g);
 bool tile_supported(int by, int lead);
 
 // host geometry (lbm_geometry.cpp)
 void voxelise_box(int nx, int ny, int nz, const double* spheres, int n_spheres, int prism_clip, int reservoirs,
                   int membrane_layers, uint8_t* mask);
+
+void throat_frame(const double* spheres3, int dims[3], double origin[3], double local[12]);
+void voxelise_throat(const double* spheres3, uint8_t* mask, int probe[3]);
 
 // thread-local error text
 void set_error(const std::string& msg);
@@ -131,4 +140,12 @@ struct lbm_domain {
     int meas_blocks;
     cudaStream_t stream;
     cudaEvent_t done;
+    float* d_bc;        // reservoir densities (4 floats)
+    float* d_probe;     // density at a probe cell (2 floats)
+    double bc_host[4];  // last reservoir densities set
+    // captured chunks of GRAPH_STEPS steps, one per starting buffer
+    cudaGraphExec_t graph[2];
+    cudaStream_t capture_stream;
 };
+
+constexpr int GRAPH_STEPS = 64;  // steps per captured graph (even: the buffer parity is unchanged)

@@ -1,0 +1,122 @@
+"""Drainage ladder, graph replay and batched throats on the GPU.
+
+* lbm_step replays captured graphs of 64 steps: bit-identical to launching the
+  steps one by one.
+* lbm_run_drainage against the oracle's ladder (Sec. 2.2.2) on a throat that
+  invades: S_w and p_c per increment, the invasion increment and p_c^e.
+* lbm_run_throat_batch: throat i of a batch equals throat i run alone through
+  lbm_create_domain_mask + lbm_run_drainage.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04722_gb300 as m
+    m.load()
+    return m
+
+
+def _params(lbm, **kw):
+    base = dict(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR, rho_minor=W.RHO_MINOR)
+    base.update(kw)
+    return lbm.make_params(**base)
+
+
+def test_graph_chunks_equal_single_launches(lbm):
+    shape = (40, 24, 33)
+    spheres = np.array([[16.0, 12.0, 20.0, 6.0], [5.0, 5.0, 8.0, 4.0]])
+    nz, ny, nx = shape
+    a = lbm.Domain(_params(lbm, reservoirs=True), spheres, (nx, ny, nz))
+    b = lbm.Domain(_params(lbm, reservoirs=True), spheres, (nx, ny, nz))
+    for d in (a, b):
+        d.set_densities(W.initial_densities(shape, noise=1e-3, seed=9))
+        d.set_pressure_bc(2.07, 2.0)
+    a.step(64 * 2 + 5)          # two graph replays + 5 single launches
+    for _ in range(64 * 2 + 5):
+        b.step(1)
+    fa, sa = a.state()
+    fb, sb = b.state()
+    assert sa == sb == 133
+    assert np.array_equal(fa, fb)
+    # after a tile change the graph is recaptured and results stay the same
+    a.set_tile(8, 16, 2)
+    b.set_tile(8, 16, 2)
+    a.step(64)
+    for _ in range(64):
+        b.step(1)
+    assert np.array_equal(a.state()[0], b.state()[0])
+
+
+def _invading_throat():
+    """Three spheres r = 8 on an equilateral triangle of side 24 (throat radius
+    about 5.9) across a 32^3 box, prism clip, reservoirs; probe on the axis two
+    layers upstream of the outlet."""
+    N = 32
+    R = 24.0 / math.sqrt(3.0)
+    sp = np.array([(N / 2 + R * math.cos(math.radians(a)), N / 2 + R * math.sin(math.radians(a)), N / 2, 8.0)
+                   for a in (90, 210, 330)])
+    return (N, N, N), sp, (N // 2, N // 2, N - 3)
+
+
+def test_drainage_matches_oracle(lbm, orc):
+    shape, sp, probe = _invading_throat()
+    ladder = [2.0 + 0.02 * i for i in range(16)]
+    n_steps = 300
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm, reservoirs=True, prism_clip=True), sp, (nx, ny, nz))
+    mask = orc.voxelise(shape, sp, prism=True, reservoirs=True)
+    assert np.array_equal(dom.mask(), mask)
+    rho0 = W.initial_densities(shape)
+    dom.set_densities(rho0)
+    gpu = dom.drainage(ladder, n_steps, W.RHO_MAJOR, probe)
+    cfg = orc.Config(shape=shape, tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_out=(W.RHO_MAJOR, W.RHO_MINOR))
+    f = orc.init(cfg, mask, rho0)
+    ref = orc.drainage(cfg, mask, f, ladder, n_steps, probe)
+    assert ref["invaded_at"] >= 0, "the test throat must invade"
+    assert gpu["invaded_at"] == ref["invaded_at"]
+    pc_scale = max(abs(r["p_c"]) for r in ref["rows"] if r["p_c"] == r["p_c"])
+    for i, (g, o) in enumerate(zip(gpu["rows"], ref["rows"])):
+        if i > ref["invaded_at"]:
+            break
+        assert abs(g["S_w"] - o["S_w"]) <= 5e-3 * o["S_w"], (i, g["S_w"], o["S_w"])
+        if o["p_c"] == o["p_c"]:
+            assert abs(g["p_c"] - o["p_c"]) <= 5e-3 * pc_scale, (i, g["p_c"], o["p_c"])
+    assert abs(gpu["p_ce"] - ref["p_ce"]) <= 5e-3 * abs(ref["p_ce"])
+
+
+def test_batch_equals_single_throats(lbm, orc):
+    spheres = W.sample_spheres(128)
+    throats = W.delaunay_throats(spheres, 6, seed=11)
+    ladder = [2.0 + 0.05 * i for i in range(3)]
+    n_steps = 40
+    params = _params(lbm)
+    res, rows = lbm.lbm_run_throat_batch(throats, params, ladder, n_steps, W.RHO_MAJOR)
+    for t, sph in enumerate(throats):
+        mask, probe = lbm.lbm_throat_geometry(sph)
+        assert res[t]["dims"] == (mask.shape[2], mask.shape[1], mask.shape[0])
+        assert res[t]["probe"] == probe
+        dom = lbm.Domain(_params(lbm), mask=mask)
+        single = dom.drainage(ladder, n_steps, W.RHO_MAJOR, probe)
+        dom.close()
+        assert single["invaded_at"] == res[t]["invaded_at"]
+        for i in range(len(ladder)):
+            a, b = rows[t][i], single["rows"][i]
+            for k in ("S_w", "phi_probe", "p_c_res"):
+                assert abs(a[k] - b[k]) <= 1e-12 * max(1.0, abs(b[k])), (t, i, k, a[k], b[k])
+            for k in ("p_c", "p_w", "p_nw"):
+                if b[k] == b[k]:
+                    assert abs(a[k] - b[k]) <= 1e-12 * max(1.0, abs(b[k])), (t, i, k, a[k], b[k])
+                else:
+                    assert a[k] != a[k]
+            assert a["n_interface"] == b["n_interface"]
