@@ -62,7 +62,10 @@ typedef struct {
     double body_force[3]; /* acceleration g; the body force on component s is rho_s g   */
     double rho_major;     /* density of the majority fluid of a phase (e.g. 2.0)        */
     double rho_minor;     /* density of the dissolved other fluid (e.g. 0.06)           */
-    int precision;        /* storage of the populations: 0 = FP32 (only value so far)   */
+    int precision;        /* storage of the populations: 0 = FP32; 1 = FP16 and 2 = BF16
+                             deviations (pairs of both components per direction, taken
+                             against the reading cell's previous density; collision in
+                             FP32).  lbm_run_throat_batch always uses FP32.            */
     int periodic[3];      /* 1 = periodic along x, y, z                                 */
     int reservoirs;       /* 1 = inlet layer z = 0 (non-wetting reservoir) and outlet
                              layer z = nz-1 (wetting reservoir)                          */
@@ -217,7 +220,7 @@ int lbm_get_dims(const lbm_domain* d, int dims_out[3], long long* n_fluid_cells)
  * stored values are the post-collision populations of the last step, which the
  * next step pulls from (after lbm_set_densities, values whose pull yields the
  * rest equilibrium).  Resuming from a saved state reproduces the uninterrupted
- * run bit for bit. */
+ * run bit for bit.  FP32 domains only (LBM_ERR_STATE otherwise). */
 int lbm_get_state(lbm_domain* d, float* f_out, long long* step_out);
 int lbm_set_state(lbm_domain* d, const float* f_in, long long step);
 
@@ -252,7 +255,7 @@ int lbm_measure_state_noalloc(const lbm_params* params, const int box[3], const 
  *   lead  planes queued ahead of the collided one: 2, 3 or 4 (lead 3 allows
  *         by <= 10, lead 4 allows by <= 8).
  * Results do not depend on the shape (bit for bit).  LBM_ERR_ARG for an
- * unsupported combination. */
+ * unsupported combination (16-bit storage: lead 2 and by 6, 8 or 10). */
 int lbm_set_tile(lbm_domain* d, int by, int lz, int lead);
 int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
 

@@ -42,7 +42,10 @@ int check_params(const lbm_params* p) {
         set_error("rho_major must be > 0 and rho_minor >= 0");
         return LBM_ERR_ARG;
     }
-    if (p->precision != 0) { set_error("only precision = 0 (FP32 populations) is available"); return LBM_ERR_ARG; }
+    if (p->precision < 0 || p->precision > 2) {
+        set_error("precision must be 0 (FP32), 1 (FP16 deviations) or 2 (BF16 deviations)");
+        return LBM_ERR_ARG;
+    }
     if (p->membrane_layers < 0) { set_error("membrane_layers must be >= 0"); return LBM_ERR_ARG; }
     return LBM_OK;
 }
@@ -93,17 +96,29 @@ void drop_graphs(lbm_domain* d) {
         }
 }
 
+// One step from buffer `cur` to buffer cur ^ 1 on stream s.
+cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
+    if (d->params.precision == 0)
+        return launch_step(d->f[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys, d->tile, s);
+    return launch_step16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[cur]),
+                         reinterpret_cast<uint32_t*>(d->f[cur ^ 1]), d->R[cur], d->R[cur ^ 1], d->d_nbr, d->d_nbr_nw,
+                         d->d_adh, d->geom, d->phys, d->tile, s);
+}
+
+cudaError_t prepare_one(lbm_domain* d) {
+    return d->params.precision == 0 ? prepare_step(d->tile) : prepare_step16(d->params.precision, d->tile);
+}
+
 // Capture GRAPH_STEPS step launches that start from buffer `parity` on the
 // domain's private capture stream; the graph is launched on the domain's stream.
 int capture_graph(lbm_domain* d, int parity) {
-    LBM_CUDA(prepare_step(d->tile));
+    LBM_CUDA(prepare_one(d));
     if (!d->capture_stream) LBM_CUDA(cudaStreamCreateWithFlags(&d->capture_stream, cudaStreamNonBlocking));
     LBM_CUDA(cudaStreamBeginCapture(d->capture_stream, cudaStreamCaptureModeThreadLocal));
     int cur = parity;
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < GRAPH_STEPS && err == cudaSuccess; ++i) {
-        err = launch_step(d->f[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys, d->tile,
-                          d->capture_stream);
+        err = launch_one(d, cur, d->capture_stream);
         cur ^= 1;
     }
     cudaGraph_t graph = nullptr;
@@ -136,8 +151,8 @@ int run_steps(lbm_domain* d, int n) {
         n -= GRAPH_STEPS;
     }
     for (int i = 0; i < n; ++i) {
-        LBM_CUDA(launch_step(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys,
-                             d->tile, d->stream));
+        LBM_CUDA(prepare_one(d));
+        LBM_CUDA(launch_one(d, d->cur, d->stream));
         d->cur ^= 1;
         ++d->step;
     }
@@ -148,6 +163,8 @@ void free_domain(lbm_domain* d) {
     if (!d) return;
     cudaFree(d->f[0]);
     cudaFree(d->f[1]);
+    cudaFree(d->R[0]);
+    cudaFree(d->R[1]);
     cudaFree(d->d_mask);
     cudaFree(d->d_nbr);
     cudaFree(d->d_nbr_nw);
@@ -190,7 +207,12 @@ int upload_densities(lbm_domain* d, const double* rho) {
     std::vector<float> tmp((size_t)(2 * N));
     for (long long i = 0; i < 2 * N; ++i) tmp[(size_t)i] = (float)rho[i];
     LBM_CUDA(cudaMemcpyAsync(d->d_rho, tmp.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, d->stream));
-    LBM_CUDA(launch_init(d->d_rho, d->f[0], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+    if (d->params.precision == 0) {
+        LBM_CUDA(launch_init(d->d_rho, d->f[0], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+    } else {
+        LBM_CUDA(cudaMemsetAsync(d->f[0], 0, sizeof(uint32_t) * (size_t)d->geom.plane * Q, d->stream));
+        LBM_CUDA(launch_init16(d->d_rho, d->R[0], d->geom, d->stream));
+    }
     d->cur = 0;
     d->step = 0;
     return wait_domain(d);
@@ -225,10 +247,17 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
             return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);    \
         }                                                                                 \
     } while (0)
-    const size_t fbytes = sizeof(float) * (size_t)g.plane * 2 * Q;
+    // FP32: 2 x 19 floats per cell; 16-bit: 19 pair words per cell plus the density pair
+    const size_t fbytes = (params->precision == 0 ? sizeof(float) * 2 : sizeof(uint32_t)) * (size_t)g.plane * Q;
     LBM_CUDA_D(cudaEventCreateWithFlags(&d->done, cudaEventDisableTiming));
     LBM_CUDA_D(cudaMalloc(&d->f[0], fbytes));
     LBM_CUDA_D(cudaMalloc(&d->f[1], fbytes));
+    if (params->precision != 0) {
+        LBM_CUDA_D(cudaMalloc(&d->R[0], sizeof(float2) * (size_t)g.plane));
+        LBM_CUDA_D(cudaMalloc(&d->R[1], sizeof(float2) * (size_t)g.plane));
+        LBM_CUDA_D(cudaMemsetAsync(d->R[0], 0, sizeof(float2) * (size_t)g.plane, d->stream));
+        LBM_CUDA_D(cudaMemsetAsync(d->R[1], 0, sizeof(float2) * (size_t)g.plane, d->stream));
+    }
     LBM_CUDA_D(cudaMalloc(&d->d_mask, (size_t)d->N));
     LBM_CUDA_D(cudaMalloc(&d->d_nbr, sizeof(uint32_t) * (size_t)d->N));
     LBM_CUDA_D(cudaMalloc(&d->d_nbr_nw, sizeof(uint32_t) * (size_t)d->N));
@@ -354,7 +383,11 @@ int lbm_get_density_at(lbm_domain* d, int x, int y, int z, double rho_out[2]) {
         set_error("probe cell outside the box");
         return LBM_ERR_ARG;
     }
-    LBM_CUDA(launch_probe(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
+    if (d->params.precision == 0)
+        LBM_CUDA(launch_probe(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
+    else
+        LBM_CUDA(launch_probe16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
+                                d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
     LBM_CUDA(cudaMemcpyAsync(d->h_result, d->d_probe, sizeof(float) * 2, cudaMemcpyDeviceToHost, d->stream));
     int rc = wait_domain(d);
     if (rc) return rc;
@@ -409,8 +442,13 @@ int lbm_run_drainage(lbm_domain* d, const double* rho_in_nw, int n_incr, int n_s
 
 int lbm_measure(lbm_domain* d, lbm_measurement* out) {
     if (!d || !out) { set_error("domain or out is NULL"); return LBM_ERR_ARG; }
-    LBM_CUDA(launch_measure(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials,
-                            d->meas_blocks, d->d_result, d->stream));
+    if (d->params.precision == 0)
+        LBM_CUDA(launch_measure(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials,
+                                d->meas_blocks, d->d_result, d->stream));
+    else
+        LBM_CUDA(launch_measure16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
+                                  d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials, d->meas_blocks,
+                                  d->d_result, d->stream));
     LBM_CUDA(cudaMemcpyAsync(d->h_result, d->d_result, sizeof(double) * NMEAS, cudaMemcpyDeviceToHost, d->stream));
     int rc = wait_domain(d);
     if (rc) return rc;
@@ -445,7 +483,11 @@ int lbm_measure(lbm_domain* d, lbm_measurement* out) {
 int lbm_get_density(lbm_domain* d, double* rho_out) {
     if (!d || !rho_out) { set_error("domain or rho_out is NULL"); return LBM_ERR_ARG; }
     try {
-        LBM_CUDA(launch_density(d->f[d->cur], d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        if (d->params.precision == 0)
+            LBM_CUDA(launch_density(d->f[d->cur], d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        else
+            LBM_CUDA(launch_density16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]),
+                                      d->R[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->d_rho, d->stream));
         std::vector<float> tmp((size_t)(2 * d->N));
         LBM_CUDA(cudaMemcpyAsync(tmp.data(), d->d_rho, sizeof(float) * 2 * d->N, cudaMemcpyDeviceToHost, d->stream));
         int rc = wait_domain(d);
@@ -475,6 +517,7 @@ int lbm_get_dims(const lbm_domain* d, int dims_out[3], long long* n_fluid_cells)
 
 int lbm_get_state(lbm_domain* d, float* f_out, long long* step_out) {
     if (!d || !f_out) { set_error("domain or f_out is NULL"); return LBM_ERR_ARG; }
+    if (d->params.precision != 0) { set_error("checkpoints are available for FP32 domains only"); return LBM_ERR_STATE; }
     const long long N = d->N;
     for (int p = 0; p < 2 * Q; ++p)
         LBM_CUDA(cudaMemcpyAsync(f_out + (size_t)p * N, d->f[d->cur] + (size_t)p * d->geom.plane, sizeof(float) * N,
@@ -487,6 +530,7 @@ int lbm_get_state(lbm_domain* d, float* f_out, long long* step_out) {
 
 int lbm_set_state(lbm_domain* d, const float* f_in, long long step) {
     if (!d || !f_in || step < 0) { set_error("domain or f_in is NULL, or step < 0"); return LBM_ERR_ARG; }
+    if (d->params.precision != 0) { set_error("checkpoints are available for FP32 domains only"); return LBM_ERR_STATE; }
     const long long N = d->N;
     for (int p = 0; p < 2 * Q; ++p)
         LBM_CUDA(cudaMemcpyAsync(d->f[d->cur] + (size_t)p * d->geom.plane, f_in + (size_t)p * N, sizeof(float) * N,
@@ -497,7 +541,7 @@ int lbm_set_state(lbm_domain* d, const float* f_in, long long step) {
 
 int lbm_set_tile(lbm_domain* d, int by, int lz, int lead) {
     if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
-    if (lz < 1 || !tile_supported(by, lead)) {
+    if (lz < 1 || !(d->params.precision == 0 ? tile_supported(by, lead) : tile16_supported(by, lead))) {
         set_error("unsupported tile: by in {6,8,10,12}, lz >= 1, lead in {2,3,4} (lead 3: by <= 10, lead 4: by <= 8)");
         return LBM_ERR_ARG;
     }

@@ -152,28 +152,7 @@ __global__ void __launch_bounds__(MEAS_THREADS) measure_kernel(const float* __re
         float rwf, rnf;
         int cell;
         const uint32_t w = pull_cell<false>(f, nbr, nbr_nw, g, col, z, dummy, rwf, rnf, cell);
-        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
-        if (cls == CLS_SOLID) continue;
-        const double rw = rwf, rn = rnf;
-        // mass and sanity per component where it is fluid
-        acc[MS_MASS_W] += rw;
-        if (!isfinite(rw)) acc[MS_N_NONFINITE] += 1.0;
-        else if (rw < 0.0) acc[MS_N_NEGATIVE] += 1.0;
-        if (cls != CLS_MEMBRANE) {
-            acc[MS_MASS_NW] += rn;
-            if (!isfinite(rn)) acc[MS_N_NONFINITE] += 1.0;
-            else if (rn < 0.0) acc[MS_N_NEGATIVE] += 1.0;
-        }
-        const double p = (rw + rn) / 3.0 + G * rw * rn / 3.0;  // Eq. 5
-        if (cls == CLS_INLET) { acc[MS_PIN] += p; acc[MS_N_IN] += 1.0; continue; }
-        if (cls == CLS_OUTLET) { acc[MS_POUT] += p; acc[MS_N_OUT] += 1.0; continue; }
-        if (cls == CLS_MEMBRANE) continue;
-        acc[MS_N_FLUID] += 1.0;
-        if (rw > rn) acc[MS_N_W] += 1.0;
-        const double phi = (rw - rn) / (rw + rn);
-        if (fabs(phi) < 0.5) acc[MS_N_INTERFACE] += 1.0;
-        if (phi > 0.9) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
-        if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
+        measure_accumulate(acc, (w >> CLS_SHIFT) & CLS_MASK, (double)rwf, (double)rnf, G);
     }
     __shared__ double red[MEAS_THREADS / 32][NMEAS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -226,6 +205,11 @@ cudaError_t launch_density(const float* f, float* rho, const uint32_t* nbr, cons
                            cudaStream_t s) {
     const long long N = (long long)g.nxy * g.nz;
     density_kernel<<<grid_for(N, 256), 256, 0, s>>>(f, rho, nbr, nbr_nw, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* partials, int nblocks, double* result, cudaStream_t s) {
+    finalize_kernel<<<1, 32, 0, s>>>(partials, nblocks, result);
     return cudaGetLastError();
 }
 

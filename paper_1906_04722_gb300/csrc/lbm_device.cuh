@@ -126,4 +126,30 @@ __device__ __forceinline__ uint32_t pull_cell(const float* __restrict__ fin, con
     return w;
 }
 
+// Adds one cell's contribution to the measurement sums (definitions in lbm.h):
+// mass and sanity per component where it is fluid, Eq. 5 pressure, reservoir
+// means, interior counts and bulk-phase pressures.
+__device__ __forceinline__ void measure_accumulate(double (&acc)[NMEAS], uint32_t cls, double rw, double rn,
+                                                   double G) {
+    if (cls == CLS_SOLID || cls == CLS_OUTSIDE) return;
+    acc[MS_MASS_W] += rw;
+    if (!isfinite(rw)) acc[MS_N_NONFINITE] += 1.0;
+    else if (rw < 0.0) acc[MS_N_NEGATIVE] += 1.0;
+    if (cls != CLS_MEMBRANE) {
+        acc[MS_MASS_NW] += rn;
+        if (!isfinite(rn)) acc[MS_N_NONFINITE] += 1.0;
+        else if (rn < 0.0) acc[MS_N_NEGATIVE] += 1.0;
+    }
+    const double p = (rw + rn) / 3.0 + G * rw * rn / 3.0;  // Eq. 5
+    if (cls == CLS_INLET) { acc[MS_PIN] += p; acc[MS_N_IN] += 1.0; return; }
+    if (cls == CLS_OUTLET) { acc[MS_POUT] += p; acc[MS_N_OUT] += 1.0; return; }
+    if (cls == CLS_MEMBRANE) return;
+    acc[MS_N_FLUID] += 1.0;
+    if (rw > rn) acc[MS_N_W] += 1.0;
+    const double phi = (rw - rn) / (rw + rn);
+    if (fabs(phi) < 0.5) acc[MS_N_INTERFACE] += 1.0;
+    if (phi > 0.9) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
+    if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
+}
+
 }  // namespace lbmk

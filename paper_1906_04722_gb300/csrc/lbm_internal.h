@@ -103,6 +103,21 @@ cudaError_t prepare_step(const StepTile& tile);
 cudaError_t launch_set_bc(float* bc, float in_w, float in_nw, float out_w, float out_nw, cudaStream_t s);
 cudaError_t launch_probe(const float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, int x, int y,
                          int z, float* out, cudaStream_t s);
+cudaError_t launch_finalize(const double* partials, int nblocks, double* result, cudaStream_t s);
+// 16-bit storage (precision 1 = FP16, 2 = BF16 deviations; lbm_step16.cu)
+bool tile16_supported(int by, int lead);
+cudaError_t prepare_step16(int precision, const StepTile& t);
+cudaError_t launch_step16(int precision, const uint32_t* win, uint32_t* wout, const float2* Rin, float2* Rout,
+                          const uint32_t* nbr, const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g,
+                          const Phys& p, StepTile t, cudaStream_t s);
+cudaError_t launch_init16(const float* rho0, float2* R, const Geom& g, cudaStream_t s);
+cudaError_t launch_density16(int precision, const uint32_t* w, const float2* R, const uint32_t* nbr,
+                             const uint32_t* nbr_nw, const Geom& g, float* rho, cudaStream_t s);
+cudaError_t launch_measure16(int precision, const uint32_t* w, const float2* R, const uint32_t* nbr,
+                             const uint32_t* nbr_nw, const Geom& g, double G, double* partials, int nblocks,
+                             double* result, cudaStream_t s);
+cudaError_t launch_probe16(int precision, const uint32_t* w, const float2* R, const uint32_t* nbr,
+                           const uint32_t* nbr_nw, const Geom& g, int x, int y, int z, float* out, cudaStream_t s);
 StepTile default_tile(const Geom& g);
 bool tile_supported(int by, int lead);
 
@@ -126,7 +141,8 @@ struct lbm_domain {
     lbmk::StepTile tile;
     long long N;
     long long n_fluid;
-    float* f[2];
+    float* f[2];       // populations (FP32) or 16-bit deviation pairs (uint32 words)
+    float2* R[2];      // 16-bit storage: densities of the previous time level
     int cur;
     long long step;
     uint8_t* d_mask;

@@ -112,21 +112,19 @@ __device__ __forceinline__ void plane_density(uint32_t w, const float* st, int t
     }
 }
 
-// Collide one interior fluid cell of plane z (pulled populations f) and store
-// its post-collision values.  ring holds (rho_w, rho_nw) of planes z-1..z+1 for
-// the CTA's 32 x BY cells: ring[slot * 32*BY + row*32 + lane].  Directions come
-// in opposite pairs (k, k+1) with e_{k+1} = -e_k, which halves the arithmetic of
-// the moments, the force sums and the equilibria (the symmetric and the
-// antisymmetric part of f^eq are shared by a pair).
-template <int BY>
-__device__ __forceinline__ void collide_cell(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
-                                             int cell, int z, int row, int lane, const Phys& P, const Geom& g,
-                                             float* __restrict__ fout) {
+// Collide one interior fluid cell of plane z (pulled populations f) and hand
+// each post-collision value to sink(s, k, v) (component s, direction k).  ring
+// holds (rho_w, rho_nw) of planes z-1..z+1 for the CTA's 32 x BY cells:
+// ring[slot * 32*BY + row*32 + lane].  Directions come in opposite pairs
+// (k, k+1) with e_{k+1} = -e_k, which halves the arithmetic of the moments, the
+// force sums and the equilibria (the symmetric and the antisymmetric part of
+// f^eq are shared by a pair).  The rest population is rho_s - sum_{k>=1} f*_k.
+template <int BY, class Sink>
+__device__ __forceinline__ void collide_generic(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
+                                                int z, int row, int lane, const Phys& P, Sink&& sink) {
     constexpr int NT = 32 * BY;
     const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
     const bool has_nw = cls != CLS_MEMBRANE;
-    float* __restrict__ out0 = fout + cell;
-    float* __restrict__ out1 = fout + (size_t)Q * g.plane + cell;
 
     if (cls == CLS_INLET || cls == CLS_OUTLET) {
         const float r0 = __ldg(P.bc + (cls == CLS_INLET ? 0 : 2));
@@ -137,11 +135,11 @@ __device__ __forceinline__ void collide_cell(const float (&f)[2][Q], const float
             const float va = WK(k) * r0, vb = WK(k) * r1;
             s0 += va;
             s1 += vb;
-            out0[(size_t)k * g.plane] = va;
-            out1[(size_t)k * g.plane] = vb;
+            sink(0, k, va);
+            sink(1, k, vb);
         }
-        out0[0] = r0 - s0;
-        out1[0] = r1 - s1;
+        sink(0, 0, r0 - s0);
+        sink(1, 0, r1 - s1);
         return;
     }
 
@@ -209,7 +207,6 @@ __device__ __forceinline__ void collide_cell(const float (&f)[2][Q], const float
         const float base = rs * (1.0f - 1.5f * uu);
         const float r45 = 4.5f * rs;
         const float r3 = 3.0f * rs;
-        float* __restrict__ out = s == 0 ? out0 : out1;
         float part[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 1; k < Q; k += 2) {
@@ -220,11 +217,23 @@ __device__ __forceinline__ void collide_cell(const float (&f)[2][Q], const float
             const float v0 = keep * f[s][k] + om * (sym + asym);
             const float v1 = keep * f[s][k + 1] + om * (sym - asym);
             part[(k >> 1) % 3] += v0 + v1;
-            out[(size_t)k * g.plane] = v0;
-            out[(size_t)(k + 1) * g.plane] = v1;
+            sink(s, k, v0);
+            sink(s, k + 1, v1);
         }
-        out[0] = rs - ((part[0] + part[1]) + part[2]);  // rest population: the collision keeps rho_s
+        sink(s, 0, rs - ((part[0] + part[1]) + part[2]));  // rest population: the collision keeps rho_s
     }
+}
+
+// FP32 storage: the post-collision values go straight to fout[(s*19 + k) * plane + cell].
+template <int BY>
+__device__ __forceinline__ void collide_cell(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
+                                             int cell, int z, int row, int lane, const Phys& P, const Geom& g,
+                                             float* __restrict__ fout) {
+    float* __restrict__ out0 = fout + cell;
+    float* __restrict__ out1 = fout + (size_t)Q * g.plane + cell;
+    collide_generic<BY>(f, ring, w, a, z, row, lane, P, [&](int s, int k, float v) {
+        (s == 0 ? out0 : out1)[(size_t)k * g.plane] = v;
+    });
 }
 
 // Pipeline: plane p is queued LEAD iterations before it is collided; plane z+1

@@ -1,0 +1,94 @@
+"""16-bit population storage (FP16 / BF16 deviations, FP32 collision) against
+the FP64 oracle on the single-throat workload.
+
+No precision bound is set for 16-bit storage; the errors are printed and held to
+sanity bars: density within 1 % (FP16) / 5 % (BF16) of the oracle after 500
+steps (300 at tau = 0.8), S_w within 2 %, and per-component mass conserved to 1e-4 with closed walls
+(the rounding of each cell's 18 moving deviations is fed into its rest value).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04722_gb300 as m
+    m.load()
+    return m
+
+
+def _rel(rho_g, rho_o, mask, orc):
+    fl = (mask & orc.M_SOLID) == 0
+    return max(float((np.abs(rho_g[s][fl] - rho_o[s][fl]) / np.maximum(np.abs(rho_o[s][fl]), W.RHO_MINOR)).max())
+               for s in range(2))
+
+
+@pytest.mark.parametrize("precision,bound", [(1, 1e-2), (2, 5e-2)])
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_16bit_throat32_vs_oracle(lbm, orc, precision, bound, tau):
+    shape = (32, 32, 32)
+    spheres = W.throat32_spheres()
+    params = lbm.make_params(tau=(tau, tau), G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR, reservoirs=True, prism_clip=True, precision=precision)
+    rho0 = W.initial_densities(shape, noise=1e-3, seed=1)
+    dom = lbm.Domain(params, spheres, (32, 32, 32))
+    dom.set_densities(rho0)
+    dom32 = lbm.Domain(lbm.make_params(tau=(tau, tau), G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                                       rho_minor=W.RHO_MINOR, reservoirs=True, prism_clip=True), spheres, (32, 32, 32))
+    dom32.set_densities(rho0)
+    mask = orc.voxelise(shape, spheres, prism=True, reservoirs=True)
+    f = orc.init(orc.Config(shape=shape, tau=(tau, tau)), mask, rho0)
+    # at tau = 0.8 this throat ladder diverges after about 400 steps in the FP64
+    # oracle as well (the Shan-Chen model at G = 0.9 is less stable below tau = 1),
+    # so that case is compared after 300 steps
+    n_incr = 20 if tau == 1.0 else 12
+    for rin in W.throat32_ladder(n_incr):
+        cfg = orc.Config(shape=shape, tau=(tau, tau), G=W.G_COHESION, G_ads=W.G_ADS, rho_in=(W.RHO_MINOR, rin))
+        for d in (dom, dom32):
+            d.set_pressure_bc(rin, W.RHO_MAJOR)
+            d.step(25)
+        orc.step(cfg, mask, f, 25)
+    ro = orc.density(cfg, mask, f)
+    e16 = _rel(dom.density(), ro, mask, orc)
+    e32 = _rel(dom32.density(), ro, mask, orc)
+    # at tau = 0.8 the minor component goes slightly negative in interface cells
+    # (the FP64 oracle shows the same), which lbm_measure reports as a status
+    mg, mo = dom.measure(allow_nonfinite=True), orc.measure(cfg, mask, f)
+    assert mg["n_nonfinite"] == 0 and mo["n_nonfinite"] == 0
+    rep = {"precision": {1: "fp16", 2: "bf16"}[precision], "tau": tau, "max_rel_density_err": e16,
+           "fp32_max_rel_density_err": e32, "S_w": mg["S_w"], "S_w_oracle": mo["S_w"],
+           "p_c_res": mg["p_c_res"], "p_c_res_oracle": mo["p_c_res"],
+           "mass_rel_err": [abs(mg["mass"][s] - mo["mass"][s]) / mo["mass"][s] for s in range(2)],
+           "n_negative": mg["n_negative"], "n_negative_oracle": mo["n_negative"]}
+    print(json.dumps(rep))
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, "mixed_precision_errors.jsonl"), "a") as fh:
+        fh.write(json.dumps(rep) + "\n")
+    assert e16 <= bound
+    assert abs(mg["S_w"] - mo["S_w"]) <= 2e-2 * mo["S_w"]
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_16bit_mass_conservation(lbm, precision):
+    shape = (40, 36, 44)
+    spheres = np.array([[10.0, 10.0, 10.0, 6.0], [30.0, 25.0, 28.0, 7.5]])
+    params = lbm.make_params(tau=(0.9, 0.9), G=W.G_COHESION, G_ads=W.G_ADS, precision=precision)
+    nz, ny, nx = shape
+    dom = lbm.Domain(params, spheres, (nx, ny, nz))
+    dom.set_densities(W.droplet_densities(shape, (22, 18, 20), 8.0, seed=6))
+    m0 = dom.measure()["mass"]
+    dom.step(300)
+    m1 = dom.measure()["mass"]
+    for s in range(2):
+        assert abs(m1[s] - m0[s]) <= 1e-4 * m0[s], (s, m0[s], m1[s])
