@@ -205,6 +205,45 @@ int lbm_throat_geometry(const double* spheres3, int dims_out[3], unsigned char* 
 int lbm_run_throat_batch(const double* throats, int n, const lbm_params* params, const lbm_schedule* sched,
                          lbm_throat_result* results, lbm_increment* rows, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Surrogate network.  The paper reads p_c^e off one LBM run per throat; the
+ * surrogate learns that map from LBM-generated throats so that most throats of a
+ * large packing need no LBM run, with the LBM as fallback where the ensemble
+ * members disagree.  (The paper has no network; this is the build's
+ * acceleration of the per-throat step.)  An ensemble of multilayer perceptrons,
+ * n_in -> n_layers x n_hidden (ReLU) -> n_out (linear), trained on the mean
+ * squared error with Adam.  Every layer runs on the tensor cores with BF16
+ * (half = 0) or FP16 (half = 1) operands rounded from FP32 master weights and
+ * FP32 accumulation.  Arrays are row-major host float arrays; the parameters of a
+ * member are flat: W_0 (out x in), b_0, W_1, b_1, ...
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_surrogate lbm_surrogate;
+typedef struct {
+    int n_in, n_hidden, n_layers, n_out;
+    int n_members;            /* ensemble size, 1..64                          */
+    int half;                 /* 0 = BF16 operands, 1 = FP16 operands          */
+    unsigned long long seed;  /* seeded He-normal initialisation per member    */
+} lbm_surrogate_config;
+
+int lbm_surrogate_create(const lbm_surrogate_config* cfg, void* stream, lbm_surrogate** out);
+int lbm_surrogate_num_params(const lbm_surrogate* s);
+int lbm_surrogate_get_params(lbm_surrogate* s, int member, float* params_out);
+int lbm_surrogate_set_params(lbm_surrogate* s, int member, const float* params); /* resets its Adam state */
+/* lbm_surrogate_forward -- outputs of one member for n inputs (n x n_out). */
+int lbm_surrogate_forward(lbm_surrogate* s, int member, const float* X, int n, float* Y);
+/* lbm_surrogate_gradients -- gradient of the mean squared error of one member
+ * over n samples (flat, parameter layout) and the loss; nothing is updated. */
+int lbm_surrogate_gradients(lbm_surrogate* s, int member, const float* X, const float* T, int n, float* grads,
+                            double* loss);
+/* lbm_surrogate_train -- epochs of minibatch Adam (lr, beta 0.9/0.999) for every
+ * member, order shuffled per member and epoch from shuffle_seed; epoch_loss
+ * (n_members x epochs, may be NULL) receives the mean batch loss. */
+int lbm_surrogate_train(lbm_surrogate* s, const float* X, const float* T, int n, int epochs, int batch, float lr,
+                        unsigned long long shuffle_seed, double* epoch_loss);
+/* lbm_surrogate_predict -- ensemble mean and standard deviation per output. */
+int lbm_surrogate_predict(lbm_surrogate* s, const float* X, int n, float* mean, float* spread);
+void lbm_surrogate_destroy(lbm_surrogate* s);
+
 /* lbm_get_density -- densities of the current state, 2 x N doubles
  * (component-major), 0 where a component is not fluid. Synchronising. */
 int lbm_get_density(lbm_domain* d, double* rho_out);

@@ -80,6 +80,12 @@ class lbm_throat_result(ctypes.Structure):
                 "probe": tuple(self.probe), "n_fluid": self.n_fluid}
 
 
+class lbm_surrogate_config(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int), ("n_hidden", ctypes.c_int), ("n_layers", ctypes.c_int),
+                ("n_out", ctypes.c_int), ("n_members", ctypes.c_int), ("half", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong)]
+
+
 # exported symbol -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -110,6 +116,16 @@ SIGNATURES = {
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
                                             ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
                                             ctypes.POINTER(lbm_increment), _VP]),
+    "lbm_surrogate_create": (ctypes.c_int, [ctypes.POINTER(lbm_surrogate_config), _VP, ctypes.POINTER(_VP)]),
+    "lbm_surrogate_num_params": (ctypes.c_int, [_VP]),
+    "lbm_surrogate_get_params": (ctypes.c_int, [_VP, ctypes.c_int, _FP]),
+    "lbm_surrogate_set_params": (ctypes.c_int, [_VP, ctypes.c_int, _FP]),
+    "lbm_surrogate_forward": (ctypes.c_int, [_VP, ctypes.c_int, _FP, ctypes.c_int, _FP]),
+    "lbm_surrogate_gradients": (ctypes.c_int, [_VP, ctypes.c_int, _FP, _FP, ctypes.c_int, _FP, _DP]),
+    "lbm_surrogate_train": (ctypes.c_int, [_VP, _FP, _FP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                           ctypes.c_ulonglong, _DP]),
+    "lbm_surrogate_predict": (ctypes.c_int, [_VP, _FP, ctypes.c_int, _FP, _FP]),
+    "lbm_surrogate_destroy": (None, [_VP]),
     "lbm_destroy": (None, [_VP]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -402,3 +418,89 @@ class Domain:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+class Surrogate:
+    """Ensemble MLP on the GPU (lbm_surrogate_* of the C ABI)."""
+
+    def __init__(self, n_in, n_out, n_hidden=256, n_layers=4, n_members=5, half=False, seed=0, stream=None):
+        cfg = lbm_surrogate_config(n_in, n_hidden, n_layers, n_out, n_members, int(bool(half)), int(seed))
+        self.h = ctypes.c_void_p()
+        _check(load().lbm_surrogate_create(ctypes.byref(cfg), stream if stream is not None else _torch_stream(),
+                                           ctypes.byref(self.h)), "lbm_surrogate_create")
+        self.n_in, self.n_out, self.n_members = n_in, n_out, n_members
+        self.sizes = [n_in] + [n_hidden] * n_layers + [n_out]
+        self.n_params = load().lbm_surrogate_num_params(self.h)
+
+    def get_params(self, member):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(load().lbm_surrogate_get_params(self.h, member, out.ctypes.data_as(_FP)), "lbm_surrogate_get_params")
+        return out
+
+    def set_params(self, member, flat):
+        a = _f32(flat)
+        assert a.size == self.n_params
+        _check(load().lbm_surrogate_set_params(self.h, member, a.ctypes.data_as(_FP)), "lbm_surrogate_set_params")
+
+    def layers(self, flat):
+        """Split a flat parameter vector into [(W, b), ...]."""
+        out, off = [], 0
+        for i in range(len(self.sizes) - 1):
+            nin, nout = self.sizes[i], self.sizes[i + 1]
+            W = flat[off:off + nin * nout].reshape(nout, nin)
+            off += nin * nout
+            b = flat[off:off + nout]
+            off += nout
+            out.append((W, b))
+        return out
+
+    def flatten(self, layers):
+        return np.concatenate([np.concatenate([np.asarray(W).reshape(-1), np.asarray(b).reshape(-1)])
+                               for W, b in layers]).astype(np.float32)
+
+    def forward(self, member, X):
+        X = _f32(X)
+        Y = np.empty((X.shape[0], self.n_out), dtype=np.float32)
+        _check(load().lbm_surrogate_forward(self.h, member, X.ctypes.data_as(_FP), X.shape[0], Y.ctypes.data_as(_FP)),
+               "lbm_surrogate_forward")
+        return Y
+
+    def gradients(self, member, X, T):
+        X, T = _f32(X), _f32(T)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(load().lbm_surrogate_gradients(self.h, member, X.ctypes.data_as(_FP), T.ctypes.data_as(_FP),
+                                              X.shape[0], g.ctypes.data_as(_FP), ctypes.byref(loss)),
+               "lbm_surrogate_gradients")
+        return g, loss.value
+
+    def train(self, X, T, epochs, batch, lr, seed=0):
+        X, T = _f32(X), _f32(T)
+        losses = np.zeros(self.n_members * max(1, epochs))
+        _check(load().lbm_surrogate_train(self.h, X.ctypes.data_as(_FP), T.ctypes.data_as(_FP), X.shape[0],
+                                          int(epochs), int(batch), float(lr), int(seed),
+                                          losses.ctypes.data_as(_DP)), "lbm_surrogate_train")
+        return losses.reshape(self.n_members, max(1, epochs))
+
+    def predict(self, X):
+        X = _f32(X)
+        mean = np.empty((X.shape[0], self.n_out), dtype=np.float32)
+        spread = np.empty_like(mean)
+        _check(load().lbm_surrogate_predict(self.h, X.ctypes.data_as(_FP), X.shape[0], mean.ctypes.data_as(_FP),
+                                            spread.ctypes.data_as(_FP)), "lbm_surrogate_predict")
+        return mean, spread
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

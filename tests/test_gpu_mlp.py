@@ -1,0 +1,90 @@
+"""Surrogate MLP kernels against the FP64 oracle MLP.
+
+Forward outputs, loss gradients and one Adam step of the tensor-core kernels
+(BF16 or FP16 operands rounded from FP32 masters, FP32 accumulation) are compared
+with oracle/mlp.py on the same parameters.  Bars, norm-wise relative: every GEMM
+rounds its operands once (unit roundoff u = 2^-11 for FP16, 2^-8 for BF16); the
+backward dot products over 256 hidden units cancel (terms of both signs), which
+amplifies that rounding by about sqrt(256) = 16 per layer, and the first layer's
+gradient passes through four of them: measured 1.1e-2 (FP16) and 3.1e-2 (BF16)
+there.  Bars 2e-2 (FP16) and 6e-2 (BF16); the outputs of the forward pass are held
+to 2e-3 / 1.5e-2.  Training must drive the loss of a smooth target down.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04722_gb300 as m
+    m.load()
+    return m
+
+
+def _nrel(a, b):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / max(1e-30, np.linalg.norm(b)))
+
+
+@pytest.mark.parametrize("half,tol_fwd,tol", [(1, 2e-3, 2e-2), (0, 1.5e-2, 6e-2)])
+def test_forward_and_gradients_match_oracle(lbm, half, tol_fwd, tol):
+    rng = np.random.default_rng(5)
+    sur = lbm.Surrogate(7, 17, n_hidden=256, n_layers=4, n_members=2, half=half, seed=3)
+    layers = omlp.init_params(sur.sizes, seed=9)
+    for W, b in layers:
+        b[:] = rng.standard_normal(b.shape) * 0.1
+    sur.set_params(1, sur.flatten(layers))
+    ref = [[W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)] for W, b in layers]
+    X = rng.standard_normal((300, 7))
+    T = rng.standard_normal((300, 17))
+    y = sur.forward(1, X)
+    y_ref, _ = omlp.forward(ref, X.astype(np.float32).astype(np.float64))
+    assert _nrel(y, y_ref) <= tol_fwd, _nrel(y, y_ref)
+    g, loss = sur.gradients(1, X, T)
+    g_ref = omlp.gradients(ref, X.astype(np.float32).astype(np.float64), T.astype(np.float32).astype(np.float64))
+    gl = sur.layers(g)
+    errs = [(_nrel(gW, rW), _nrel(gb, rb)) for (gW, gb), (rW, rb) in zip(gl, g_ref)]
+    print("half" if half else "bf16", "forward", _nrel(y, y_ref), "gradients per layer", errs)
+    for i, (eW, eb) in enumerate(errs):
+        assert eW <= tol and eb <= tol, (i, eW, eb)
+    assert abs(loss - omlp.loss(ref, X, T)) <= tol * omlp.loss(ref, X, T)
+
+
+def test_adam_step_matches_oracle(lbm):
+    """One full-batch training step: new parameters equal the oracle's Adam
+    update applied with the GPU's own gradient (so only the update is tested)."""
+    rng = np.random.default_rng(6)
+    sur = lbm.Surrogate(7, 17, n_hidden=64, n_layers=2, n_members=1, half=1, seed=4)
+    p0 = sur.get_params(0)
+    X = rng.standard_normal((128, 7))
+    T = rng.standard_normal((128, 17))
+    g, _ = sur.gradients(0, X, T)
+    sur.train(X, T, epochs=1, batch=128, lr=1e-3, seed=1)
+    p1 = sur.get_params(0)
+    params = [[W.astype(np.float64), b.astype(np.float64)] for W, b in sur.layers(p0.copy())]
+    grads = [[W.astype(np.float64), b.astype(np.float64)] for W, b in sur.layers(g)]
+    omlp.adam_step(params, grads, {}, lr=1e-3)
+    want = sur.flatten(params)
+    assert np.allclose(p1, want, rtol=0, atol=2e-6), np.abs(p1 - want).max()
+
+
+def test_training_reduces_loss_and_ensemble_spread(lbm):
+    rng = np.random.default_rng(7)
+    X = rng.uniform(-1, 1, (4096, 7)).astype(np.float32)
+    T = np.stack([np.sin(X[:, 0] * 2) + X[:, 1] * X[:, 2], np.cos(X[:, 3]) - 0.5 * X[:, 6]], axis=1)
+    sur = lbm.Surrogate(7, 2, n_hidden=128, n_layers=3, n_members=3, half=0, seed=8)
+    losses = sur.train(X, T, epochs=30, batch=256, lr=2e-3, seed=2)
+    assert np.all(losses[:, -1] < 0.05 * losses[:, 0]), losses[:, [0, -1]]
+    Xt = rng.uniform(-1, 1, (512, 7)).astype(np.float32)
+    Tt = np.stack([np.sin(Xt[:, 0] * 2) + Xt[:, 1] * Xt[:, 2], np.cos(Xt[:, 3]) - 0.5 * Xt[:, 6]], axis=1)
+    mean, spread = sur.predict(Xt)
+    assert np.sqrt(np.mean((mean - Tt) ** 2)) < 0.1
+    members = np.stack([sur.forward(m, Xt) for m in range(3)])
+    assert np.allclose(mean, members.mean(axis=0), atol=1e-5)
+    assert np.allclose(spread, members.std(axis=0, ddof=1), atol=1e-5)
