@@ -1,0 +1,90 @@
+"""The trained surrogate against the LBM it replaces.
+
+Training throats come from the batched LBM on seeded packings; held-out throats
+from another packing are predicted by the ensemble with LBM fallback where the
+members disagree on p_c^e by more than a relative spread (2 %, the design value,
+and 5 %).  The LBM result of every held-out throat judges the network.  Shown: the
+p_c^e error of the throats the network answers, the fallback fraction, and the
+throats per second gained over running the LBM for every held-out throat.  The
+LBM's p_c^e is read off a 32-step pressure ladder and depends on how the spheres
+fall on the lattice, so it is not a smooth function of the seven features: the
+bars are a median error below 8 % and more than half the throats answered at 5 %.
+"""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04722_gb300 as m
+    m.load()
+    return m
+
+
+def test_surrogate_gain_over_lbm(lbm):
+    from paper_1906_04722_gb300 import surrogate as S
+
+    g_ads = W.G_ADS
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=g_ads, rho_major=W.RHO_MAJOR, rho_minor=W.RHO_MINOR)
+    theta = S.contact_angle_estimate(g_ads[0], g_ads[1], W.G_COHESION, W.RHO_MAJOR, W.RHO_MINOR)
+    ladder = [2.0 + 0.02 * i for i in range(32)]
+    n_steps = 100
+    # training throats: three seeded packings, 1024 facets each
+    Xs, Ys = [], []
+    t0 = time.perf_counter()
+    for seed in (10, 11, 12):
+        tri = W.delaunay_throats(W.sample_spheres(192, seed=seed), 1024, seed=seed)
+        res, rows = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
+        X, R = S.throat_features(tri, theta)
+        Y, ok = S.ThroatSurrogate.targets(res, rows, R)
+        Xs.append(X[ok])
+        Ys.append(Y[ok])
+    t_gen = time.perf_counter() - t0
+    X = np.concatenate(Xs)
+    Y = np.concatenate(Ys)
+    sur = S.ThroatSurrogate(n_incr=len(ladder), n_members=5, seed=1)
+    t0 = time.perf_counter()
+    losses = sur.fit(X, Y, epochs=300, batch=256, lr=1e-3, seed=2)
+    t_train = time.perf_counter() - t0
+    # held-out throats from another packing, judged by the LBM
+    tri = W.delaunay_throats(W.sample_spheres(192, seed=20), 1024, seed=20)
+    t0 = time.perf_counter()
+    res_ref, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
+    t_lbm_all = time.perf_counter() - t0
+    truth = np.array([r["p_ce"] for r in res_ref])
+    rep = {"train_throats": int(len(X)), "generate_s": t_gen, "train_s": t_train,
+           "loss_first_last": [float(losses[:, 0].mean()), float(losses[:, -1].mean())],
+           "held_out": int(len(tri)), "throats_per_s_lbm_batched": len(tri) / t_lbm_all}
+    ok = np.isfinite(truth)
+    for tol in (0.02, 0.05):
+        sur.spread_tol = tol
+        pce, fell, t_net, t_fb = sur.predict_with_fallback(tri, theta, params, ladder, n_steps, W.RHO_MAJOR)
+        answered = ok & ~fell
+        err = np.abs(pce[ok] - truth[ok]) / truth[ok]
+        err_ans = np.abs(pce[answered] - truth[answered]) / truth[answered]
+        rep[f"tol_{tol}"] = {"fallback_fraction": float(fell.mean()), "answered": int(answered.sum()),
+                             "pce_rel_err_answered_median": float(np.median(err_ans)) if err_ans.size else None,
+                             "pce_rel_err_answered_p90": float(np.percentile(err_ans, 90)) if err_ans.size else None,
+                             "pce_rel_err_all_median": float(np.median(err)),
+                             "throats_per_s_surrogate_with_fallback": len(tri) / (t_net + t_fb)}
+    print(json.dumps(rep))
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, "surrogate_report.json"), "w") as fh:
+        json.dump(rep, fh, indent=1)
+    assert losses[:, -1].mean() < 0.2 * losses[:, 0].mean()
+    r5 = rep["tol_0.05"]
+    assert r5["fallback_fraction"] < 0.5
+    assert r5["pce_rel_err_all_median"] < 0.08
+    assert r5["throats_per_s_surrogate_with_fallback"] > rep["throats_per_s_lbm_batched"]
