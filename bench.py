@@ -15,7 +15,13 @@ Printed JSON line (rank 0):
   e2e        the same metric through the public C ABI from host data: domain
              creation from the host sphere list, then per step
              set_pressure_bc + 100 time steps + a measurement read back;
-  cpu_baseline  the FP64 oracle on a bounded crop of the same sample.
+  cpu_baseline  the FP64 oracle on a bounded crop of the same sample;
+  throats    pore throats per second on 1024 Delaunay throats of the sample
+             packing (boxes 24^3..64^3): the plain per-throat loop (create,
+             ladder of set_pressure_bc + steps + measure, destroy) on a strided
+             subset, the batched persistent launch, and the trained surrogate with
+             batched-LBM fallback where the ensemble spread exceeds 2 % (and 5 %),
+             with the surrogate's p_c^e error against the batched LBM.
 --impl reference times that oracle alone (the method has no other reference
 implementation): rank 0 only.
 """
@@ -50,6 +56,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-throats", action="store_true")
+    ap.add_argument("--throat-steps", type=int, default=100,
+                    help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--size", type=int, default=192,
                     help="box edge of the drainage sample (192 = the benchmark workload; smaller edges "
                          "scale the sphere count with the volume, for profiling captures)")
@@ -207,6 +216,83 @@ def cpu_baseline():
             "sample": oc.sample_text(steps)}
 
 
+def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
+    """Throats per second: plain loop vs batched vs surrogate with fallback.
+
+    The ladder is 32 increments of the nw reservoir density (2.0 + 0.02 i) with
+    n_steps time steps each, for every arm.  The surrogate is trained first on
+    two other seeded packings (its cost is reported, not counted in throats/s:
+    it is paid once for all throats of a network).  Every rank works on its own
+    held-out packing; tmax(t) is the maximum of t over ranks, and the rates
+    are whole-job: world x throats per rank / that maximum."""
+    from paper_1906_04722_gb300 import surrogate as S
+
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR)
+    theta = S.contact_angle_estimate(W.G_ADS[0], W.G_ADS[1], W.G_COHESION, W.RHO_MAJOR, W.RHO_MINOR)
+    ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
+    out = {"workload": "1024 Delaunay throats of a 300-sphere 192^3 RSA packing, boxes 24^3..64^3, "
+                       f"32 increments x {n_steps} steps", "unit": "throats/s"}
+    # training set from two other packings
+    t0 = time.perf_counter()
+    Xs, Ys = [], []
+    for seed in (10 + 2 * rank, 11 + 2 * rank):
+        tri = W.delaunay_throats(W.sample_spheres(192, seed=100 + seed), 1024, seed=100 + seed)
+        res, rows = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
+        X, R = S.throat_features(tri, theta)
+        Y, ok = S.ThroatSurrogate.targets(res, rows, R)
+        Xs.append(X[ok])
+        Ys.append(Y[ok])
+    t_gen = time.perf_counter() - t0
+    sur = S.ThroatSurrogate(n_incr=len(ladder), n_members=5, seed=1)
+    t0 = time.perf_counter()
+    losses = sur.fit(np.concatenate(Xs), np.concatenate(Ys), epochs=300, batch=256, lr=1e-3, seed=2)
+    t_train = time.perf_counter() - t0
+    out["surrogate_training"] = {"throats": int(sum(len(x) for x in Xs)), "lbm_s": t_gen, "train_s": t_train,
+                                 "loss_first_last": [float(losses[:, 0].mean()), float(losses[:, -1].mean())]}
+
+    tri = W.delaunay_throats(W.sample_spheres(192, seed=3 + 1000 * rank), 1024, seed=3 + 1000 * rank)
+    n = len(tri)
+    # batched
+    sync()
+    t0 = time.perf_counter()
+    res_ref, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
+    sync()
+    t_batch = tmax(time.perf_counter() - t0)
+    truth = np.array([r["p_ce"] for r in res_ref])
+    out["batched"] = world * n / t_batch
+    # plain per-throat loop on every 32nd throat
+    sub = tri[::32]
+    sync()
+    t0 = time.perf_counter()
+    for th in sub:
+        mask, probe = lbm.lbm_throat_geometry(th)
+        d = lbm.Domain(params, mask=mask)
+        d.drainage(ladder, n_steps, W.RHO_MAJOR, probe)
+        d.close()
+    sync()
+    t_plain = tmax(time.perf_counter() - t0)
+    out["plain"] = world * len(sub) / t_plain
+    out["plain_sample"] = f"{len(sub)} throats (every 32nd)"
+    out["batched_vs_plain"] = out["batched"] / out["plain"]
+    ok = np.isfinite(truth)
+    for tol in (0.02, 0.05):
+        sur.spread_tol = tol
+        sync()
+        t0 = time.perf_counter()
+        pce, fell, _, _ = sur.predict_with_fallback(tri, theta, params, ladder, n_steps, W.RHO_MAJOR)
+        sync()
+        dt = tmax(time.perf_counter() - t0)
+        ans = ok & ~fell
+        err = np.abs(pce[ans] - truth[ans]) / truth[ans]
+        out[f"surrogate_spread_{int(tol * 100)}pct"] = {
+            "value": world * n / dt, "vs_plain": world * n / dt / out["plain"], "fallback_fraction": float(fell.mean()),
+            "pce_rel_err_answered_median": float(np.median(err)) if err.size else None,
+            "pce_rel_err_answered_p90": float(np.percentile(err, 90)) if err.size else None}
+    sur.net.close()
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle itself as the reference arm, on the host cores, rank 0 only."""
     if rank != 0:
@@ -303,6 +389,19 @@ def run_ours(args, rank, world, local):
         d2h = 16 * 8
 
     clocks = clk.summary()
+
+    def tmax(v):
+        if dist is None:
+            return v
+        tt = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    def sync():
+        torch.cuda.synchronize()
+        barrier()
+
+    throats = None if args.no_throats else throat_bench(lbm, W, args.throat_steps, rank, world, sync, tmax)
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -321,6 +420,8 @@ def run_ours(args, rank, world, local):
            "check": {"S_w": m["S_w"], "p_c_res": m["p_c_res"], "mass": m["mass"]}}
     if clocks:
         out["clocks"] = clocks
+    if throats is not None:
+        out["throats"] = throats
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
