@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-throats", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="time the default kernel instead of the autotuned one")
+    ap.add_argument("--shape", default="", help="fixed step kernel shape instead of tuning: tma:LZ or staged:BY:LZ:LEAD")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--size", type=int, default=192,
@@ -101,23 +103,27 @@ def read_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+STEP_SOURCES = ("lbm_step.cu", "lbm_step_core.cuh", "lbm_step_tma.cu", "lbm_device.cuh", "lbm_internal.h")
+
+
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("lbm_step.cu", "lbm_device.cuh", "lbm_internal.h"):
+    for f in STEP_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1906_04722_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def read_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    valid only while the kernel sources are unchanged."""
+def read_traffic(kernel_name):
+    """DRAM bytes per launch of the given step kernel from the committed ncu
+    summary, valid only while the step kernel sources are unchanged."""
     p = os.path.join(ROOT, "profiles", "sc_step_sample192_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
-        if d.get("kernel_hash") == kernel_hash():
-            return float(d["dram_bytes_per_launch"])
+        k = d.get("kernels", {}).get(kernel_name)
+        if k and k.get("kernel_hash") == kernel_hash():
+            return float(k["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -341,6 +347,27 @@ def run_ours(args, rank, world, local):
     mask = dom.mask()
     n_upd, bytes_per_step = update_bytes(mask)
     dom.set_pressure_bc(2.1, W.RHO_MAJOR)
+    # the library's autotuner picks the step kernel and its launch shape on this
+    # domain (state restored afterwards); untimed
+    if args.shape:
+        f = args.shape.split(":")
+        tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else
+                 {"kind": "staged", "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
+    else:
+        tuned = dom.autotune(trial_steps=20) if not args.no_tune else None
+
+    def apply_tuned(d):
+        if tuned is None:
+            return
+        if tuned["kind"] == "tma":
+            d.set_step_kernel(lbm.KERNEL_TMA, tuned["lz"])
+        else:
+            d.set_tile(tuned["by"], tuned["lz"], tuned["lead"])
+
+    apply_tuned(dom)
+
+    kind, _ = dom.step_kernel()
+    kernel_name = "sc_step_tma_kernel" if kind == lbm.KERNEL_TMA else "sc_step_kernel<%d,%d>" % lbm.lbm_get_tile(dom.h)[::2]
     dom.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -375,6 +402,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d2 = lbm.Domain(params, spheres, box)
+        apply_tuned(d2)
         ladder = [W.RHO_MAJOR + 0.005 * i for i in range(args.e2e_steps)]
         for rin in ladder:
             d2.set_pressure_bc(rin, W.RHO_MAJOR)
@@ -409,10 +437,11 @@ def run_ours(args, rank, world, local):
                                   "reservoirs + 3 membrane layers, FP32 populations, one fused step per launch",
                       "fluid_cells": n_upd, "global_batch": world, "seq_len": 0,
                       "parallelism": "replicas" if world > 1 else "single GPU",
-                      "l2": "inputs larger than L2 (2 x 1.08 GB population buffers)"},
+                      "l2": "inputs larger than L2 (2 x 1.08 GB population buffers)",
+                      "step_kernel": tuned if tuned is not None else "default"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": read_traffic(), "peak_kind": peak_kind,
-                        "kernel": "sc_step_kernel<6,2>", "algorithmic_bytes_per_launch": bytes_per_step},
+                        "frac": achieved / peak, "traffic": read_traffic(kernel_name), "peak_kind": peak_kind,
+                        "kernel": kernel_name, "algorithmic_bytes_per_launch": bytes_per_step},
            "gpu_launches": args.steps,
            "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "step": f"set_pressure_bc + {E2E_SUBSTEPS} time steps + lbm_measure; domain creation "

@@ -298,6 +298,44 @@ int lbm_measure_state_noalloc(const lbm_params* params, const int box[3], const 
 int lbm_set_tile(lbm_domain* d, int by, int lz, int lead);
 int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
 
+/* lbm_set_step_kernel / lbm_get_step_kernel -- which kernel advances an FP32
+ * domain (16-bit storage always uses the staged kernel).
+ *   LBM_KERNEL_STAGED  every thread queues its cell's 2 x 19 pulls as 4-byte
+ *                      asynchronous copies (any box, any periodic axes); its
+ *                      shape is set with lbm_set_tile;
+ *   LBM_KERNEL_TMA     one thread per CTA loads whole population planes of a
+ *                      32 x 8 tile with the tensor memory accelerator (boxes
+ *                      without periodic x or y and with nx a multiple of 4);
+ *                      lz planes per CTA z-segment (lz <= 0: the default).
+ * New FP32 domains use LBM_KERNEL_TMA where it applies.  Both give the same
+ * results up to the rounding of the force sums (not bit for bit).  LBM_ERR_ARG
+ * for an unknown kind, LBM_ERR_STATE when the kernel does not apply to the
+ * domain.  lbm_set_tile switches the domain to LBM_KERNEL_STAGED. */
+#define LBM_KERNEL_STAGED 0
+#define LBM_KERNEL_TMA 1
+int lbm_set_step_kernel(lbm_domain* d, int kind, int lz);
+int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
+
+/* lbm_autotune -- time the step kernels and launch shapes that apply to the
+ * domain on the domain itself and keep the fastest.
+ *   trial_steps  time steps timed per candidate (>= 1), after one untimed step;
+ *   out          optional: the chosen shape and its time per step.
+ * Candidates: for FP32 domains the TMA kernel (where it applies) with z
+ * segments of 8 .. 48 planes and the staged kernel with by in {6, 8, 10}, lead
+ * in {2, 3} and z segments of 8 .. 32 planes; for 16-bit storage by in
+ * {6, 8, 10} with lead 2.  Timing uses CUDA events on the domain's stream.  The
+ * populations, the step counter and (16-bit) the density fields are saved
+ * before and restored after, bit for bit: a tuned domain continues exactly where
+ * it stood.  Needs one extra population buffer of device memory while it runs
+ * (LBM_ERR_OOM otherwise).  Synchronising. */
+typedef struct {
+    int kind;           /* LBM_KERNEL_STAGED or LBM_KERNEL_TMA */
+    int by, lz, lead;   /* the shape (by and lead: staged kernel only) */
+    double ms_per_step; /* its measured time per step */
+    int n_candidates;   /* shapes timed */
+} lbm_tune_result;
+int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out);
+
 /* lbm_destroy -- release the domain (NULL is ignored). */
 void lbm_destroy(lbm_domain* d);
 

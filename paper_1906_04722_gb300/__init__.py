@@ -80,6 +80,15 @@ class lbm_throat_result(ctypes.Structure):
                 "probe": tuple(self.probe), "n_fluid": self.n_fluid}
 
 
+class lbm_tune_result(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("by", ctypes.c_int), ("lz", ctypes.c_int), ("lead", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {"kind": "tma" if self.kind == 1 else "staged", "by": self.by, "lz": self.lz, "lead": self.lead,
+                "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates}
+
+
 class lbm_surrogate_config(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_int), ("n_hidden", ctypes.c_int), ("n_layers", ctypes.c_int),
                 ("n_out", ctypes.c_int), ("n_members", ctypes.c_int), ("half", ctypes.c_int),
@@ -112,6 +121,9 @@ SIGNATURES = {
                                                  ctypes.POINTER(lbm_measurement)]),
     "lbm_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_get_tile": (ctypes.c_int, [_VP, _IP, _IP, _IP]),
+    "lbm_set_step_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "lbm_get_step_kernel": (ctypes.c_int, [_VP, _IP, _IP]),
+    "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_tune_result)]),
     "lbm_throat_geometry": (ctypes.c_int, [_DP, _IP, _U8P, _IP]),
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
                                             ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
@@ -311,6 +323,27 @@ def lbm_get_tile(h):
     return a.value, b.value, c.value
 
 
+KERNEL_STAGED = 0
+KERNEL_TMA = 1
+
+
+def lbm_set_step_kernel(h, kind: int, lz: int = 0):
+    _check(load().lbm_set_step_kernel(h, int(kind), int(lz)), "lbm_set_step_kernel")
+
+
+def lbm_get_step_kernel(h):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().lbm_get_step_kernel(h, ctypes.byref(a), ctypes.byref(b)), "lbm_get_step_kernel")
+    return a.value, b.value
+
+
+def lbm_autotune(h, trial_steps: int = 20):
+    """Times the step kernels / shapes on the domain, keeps the fastest, restores the state."""
+    r = lbm_tune_result()
+    _check(load().lbm_autotune(h, int(trial_steps), ctypes.byref(r)), "lbm_autotune")
+    return r.as_dict()
+
+
 def lbm_throat_geometry(spheres3):
     """(mask uint8[nz, ny, nx], probe (x, y, z)) of the throat box of three spheres."""
     sp = np.ascontiguousarray(np.asarray(spheres3, dtype=np.float64).reshape(3, 4))
@@ -401,6 +434,15 @@ class Domain:
 
     def tile(self):
         return lbm_get_tile(self.h)
+
+    def set_step_kernel(self, kind, lz=0):
+        lbm_set_step_kernel(self.h, kind, lz)
+
+    def step_kernel(self):
+        return lbm_get_step_kernel(self.h)
+
+    def autotune(self, trial_steps=20):
+        return lbm_autotune(self.h, trial_steps)
 
     def close(self):
         if getattr(self, "h", None):

@@ -98,6 +98,9 @@ void drop_graphs(lbm_domain* d) {
 
 // One step from buffer `cur` to buffer cur ^ 1 on stream s.
 cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA)
+        return launch_step_tma(d->tma, cur, d->f[cur], d->f[cur ^ 1], d->d_nbr_nw, d->d_adh, d->geom, d->phys,
+                               d->tile.tma_lz, d->d_err, s);
     if (d->params.precision == 0)
         return launch_step(d->f[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys, d->tile, s);
     return launch_step16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[cur]),
@@ -106,6 +109,7 @@ cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
 }
 
 cudaError_t prepare_one(lbm_domain* d) {
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA) return prepare_step_tma();
     return d->params.precision == 0 ? prepare_step(d->tile) : prepare_step16(d->params.precision, d->tile);
 }
 
@@ -141,6 +145,13 @@ int capture_graph(lbm_domain* d, int parity) {
 
 // n steps: whole chunks replay a captured graph, the remainder is launched one by one.
 int run_steps(lbm_domain* d, int n) {
+    if (n <= 0) return LBM_OK;
+    const bool tma = d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA;
+    if (tma && !d->ghosts_ok) {
+        LBM_CUDA(launch_ghost_fill(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        d->ghosts_ok = true;
+    }
+    if (!tma) d->ghosts_ok = false;
     while (n >= GRAPH_STEPS) {
         if (!d->graph[d->cur]) {
             int rc = capture_graph(d, d->cur);
@@ -174,6 +185,7 @@ void free_domain(lbm_domain* d) {
     cudaFree(d->d_result);
     cudaFree(d->d_bc);
     cudaFree(d->d_probe);
+    cudaFree(d->d_err);
     drop_graphs(d);
     if (d->capture_stream) cudaStreamDestroy(d->capture_stream);
     if (d->h_result) cudaFreeHost(d->h_result);
@@ -187,7 +199,19 @@ int wait_domain(lbm_domain* d) {
     const auto t0 = std::chrono::steady_clock::now();
     while (true) {
         cudaError_t e = cudaEventQuery(d->done);
-        if (e == cudaSuccess) return LBM_OK;
+        if (e == cudaSuccess) {
+            if (d->tma_ok) {
+                // a step kernel whose bounded wait for its loads ran out leaves a flag
+                int flag = 0;
+                LBM_CUDA(cudaMemcpy(&flag, d->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+                if (flag) {
+                    LBM_CUDA(cudaMemset(d->d_err, 0, sizeof(int)));
+                    set_error("a step kernel gave up waiting for its population loads");
+                    return LBM_ERR_TIMEOUT;
+                }
+            }
+            return LBM_OK;
+        }
         if (e != cudaErrorNotReady) {
             set_error(std::string("device work failed: ") + cudaGetErrorString(e));
             return LBM_ERR_CUDA;
@@ -215,6 +239,7 @@ int upload_densities(lbm_domain* d, const double* rho) {
     }
     d->cur = 0;
     d->step = 0;
+    d->ghosts_ok = false;
     return wait_domain(d);
 }
 
@@ -269,6 +294,8 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     LBM_CUDA_D(cudaMallocHost(&d->h_result, sizeof(double) * NMEAS));
     LBM_CUDA_D(cudaMalloc(&d->d_bc, sizeof(float) * 4));
     LBM_CUDA_D(cudaMalloc(&d->d_probe, sizeof(float) * 2));
+    LBM_CUDA_D(cudaMalloc(&d->d_err, sizeof(int)));
+    LBM_CUDA_D(cudaMemsetAsync(d->d_err, 0, sizeof(int), d->stream));
     fill_phys(d);
     if (int rc = set_bc(d, params->rho_major, params->rho_major)) return fail(rc);
     // the untouched planes between N and the plane stride stay zero
@@ -277,6 +304,13 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     LBM_CUDA_D(cudaMemcpyAsync(d->d_mask, mask_host, (size_t)d->N, cudaMemcpyHostToDevice, d->stream));
     LBM_CUDA_D(launch_geometry(d->d_mask, d->d_nbr, d->d_nbr_nw, d->d_adh, g, d->stream));
 #undef LBM_CUDA_D
+    // FP32 boxes the TMA kernel can serve use it by default
+    if (params->precision == 0 && tma_step_applicable(g) &&
+        encode_step_maps(g, d->f[0], d->f[1], d->d_nbr, d->tma) == cudaSuccess) {
+        d->tma_ok = true;
+        d->tile.kind = LBM_KERNEL_TMA;
+        d->tile.tma_lz = tma_default_lz(g);
+    }
     long long nf = 0;
     for (long long c = 0; c < d->N; ++c)
         if (mask_host[c] == 0) ++nf;
@@ -536,6 +570,7 @@ int lbm_set_state(lbm_domain* d, const float* f_in, long long step) {
         LBM_CUDA(cudaMemcpyAsync(d->f[d->cur] + (size_t)p * d->geom.plane, f_in + (size_t)p * N, sizeof(float) * N,
                                  cudaMemcpyHostToDevice, d->stream));
     d->step = step;
+    d->ghosts_ok = false;
     return wait_domain(d);
 }
 
@@ -548,7 +583,30 @@ int lbm_set_tile(lbm_domain* d, int by, int lz, int lead) {
     d->tile.by = by;
     d->tile.lz = lz > d->geom.nz ? d->geom.nz : lz;
     d->tile.lead = lead;
+    d->tile.kind = LBM_KERNEL_STAGED;
     drop_graphs(d);  // captured with the old shape
+    return LBM_OK;
+}
+
+int lbm_set_step_kernel(lbm_domain* d, int kind, int lz) {
+    if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
+    if (kind != LBM_KERNEL_STAGED && kind != LBM_KERNEL_TMA) { set_error("unknown step kernel"); return LBM_ERR_ARG; }
+    if (kind == LBM_KERNEL_TMA) {
+        if (d->params.precision != 0 || !d->tma_ok) {
+            set_error("the TMA step kernel needs an FP32 domain without periodic x or y and with nx % 4 == 0");
+            return LBM_ERR_STATE;
+        }
+        d->tile.tma_lz = lz <= 0 ? tma_default_lz(d->geom) : (lz > d->geom.nz ? d->geom.nz : lz);
+    }
+    d->tile.kind = kind;
+    drop_graphs(d);
+    return LBM_OK;
+}
+
+int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz) {
+    if (!d || !kind || !lz) { set_error("NULL argument"); return LBM_ERR_ARG; }
+    *kind = d->tile.kind;
+    *lz = d->tile.kind == LBM_KERNEL_TMA ? d->tile.tma_lz : d->tile.lz;
     return LBM_OK;
 }
 
@@ -557,6 +615,111 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead) {
     *by = d->tile.by;
     *lz = d->tile.lz;
     *lead = d->tile.lead;
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
+    if (!d || trial_steps < 1) { set_error("domain is NULL or trial_steps < 1"); return LBM_ERR_ARG; }
+    int rc = wait_domain(d);
+    if (rc) return rc;
+    const Geom& g = d->geom;
+    const bool fp32 = d->params.precision == 0;
+    const size_t fbytes = (fp32 ? sizeof(float) * 2 : sizeof(uint32_t)) * (size_t)g.plane * Q;
+    const size_t rbytes = fp32 ? 0 : sizeof(float2) * (size_t)g.plane;
+    const StepTile orig = d->tile;
+    const int cur = d->cur;
+    const long long step = d->step;
+    // candidates
+    std::vector<StepTile> cand;
+    auto add = [&](int kind, int by, int lz, int lead) {
+        StepTile t = orig;
+        t.kind = kind;
+        t.by = by;
+        t.lead = lead;
+        if (kind == LBM_KERNEL_TMA) t.tma_lz = lz > g.nz ? g.nz : lz;
+        else t.lz = lz > g.nz ? g.nz : lz;
+        cand.push_back(t);
+    };
+    if (fp32 && d->tma_ok)
+        for (int lz : {8, 12, 16, 24, 32, 48}) add(LBM_KERNEL_TMA, orig.by, lz, orig.lead);
+    for (int by : {6, 8, 10})
+        for (int lead : {2, 3})
+            for (int lz : {8, 16, 32}) {
+                if (fp32 ? !tile_supported(by, lead) : !tile16_supported(by, lead)) continue;
+                add(LBM_KERNEL_STAGED, by, lz, lead);
+            }
+    void* fsave = nullptr;
+    void* rsave = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(fsave);
+        cudaFree(rsave);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    auto restore = [&]() -> int {
+        LBM_CUDA(cudaMemcpyAsync(d->f[cur], fsave, fbytes, cudaMemcpyDeviceToDevice, d->stream));
+        if (rbytes) LBM_CUDA(cudaMemcpyAsync(d->R[cur], rsave, rbytes, cudaMemcpyDeviceToDevice, d->stream));
+        d->cur = cur;
+        d->step = step;
+        d->ghosts_ok = false;
+        return LBM_OK;
+    };
+    auto fail = [&](int code) {
+        d->tile = orig;
+        drop_graphs(d);
+        if (fsave) restore();
+        wait_domain(d);
+        cleanup();
+        return code;
+    };
+    cudaError_t e = cudaMalloc(&fsave, fbytes);
+    if (e == cudaSuccess && rbytes) e = cudaMalloc(&rsave, rbytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        set_error(std::string("lbm_autotune: ") + cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA);
+    }
+    e = cudaMemcpyAsync(fsave, d->f[cur], fbytes, cudaMemcpyDeviceToDevice, d->stream);
+    if (e == cudaSuccess && rbytes) e = cudaMemcpyAsync(rsave, d->R[cur], rbytes, cudaMemcpyDeviceToDevice, d->stream);
+    if (e != cudaSuccess) {
+        set_error(std::string("lbm_autotune: ") + cudaGetErrorString(e));
+        return fail(LBM_ERR_CUDA);
+    }
+    double best = 1e300;
+    StepTile best_t = orig;
+    for (const StepTile& t : cand) {
+        d->tile = t;
+        drop_graphs(d);
+        if ((rc = restore())) return fail(rc);
+        if ((rc = run_steps(d, 1))) return fail(rc);  // untimed: kernel set-up, ghost stores
+        if (cudaEventRecord(e0, d->stream) != cudaSuccess) return fail(LBM_ERR_CUDA);
+        if ((rc = run_steps(d, trial_steps))) return fail(rc);
+        if (cudaEventRecord(e1, d->stream) != cudaSuccess) return fail(LBM_ERR_CUDA);
+        if ((rc = wait_domain(d))) return fail(rc);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return fail(LBM_ERR_CUDA);
+        const double per = ms / trial_steps;
+        if (per < best) {
+            best = per;
+            best_t = t;
+        }
+    }
+    d->tile = best_t;
+    drop_graphs(d);
+    if ((rc = restore())) return fail(rc);
+    rc = wait_domain(d);
+    cleanup();
+    if (rc) return rc;
+    if (out) {
+        out->kind = best_t.kind;
+        out->by = best_t.by;
+        out->lz = best_t.kind == LBM_KERNEL_TMA ? best_t.tma_lz : best_t.lz;
+        out->lead = best_t.lead;
+        out->ms_per_step = best;
+        out->n_candidates = (int)cand.size();
+    }
     return LBM_OK;
 }
 

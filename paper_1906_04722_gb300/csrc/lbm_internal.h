@@ -1,6 +1,7 @@
 // lbm_internal.h -- shared declarations of the CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -86,6 +87,15 @@ struct StepTile {
     int by;    // block rows including the two halo rows (6, 8, 10 or 12)
     int lz;    // z-segment length per CTA
     int lead;  // planes queued ahead of the collided plane (2, 3 or 4)
+    int kind;  // LBM_KERNEL_STAGED or LBM_KERNEL_TMA
+    int tma_lz;  // z-segment length of the TMA kernel
+};
+
+// Tensor maps of the TMA step kernel (lbm_step_tma.cu): the two population
+// buffers as 4-D tensors (x, y, z, array) and the geometry words (x, y, z).
+struct TmaMaps {
+    CUtensorMap f[2];
+    CUtensorMap w;
 };
 
 cudaError_t launch_geometry(const uint8_t* mask, uint32_t* nbr, uint32_t* nbr_nw, uint32_t* adh, const Geom& g,
@@ -120,6 +130,15 @@ cudaError_t launch_probe16(int precision, const uint32_t* w, const float2* R, co
                            const uint32_t* nbr_nw, const Geom& g, int x, int y, int z, float* out, cudaStream_t s);
 StepTile default_tile(const Geom& g);
 bool tile_supported(int by, int lead);
+// TMA step kernel (FP32; no periodic x / y, nx % 4 == 0)
+bool tma_step_applicable(const Geom& g);
+int tma_default_lz(const Geom& g);
+cudaError_t encode_step_maps(const Geom& g, float* f0, float* f1, const uint32_t* nbr, TmaMaps& m);
+cudaError_t prepare_step_tma();
+cudaError_t launch_step_tma(const TmaMaps& m, int cur, const float* fin, float* fout, const uint32_t* nbr_nw,
+                            const uint32_t* adh, const Geom& g, const Phys& p, int lz, int* err, cudaStream_t s);
+// ghost stores (the reflected populations the TMA kernel pulls from wall cells) of a state
+cudaError_t launch_ghost_fill(float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, cudaStream_t s);
 
 // host geometry (lbm_geometry.cpp)
 void voxelise_box(int nx, int ny, int nz, const double* spheres, int n_spheres, int prism_clip, int reservoirs,
@@ -162,6 +181,10 @@ struct lbm_domain {
     // captured chunks of GRAPH_STEPS steps, one per starting buffer
     cudaGraphExec_t graph[2];
     cudaStream_t capture_stream;
+    lbmk::TmaMaps tma;  // valid when tma_ok
+    bool tma_ok;
+    bool ghosts_ok;     // the current FP32 state holds the TMA kernel's ghost stores
+    int* d_err;         // set by a step kernel whose bounded wait ran out
 };
 
 constexpr int GRAPH_STEPS = 64;  // steps per captured graph (even: the buffer parity is unchanged)

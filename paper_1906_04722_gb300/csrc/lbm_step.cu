@@ -170,6 +170,8 @@ StepTile default_tile(const Geom& g) {
     if (lz < 16) lz = 16;
     if (lz > g.nz) lz = g.nz;
     t.lz = lz;
+    t.kind = LBM_KERNEL_STAGED;
+    t.tma_lz = 0;
     return t;
 }
 

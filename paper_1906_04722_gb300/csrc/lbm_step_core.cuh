@@ -119,10 +119,12 @@ __device__ __forceinline__ void plane_density(uint32_t w, const float* st, int t
 // (k, k+1) with e_{k+1} = -e_k, which halves the arithmetic of the moments, the
 // force sums and the equilibria (the symmetric and the antisymmetric part of
 // f^eq are shared by a pair).  The rest population is rho_s - sum_{k>=1} f*_k.
-template <int BY, class Sink>
-__device__ __forceinline__ void collide_generic(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
-                                                int z, int row, int lane, const Phys& P, Sink&& sink) {
-    constexpr int NT = 32 * BY;
+//
+// collide_ring is the general form: the density planes are RPLANE float2 apart
+// and their rows RROW apart, and (row, lane) are the cell's coordinates in them.
+template <int RROW, int RPLANE, class Sink>
+__device__ __forceinline__ void collide_ring(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
+                                             int z, int row, int lane, const Phys& P, Sink&& sink) {
     const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
     const bool has_nw = cls != CLS_MEMBRANE;
 
@@ -144,7 +146,7 @@ __device__ __forceinline__ void collide_generic(const float (&f)[2][Q], const fl
     }
 
     auto rho_at = [&](int k) {
-        return ring[((z + EZ(k)) & 3) * NT + (row + EY(k)) * 32 + (lane + EX(k))];
+        return ring[((z + EZ(k)) & 3) * RPLANE + (row + EY(k)) * RROW + (lane + EX(k))];
     };
     const float2 r00 = rho_at(0);
     const float rw = r00.x;
@@ -222,6 +224,13 @@ __device__ __forceinline__ void collide_generic(const float (&f)[2][Q], const fl
         }
         sink(s, 0, rs - ((part[0] + part[1]) + part[2]));  // rest population: the collision keeps rho_s
     }
+}
+
+// The ring of the staged kernels: planes of 32 x BY cells, one per thread.
+template <int BY, class Sink>
+__device__ __forceinline__ void collide_generic(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
+                                                int z, int row, int lane, const Phys& P, Sink&& sink) {
+    collide_ring<32, 32 * BY>(f, ring, w, a, z, row, lane, P, static_cast<Sink&&>(sink));
 }
 
 // FP32 storage: the post-collision values go straight to fout[(s*19 + k) * plane + cell].

@@ -1,0 +1,144 @@
+"""The two FP32 step kernels (staged cp.async and TMA plane loads) against the
+FP64 oracle and against each other.
+
+Boxes are chosen so that the TMA kernel's 32 x 8 tiles have ragged tails in x
+and y and its z segments ragged ends; grains carry adhesion, the closed-z case
+has reservoirs and a membrane, the periodic-z case wraps the plane loads.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL_RHO = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_04722_gb300 as m
+    m.load()
+    return m
+
+
+def _params(lbm, **kw):
+    base = dict(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR, rho_minor=W.RHO_MINOR)
+    base.update(kw)
+    return lbm.make_params(**base)
+
+
+def _rel_err(rho_gpu, rho_orc, mask, orc):
+    err = 0.0
+    for s in range(2):
+        fl = (mask & orc.M_SOLID) == 0
+        if s == 1:
+            fl &= (mask & orc.M_MEMBRANE) == 0
+        d = np.abs(rho_gpu[s][fl] - rho_orc[s][fl]) / np.abs(rho_orc[s][fl])
+        err = max(err, float(d.max()))
+    return err
+
+
+SHAPE = (45, 29, 68)  # (nz, ny, nx): x tiles 32 + 32 + 4, y tiles 8 x 3 + 5
+SPHERES = np.array([[10.0, 8.0, 6.0, 5.3], [40.2, 20.5, 15.0, 6.1], [60.0, 3.0, 30.0, 4.0],
+                    [33.0, 14.0, 40.0, 5.5]])
+
+
+def _case(lbm, orc, periodic_z):
+    nz, ny, nx = SHAPE
+    if periodic_z:
+        flags, oflags = dict(periodic=(0, 0, 1)), dict()
+        rho0 = W.droplet_densities(SHAPE, (20, 14, 40), 7.0, seed=21)
+        ckw = dict(periodic=(0, 0, 1))
+    else:
+        flags, oflags = dict(reservoirs=True, membrane_layers=2), dict(reservoirs=True, membrane_layers=2)
+        rho0 = W.initial_densities(SHAPE, noise=1e-3, seed=22)
+        ckw = dict(rho_in=(W.RHO_MINOR, 2.08), rho_out=(W.RHO_MAJOR, W.RHO_MINOR))
+    mask = orc.voxelise(SHAPE, SPHERES, **oflags)
+    cfg = orc.Config(shape=SHAPE, tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, **ckw)
+    return flags, mask, cfg, rho0
+
+
+def _gpu_run(lbm, flags, rho0, steps, kernel, lz=0):
+    nz, ny, nx = SHAPE
+    dom = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
+    if kernel == lbm.KERNEL_TMA:
+        dom.set_step_kernel(kernel, lz)
+    else:
+        dom.set_tile(6, 16, 2)
+    assert dom.step_kernel()[0] == kernel
+    dom.set_densities(rho0)
+    if not flags.get("periodic"):
+        dom.set_pressure_bc(2.08, W.RHO_MAJOR)
+    dom.step(steps)
+    return dom
+
+
+@pytest.mark.parametrize("periodic_z", [0, 1])
+def test_tma_kernel_matches_oracle(lbm, orc, periodic_z):
+    flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
+    dom = _gpu_run(lbm, flags, rho0, 70, lbm.KERNEL_TMA, lz=13)
+    assert np.array_equal(dom.mask(), mask)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 70)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+def test_tma_default_kernel_choice(lbm):
+    nz, ny, nx = SHAPE
+    d1 = lbm.Domain(_params(lbm), SPHERES, (nx, ny, nz))
+    assert d1.step_kernel()[0] == lbm.KERNEL_TMA
+    d2 = lbm.Domain(_params(lbm, periodic=(1, 0, 0)), SPHERES, (nx, ny, nz))
+    assert d2.step_kernel()[0] == lbm.KERNEL_STAGED
+    with pytest.raises(lbm.LbmError):
+        d2.set_step_kernel(lbm.KERNEL_TMA)
+    d3 = lbm.Domain(_params(lbm), SPHERES, (nx - 1, ny, nz))  # nx % 4 != 0
+    assert d3.step_kernel()[0] == lbm.KERNEL_STAGED
+
+
+def test_tma_segments_bitwise(lbm, orc):
+    """The z-segment length changes which CTA computes a plane, not how."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, 0)
+    ref = _gpu_run(lbm, flags, rho0, 40, lbm.KERNEL_TMA, lz=45).state()[0]
+    for lz in (4, 7, 11):
+        got = _gpu_run(lbm, flags, rho0, 40, lbm.KERNEL_TMA, lz=lz).state()[0]
+        assert np.array_equal(got, ref), lz
+
+
+@pytest.mark.parametrize("periodic_z", [0, 1])
+def test_staged_and_tma_agree(lbm, orc, periodic_z):
+    """Same FP32 model, different rounding (the TMA kernel folds omega w_k into
+    its equilibrium constants): after 100 steps the densities differ by at most
+    about one FP32 ulp (6e-8 relative) per step, 6e-6; the bar is 5e-6, each
+    kernel being held to the FP64 oracle at 1e-5 separately."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
+    a = _gpu_run(lbm, flags, rho0, 100, lbm.KERNEL_TMA).density()
+    b = _gpu_run(lbm, flags, rho0, 100, lbm.KERNEL_STAGED).density()
+    assert _rel_err(a, b, mask, orc) <= 5e-6
+
+
+def test_autotune_restores_state_and_keeps_parity(lbm, orc):
+    """Tuning runs trial steps on the domain itself; afterwards the state and the
+    step counter are the ones before, bit for bit, and the tuned kernel still
+    matches the oracle."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, 0)
+    nz, ny, nx = SHAPE
+    dom = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
+    dom.set_densities(rho0)
+    dom.set_pressure_bc(2.08, W.RHO_MAJOR)
+    dom.step(5)
+    before, st = dom.state()
+    res = dom.autotune(trial_steps=4)
+    after, st2 = dom.state()
+    assert st2 == st == 5
+    assert np.array_equal(before, after)
+    assert res["n_candidates"] >= 10 and res["ms_per_step"] > 0
+    kind, lz = dom.step_kernel()
+    assert kind == (lbm.KERNEL_TMA if res["kind"] == "tma" else lbm.KERNEL_STAGED) and lz == res["lz"]
+    dom.step(65)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 70)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
