@@ -307,8 +307,9 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  *                      32 x 8 tile with the tensor memory accelerator (boxes
  *                      without periodic x or y and with nx a multiple of 4);
  *                      lz planes per CTA z-segment (lz <= 0: the default).
- * New FP32 domains use LBM_KERNEL_TMA where it applies.  Both give the same
- * results up to the rounding of the force sums (not bit for bit).  LBM_ERR_ARG
+ * New domains use LBM_KERNEL_STAGED (the faster one on small boxes; lbm_autotune
+ * times both on the domain).  Both give the same results up to rounding (not
+ * bit for bit: the TMA kernel folds omega w_k into its equilibrium constants).  LBM_ERR_ARG
  * for an unknown kind, LBM_ERR_STATE when the kernel does not apply to the
  * domain.  lbm_set_tile switches the domain to LBM_KERNEL_STAGED. */
 #define LBM_KERNEL_STAGED 0

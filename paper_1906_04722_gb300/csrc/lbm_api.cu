@@ -304,11 +304,11 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     LBM_CUDA_D(cudaMemcpyAsync(d->d_mask, mask_host, (size_t)d->N, cudaMemcpyHostToDevice, d->stream));
     LBM_CUDA_D(launch_geometry(d->d_mask, d->d_nbr, d->d_nbr_nw, d->d_adh, g, d->stream));
 #undef LBM_CUDA_D
-    // FP32 boxes the TMA kernel can serve use it by default
+    // FP32 boxes the TMA kernel can serve get its tensor maps; the staged kernel
+    // stays the default (lbm_set_step_kernel and lbm_autotune select the other)
     if (params->precision == 0 && tma_step_applicable(g) &&
         encode_step_maps(g, d->f[0], d->f[1], d->d_nbr, d->tma) == cudaSuccess) {
         d->tma_ok = true;
-        d->tile.kind = LBM_KERNEL_TMA;
         d->tile.tma_lz = tma_default_lz(g);
     }
     long long nf = 0;

@@ -6,7 +6,9 @@
 // geometry words, found through a record table) and a persistent grid of CTAs
 // pulls throats off a work counter, largest first.  A CTA owns its throat for a
 // whole increment: it runs the increment's time steps on the throat box tile by
-// tile (step_column, the same fused step as the single-domain kernel), with a
+// tile (step_column, the same fused step as the single-domain kernel), over the
+// tiles whose columns hold a non-solid cell (the box is the bounding box of a
+// triangular prism: the columns outside the triangle are solid), with a
 // CTA barrier between steps as the only synchronisation, then measures the throat
 // (FP64 CTA reduction) and reads the probe cell.  One launch per increment; the
 // launches of all increments are captured in one CUDA graph.
@@ -28,6 +30,8 @@ struct ThroatRec {
     long long f_off;  // offset of the throat's populations in each population arena (floats)
     long long c_off;  // offset of its cells in the per-cell arenas
     int probe;        // probe cell index in the box, -1 if none
+    int tile_begin;   // this throat's active tiles in the tile list
+    int tile_count;
 };
 
 constexpr int BATCH_BY = 6;
@@ -112,7 +116,8 @@ __device__ void measure_throat(const float* __restrict__ f, const uint32_t* __re
 template <int BY, int LEAD>
 __global__ void __launch_bounds__(32 * BY, 2)
     throat_batch_kernel(const ThroatRec* __restrict__ recs, const int* __restrict__ order, int n,
-                        int* __restrict__ counter, float* arena0, float* arena1, const uint32_t* __restrict__ nbr,
+                        int* __restrict__ counter, const int* __restrict__ tiles, float* arena0, float* arena1,
+                        const uint32_t* __restrict__ nbr,
                         const uint32_t* __restrict__ nbr_nw, const uint32_t* __restrict__ adh, Phys P, int n_steps,
                         int parity, double G, double rho_in_nw, lbm_increment* __restrict__ rows, int incr,
                         int n_incr) {
@@ -130,18 +135,22 @@ __global__ void __launch_bounds__(32 * BY, 2)
         const Geom g = recs[id].g;
         const long long f_off = recs[id].f_off, c_off = recs[id].c_off;
         const int probe = recs[id].probe;
+        const int tb = recs[id].tile_begin, tc = recs[id].tile_count;
         float* buf[2] = {arena0 + f_off, arena1 + f_off};
         const uint32_t* tn = nbr + c_off;
         const uint32_t* tnn = nbr_nw + c_off;
         const uint32_t* ta = adh + c_off;
-        const int tiles_x = (g.nx + 29) / 30, tiles_y = (g.ny + BY - 3) / (BY - 2);
         int cur = parity;
         for (int s = 0; s < n_steps; ++s) {
-            for (int ty = 0; ty < tiles_y; ++ty)
-                for (int tx = 0; tx < tiles_x; ++tx) {
-                    step_column<BY, LEAD>(buf[cur], buf[cur ^ 1], tn, tnn, ta, g, P, tx, ty, 0, g.nz, smem);
-                    __syncthreads();
-                }
+            // only tiles whose columns hold a non-solid cell: a throat box is
+            // the bounding box of a triangular prism, and the columns outside
+            // the triangle are solid from end to end
+            for (int i = 0; i < tc; ++i) {
+                const int packed = __ldg(tiles + tb + i);
+                step_column<BY, LEAD>(buf[cur], buf[cur ^ 1], tn, tnn, ta, g, P, packed & 0xffff, packed >> 16, 0,
+                                      g.nz, smem);
+                __syncthreads();
+            }
             cur ^= 1;
         }
         measure_throat(buf[cur], tn, tnn, g, G, probe, rho_in_nw, red, rows + (size_t)id * n_incr + incr);
@@ -300,24 +309,46 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             for (uint8_t m : masks[t]) nf += m == 0;
             r.n_fluid = nf;
         }
-        // largest boxes first
+        // active tiles of each throat: the (30 x 4)-column tiles of the step
+        // kernel that hold a non-solid cell at some height
+        std::vector<int> tiles;
+        for (int t = 0; t < n; ++t) {
+            const Geom& g = recs[t].g;
+            std::vector<uint8_t> col((size_t)g.nxy, 0);
+            for (int z = 0; z < g.nz; ++z)
+                for (int c = 0; c < g.nxy; ++c)
+                    if (!(masks[t][(size_t)z * g.nxy + c] & LBM_MASK_SOLID)) col[(size_t)c] = 1;
+            const int TYB = BATCH_BY - 2;
+            recs[t].tile_begin = (int)tiles.size();
+            for (int ty = 0; ty * TYB < g.ny; ++ty)
+                for (int tx = 0; tx * 30 < g.nx; ++tx) {
+                    bool any = false;
+                    for (int y = ty * TYB; y < std::min(g.ny, ty * TYB + TYB) && !any; ++y)
+                        for (int x = tx * 30; x < std::min(g.nx, tx * 30 + 30); ++x)
+                            if (col[(size_t)y * g.nx + x]) { any = true; break; }
+                    if (any) tiles.push_back(tx | (ty << 16));
+                }
+            recs[t].tile_count = (int)tiles.size() - recs[t].tile_begin;
+        }
+        // most work first (active tiles x planes)
         std::vector<int> order((size_t)n);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return (long long)recs[a].g.nxy * recs[a].g.nz > (long long)recs[b].g.nxy * recs[b].g.nz;
+            return (long long)recs[a].tile_count * recs[a].g.nz > (long long)recs[b].tile_count * recs[b].g.nz;
         });
 
         float *a0 = nullptr, *a1 = nullptr, *d_bc = nullptr;
         uint8_t* d_mask = nullptr;
         uint32_t *d_nbr = nullptr, *d_nbr_nw = nullptr, *d_adh = nullptr;
         ThroatRec* d_recs = nullptr;
-        int *d_order = nullptr, *d_counter = nullptr;
+        int *d_order = nullptr, *d_counter = nullptr, *d_tiles = nullptr;
         lbm_increment* d_rows = nullptr;
         cudaGraphExec_t exec = nullptr;
         cudaStream_t cap = nullptr;
         auto cleanup = [&]() {
             cudaFree(a0); cudaFree(a1); cudaFree(d_bc); cudaFree(d_mask); cudaFree(d_nbr); cudaFree(d_nbr_nw);
             cudaFree(d_adh); cudaFree(d_recs); cudaFree(d_order); cudaFree(d_counter); cudaFree(d_rows);
+            cudaFree(d_tiles);
             if (exec) cudaGraphExecDestroy(exec);
             if (cap) cudaStreamDestroy(cap);
         };
@@ -337,6 +368,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         BATCH_CUDA(cudaMalloc(&d_adh, sizeof(uint32_t) * (size_t)c_tot));
         BATCH_CUDA(cudaMalloc(&d_recs, sizeof(ThroatRec) * (size_t)n));
         BATCH_CUDA(cudaMalloc(&d_order, sizeof(int) * (size_t)n));
+        BATCH_CUDA(cudaMalloc(&d_tiles, sizeof(int) * std::max<size_t>(1, tiles.size())));
         BATCH_CUDA(cudaMalloc(&d_counter, sizeof(int) * (size_t)I));
         BATCH_CUDA(cudaMalloc(&d_rows, sizeof(lbm_increment) * (size_t)n * I));
         BATCH_CUDA(cudaMalloc(&d_bc, sizeof(float) * 4 * (size_t)I));
@@ -352,6 +384,9 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             BATCH_CUDA(cudaMemcpyAsync(d_recs, recs.data(), sizeof(ThroatRec) * (size_t)n, cudaMemcpyHostToDevice,
                                        stream));
             BATCH_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, stream));
+            if (!tiles.empty())
+                BATCH_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice,
+                                           stream));
             std::vector<float> bc((size_t)4 * I);
             for (int i = 0; i < I; ++i) {
                 bc[4 * i + 0] = (float)params->rho_minor;
@@ -391,7 +426,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             Phys Pi = P;
             Pi.bc = d_bc + 4 * i;
             const int parity = (int)(((long long)i * sched->n_steps) & 1);
-            kern<<<grid, dim3(32, BATCH_BY), smem, cap>>>(d_recs, d_order, n, d_counter + i, a0, a1, d_nbr, d_nbr_nw,
+            kern<<<grid, dim3(32, BATCH_BY), smem, cap>>>(d_recs, d_order, n, d_counter + i, d_tiles, a0, a1, d_nbr,
+                                                          d_nbr_nw,
                                                           d_adh, Pi, sched->n_steps, parity, params->G,
                                                           sched->rho_in_nw[i], d_rows, i, I);
             cerr = cudaGetLastError();

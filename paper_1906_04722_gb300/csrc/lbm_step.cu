@@ -160,16 +160,22 @@ __global__ void probe_kernel(const float* __restrict__ f, const uint32_t* __rest
 
 StepTile default_tile(const Geom& g) {
     // 32 x 6 threads per CTA (30 x 4 interior columns), two planes queued ahead:
-    // two CTAs per SM.  z segments sized for about eight waves on 152 SMs.
+    // two CTAs per SM.  z segments: long enough that the two halo planes a
+    // segment pulls twice stay a small share (at most 32 planes), short enough
+    // that a small box still gives about two CTAs per SM -- a CTA walks its
+    // segment plane after plane, so on a throat-sized box the segment length is
+    // the step's latency.
     StepTile t;
     t.by = 6;
     t.lead = 2;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles_xy = (long long)((g.nx + 29) / 30) * ((g.ny + (t.by - 2) - 1) / (t.by - 2));
-    const long long want_segments = (4LL * 2 * 152 + tiles_xy - 1) / tiles_xy;
-    int lz = (int)((g.nz + want_segments - 1) / want_segments);
-    if (lz < 16) lz = 16;
+    long long lz = (g.nz * tiles_xy + 2LL * sms - 1) / (2LL * sms);
+    if (lz < 2) lz = 2;
+    if (lz > 32) lz = 32;
     if (lz > g.nz) lz = g.nz;
-    t.lz = lz;
+    t.lz = (int)lz;
     t.kind = LBM_KERNEL_STAGED;
     t.tma_lz = 0;
     return t;

@@ -90,13 +90,16 @@ def test_tma_kernel_matches_oracle(lbm, orc, periodic_z):
 def test_tma_default_kernel_choice(lbm):
     nz, ny, nx = SHAPE
     d1 = lbm.Domain(_params(lbm), SPHERES, (nx, ny, nz))
+    assert d1.step_kernel()[0] == lbm.KERNEL_STAGED  # the default
+    d1.set_step_kernel(lbm.KERNEL_TMA)
     assert d1.step_kernel()[0] == lbm.KERNEL_TMA
     d2 = lbm.Domain(_params(lbm, periodic=(1, 0, 0)), SPHERES, (nx, ny, nz))
     assert d2.step_kernel()[0] == lbm.KERNEL_STAGED
     with pytest.raises(lbm.LbmError):
         d2.set_step_kernel(lbm.KERNEL_TMA)
     d3 = lbm.Domain(_params(lbm), SPHERES, (nx - 1, ny, nz))  # nx % 4 != 0
-    assert d3.step_kernel()[0] == lbm.KERNEL_STAGED
+    with pytest.raises(lbm.LbmError):
+        d3.set_step_kernel(lbm.KERNEL_TMA)
 
 
 def test_tma_segments_bitwise(lbm, orc):
