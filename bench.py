@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-throats", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="time the default kernel instead of the autotuned one")
-    ap.add_argument("--shape", default="", help="fixed step kernel shape instead of tuning: tma:LZ or staged:BY:LZ:LEAD")
+    ap.add_argument("--shape", default="",
+                    help="fixed step kernel shape instead of tuning: tma:LZ, split, or staged:BY:LZ:LEAD")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--size", type=int, default=192,
@@ -351,7 +352,7 @@ def run_ours(args, rank, world, local):
     # domain (state restored afterwards); untimed
     if args.shape:
         f = args.shape.split(":")
-        tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else
+        tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
                  {"kind": "staged", "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
     else:
         tuned = dom.autotune(trial_steps=20) if not args.no_tune else None
@@ -361,13 +362,21 @@ def run_ours(args, rank, world, local):
             return
         if tuned["kind"] == "tma":
             d.set_step_kernel(lbm.KERNEL_TMA, tuned["lz"])
+        elif tuned["kind"] == "split":
+            d.set_step_kernel(lbm.KERNEL_SPLIT)
         else:
             d.set_tile(tuned["by"], tuned["lz"], tuned["lead"])
 
     apply_tuned(dom)
 
     kind, _ = dom.step_kernel()
-    kernel_name = "sc_step_tma_kernel" if kind == lbm.KERNEL_TMA else "sc_step_kernel<%d,%d>" % lbm.lbm_get_tile(dom.h)[::2]
+    if kind == lbm.KERNEL_TMA:
+        kernel_name = "sc_step_tma_kernel"
+    elif kind == lbm.KERNEL_SPLIT:
+        kernel_name = "density_pair_kernel + sc_step_split_kernel (one step)"
+    else:
+        by, _, lead = lbm.lbm_get_tile(dom.h)
+        kernel_name = ("sc_step_kernel<%d,%d>" if lead >= 2 else "sc_step_dp_kernel<%d,%d>") % (by, lead)
     dom.step(args.warmup)
     torch.cuda.synchronize()
 

@@ -306,7 +306,10 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  *   LBM_KERNEL_TMA     one thread per CTA loads whole population planes of a
  *                      32 x 8 tile with the tensor memory accelerator (boxes
  *                      without periodic x or y and with nx a multiple of 4);
- *                      lz planes per CTA z-segment (lz <= 0: the default).
+ *                      lz planes per CTA z-segment (lz <= 0: the default);
+ *   LBM_KERNEL_SPLIT   two launches per step: every cell's density pair into a
+ *                      field, then pull + collision reading the 18 neighbour
+ *                      densities from it (any box; FP32 only; lz ignored).
  * New domains use LBM_KERNEL_STAGED (the faster one on small boxes; lbm_autotune
  * times both on the domain).  Both give the same results up to rounding (not
  * bit for bit: the TMA kernel folds omega w_k into its equilibrium constants).  LBM_ERR_ARG
@@ -314,6 +317,7 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  * domain.  lbm_set_tile switches the domain to LBM_KERNEL_STAGED. */
 #define LBM_KERNEL_STAGED 0
 #define LBM_KERNEL_TMA 1
+#define LBM_KERNEL_SPLIT 2
 int lbm_set_step_kernel(lbm_domain* d, int kind, int lz);
 int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
 
@@ -322,9 +326,10 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
  *   trial_steps  time steps timed per candidate (>= 1), after one untimed step;
  *   out          optional: the chosen shape and its time per step.
  * Candidates: for FP32 domains the TMA kernel (where it applies) with z
- * segments of 8 .. 48 planes and the staged kernel with by in {6, 8, 10}, lead
- * in {2, 3} and z segments of 8 .. 32 planes; for 16-bit storage by in
- * {6, 8, 10} with lead 2.  Timing uses CUDA events on the domain's stream.  The
+ * segments of 8 .. 48 planes, the two-launch kernel, and the staged kernel with
+ * by in {6, 8, 10}, lead in {0, 1, 2, 3} (0 and 1: the double-pull variant) and
+ * z segments of 8 .. 32 planes; for 16-bit storage by in {6, 8, 10} with lead 2.
+ * Timing uses CUDA events on the domain's stream.  The
  * populations, the step counter and (16-bit) the density fields are saved
  * before and restored after, bit for bit: a tuned domain continues exactly where
  * it stood.  Needs one extra population buffer of device memory while it runs

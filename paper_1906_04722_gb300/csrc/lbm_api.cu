@@ -101,6 +101,9 @@ cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA)
         return launch_step_tma(d->tma, cur, d->f[cur], d->f[cur ^ 1], d->d_nbr_nw, d->d_adh, d->geom, d->phys,
                                d->tile.tma_lz, d->d_err, s);
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_SPLIT)
+        return launch_step_split(d->f[cur], d->f[cur ^ 1], d->d_rho2, d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom,
+                                 d->phys, s);
     if (d->params.precision == 0)
         return launch_step(d->f[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys, d->tile, s);
     return launch_step16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[cur]),
@@ -110,6 +113,7 @@ cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
 
 cudaError_t prepare_one(lbm_domain* d) {
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA) return prepare_step_tma();
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_SPLIT) return cudaSuccess;
     return d->params.precision == 0 ? prepare_step(d->tile) : prepare_step16(d->params.precision, d->tile);
 }
 
@@ -186,6 +190,7 @@ void free_domain(lbm_domain* d) {
     cudaFree(d->d_bc);
     cudaFree(d->d_probe);
     cudaFree(d->d_err);
+    cudaFree(d->d_rho2);
     drop_graphs(d);
     if (d->capture_stream) cudaStreamDestroy(d->capture_stream);
     if (d->h_result) cudaFreeHost(d->h_result);
@@ -295,6 +300,7 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     LBM_CUDA_D(cudaMalloc(&d->d_bc, sizeof(float) * 4));
     LBM_CUDA_D(cudaMalloc(&d->d_probe, sizeof(float) * 2));
     LBM_CUDA_D(cudaMalloc(&d->d_err, sizeof(int)));
+    if (params->precision == 0) LBM_CUDA_D(cudaMalloc(&d->d_rho2, sizeof(float2) * (size_t)d->N));
     LBM_CUDA_D(cudaMemsetAsync(d->d_err, 0, sizeof(int), d->stream));
     fill_phys(d);
     if (int rc = set_bc(d, params->rho_major, params->rho_major)) return fail(rc);
@@ -590,7 +596,14 @@ int lbm_set_tile(lbm_domain* d, int by, int lz, int lead) {
 
 int lbm_set_step_kernel(lbm_domain* d, int kind, int lz) {
     if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
-    if (kind != LBM_KERNEL_STAGED && kind != LBM_KERNEL_TMA) { set_error("unknown step kernel"); return LBM_ERR_ARG; }
+    if (kind != LBM_KERNEL_STAGED && kind != LBM_KERNEL_TMA && kind != LBM_KERNEL_SPLIT) {
+        set_error("unknown step kernel");
+        return LBM_ERR_ARG;
+    }
+    if (kind == LBM_KERNEL_SPLIT && d->params.precision != 0) {
+        set_error("the two-launch step kernel needs an FP32 domain");
+        return LBM_ERR_STATE;
+    }
     if (kind == LBM_KERNEL_TMA) {
         if (d->params.precision != 0 || !d->tma_ok) {
             set_error("the TMA step kernel needs an FP32 domain without periodic x or y and with nx % 4 == 0");
@@ -642,8 +655,9 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     };
     if (fp32 && d->tma_ok)
         for (int lz : {8, 12, 16, 24, 32, 48}) add(LBM_KERNEL_TMA, orig.by, lz, orig.lead);
+    if (fp32) add(LBM_KERNEL_SPLIT, orig.by, orig.lz, orig.lead);
     for (int by : {6, 8, 10})
-        for (int lead : {2, 3})
+        for (int lead : {0, 1, 2, 3})
             for (int lz : {8, 16, 32}) {
                 if (fp32 ? !tile_supported(by, lead) : !tile16_supported(by, lead)) continue;
                 add(LBM_KERNEL_STAGED, by, lz, lead);

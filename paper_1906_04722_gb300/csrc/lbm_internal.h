@@ -87,7 +87,7 @@ struct StepTile {
     int by;    // block rows including the two halo rows (6, 8, 10 or 12)
     int lz;    // z-segment length per CTA
     int lead;  // planes queued ahead of the collided plane (2, 3 or 4)
-    int kind;  // LBM_KERNEL_STAGED or LBM_KERNEL_TMA
+    int kind;  // LBM_KERNEL_STAGED, LBM_KERNEL_TMA or LBM_KERNEL_SPLIT
     int tma_lz;  // z-segment length of the TMA kernel
 };
 
@@ -137,6 +137,11 @@ cudaError_t encode_step_maps(const Geom& g, float* f0, float* f1, const uint32_t
 cudaError_t prepare_step_tma();
 cudaError_t launch_step_tma(const TmaMaps& m, int cur, const float* fin, float* fout, const uint32_t* nbr_nw,
                             const uint32_t* adh, const Geom& g, const Phys& p, int lz, int* err, cudaStream_t s);
+// two-launch step: densities first, then pull + collide reading the neighbour
+// densities from rho2 (lbm_step_split.cu)
+cudaError_t launch_step_split(const float* fin, float* fout, float2* rho2, const uint32_t* nbr,
+                              const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p,
+                              cudaStream_t s);
 // ghost stores (the reflected populations the TMA kernel pulls from wall cells) of a state
 cudaError_t launch_ghost_fill(float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, cudaStream_t s);
 
@@ -185,6 +190,7 @@ struct lbm_domain {
     bool tma_ok;
     bool ghosts_ok;     // the current FP32 state holds the TMA kernel's ghost stores
     int* d_err;         // set by a step kernel whose bounded wait ran out
+    float2* d_rho2;     // FP32 domains: (rho_w, rho_nw) per cell for the two-launch step
 };
 
 constexpr int GRAPH_STEPS = 64;  // steps per captured graph (even: the buffer parity is unchanged)

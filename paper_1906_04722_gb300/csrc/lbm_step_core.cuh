@@ -120,11 +120,11 @@ __device__ __forceinline__ void plane_density(uint32_t w, const float* st, int t
 // force sums and the equilibria (the symmetric and the antisymmetric part of
 // f^eq are shared by a pair).  The rest population is rho_s - sum_{k>=1} f*_k.
 //
-// collide_ring is the general form: the density planes are RPLANE float2 apart
-// and their rows RROW apart, and (row, lane) are the cell's coordinates in them.
-template <int RROW, int RPLANE, class Sink>
-__device__ __forceinline__ void collide_ring(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
-                                             int z, int row, int lane, const Phys& P, Sink&& sink) {
+// collide_core is the general form: rho_at(k) returns (rho_w, rho_nw) at x + e_k
+// (k = 0: the cell itself), 0 where that cell is not fluid.
+template <class RhoAt, class Sink>
+__device__ __forceinline__ void collide_core(const float (&f)[2][Q], uint32_t w, uint32_t a, const Phys& P,
+                                             RhoAt&& rho_at, Sink&& sink) {
     const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
     const bool has_nw = cls != CLS_MEMBRANE;
 
@@ -145,9 +145,6 @@ __device__ __forceinline__ void collide_ring(const float (&f)[2][Q], const float
         return;
     }
 
-    auto rho_at = [&](int k) {
-        return ring[((z + EZ(k)) & 3) * RPLANE + (row + EY(k)) * RROW + (lane + EX(k))];
-    };
     const float2 r00 = rho_at(0);
     const float rw = r00.x;
     const float rn = r00.y;
@@ -224,6 +221,16 @@ __device__ __forceinline__ void collide_ring(const float (&f)[2][Q], const float
         }
         sink(s, 0, rs - ((part[0] + part[1]) + part[2]));  // rest population: the collision keeps rho_s
     }
+}
+
+// A ring of density planes in shared memory: planes RPLANE float2 apart, rows
+// RROW apart, (row, lane) the cell's coordinates in them, plane z at z & 3.
+template <int RROW, int RPLANE, class Sink>
+__device__ __forceinline__ void collide_ring(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,
+                                             int z, int row, int lane, const Phys& P, Sink&& sink) {
+    collide_core(f, w, a, P,
+                 [&](int k) { return ring[((z + EZ(k)) & 3) * RPLANE + (row + EY(k)) * RROW + (lane + EX(k))]; },
+                 static_cast<Sink&&>(sink));
 }
 
 // The ring of the staged kernels: planes of 32 x BY cells, one per thread.

@@ -1,5 +1,5 @@
-"""The two FP32 step kernels (staged cp.async and TMA plane loads) against the
-FP64 oracle and against each other.
+"""The FP32 step kernels (staged cp.async, its double-pull variant, TMA plane
+loads, the two-launch form) against the FP64 oracle and against each other.
 
 Boxes are chosen so that the TMA kernel's 32 x 8 tiles have ragged tails in x
 and y and its z segments ragged ends; grains carry adhesion, the closed-z case
@@ -65,8 +65,10 @@ def _case(lbm, orc, periodic_z):
 def _gpu_run(lbm, flags, rho0, steps, kernel, lz=0):
     nz, ny, nx = SHAPE
     dom = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
-    if kernel == lbm.KERNEL_TMA:
+    if kernel in (lbm.KERNEL_TMA, lbm.KERNEL_SPLIT):
         dom.set_step_kernel(kernel, lz)
+    elif isinstance(lz, tuple):
+        dom.set_tile(*lz)
     else:
         dom.set_tile(6, 16, 2)
     assert dom.step_kernel()[0] == kernel
@@ -140,8 +142,46 @@ def test_autotune_restores_state_and_keeps_parity(lbm, orc):
     assert np.array_equal(before, after)
     assert res["n_candidates"] >= 10 and res["ms_per_step"] > 0
     kind, lz = dom.step_kernel()
-    assert kind == (lbm.KERNEL_TMA if res["kind"] == "tma" else lbm.KERNEL_STAGED) and lz == res["lz"]
+    assert kind == {"staged": lbm.KERNEL_STAGED, "tma": lbm.KERNEL_TMA, "split": lbm.KERNEL_SPLIT}[res["kind"]]
+    if res["kind"] != "split":
+        assert lz == res["lz"]
     dom.step(65)
     f = orc.init(cfg, mask, rho0)
     orc.step(cfg, mask, f, 70)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+@pytest.mark.parametrize("periodic_z", [0, 1])
+def test_split_kernel_matches_oracle(lbm, orc, periodic_z):
+    flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
+    dom = _gpu_run(lbm, flags, rho0, 70, lbm.KERNEL_SPLIT)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 70)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+def test_split_kernel_periodic_xy(lbm, orc):
+    """The two-launch kernel serves any periodicity (the TMA kernel does not)."""
+    shape = (20, 13, 41)
+    spheres = np.array([[20.0, 6.0, 10.0, 4.5]])
+    rho0 = W.droplet_densities(shape, (8, 6, 9), 4.0, seed=3)
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm, periodic=(1, 1, 0)), spheres, (nx, ny, nz))
+    dom.set_step_kernel(lbm.KERNEL_SPLIT)
+    dom.set_densities(rho0)
+    dom.step(60)
+    mask = orc.voxelise(shape, spheres)
+    cfg = orc.Config(shape=shape, tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, periodic=(1, 1, 0))
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 60)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+@pytest.mark.parametrize("shape", [(6, 8, 0), (8, 8, 1), (10, 16, 0), (8, 16, 3), (10, 8, 2)])
+def test_staged_shapes_match_oracle(lbm, orc, shape):
+    """Every staged shape the autotuner may pick (lead 0 and 1: the double-pull variant)."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, 0)
+    dom = _gpu_run(lbm, flags, rho0, 40, lbm.KERNEL_STAGED, lz=shape)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 40)
     assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
