@@ -75,6 +75,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest value over all ranks (the job ends when its slowest rank
+    does); the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds_local: float, world: int, dist=None, device="cpu") -> float:
+    """Units per second of the whole job: every rank processed units_per_rank
+    (replicas, weak scaling) in at most the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(seconds_local, dist, device)
+
+
 def sample_geometry(edge: int = 192):
     import workloads as W
     return W.sample_spheres(edge), (edge, edge, edge)
@@ -392,11 +409,8 @@ def run_ours(args, rank, world, local):
     barrier()
     per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    t = torch.tensor([total_ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * n_upd * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_rate(n_upd * args.steps, total_ms / 1e3, world) / 1e6
     mean_ms = float(np.mean(per))
     peak, peak_kind = read_peaks()
     achieved = bytes_per_step / (mean_ms / 1e3) / 1e9
@@ -428,11 +442,7 @@ def run_ours(args, rank, world, local):
     clocks = clk.summary()
 
     def tmax(v):
-        if dist is None:
-            return v
-        tt = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+        return max_over_ranks(v, dist, "cuda")
 
     def sync():
         torch.cuda.synchronize()

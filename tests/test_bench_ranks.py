@@ -1,0 +1,67 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks (the replicas a
+torchrun launch starts, one per GPU) agree on the slowest rank's time and
+report the whole job's rate; the reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, lr = bench.dist_env()
+    seconds = [2.0, 3.0][rank]  # rank 1 is the slow one
+    t = bench.max_over_ranks(seconds, dist)
+    rate = bench.whole_job_rate(600.0, seconds, world, dist)
+    dist.destroy_process_group()
+    q.put((rank, r, w, lr, t, rate))
+
+
+def test_two_gloo_ranks_agree_on_the_slowest_time():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, r, w, lr, t, rate in out:
+        assert (r, w, lr) == (rank, 2, rank)
+        assert t == 3.0
+        assert rate == pytest.approx(2 * 600.0 / 3.0)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(1.5) == 1.5
+    assert bench.whole_job_rate(100.0, 2.0, 1) == 50.0
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Args:
+        gpus, steps, warmup = 2, 1, 0
+
+    assert bench.run_reference(Args(), 1, 2) == 0
+    assert capsys.readouterr().out == ""
