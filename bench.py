@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--no-throats", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="time the default kernel instead of the autotuned one")
     ap.add_argument("--shape", default="",
-                    help="fixed step kernel shape instead of tuning: tma:LZ, split, or staged:BY:LZ:LEAD")
+                    help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD "
+                         "or staged2:BY:LZ:2")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--size", type=int, default=192,
@@ -370,7 +371,7 @@ def run_ours(args, rank, world, local):
     if args.shape:
         f = args.shape.split(":")
         tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
-                 {"kind": "staged", "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
+                 {"kind": f[0], "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
     else:
         tuned = dom.autotune(trial_steps=20) if not args.no_tune else None
 
@@ -381,6 +382,9 @@ def run_ours(args, rank, world, local):
             d.set_step_kernel(lbm.KERNEL_TMA, tuned["lz"])
         elif tuned["kind"] == "split":
             d.set_step_kernel(lbm.KERNEL_SPLIT)
+        elif tuned["kind"] == "staged2":
+            d.set_tile(tuned["by"], tuned["lz"], 2)
+            d.set_step_kernel(lbm.KERNEL_STAGED2, tuned["lz"])
         else:
             d.set_tile(tuned["by"], tuned["lz"], tuned["lead"])
 
@@ -391,6 +395,8 @@ def run_ours(args, rank, world, local):
         kernel_name = "sc_step_tma_kernel"
     elif kind == lbm.KERNEL_SPLIT:
         kernel_name = "density_pair_kernel + sc_step_split_kernel (one step)"
+    elif kind == lbm.KERNEL_STAGED2:
+        kernel_name = "sc_step2_kernel<%d,2>" % lbm.lbm_get_tile(dom.h)[0]
     else:
         by, _, lead = lbm.lbm_get_tile(dom.h)
         kernel_name = ("sc_step_kernel<%d,%d>" if lead >= 2 else "sc_step_dp_kernel<%d,%d>") % (by, lead)

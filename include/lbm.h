@@ -309,7 +309,10 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  *                      lz planes per CTA z-segment (lz <= 0: the default);
  *   LBM_KERNEL_SPLIT   two launches per step: every cell's density pair into a
  *                      field, then pull + collision reading the 18 neighbour
- *                      densities from it (any box; FP32 only; lz ignored).
+ *                      densities from it (any box; FP32 only; lz ignored);
+ *   LBM_KERNEL_STAGED2 the staged kernel with two threads per cell, one per
+ *                      fluid component (any box; FP32 only; by 6 or 8, lead 2,
+ *                      lz planes per z segment, lz <= 0: keep the current).
  * New domains use LBM_KERNEL_STAGED (the faster one on small boxes; lbm_autotune
  * times both on the domain).  Both give the same results up to rounding (not
  * bit for bit: the TMA kernel folds omega w_k into its equilibrium constants).  LBM_ERR_ARG
@@ -318,6 +321,7 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
 #define LBM_KERNEL_STAGED 0
 #define LBM_KERNEL_TMA 1
 #define LBM_KERNEL_SPLIT 2
+#define LBM_KERNEL_STAGED2 3
 int lbm_set_step_kernel(lbm_domain* d, int kind, int lz);
 int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
 
@@ -326,7 +330,8 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
  *   trial_steps  time steps timed per candidate (>= 1), after one untimed step;
  *   out          optional: the chosen shape and its time per step.
  * Candidates: for FP32 domains the TMA kernel (where it applies) with z
- * segments of 8 .. 48 planes, the two-launch kernel, and the staged kernel with
+ * segments of 8 .. 48 planes, the two-launch kernel, the two-threads-per-cell
+ * staged kernel (by 6 or 8, z segments of 8 .. 32), and the staged kernel with
  * by in {6, 8, 10}, lead in {0, 1, 2, 3} (0 and 1: the double-pull variant) and
  * z segments of 8 .. 32 planes; for 16-bit storage by in {6, 8, 10} with lead 2.
  * Timing uses CUDA events on the domain's stream.  The

@@ -85,7 +85,7 @@ class lbm_tune_result(ctypes.Structure):
                 ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int)]
 
     def as_dict(self) -> dict:
-        return {"kind": {0: "staged", 1: "tma", 2: "split"}.get(self.kind, "?"), "by": self.by, "lz": self.lz, "lead": self.lead,
+        return {"kind": {0: "staged", 1: "tma", 2: "split", 3: "staged2"}.get(self.kind, "?"), "by": self.by, "lz": self.lz, "lead": self.lead,
                 "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates}
 
 
@@ -326,6 +326,7 @@ def lbm_get_tile(h):
 KERNEL_STAGED = 0
 KERNEL_TMA = 1
 KERNEL_SPLIT = 2
+KERNEL_STAGED2 = 3
 
 
 def lbm_set_step_kernel(h, kind: int, lz: int = 0):

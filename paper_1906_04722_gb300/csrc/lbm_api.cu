@@ -101,6 +101,8 @@ cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA)
         return launch_step_tma(d->tma, cur, d->f[cur], d->f[cur ^ 1], d->d_nbr_nw, d->d_adh, d->geom, d->phys,
                                d->tile.tma_lz, d->d_err, s);
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_STAGED2)
+        return launch_step2(d->f[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom, d->phys, d->tile, s);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_SPLIT)
         return launch_step_split(d->f[cur], d->f[cur ^ 1], d->d_rho2, d->d_nbr, d->d_nbr_nw, d->d_adh, d->geom,
                                  d->phys, s);
@@ -114,6 +116,7 @@ cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
 cudaError_t prepare_one(lbm_domain* d) {
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA) return prepare_step_tma();
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_SPLIT) return cudaSuccess;
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_STAGED2) return prepare_step2(d->tile);
     return d->params.precision == 0 ? prepare_step(d->tile) : prepare_step16(d->params.precision, d->tile);
 }
 
@@ -596,13 +599,19 @@ int lbm_set_tile(lbm_domain* d, int by, int lz, int lead) {
 
 int lbm_set_step_kernel(lbm_domain* d, int kind, int lz) {
     if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
-    if (kind != LBM_KERNEL_STAGED && kind != LBM_KERNEL_TMA && kind != LBM_KERNEL_SPLIT) {
+    if (kind != LBM_KERNEL_STAGED && kind != LBM_KERNEL_TMA && kind != LBM_KERNEL_SPLIT &&
+        kind != LBM_KERNEL_STAGED2) {
         set_error("unknown step kernel");
         return LBM_ERR_ARG;
     }
-    if (kind == LBM_KERNEL_SPLIT && d->params.precision != 0) {
-        set_error("the two-launch step kernel needs an FP32 domain");
+    if ((kind == LBM_KERNEL_SPLIT || kind == LBM_KERNEL_STAGED2) && d->params.precision != 0) {
+        set_error("the two-launch and two-threads-per-cell step kernels need an FP32 domain");
         return LBM_ERR_STATE;
+    }
+    if (kind == LBM_KERNEL_STAGED2) {
+        d->tile.by = tile2_supported(d->tile.by, 2) ? d->tile.by : 6;
+        d->tile.lead = 2;
+        if (lz > 0) d->tile.lz = lz > d->geom.nz ? d->geom.nz : lz;
     }
     if (kind == LBM_KERNEL_TMA) {
         if (d->params.precision != 0 || !d->tma_ok) {
@@ -619,7 +628,7 @@ int lbm_set_step_kernel(lbm_domain* d, int kind, int lz) {
 int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz) {
     if (!d || !kind || !lz) { set_error("NULL argument"); return LBM_ERR_ARG; }
     *kind = d->tile.kind;
-    *lz = d->tile.kind == LBM_KERNEL_TMA ? d->tile.tma_lz : d->tile.lz;
+    *lz = d->tile.kind == LBM_KERNEL_TMA ? d->tile.tma_lz : d->tile.lz;  // staged kinds: the z segment
     return LBM_OK;
 }
 
@@ -656,6 +665,9 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     if (fp32 && d->tma_ok)
         for (int lz : {8, 12, 16, 24, 32, 48}) add(LBM_KERNEL_TMA, orig.by, lz, orig.lead);
     if (fp32) add(LBM_KERNEL_SPLIT, orig.by, orig.lz, orig.lead);
+    if (fp32)
+        for (int by : {6, 8})
+            for (int lz : {8, 16, 32}) add(LBM_KERNEL_STAGED2, by, lz, 2);
     for (int by : {6, 8, 10})
         for (int lead : {0, 1, 2, 3})
             for (int lz : {8, 16, 32}) {

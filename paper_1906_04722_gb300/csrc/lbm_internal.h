@@ -87,7 +87,7 @@ struct StepTile {
     int by;    // block rows including the two halo rows (6, 8, 10 or 12)
     int lz;    // z-segment length per CTA
     int lead;  // planes queued ahead of the collided plane (2, 3 or 4)
-    int kind;  // LBM_KERNEL_STAGED, LBM_KERNEL_TMA or LBM_KERNEL_SPLIT
+    int kind;  // LBM_KERNEL_STAGED, LBM_KERNEL_TMA, LBM_KERNEL_SPLIT or LBM_KERNEL_STAGED2
     int tma_lz;  // z-segment length of the TMA kernel
 };
 
@@ -137,6 +137,11 @@ cudaError_t encode_step_maps(const Geom& g, float* f0, float* f1, const uint32_t
 cudaError_t prepare_step_tma();
 cudaError_t launch_step_tma(const TmaMaps& m, int cur, const float* fin, float* fout, const uint32_t* nbr_nw,
                             const uint32_t* adh, const Geom& g, const Phys& p, int lz, int* err, cudaStream_t s);
+// staged step with two threads per cell, one per component (lbm_step2.cu)
+bool tile2_supported(int by, int lead);
+cudaError_t prepare_step2(const StepTile& t);
+cudaError_t launch_step2(const float* fin, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                         const uint32_t* adh, const Geom& g, const Phys& p, const StepTile& t, cudaStream_t s);
 // two-launch step: densities first, then pull + collide reading the neighbour
 // densities from rho2 (lbm_step_split.cu)
 cudaError_t launch_step_split(const float* fin, float* fout, float2* rho2, const uint32_t* nbr,

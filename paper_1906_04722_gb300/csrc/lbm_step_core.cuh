@@ -240,6 +240,110 @@ __device__ __forceinline__ void collide_generic(const float (&f)[2][Q], const fl
     collide_ring<32, 32 * BY>(f, ring, w, a, z, row, lane, P, static_cast<Sink&&>(sink));
 }
 
+// Momentum of component s (Eq. 3) over opposite pairs, in the order of the
+// staged kernel.
+__device__ __forceinline__ void momentum(const float (&f)[Q], float (&j)[3]) {
+    j[0] = j[1] = j[2] = 0.f;
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) {
+        const float d = f[k] - f[k + 1];
+        if (EX(k)) j[0] += EX(k) > 0 ? d : -d;
+        if (EY(k)) j[1] += EY(k) > 0 ? d : -d;
+        if (EZ(k)) j[2] += EZ(k) > 0 ? d : -d;
+    }
+}
+
+// Collision of component s of one interior cell of plane z, for kernels that
+// run one thread per cell and component: the arithmetic of collide_core for one
+// component (the same operations in the same order).  f: the pulled populations;
+// cls, a: the cell's class and adhesion word; j: this component's momentum; jo:
+// the other component's (0 where it is not fluid).  rho holds density planes
+// [4][2][RPLANE] (plane z at z & 3, then component, rows RROW apart); rc is the
+// cell's index in a plane.  sink(k, v) receives every f*_k; it may overwrite
+// f[k] (each f[k] is read before its sink call).
+template <int RROW, int RPLANE, class Sink>
+__device__ __forceinline__ void collide_component(const float (&f)[Q], uint32_t cls, uint32_t a, int s,
+                                                  const float (&j)[3], const float (&jo)[3], const float* rho, int z,
+                                                  int rc, const Phys& P, Sink&& sink) {
+    if (cls == CLS_INLET || cls == CLS_OUTLET) {
+        const float r = __ldg(P.bc + (cls == CLS_INLET ? 0 : 2) + s);  // device array: indexing is fine
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            const float v = WK(k) * r;
+            sum += v;
+            sink(k, v);
+        }
+        sink(0, r - sum);
+        return;
+    }
+    const float* rz = rho + ((z & 3) * 2) * RPLANE;
+    const float rw = rz[rc], rn = rz[RPLANE + rc];
+    const float rs = s == 0 ? rw : rn;
+    const bool has_nw = cls != CLS_MEMBRANE;
+    // cohesion sum over the other component's neighbour densities
+    float coh[3] = {0.f, 0.f, 0.f};
+    {
+        const int so = s ^ 1;
+#pragma unroll
+        for (int k = 1; k < Q; k += 2) {
+            const float p = rho[(((z + EZ(k)) & 3) * 2 + so) * RPLANE + rc + EY(k) * RROW + EX(k)];
+            const float m = rho[(((z - EZ(k)) & 3) * 2 + so) * RPLANE + rc - EY(k) * RROW - EX(k)];
+            const float dd = WK(k) * (p - m);
+            if (EX(k)) coh[0] += EX(k) > 0 ? dd : -dd;
+            if (EY(k)) coh[1] += EY(k) > 0 ? dd : -dd;
+            if (EZ(k)) coh[2] += EZ(k) > 0 ? dd : -dd;
+        }
+    }
+    float ad[3] = {0.f, 0.f, 0.f};
+    if (a != 0u) {
+        ad[0] = (float)(int8_t)(a & 0xffu) * (1.0f / 36.0f);
+        ad[1] = (float)(int8_t)((a >> 8) & 0xffu) * (1.0f / 36.0f);
+        ad[2] = (float)(int8_t)((a >> 16) & 0xffu) * (1.0f / 36.0f);
+    }
+    float up[3];
+    {
+        const float den = rw * P.omega[0] + (has_nw ? rn * P.omega[1] : 0.f);
+        const float inv = den != 0.f ? 1.0f / den : 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float j0 = s == 0 ? j[c] : jo[c];
+            const float j1 = s == 0 ? jo[c] : j[c];
+            up[c] = (j0 * P.omega[0] + (has_nw ? j1 * P.omega[1] : 0.f)) * inv;
+        }
+    }
+    // the thread's component is a run-time value: select the parameters (an
+    // indexed kernel parameter would be copied to local memory)
+    const float gads = s == 0 ? P.Gads[0] : P.Gads[1];
+    const float tau = s == 0 ? P.tau[0] : P.tau[1];
+    float ueq[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float F = -P.G * rs * coh[c] - gads * rs * ad[c] + rs * P.g[c];
+        ueq[c] = up[c] + (rs != 0.f ? tau * F / rs : 0.f);
+    }
+    const float uu = ueq[0] * ueq[0] + ueq[1] * ueq[1] + ueq[2] * ueq[2];
+    const float om = s == 0 ? P.omega[0] : P.omega[1];
+    const float keep = 1.0f - om;
+    const float base = rs * (1.0f - 1.5f * uu);
+    const float r45 = 4.5f * rs;
+    const float r3 = 3.0f * rs;
+    float part[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 1; k < Q; k += 2) {
+        const float eu = (float)EX(k) * ueq[0] + (float)EY(k) * ueq[1] + (float)EZ(k) * ueq[2];
+        const float sym = WK(k) * (base + r45 * eu * eu);
+        const float asym = WK(k) * (r3 * eu);
+        const float v0 = keep * f[k] + om * (sym + asym);
+        const float v1 = keep * f[k + 1] + om * (sym - asym);
+        part[(k >> 1) % 3] += v0 + v1;
+        sink(k, v0);
+        sink(k + 1, v1);
+    }
+    const float v = rs - ((part[0] + part[1]) + part[2]);  // rest population: the collision keeps rho_s
+    sink(0, v);
+}
+
 // FP32 storage: the post-collision values go straight to fout[(s*19 + k) * plane + cell].
 template <int BY>
 __device__ __forceinline__ void collide_cell(const float (&f)[2][Q], const float2* ring, uint32_t w, uint32_t a,

@@ -232,114 +232,6 @@ __device__ __forceinline__ bool cell_pull(const float* sl, const uint32_t* wsl, 
     return true;
 }
 
-// Momentum of component s (Eq. 3) over opposite pairs, in the order of the
-// staged kernel.
-__device__ __forceinline__ void momentum(const float (&f)[Q], float (&j)[3]) {
-    j[0] = j[1] = j[2] = 0.f;
-#pragma unroll
-    for (int k = 1; k < Q; k += 2) {
-        const float d = f[k] - f[k + 1];
-        if (EX(k)) j[0] += EX(k) > 0 ? d : -d;
-        if (EY(k)) j[1] += EY(k) > 0 ? d : -d;
-        if (EZ(k)) j[2] += EZ(k) > 0 ? d : -d;
-    }
-}
-
-// Collision of component s of one interior cell of plane z: the arithmetic of
-// collide_ring for one component (moments, forces and velocities in the same
-// order; the equilibrium with omega w_k folded into per-cell constants).  j: this
-// component's momentum; jo: the other component's (0 where it is not fluid).
-// rho: density planes [4][2][RHO_PLANE]; rc: the cell's index in a plane.
-// Post-collision values go to o[k * pl] and back into h.f.
-__device__ __forceinline__ void collide_component(Held& h, int s, const float (&j)[3], const float (&jo)[3],
-                                                  const float* rho, int z, int rc, const Phys& P,
-                                                  float* __restrict__ o, int pl) {
-    if (h.cls == CLS_INLET || h.cls == CLS_OUTLET) {
-        const float r = __ldg(P.bc + (h.cls == CLS_INLET ? 0 : 2) + s);  // device array: indexing is fine
-        float sum = 0.f;
-#pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            const float v = WK(k) * r;
-            sum += v;
-            o[k * pl] = v;
-            h.f[k] = v;
-        }
-        o[0] = r - sum;
-        h.f[0] = r - sum;
-        return;
-    }
-    const float* rz = rho + ((z & 3) * 2) * RHO_PLANE;
-    const float rw = rz[rc], rn = rz[RHO_PLANE + rc];
-    const float rs = s == 0 ? rw : rn;
-    const bool has_nw = h.cls != CLS_MEMBRANE;
-    // cohesion sum over the other component's neighbour densities
-    float coh[3] = {0.f, 0.f, 0.f};
-    {
-        const int so = s ^ 1;
-#pragma unroll
-        for (int k = 1; k < Q; k += 2) {
-            const float p = rho[(((z + EZ(k)) & 3) * 2 + so) * RHO_PLANE + rc + EY(k) * RHO_W + EX(k)];
-            const float m = rho[(((z - EZ(k)) & 3) * 2 + so) * RHO_PLANE + rc - EY(k) * RHO_W - EX(k)];
-            const float dd = WK(k) * (p - m);
-            if (EX(k)) coh[0] += EX(k) > 0 ? dd : -dd;
-            if (EY(k)) coh[1] += EY(k) > 0 ? dd : -dd;
-            if (EZ(k)) coh[2] += EZ(k) > 0 ? dd : -dd;
-        }
-    }
-    float ad[3] = {0.f, 0.f, 0.f};
-    if (h.a != 0u) {
-        ad[0] = (float)(int8_t)(h.a & 0xffu) * (1.0f / 36.0f);
-        ad[1] = (float)(int8_t)((h.a >> 8) & 0xffu) * (1.0f / 36.0f);
-        ad[2] = (float)(int8_t)((h.a >> 16) & 0xffu) * (1.0f / 36.0f);
-    }
-    float up[3];
-    {
-        const float den = rw * P.omega[0] + (has_nw ? rn * P.omega[1] : 0.f);
-        const float inv = den != 0.f ? 1.0f / den : 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float j0 = s == 0 ? j[c] : jo[c];
-            const float j1 = s == 0 ? jo[c] : j[c];
-            up[c] = (j0 * P.omega[0] + (has_nw ? j1 * P.omega[1] : 0.f)) * inv;
-        }
-    }
-    // the thread's component is a run-time value: select the parameters (an
-    // indexed kernel parameter would be copied to local memory)
-    const float gads = s == 0 ? P.Gads[0] : P.Gads[1];
-    const float tau = s == 0 ? P.tau[0] : P.tau[1];
-    float ueq[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float F = -P.G * rs * coh[c] - gads * rs * ad[c] + rs * P.g[c];
-        ueq[c] = up[c] + (rs != 0.f ? tau * F / rs : 0.f);
-    }
-    const float uu = ueq[0] * ueq[0] + ueq[1] * ueq[1] + ueq[2] * ueq[2];
-    const float om = s == 0 ? P.omega[0] : P.omega[1];
-    const float keep = 1.0f - om;
-    // omega w_k f^eq_k = A_w + B_w (e_k.u)^2 +- C_w (e_k.u) for the face (1/18)
-    // and edge (1/36) weights: the constants are formed once per cell
-    const float base = rs * (1.0f - 1.5f * uu);
-    const float A1 = om * (1.0f / 18.0f) * base, A2 = om * (1.0f / 36.0f) * base;
-    const float B1 = om * (1.0f / 18.0f) * (4.5f * rs), B2 = om * (1.0f / 36.0f) * (4.5f * rs);
-    const float C1 = om * (1.0f / 18.0f) * (3.0f * rs), C2 = om * (1.0f / 36.0f) * (3.0f * rs);
-    float part[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 1; k < Q; k += 2) {
-        const float eu = (float)EX(k) * ueq[0] + (float)EY(k) * ueq[1] + (float)EZ(k) * ueq[2];
-        const float sym = (k <= 6 ? B1 : B2) * (eu * eu) + (k <= 6 ? A1 : A2);
-        const float asym = (k <= 6 ? C1 : C2) * eu;
-        const float v0 = keep * h.f[k] + (sym + asym);
-        const float v1 = keep * h.f[k + 1] + (sym - asym);
-        part[(k >> 1) % 3] += v0 + v1;
-        o[k * pl] = v0;
-        o[(k + 1) * pl] = v1;
-        h.f[k] = v0;
-        h.f[k + 1] = v1;
-    }
-    const float v = rs - ((part[0] + part[1]) + part[2]);  // rest population: the collision keeps rho_s
-    o[0] = v;
-    h.f[0] = v;
-}
 
 __global__ void __launch_bounds__(TT_THREADS, 1)
     sc_step_tma_kernel(const __grid_constant__ CUtensorMap tm_f, const __grid_constant__ CUtensorMap tm_w,
@@ -471,7 +363,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
             for (int c = 0; c < 3; ++c) jo[c] = xch[((s ^ 1) * 3 + c) * TT_CELLS + t];
             const int pl = g.plane;
             float* __restrict__ o = fout + s * (Q * pl) + prev.cell;
-            collide_component(prev, s, j, jo, rho, d - 1, rc, P, o, pl);
+            collide_component<RHO_W, RHO_PLANE>(prev.f, prev.cls, prev.a, s, j, jo, rho, d - 1, rc, P,
+                                                [&](int k, float v) {
+                                                    o[k * pl] = v;
+                                                    prev.f[k] = v;  // for the ghost stores below
+                                                });
             // ghost stores: where x + e_k (inside the box) is not fluid for this
             // component, f*_k goes to that cell's slot of array kbar
             uint32_t gm = swap_pairs(prev.bits);

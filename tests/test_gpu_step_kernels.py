@@ -115,8 +115,8 @@ def test_tma_segments_bitwise(lbm, orc):
 
 @pytest.mark.parametrize("periodic_z", [0, 1])
 def test_staged_and_tma_agree(lbm, orc, periodic_z):
-    """Same FP32 model, different rounding (the TMA kernel folds omega w_k into
-    its equilibrium constants): after 100 steps the densities differ by at most
+    """Same FP32 arithmetic per cell, different summation contexts (the compiler
+    may contract differently): after 100 steps the densities differ by at most
     about one FP32 ulp (6e-8 relative) per step, 6e-6; the bar is 5e-6, each
     kernel being held to the FP64 oracle at 1e-5 separately."""
     flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
@@ -142,7 +142,8 @@ def test_autotune_restores_state_and_keeps_parity(lbm, orc):
     assert np.array_equal(before, after)
     assert res["n_candidates"] >= 10 and res["ms_per_step"] > 0
     kind, lz = dom.step_kernel()
-    assert kind == {"staged": lbm.KERNEL_STAGED, "tma": lbm.KERNEL_TMA, "split": lbm.KERNEL_SPLIT}[res["kind"]]
+    assert kind == {"staged": lbm.KERNEL_STAGED, "tma": lbm.KERNEL_TMA, "split": lbm.KERNEL_SPLIT,
+                    "staged2": lbm.KERNEL_STAGED2}[res["kind"]]
     if res["kind"] != "split":
         assert lz == res["lz"]
     dom.step(65)
@@ -184,4 +185,64 @@ def test_staged_shapes_match_oracle(lbm, orc, shape):
     dom = _gpu_run(lbm, flags, rho0, 40, lbm.KERNEL_STAGED, lz=shape)
     f = orc.init(cfg, mask, rho0)
     orc.step(cfg, mask, f, 40)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+@pytest.mark.parametrize("by,lz", [(6, 8), (6, 16), (8, 13)])
+@pytest.mark.parametrize("periodic_z", [0, 1])
+def test_staged2_kernel_matches_oracle(lbm, orc, by, lz, periodic_z):
+    """Two threads per cell (one per component), every shape the autotuner may pick."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
+    nz, ny, nx = SHAPE
+    dom = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
+    dom.set_tile(by, lz, 2)
+    dom.set_step_kernel(lbm.KERNEL_STAGED2, lz)
+    assert dom.step_kernel() == (lbm.KERNEL_STAGED2, lz)
+    dom.set_densities(rho0)
+    if not periodic_z:
+        dom.set_pressure_bc(2.08, W.RHO_MAJOR)
+    dom.step(70)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 70)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+def test_staged2_periodic_xy(lbm, orc):
+    shape = (20, 13, 41)
+    spheres = np.array([[20.0, 6.0, 10.0, 4.5]])
+    rho0 = W.droplet_densities(shape, (8, 6, 9), 4.0, seed=3)
+    nz, ny, nx = shape
+    dom = lbm.Domain(_params(lbm, periodic=(1, 1, 0)), spheres, (nx, ny, nz))
+    dom.set_step_kernel(lbm.KERNEL_STAGED2, 8)
+    dom.set_densities(rho0)
+    dom.step(60)
+    mask = orc.voxelise(shape, spheres)
+    cfg = orc.Config(shape=shape, tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, periodic=(1, 1, 0))
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 60)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+@pytest.mark.parametrize("kernel", ["staged", "tma", "split", "staged2"])
+def test_unequal_tau_and_body_force_every_kernel(lbm, orc, kernel):
+    """tau = (0.8, 1.2) with a body force (weakly damped, the most rounding
+    sensitive case of the suite) for every FP32 kernel."""
+    shape = (41, 16, 36)
+    spheres = np.array([[18.0, 8.0, 10.0, 4.5]])
+    rho0 = W.droplet_densities(shape, (9, 8, 25), 4.0, seed=3)
+    nz, ny, nx = shape
+    kw = dict(tau=(0.8, 1.2))
+    dom = lbm.Domain(_params(lbm, body_force=(1e-5, 0, -2e-5), **kw), spheres, (nx, ny, nz))
+    if kernel == "tma":
+        dom.set_step_kernel(lbm.KERNEL_TMA, 8)
+    elif kernel == "split":
+        dom.set_step_kernel(lbm.KERNEL_SPLIT)
+    elif kernel == "staged2":
+        dom.set_step_kernel(lbm.KERNEL_STAGED2, 8)
+    dom.set_densities(rho0)
+    dom.step(80)
+    mask = orc.voxelise(shape, spheres)
+    cfg = orc.Config(shape=shape, G=W.G_COHESION, G_ads=W.G_ADS, g=(1e-5, 0, -2e-5), **kw)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 80)
     assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
