@@ -246,3 +246,14 @@ def test_unequal_tau_and_body_force_every_kernel(lbm, orc, kernel):
     f = orc.init(cfg, mask, rho0)
     orc.step(cfg, mask, f, 80)
     assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+
+
+def test_staged_and_double_pull_bitwise(lbm, orc):
+    """The staged kernel (pulls queued as asynchronous copies into shared memory)
+    and the double-pull kernel (pulls from global memory twice) sum the
+    densities in the same order and share the collision: the same state bit for
+    bit."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, 0)
+    a = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED, lz=(6, 16, 2)).state()[0]
+    b = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED, lz=(6, 16, 0)).state()[0]
+    assert np.array_equal(a, b)
