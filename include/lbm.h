@@ -347,6 +347,14 @@ typedef struct {
 } lbm_tune_result;
 int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out);
 
+/* lbm_selftest_bounded_wait -- checks the failure path of the TMA step kernel's
+ * waits on the GPU: one CTA waits on an mbarrier that nothing ever completes,
+ * with the same bounded wait the kernel uses, limited to limit_us microseconds
+ * (1 .. 1e7).  *gave_up is set to 1 when the wait gave up and reported it (the
+ * expected outcome), 0 otherwise.  No copy is in flight and the context stays
+ * usable.  Synchronising (legacy default stream).  No counterpart in the paper. */
+int lbm_selftest_bounded_wait(int limit_us, int* gave_up);
+
 /* lbm_destroy -- release the domain (NULL is ignored). */
 void lbm_destroy(lbm_domain* d);
 

@@ -124,6 +124,7 @@ SIGNATURES = {
     "lbm_set_step_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "lbm_get_step_kernel": (ctypes.c_int, [_VP, _IP, _IP]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_tune_result)]),
+    "lbm_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, _IP]),
     "lbm_throat_geometry": (ctypes.c_int, [_DP, _IP, _U8P, _IP]),
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
                                             ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
@@ -344,6 +345,13 @@ def lbm_autotune(h, trial_steps: int = 20):
     r = lbm_tune_result()
     _check(load().lbm_autotune(h, int(trial_steps), ctypes.byref(r)), "lbm_autotune")
     return r.as_dict()
+
+
+def lbm_selftest_bounded_wait(limit_us: int) -> bool:
+    """True when a bounded mbarrier wait that nothing completes gave up and said so."""
+    flag = ctypes.c_int(0)
+    _check(load().lbm_selftest_bounded_wait(int(limit_us), ctypes.byref(flag)), "lbm_selftest_bounded_wait")
+    return flag.value == 1
 
 
 def lbm_throat_geometry(spheres3):

@@ -159,6 +159,7 @@ int run_steps(lbm_domain* d, int n) {
         d->ghosts_ok = true;
     }
     if (!tma) d->ghosts_ok = false;
+    if (tma) d->tma_pending = true;
     while (n >= GRAPH_STEPS) {
         if (!d->graph[d->cur]) {
             int rc = capture_graph(d, d->cur);
@@ -193,6 +194,7 @@ void free_domain(lbm_domain* d) {
     cudaFree(d->d_bc);
     cudaFree(d->d_probe);
     cudaFree(d->d_err);
+    if (d->h_err) cudaFreeHost(d->h_err);
     cudaFree(d->d_rho2);
     drop_graphs(d);
     if (d->capture_stream) cudaStreamDestroy(d->capture_stream);
@@ -203,17 +205,20 @@ void free_domain(lbm_domain* d) {
 
 // Bounded wait for the domain's queued work: polls an event for up to 60 s.
 int wait_domain(lbm_domain* d) {
+    // a TMA step kernel whose bounded wait for its loads ran out leaves a flag:
+    // read it on the domain's stream, behind the work being waited for
+    const bool check = d->tma_pending;
+    if (check) LBM_CUDA(cudaMemcpyAsync(d->h_err, d->d_err, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
     LBM_CUDA(cudaEventRecord(d->done, d->stream));
     const auto t0 = std::chrono::steady_clock::now();
     while (true) {
         cudaError_t e = cudaEventQuery(d->done);
         if (e == cudaSuccess) {
-            if (d->tma_ok) {
-                // a step kernel whose bounded wait for its loads ran out leaves a flag
-                int flag = 0;
-                LBM_CUDA(cudaMemcpy(&flag, d->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-                if (flag) {
-                    LBM_CUDA(cudaMemset(d->d_err, 0, sizeof(int)));
+            if (check) {
+                d->tma_pending = false;
+                if (*d->h_err) {
+                    *d->h_err = 0;
+                    LBM_CUDA(cudaMemsetAsync(d->d_err, 0, sizeof(int), d->stream));
                     set_error("a step kernel gave up waiting for its population loads");
                     return LBM_ERR_TIMEOUT;
                 }
@@ -303,6 +308,8 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     LBM_CUDA_D(cudaMalloc(&d->d_bc, sizeof(float) * 4));
     LBM_CUDA_D(cudaMalloc(&d->d_probe, sizeof(float) * 2));
     LBM_CUDA_D(cudaMalloc(&d->d_err, sizeof(int)));
+    LBM_CUDA_D(cudaMallocHost(&d->h_err, sizeof(int)));
+    *d->h_err = 0;
     if (params->precision == 0) LBM_CUDA_D(cudaMalloc(&d->d_rho2, sizeof(float2) * (size_t)d->N));
     LBM_CUDA_D(cudaMemsetAsync(d->d_err, 0, sizeof(int), d->stream));
     fill_phys(d);
@@ -746,6 +753,26 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
         out->ms_per_step = best;
         out->n_candidates = (int)cand.size();
     }
+    return LBM_OK;
+}
+
+int lbm_selftest_bounded_wait(int limit_us, int* gave_up) {
+    if (!gave_up || limit_us < 1 || limit_us > 10000000) {
+        set_error("lbm_selftest_bounded_wait: gave_up is NULL or limit_us outside [1, 1e7]");
+        return LBM_ERR_ARG;
+    }
+    int* d_flag = nullptr;
+    int h = 0;
+    LBM_CUDA(cudaMalloc(&d_flag, sizeof(int)));
+    cudaError_t e = cudaMemset(d_flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = launch_wait_selftest(1000LL * limit_us, d_flag, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d_flag);
+    if (e != cudaSuccess) {
+        set_error(std::string("lbm_selftest_bounded_wait: ") + cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    *gave_up = h;
     return LBM_OK;
 }
 

@@ -147,6 +147,8 @@ cudaError_t launch_step2(const float* fin, float* fout, const uint32_t* nbr, con
 cudaError_t launch_step_split(const float* fin, float* fout, float2* rho2, const uint32_t* nbr,
                               const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p,
                               cudaStream_t s);
+// one CTA waiting, bounded, on an mbarrier that nothing completes (self-test)
+cudaError_t launch_wait_selftest(long long limit_ns, int* gave_up, cudaStream_t s);
 // ghost stores (the reflected populations the TMA kernel pulls from wall cells) of a state
 cudaError_t launch_ghost_fill(float* f, const uint32_t* nbr, const uint32_t* nbr_nw, const Geom& g, cudaStream_t s);
 
@@ -195,6 +197,8 @@ struct lbm_domain {
     bool tma_ok;
     bool ghosts_ok;     // the current FP32 state holds the TMA kernel's ghost stores
     int* d_err;         // set by a step kernel whose bounded wait ran out
+    int* h_err;         // pinned copy of d_err, read after a wait
+    bool tma_pending;   // a TMA step ran since d_err was last read
     float2* d_rho2;     // FP32 domains: (rho_w, rho_nw) per cell for the two-launch step
 };
 

@@ -105,15 +105,29 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Wait for the phase of the given parity, for at most WAIT_LIMIT_NS.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Wait for the phase of the given parity, for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit_ns = WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if ((long long)(global_ns() - t0) > WAIT_LIMIT_NS) return false;
+        if ((long long)(global_ns() - t0) > limit_ns) return false;
     }
+}
+
+// Self-test of the bounded wait: an mbarrier that nothing ever completes.  The
+// wait must give up after limit_ns and say so; no copy is in flight.
+__global__ void wait_selftest_kernel(long long limit_ns, int* gave_up) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) *gave_up = 1;
 }
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -504,6 +518,11 @@ cudaError_t launch_step_tma(const TmaMaps& m, int cur, const float* fin, float* 
     if (lz < 1) return cudaErrorInvalidValue;
     dim3 grid((g.nx + TT_X - 1) / TT_X, (g.ny + TT_Y - 1) / TT_Y, (g.nz + lz - 1) / lz);
     sc_step_tma_kernel<<<grid, TT_THREADS, SM_TOTAL, s>>>(m.f[cur], m.w, fin, fout, nbr_nw, adh, g, p, lz, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(long long limit_ns, int* gave_up, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(limit_ns, gave_up);
     return cudaGetLastError();
 }
 

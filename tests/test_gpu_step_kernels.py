@@ -257,3 +257,18 @@ def test_staged_and_double_pull_bitwise(lbm, orc):
     a = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED, lz=(6, 16, 2)).state()[0]
     b = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED, lz=(6, 16, 0)).state()[0]
     assert np.array_equal(a, b)
+
+
+def test_bounded_wait_gives_up_and_reports(lbm):
+    """The TMA kernel's waits are bounded: a wait on an mbarrier that nothing
+    completes (a flag nobody sets) gives up after its limit and reports it, and
+    the context stays usable for the next domain."""
+    import time
+    t0 = time.perf_counter()
+    assert lbm.lbm_selftest_bounded_wait(20000)  # 20 ms
+    assert time.perf_counter() - t0 < 30.0
+    nz, ny, nx = SHAPE
+    dom = lbm.Domain(_params(lbm, periodic=(0, 0, 1)), SPHERES, (nx, ny, nz))
+    dom.set_step_kernel(lbm.KERNEL_TMA, 8)
+    dom.step(3)
+    assert dom.measure()["n_nonfinite"] == 0
