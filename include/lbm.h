@@ -167,6 +167,9 @@ typedef struct {
     int n_steps;              /* time steps per increment (>= 0)                      */
     const double* rho_in_nw;  /* n_incr inlet non-wetting densities (host, caller's)  */
     double rho_out_w;         /* outlet wetting density                               */
+    int per_throat;           /* lbm_run_throat_batch: 1 = rho_in_nw holds one ladder
+                                 per throat, n x n_incr throat-major; 0 = one ladder
+                                 for all throats                                      */
 } lbm_schedule;
 
 /* Per-throat outcome of a batch. */

@@ -68,7 +68,8 @@ class lbm_increment(ctypes.Structure):
 
 class lbm_schedule(ctypes.Structure):
     _fields_ = [("n_incr", ctypes.c_int), ("n_steps", ctypes.c_int),
-                ("rho_in_nw", ctypes.POINTER(ctypes.c_double)), ("rho_out_w", ctypes.c_double)]
+                ("rho_in_nw", ctypes.POINTER(ctypes.c_double)), ("rho_out_w", ctypes.c_double),
+                ("per_throat", ctypes.c_int)]
 
 
 class lbm_throat_result(ctypes.Structure):
@@ -368,12 +369,17 @@ def lbm_throat_geometry(spheres3):
 
 
 def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None):
-    """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict)."""
+    """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
+    rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr)."""
     th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
     n = th.shape[0]
     lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
     sch = lbm_schedule()
-    sch.n_incr = lad.shape[0]
+    if lad.ndim == 2:
+        if lad.shape[0] != n:
+            raise ValueError("per-throat ladders need one row per throat")
+        sch.per_throat = 1
+    sch.n_incr = lad.shape[-1]
     sch.n_steps = int(n_steps)
     sch.rho_in_nw = lad.ctypes.data_as(_DP)
     sch.rho_out_w = float(rho_out_w)

@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(32 * BY, 2)
                         int* __restrict__ counter, const int* __restrict__ tiles, float* arena0, float* arena1,
                         const uint32_t* __restrict__ nbr,
                         const uint32_t* __restrict__ nbr_nw, const uint32_t* __restrict__ adh, Phys P, int n_steps,
-                        int parity, double G, double rho_in_nw, lbm_increment* __restrict__ rows, int incr,
-                        int n_incr) {
+                        int parity, double G, const float* __restrict__ bc_all, const double* __restrict__ rin_all,
+                        int ladder_stride, lbm_increment* __restrict__ rows, int incr, int n_incr) {
     extern __shared__ float smem[];
     __shared__ int s_t;
     __shared__ double red[32];
@@ -136,6 +136,12 @@ __global__ void __launch_bounds__(32 * BY, 2)
         const long long f_off = recs[id].f_off, c_off = recs[id].c_off;
         const int probe = recs[id].probe;
         const int tb = recs[id].tile_begin, tc = recs[id].tile_count;
+        // this throat's reservoir densities of this increment (its own ladder,
+        // or the shared one when ladder_stride is 0)
+        const size_t li = (size_t)id * ladder_stride + incr;
+        Phys Pt = P;
+        Pt.bc = bc_all + 4 * li;
+        const double rho_in_nw = rin_all[li];
         float* buf[2] = {arena0 + f_off, arena1 + f_off};
         const uint32_t* tn = nbr + c_off;
         const uint32_t* tnn = nbr_nw + c_off;
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(32 * BY, 2)
             // the triangle are solid from end to end
             for (int i = 0; i < tc; ++i) {
                 const int packed = __ldg(tiles + tb + i);
-                step_column<BY, LEAD>(buf[cur], buf[cur ^ 1], tn, tnn, ta, g, P, packed & 0xffff, packed >> 16, 0,
+                step_column<BY, LEAD>(buf[cur], buf[cur ^ 1], tn, tnn, ta, g, Pt, packed & 0xffff, packed >> 16, 0,
                                       g.nz, smem);
                 __syncthreads();
             }
@@ -264,7 +270,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                                     const lbm_schedule* sched, lbm_throat_result* results, lbm_increment* rows,
                                     void* stream_ptr) {
     if (!throats || n < 1 || !params || !sched || !results || !rows || !sched->rho_in_nw || sched->n_incr < 1 ||
-        sched->n_steps < 0) {
+        sched->n_steps < 0 || (sched->per_throat != 0 && sched->per_throat != 1)) {
         set_error("lbm_run_throat_batch: NULL argument or empty batch/schedule");
         return LBM_ERR_ARG;
     }
@@ -342,6 +348,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         uint32_t *d_nbr = nullptr, *d_nbr_nw = nullptr, *d_adh = nullptr;
         ThroatRec* d_recs = nullptr;
         int *d_order = nullptr, *d_counter = nullptr, *d_tiles = nullptr;
+        double* d_rin = nullptr;
         lbm_increment* d_rows = nullptr;
         cudaGraphExec_t exec = nullptr;
         cudaStream_t cap = nullptr;
@@ -349,6 +356,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             cudaFree(a0); cudaFree(a1); cudaFree(d_bc); cudaFree(d_mask); cudaFree(d_nbr); cudaFree(d_nbr_nw);
             cudaFree(d_adh); cudaFree(d_recs); cudaFree(d_order); cudaFree(d_counter); cudaFree(d_rows);
             cudaFree(d_tiles);
+            cudaFree(d_rin);
             if (exec) cudaGraphExecDestroy(exec);
             if (cap) cudaStreamDestroy(cap);
         };
@@ -371,7 +379,9 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         BATCH_CUDA(cudaMalloc(&d_tiles, sizeof(int) * std::max<size_t>(1, tiles.size())));
         BATCH_CUDA(cudaMalloc(&d_counter, sizeof(int) * (size_t)I));
         BATCH_CUDA(cudaMalloc(&d_rows, sizeof(lbm_increment) * (size_t)n * I));
-        BATCH_CUDA(cudaMalloc(&d_bc, sizeof(float) * 4 * (size_t)I));
+        const int L = sched->per_throat ? n : 1;  // ladders
+        BATCH_CUDA(cudaMalloc(&d_bc, sizeof(float) * 4 * (size_t)I * L));
+        BATCH_CUDA(cudaMalloc(&d_rin, sizeof(double) * (size_t)I * L));
         BATCH_CUDA(cudaMemsetAsync(a0, 0, sizeof(float) * (size_t)f_tot, stream));
         BATCH_CUDA(cudaMemsetAsync(a1, 0, sizeof(float) * (size_t)f_tot, stream));
         {
@@ -387,20 +397,23 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             if (!tiles.empty())
                 BATCH_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice,
                                            stream));
-            std::vector<float> bc((size_t)4 * I);
-            for (int i = 0; i < I; ++i) {
+            std::vector<float> bc((size_t)4 * I * L);
+            for (size_t i = 0; i < (size_t)I * L; ++i) {
                 bc[4 * i + 0] = (float)params->rho_minor;
                 bc[4 * i + 1] = (float)sched->rho_in_nw[i];
                 bc[4 * i + 2] = (float)sched->rho_out_w;
                 bc[4 * i + 3] = (float)params->rho_minor;
             }
             BATCH_CUDA(cudaMemcpyAsync(d_bc, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice, stream));
+            BATCH_CUDA(cudaMemcpyAsync(d_rin, sched->rho_in_nw, sizeof(double) * (size_t)I * L,
+                                       cudaMemcpyHostToDevice, stream));
             throat_init_kernel<<<n, 256, 0, stream>>>(d_recs, n, a0, d_nbr, d_nbr_nw, (float)params->rho_major,
                                                       (float)params->rho_minor);
             BATCH_CUDA(cudaGetLastError());
             BATCH_CUDA(cudaStreamSynchronize(stream));  // host staging buffers go out of scope
         }
         Phys P;
+        P.bc = d_bc;  // per throat and increment inside the kernel
         for (int s = 0; s < 2; ++s) {
             P.tau[s] = (float)params->tau[s];
             P.omega[s] = (float)(1.0 / params->tau[s]);
@@ -423,13 +436,10 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         BATCH_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t cerr = cudaMemsetAsync(d_counter, 0, sizeof(int) * (size_t)I, cap);
         for (int i = 0; i < I && cerr == cudaSuccess; ++i) {
-            Phys Pi = P;
-            Pi.bc = d_bc + 4 * i;
             const int parity = (int)(((long long)i * sched->n_steps) & 1);
             kern<<<grid, dim3(32, BATCH_BY), smem, cap>>>(d_recs, d_order, n, d_counter + i, d_tiles, a0, a1, d_nbr,
-                                                          d_nbr_nw,
-                                                          d_adh, Pi, sched->n_steps, parity, params->G,
-                                                          sched->rho_in_nw[i], d_rows, i, I);
+                                                          d_nbr_nw, d_adh, P, sched->n_steps, parity, params->G, d_bc,
+                                                          d_rin, sched->per_throat ? I : 0, d_rows, i, I);
             cerr = cudaGetLastError();
         }
         cudaGraph_t graph = nullptr;

@@ -47,6 +47,61 @@ def throat_features(triples: np.ndarray, theta: float) -> np.ndarray:
     return X.astype(np.float32), R
 
 
+def throat_incircle(triples) -> np.ndarray:
+    """Radius (lattice units) of the widest circle in the plane of a throat's
+    three centres, inside their triangle, that stays clear of the three spheres:
+    the constriction the non-wetting fluid has to pass (Sec. 2.2.2), whose entry
+    pressure scales as its inverse (Young-Laplace).  Maximises
+    min_k(|p - c_k| - r_k) over the triangle: a barycentric grid, then two local
+    refinements; 0 where the spheres close the throat."""
+    t = np.asarray(triples, dtype=np.float64).reshape(-1, 3, 4)
+    n = len(t)
+    c, r = t[:, :, :3], t[:, :, 3]
+    e1 = c[:, 1] - c[:, 0]
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    w = c[:, 2] - c[:, 0]
+    e2 = w - (w * e1).sum(axis=1, keepdims=True) * e1
+    e2 /= np.linalg.norm(e2, axis=1, keepdims=True)
+    # centres in the plane's 2-D frame
+    q = np.stack([((c - c[:, :1]) * e1[:, None]).sum(-1), ((c - c[:, :1]) * e2[:, None]).sum(-1)], axis=-1)
+
+    def clearance(pts):  # n x m x 2
+        d = np.linalg.norm(pts[:, :, None, :] - q[:, None, :, :], axis=-1) - r[:, None, :]
+        return d.min(axis=2)
+
+    def search(lam):  # lam: n x m x 3 barycentric weights (>= 0, summing to 1)
+        pts = np.einsum("nmk,nkd->nmd", lam, q)
+        val = clearance(pts)
+        k = val.argmax(axis=1)
+        return lam[np.arange(n), k], val[np.arange(n), k]
+
+    N = 48
+    ij = np.array([(a, b) for a in range(N + 1) for b in range(N + 1 - a)], dtype=np.float64) / N
+    lam0 = np.stack([ij[:, 0], ij[:, 1], 1.0 - ij[:, 0] - ij[:, 1]], axis=-1)
+    best, val = search(np.broadcast_to(lam0, (n,) + lam0.shape))
+    h = 1.0 / N
+    g = np.linspace(-1.0, 1.0, 21)
+    da, db = np.meshgrid(g, g, indexing="ij")
+    for _ in range(2):
+        la = best[:, None, 0] + h * da.ravel()[None]
+        lb = best[:, None, 1] + h * db.ravel()[None]
+        lam = np.stack([la, lb, 1.0 - la - lb], axis=-1)
+        lam = np.clip(lam, 0.0, None)
+        lam /= lam.sum(axis=-1, keepdims=True)
+        best, val = search(lam)
+        h /= 10.0
+    return np.maximum(val, 0.0)
+
+
+def pressure_ladder(r_in, n_incr, lo, hi, rho_major, rho_minor, G):
+    """Per-throat reservoir ladders: n_incr inlet densities per throat whose
+    reservoir pressure differences p_c,res span [lo, hi] / r_in (Eq. 5 at the
+    inlet and outlet layers: p_c,res = (rho_in - rho_major) (1 + G rho_minor) / 3)."""
+    r_in = np.maximum(np.asarray(r_in, dtype=np.float64), 0.5)
+    pc = np.linspace(lo, hi, n_incr)[None, :] / r_in[:, None]
+    return rho_major + 3.0 * pc / (1.0 + G * rho_minor)
+
+
 class ThroatSurrogate:
     """Ensemble surrogate of the per-throat LBM drainage."""
 
@@ -99,7 +154,9 @@ class ThroatSurrogate:
         t_lbm = 0.0
         if fall.any():
             t0 = time.perf_counter()
-            res, _ = lbm_run_throat_batch(np.asarray(triples)[fall], params, rho_in_nw, n_steps, rho_out_w)
+            lad = np.asarray(rho_in_nw)
+            res, _ = lbm_run_throat_batch(np.asarray(triples)[fall], params, lad[fall] if lad.ndim == 2 else lad,
+                                          n_steps, rho_out_w)
             t_lbm = time.perf_counter() - t0
             pce = pce.copy()
             pce[fall] = [r["p_ce"] for r in res]

@@ -121,3 +121,27 @@ def test_batch_equals_single_throats(lbm, orc):
                 else:
                     assert a[k] != a[k]
             assert a["n_interface"] == b["n_interface"]
+
+
+def test_batch_with_per_throat_ladders(lbm):
+    """Each throat its own reservoir ladder (scaled by its constriction radius):
+    the batch equals every throat run alone on its ladder with the same kernel."""
+    from paper_1906_04722_gb300 import surrogate as S
+    spheres = W.sample_spheres(128)
+    throats = W.delaunay_throats(spheres, 5, seed=12)
+    ladders = S.pressure_ladder(S.throat_incircle(throats), 3, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
+    assert len({tuple(np.round(l, 9)) for l in ladders}) == len(throats)  # distinct ladders
+    n_steps = 30
+    res, rows = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, n_steps, W.RHO_MAJOR)
+    for t, sph in enumerate(throats):
+        mask, probe = lbm.lbm_throat_geometry(sph)
+        dom = lbm.Domain(_params(lbm), mask=mask)
+        dom.set_tile(6, 16, 2)  # the batch runs the staged step: same kernel, same rounding
+        single = dom.drainage(ladders[t], n_steps, W.RHO_MAJOR, probe)
+        dom.close()
+        assert single["invaded_at"] == res[t]["invaded_at"]
+        for i in range(ladders.shape[1]):
+            a, b = rows[t][i], single["rows"][i]
+            assert a["rho_in_nw"] == b["rho_in_nw"] == ladders[t][i]
+            for k in ("S_w", "phi_probe", "p_c_res"):
+                assert abs(a[k] - b[k]) <= 1e-12 * max(1.0, abs(b[k])), (t, i, k, a[k], b[k])
