@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-throats", action="store_true")
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=0,
+                    help="population storage: 0 FP32 (the benchmark), 1 FP16 / 2 BF16 deviations")
     ap.add_argument("--drainage", action="store_true",
                     help="instead of the benchmark: the full drainage of the sample (20 increments x 5000 steps), "
                          "one JSON line with the p_c - S_w curve")
@@ -363,11 +365,15 @@ def run_ours(args, rank, world, local):
 
     spheres, box = sample_geometry(args.size)
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
-                             rho_minor=W.RHO_MINOR, reservoirs=True, membrane_layers=3)
+                             rho_minor=W.RHO_MINOR, reservoirs=True, membrane_layers=3, precision=args.precision)
     stream = torch.cuda.Stream()
     dom = lbm.Domain(params, spheres, box, stream=ctypes.c_void_p(stream.cuda_stream))
     mask = dom.mask()
     n_upd, bytes_per_step = update_bytes(mask)
+    if args.precision:
+        # 16-bit storage: 19 pair words read + written and the density pair read
+        # + written per non-solid cell
+        bytes_per_step = n_upd * (19 * 4 * 2 + 8 + 8)
     dom.set_pressure_bc(2.1, W.RHO_MAJOR)
     # the library's autotuner picks the step kernel and its launch shape on this
     # domain (state restored afterwards); untimed
@@ -394,7 +400,10 @@ def run_ours(args, rank, world, local):
     apply_tuned(dom)
 
     kind, _ = dom.step_kernel()
-    if kind == lbm.KERNEL_TMA:
+    if args.precision:
+        by, _, lead = lbm.lbm_get_tile(dom.h)
+        kernel_name = "sc_step16_kernel<%s,%d,%d>" % ("half2" if args.precision == 1 else "bfloat162", by, lead)
+    elif kind == lbm.KERNEL_TMA:
         kernel_name = "sc_step_tma_kernel"
     elif kind == lbm.KERNEL_SPLIT:
         kernel_name = "density_pair_kernel + sc_step_split_kernel (one step)"
@@ -460,7 +469,8 @@ def run_ours(args, rank, world, local):
     throats = None if args.no_throats else throat_bench(lbm, W, args.throat_steps, rank, world, sync, tmax)
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "f16 deviations, f32 math", 2: "bf16 deviations, f32 math"}[args.precision],
+           "data": "synthetic",
            "config": {"workload": f"sample{args.size}: {args.size}^3, {len(spheres)} RSA spheres r~U[10,14], "
                                   "reservoirs + 3 membrane layers, FP32 populations, one fused step per launch",
                       "fluid_cells": n_upd, "global_batch": world, "seq_len": 0,
