@@ -480,7 +480,7 @@ def run_ours(args, rank, world, local):
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": read_traffic(kernel_name), "peak_kind": peak_kind,
                         "kernel": kernel_name, "algorithmic_bytes_per_launch": bytes_per_step},
-           "gpu_launches": args.steps,
+           "gpu_launches": args.steps * (2 if kind == lbm.KERNEL_SPLIT and not args.precision else 1),
            "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "step": f"set_pressure_bc + {E2E_SUBSTEPS} time steps + lbm_measure; domain creation "
                            "from the host sphere list inside the timed region"},
