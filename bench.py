@@ -127,26 +127,31 @@ def read_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-STEP_SOURCES = ("lbm_step.cu", "lbm_step_core.cuh", "lbm_step_tma.cu", "lbm_device.cuh", "lbm_internal.h")
+# the sources each step kernel is compiled from: a traffic record holds while they are unchanged
+KERNEL_SOURCES = {
+    "sc_step_kernel": ("lbm_step.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
+    "sc_step_tma_kernel": ("lbm_step_tma.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
+}
 
 
-def kernel_hash():
+def kernel_hash(kernel_name="sc_step_kernel"):
+    key = "sc_step_tma_kernel" if kernel_name.startswith("sc_step_tma") else "sc_step_kernel"
     h = hashlib.sha256()
-    for f in STEP_SOURCES:
+    for f in KERNEL_SOURCES[key]:
         h.update(open(os.path.join(ROOT, "paper_1906_04722_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def read_traffic(kernel_name):
     """DRAM bytes per launch of the given step kernel from the committed ncu
-    summary, valid only while the step kernel sources are unchanged."""
+    summary, valid only while that kernel's sources are unchanged."""
     p = os.path.join(ROOT, "profiles", "sc_step_sample192_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
         k = d.get("kernels", {}).get(kernel_name)
-        if k and k.get("kernel_hash") == kernel_hash():
+        if k and k.get("kernel_hash") == kernel_hash(kernel_name):
             return float(k["dram_bytes_per_launch"])
     except Exception:
         pass
