@@ -170,7 +170,21 @@ typedef struct {
     int per_throat;           /* lbm_run_throat_batch: 1 = rho_in_nw holds one ladder
                                  per throat, n x n_incr throat-major; 0 = one ladder
                                  for all throats                                      */
+    int batch_form;           /* lbm_run_throat_batch: LBM_BATCH_AUTO, _PERSISTENT or
+                                 _PER_STEP (below)                                    */
 } lbm_schedule;
+
+/* Forms of lbm_run_throat_batch.  PERSISTENT: one launch per increment, a CTA
+ * takes a whole throat off a work counter and runs all of the increment's steps
+ * on it (no grid-wide synchronisation; best when the throats outnumber the CTAs
+ * that fit on the GPU).  PER_STEP: one launch per time step over a work list of
+ * every throat's active tiles and z segments, so that a few large throats still
+ * fill the GPU.  Both give bit-identical rows.  AUTO is PER_STEP, which was
+ * faster at every batch size measured (about 1.2x at 1024 throats, 3-4x at a
+ * hundred). */
+#define LBM_BATCH_AUTO 0
+#define LBM_BATCH_PERSISTENT 1
+#define LBM_BATCH_PER_STEP 2
 
 /* Per-throat outcome of a batch. */
 typedef struct {

@@ -69,7 +69,7 @@ class lbm_increment(ctypes.Structure):
 class lbm_schedule(ctypes.Structure):
     _fields_ = [("n_incr", ctypes.c_int), ("n_steps", ctypes.c_int),
                 ("rho_in_nw", ctypes.POINTER(ctypes.c_double)), ("rho_out_w", ctypes.c_double),
-                ("per_throat", ctypes.c_int)]
+                ("per_throat", ctypes.c_int), ("batch_form", ctypes.c_int)]
 
 
 class lbm_throat_result(ctypes.Structure):
@@ -329,6 +329,9 @@ KERNEL_STAGED = 0
 KERNEL_TMA = 1
 KERNEL_SPLIT = 2
 KERNEL_STAGED2 = 3
+BATCH_AUTO = 0
+BATCH_PERSISTENT = 1
+BATCH_PER_STEP = 2
 
 
 def lbm_set_step_kernel(h, kind: int, lz: int = 0):
@@ -368,9 +371,11 @@ def lbm_throat_geometry(spheres3):
     return mask, tuple(probe)
 
 
-def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None):
+def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None,
+                         form: int = 0):
     """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
-    rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr)."""
+    rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr).
+    form: BATCH_AUTO, BATCH_PERSISTENT or BATCH_PER_STEP."""
     th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
     n = th.shape[0]
     lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
@@ -383,6 +388,9 @@ def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, r
     sch.n_steps = int(n_steps)
     sch.rho_in_nw = lad.ctypes.data_as(_DP)
     sch.rho_out_w = float(rho_out_w)
+    if form not in (BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP):
+        raise ValueError("form must be BATCH_AUTO, BATCH_PERSISTENT or BATCH_PER_STEP")
+    sch.batch_form = int(form)
     res = (lbm_throat_result * n)()
     rows = (lbm_increment * (n * sch.n_incr))()
     _check(load().lbm_run_throat_batch(th.ctypes.data_as(_DP), n, ctypes.byref(params), ctypes.byref(sch), res, rows,

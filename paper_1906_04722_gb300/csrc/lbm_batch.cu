@@ -12,6 +12,13 @@
 // CTA barrier between steps as the only synchronisation, then measures the throat
 // (FP64 CTA reduction) and reads the probe cell.  One launch per increment; the
 // launches of all increments are captured in one CUDA graph.
+//
+// A batch of few throats leaves most SMs idle in that form and waits on its
+// largest throat.  The per-step form spreads every throat over many CTAs
+// instead: one launch per time step over a work list of (throat, active tile,
+// z segment) items, the kernel boundary ordering the steps, then one
+// measurement launch with a CTA per throat.  One increment is captured as a
+// graph and relaunched; the increment index lives in device memory.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -164,6 +171,49 @@ __global__ void __launch_bounds__(32 * BY, 2)
     }
 }
 
+// One time step of the work item blockIdx.x (throat, tile, z range) of the batch;
+// fin / fout are the population arenas of this step.
+template <int BY, int LEAD>
+__global__ void __launch_bounds__(32 * BY, 2)
+    throat_item_step_kernel(const ThroatRec* __restrict__ recs, const int4* __restrict__ items,
+                            const float* __restrict__ fin, float* __restrict__ fout,
+                            const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
+                            const uint32_t* __restrict__ adh, Phys P, const float* __restrict__ bc_all,
+                            int ladder_stride, const int* __restrict__ incr_now) {
+    extern __shared__ float smem[];
+    const int4 it = items[blockIdx.x];  // (throat, tx | ty << 16, z0, z1)
+    const int id = it.x;
+    const Geom g = recs[id].g;
+    const long long f_off = recs[id].f_off, c_off = recs[id].c_off;
+    Phys Pt = P;
+    Pt.bc = bc_all + 4 * ((size_t)id * ladder_stride + *incr_now);
+    step_column<BY, LEAD>(fin + f_off, fout + f_off, nbr + c_off, nbr_nw + c_off, adh + c_off, g, Pt, it.y & 0xffff,
+                          it.y >> 16, it.z, it.w, smem);
+}
+
+// Measurements of throat blockIdx.x at the end of increment *incr_now, then
+// (last CTA to finish) the increment index moves on.
+__global__ void __launch_bounds__(BATCH_THREADS)
+    throat_item_measure_kernel(const ThroatRec* __restrict__ recs, int n, const float* __restrict__ f,
+                               const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw, double G,
+                               const double* __restrict__ rin_all, int ladder_stride, lbm_increment* __restrict__ rows,
+                               int n_incr, int* incr_now, int* done) {
+    __shared__ double red[32];
+    const int id = blockIdx.x;
+    const int incr = *incr_now;
+    const Geom g = recs[id].g;
+    measure_throat(f + recs[id].f_off, nbr + recs[id].c_off, nbr_nw + recs[id].c_off, g, G, recs[id].probe,
+                   rin_all[(size_t)id * ladder_stride + incr], red, rows + (size_t)id * n_incr + incr);
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1) == n - 1) {  // every CTA has read the index
+            *done = 0;
+            *incr_now = incr + 1;
+        }
+    }
+}
+
 // Rest-equilibrium start of every throat: wetting fluid (rho_major, rho_minor)
 // everywhere, (rho_minor, rho_major) on the inlet layer; stored so that the first
 // pull yields exactly that (as init_kernel).
@@ -270,7 +320,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                                     const lbm_schedule* sched, lbm_throat_result* results, lbm_increment* rows,
                                     void* stream_ptr) {
     if (!throats || n < 1 || !params || !sched || !results || !rows || !sched->rho_in_nw || sched->n_incr < 1 ||
-        sched->n_steps < 0 || (sched->per_throat != 0 && sched->per_throat != 1)) {
+        sched->n_steps < 0 || (sched->per_throat != 0 && sched->per_throat != 1) || sched->batch_form < 0 ||
+        sched->batch_form > LBM_BATCH_PER_STEP) {
         set_error("lbm_run_throat_batch: NULL argument or empty batch/schedule");
         return LBM_ERR_ARG;
     }
@@ -347,7 +398,9 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         uint8_t* d_mask = nullptr;
         uint32_t *d_nbr = nullptr, *d_nbr_nw = nullptr, *d_adh = nullptr;
         ThroatRec* d_recs = nullptr;
-        int *d_order = nullptr, *d_counter = nullptr, *d_tiles = nullptr;
+        int *d_order = nullptr, *d_counter = nullptr, *d_tiles = nullptr, *d_incr = nullptr;
+        int4* d_items = nullptr;
+        cudaGraphExec_t exec2[2] = {nullptr, nullptr};
         double* d_rin = nullptr;
         lbm_increment* d_rows = nullptr;
         cudaGraphExec_t exec = nullptr;
@@ -357,7 +410,11 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             cudaFree(d_adh); cudaFree(d_recs); cudaFree(d_order); cudaFree(d_counter); cudaFree(d_rows);
             cudaFree(d_tiles);
             cudaFree(d_rin);
+            cudaFree(d_incr);
+            cudaFree(d_items);
             if (exec) cudaGraphExecDestroy(exec);
+            for (cudaGraphExec_t& e : exec2)
+                if (e) cudaGraphExecDestroy(e);
             if (cap) cudaStreamDestroy(cap);
         };
 #define BATCH_CUDA(call)                               \
@@ -430,9 +487,68 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         BATCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem));
         const int grid = std::max(1, std::min(n, sms * std::max(1, per_sm)));
-
-        // one launch per increment, all captured in one graph
+        const int form = sched->batch_form == LBM_BATCH_PERSISTENT ? LBM_BATCH_PERSISTENT : LBM_BATCH_PER_STEP;
         BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+
+        if (form == LBM_BATCH_PER_STEP) {
+            // work list: every active tile of every throat, its column cut into
+            // z segments of at most 32 planes (largest throats first)
+            std::vector<int4> items;
+            for (int t : order) {
+                const int nz = recs[t].g.nz, nseg = (nz + 31) / 32;
+                for (int i = 0; i < recs[t].tile_count; ++i)
+                    for (int sgi = 0; sgi < nseg; ++sgi)
+                        items.push_back(make_int4(t, tiles[(size_t)recs[t].tile_begin + i], (int)((long long)nz * sgi / nseg),
+                                                  (int)((long long)nz * (sgi + 1) / nseg)));
+            }
+            auto ikern = throat_item_step_kernel<BATCH_BY, BATCH_LEAD>;
+            BATCH_CUDA(cudaFuncSetAttribute(ikern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            BATCH_CUDA(cudaMalloc(&d_items, sizeof(int4) * std::max<size_t>(1, items.size())));
+            BATCH_CUDA(cudaMalloc(&d_incr, sizeof(int) * 2));  // increment index, finished-CTA count
+            BATCH_CUDA(cudaMemsetAsync(d_incr, 0, sizeof(int) * 2, stream));
+            if (!items.empty())
+                BATCH_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                                           stream));
+            BATCH_CUDA(cudaStreamSynchronize(stream));
+            // one increment per graph; with an odd number of steps the arenas
+            // swap roles from one increment to the next: two graphs
+            const int n_graphs = (sched->n_steps & 1) ? 2 : 1;
+            for (int gi = 0; gi < n_graphs; ++gi) {
+                BATCH_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+                cudaError_t cerr = cudaSuccess;
+                for (int st = 0; st < sched->n_steps && cerr == cudaSuccess && !items.empty(); ++st) {
+                    const int c = (gi + st) & 1;
+                    ikern<<<(unsigned)items.size(), dim3(32, BATCH_BY), smem, cap>>>(
+                        d_recs, d_items, c ? a1 : a0, c ? a0 : a1, d_nbr, d_nbr_nw, d_adh, P, d_bc,
+                        sched->per_throat ? I : 0, d_incr);
+                    cerr = cudaGetLastError();
+                }
+                if (cerr == cudaSuccess) {
+                    const int c = (gi + sched->n_steps) & 1;
+                    throat_item_measure_kernel<<<n, dim3(32, BATCH_BY), 0, cap>>>(
+                        d_recs, n, c ? a1 : a0, d_nbr, d_nbr_nw, params->G, d_rin, sched->per_throat ? I : 0, d_rows,
+                        I, d_incr, d_incr + 1);
+                    cerr = cudaGetLastError();
+                }
+                cudaGraph_t graph = nullptr;
+                cudaError_t eend = cudaStreamEndCapture(cap, &graph);
+                if (cerr != cudaSuccess || eend != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    cleanup();
+                    return fail_cuda(cerr != cudaSuccess ? cerr : eend, "capture of the throat batch");
+                }
+                cudaError_t einst = cudaGraphInstantiate(&exec2[gi], graph, 0);
+                cudaGraphDestroy(graph);
+                if (einst != cudaSuccess) {
+                    exec2[gi] = nullptr;
+                    cleanup();
+                    return fail_cuda(einst, "cudaGraphInstantiate");
+                }
+            }
+            for (int i = 0; i < I; ++i)
+                BATCH_CUDA(cudaGraphLaunch(exec2[(int)(((long long)i * sched->n_steps) & 1) % n_graphs], stream));
+        } else {
+        // one launch per increment, all captured in one graph
         BATCH_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t cerr = cudaMemsetAsync(d_counter, 0, sizeof(int) * (size_t)I, cap);
         for (int i = 0; i < I && cerr == cudaSuccess; ++i) {
@@ -457,6 +573,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             return fail_cuda(einst, "cudaGraphInstantiate");
         }
         BATCH_CUDA(cudaGraphLaunch(exec, stream));
+        }
         BATCH_CUDA(cudaMemcpyAsync(rows, d_rows, sizeof(lbm_increment) * (size_t)n * I, cudaMemcpyDeviceToHost,
                                    stream));
         BATCH_CUDA(cudaStreamSynchronize(stream));

@@ -145,3 +145,29 @@ def test_batch_with_per_throat_ladders(lbm):
             assert a["rho_in_nw"] == b["rho_in_nw"] == ladders[t][i]
             for k in ("S_w", "phi_probe", "p_c_res"):
                 assert abs(a[k] - b[k]) <= 1e-12 * max(1.0, abs(b[k])), (t, i, k, a[k], b[k])
+
+
+@pytest.mark.parametrize("n_steps", [25, 0])
+def test_batch_forms_agree(lbm, n_steps):
+    """The persistent form (a CTA per throat per increment) and the per-step form
+    (a launch per step over every throat's tiles and z segments) run the same
+    step on the same cells: their rows are equal bit for bit.  An odd number of
+    steps swaps the arenas from one increment to the next (two graphs in the
+    per-step form); per-throat ladders select each throat's reservoir densities."""
+    from paper_1906_04722_gb300 import surrogate as S
+    spheres = W.sample_spheres(128)
+    throats = W.delaunay_throats(spheres, 9, seed=13)
+    ladders = S.pressure_ladder(S.throat_incircle(throats), 4, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
+    out = {}
+    for form in (lbm.BATCH_PERSISTENT, lbm.BATCH_PER_STEP):
+        out[form] = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, n_steps, W.RHO_MAJOR, form=form)
+    (ra, rowsa), (rb, rowsb) = out[lbm.BATCH_PERSISTENT], out[lbm.BATCH_PER_STEP]
+    for t in range(len(throats)):
+        assert ra[t]["invaded_at"] == rb[t]["invaded_at"]
+        assert ra[t]["p_ce"] == rb[t]["p_ce"] or (math.isnan(ra[t]["p_ce"]) and math.isnan(rb[t]["p_ce"]))
+        for i in range(ladders.shape[1]):
+            a, b = rowsa[t][i], rowsb[t][i]
+            assert a["rho_in_nw"] == b["rho_in_nw"] == ladders[t][i]
+            for k in ("S_w", "phi_probe", "p_c_res", "p_c", "p_w", "p_nw"):
+                assert a[k] == b[k] or (a[k] != a[k] and b[k] != b[k]), (t, i, k, a[k], b[k])
+            assert a["n_interface"] == b["n_interface"]

@@ -88,3 +88,20 @@ def test_training_reduces_loss_and_ensemble_spread(lbm):
     members = np.stack([sur.forward(m, Xt) for m in range(3)])
     assert np.allclose(mean, members.mean(axis=0), atol=1e-5)
     assert np.allclose(spread, members.std(axis=0, ddof=1), atol=1e-5)
+
+
+def test_members_train_independently(lbm):
+    """All members step together, one launch per layer: member 0 of a two-member
+    ensemble ends bit for bit where the same member trained alone ends (same
+    initialisation seed, same shuffle seed)."""
+    rng = np.random.default_rng(11)
+    X = rng.uniform(-1, 1, (700, 7)).astype(np.float32)
+    T = np.stack([np.sin(X[:, 0]), X[:, 1] * X[:, 2]], axis=1)
+    alone = lbm.Surrogate(7, 2, n_hidden=96, n_layers=2, n_members=1, half=0, seed=21)
+    pair = lbm.Surrogate(7, 2, n_hidden=96, n_layers=2, n_members=2, half=0, seed=21)
+    assert np.array_equal(alone.get_params(0), pair.get_params(0))
+    la = alone.train(X, T, epochs=3, batch=128, lr=1e-3, seed=5)
+    lp = pair.train(X, T, epochs=3, batch=128, lr=1e-3, seed=5)
+    assert np.array_equal(alone.get_params(0), pair.get_params(0))
+    assert not np.array_equal(pair.get_params(0), pair.get_params(1))
+    assert np.allclose(la[0], lp[0], rtol=1e-12, atol=0)
