@@ -296,14 +296,18 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
     t_batch = tmax(time.perf_counter() - t0)
     truth = np.array([r["p_ce"] for r in res_ref])
     out["batched"] = world * n / t_batch
-    out["batch_form"] = "one launch per time step over every throat's tiles and z segments"
-    # the same batch in the persistent form (a CTA per throat per increment), for context
-    sync()
-    t0 = time.perf_counter()
-    res_p, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR, form=lbm.BATCH_PERSISTENT)
-    sync()
-    out["batched_persistent_form"] = world * n / tmax(time.perf_counter() - t0)
-    out["forms_agree"] = bool(np.array_equal(truth, np.array([r["p_ce"] for r in res_p]), equal_nan=True))
+    out["batch_form"] = "cell list: a density launch and a step launch per time step over every non-solid cell"
+    # the same batch in the other two forms, for context
+    out["other_forms"] = {}
+    agree = True
+    for form, name in ((lbm.BATCH_PER_STEP, "tiles_per_step"), (lbm.BATCH_PERSISTENT, "persistent")):
+        sync()
+        t0 = time.perf_counter()
+        res_f, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR, form=form)
+        sync()
+        out["other_forms"][name] = world * n / tmax(time.perf_counter() - t0)
+        agree &= bool(np.array_equal(truth, np.array([r["p_ce"] for r in res_f]), equal_nan=True))
+    out["forms_agree"] = agree
     # plain per-throat loop on every 32nd throat
     sub = tri[::32]
     sync()

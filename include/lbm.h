@@ -179,12 +179,15 @@ typedef struct {
  * on it (no grid-wide synchronisation; best when the throats outnumber the CTAs
  * that fit on the GPU).  PER_STEP: one launch per time step over a work list of
  * every throat's active tiles and z segments, so that a few large throats still
- * fill the GPU.  Both give bit-identical rows.  AUTO is PER_STEP, which was
- * faster at every batch size measured (about 1.2x at 1024 throats, 3-4x at a
- * hundred). */
+ * fill the GPU.  CELLS: two launches per time step over a list of every
+ * throat's non-solid cells, one thread per cell (a density pass, then the step
+ * reading the neighbour densities it stored), so that the grain inside the
+ * throat boxes costs neither lanes nor traffic.  All forms give bit-identical
+ * rows.  AUTO is CELLS. */
 #define LBM_BATCH_AUTO 0
 #define LBM_BATCH_PERSISTENT 1
 #define LBM_BATCH_PER_STEP 2
+#define LBM_BATCH_CELLS 3
 
 /* Per-throat outcome of a batch. */
 typedef struct {

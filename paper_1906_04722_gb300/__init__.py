@@ -332,6 +332,7 @@ KERNEL_STAGED2 = 3
 BATCH_AUTO = 0
 BATCH_PERSISTENT = 1
 BATCH_PER_STEP = 2
+BATCH_CELLS = 3
 
 
 def lbm_set_step_kernel(h, kind: int, lz: int = 0):
@@ -375,7 +376,7 @@ def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, r
                          form: int = 0):
     """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
     rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr).
-    form: BATCH_AUTO, BATCH_PERSISTENT or BATCH_PER_STEP."""
+    form: BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP or BATCH_CELLS."""
     th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
     n = th.shape[0]
     lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
@@ -388,8 +389,8 @@ def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, r
     sch.n_steps = int(n_steps)
     sch.rho_in_nw = lad.ctypes.data_as(_DP)
     sch.rho_out_w = float(rho_out_w)
-    if form not in (BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP):
-        raise ValueError("form must be BATCH_AUTO, BATCH_PERSISTENT or BATCH_PER_STEP")
+    if form not in (BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS):
+        raise ValueError("form must be BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP or BATCH_CELLS")
     sch.batch_form = int(form)
     res = (lbm_throat_result * n)()
     rows = (lbm_increment * (n * sch.n_incr))()

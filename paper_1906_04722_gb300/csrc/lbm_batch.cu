@@ -20,6 +20,7 @@
 // measurement launch with a CTA per throat.  One increment is captured as a
 // graph and relaunched; the increment index lives in device memory.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -214,6 +215,80 @@ __global__ void __launch_bounds__(BATCH_THREADS)
     }
 }
 
+// The cell-list form.  A list item is (throat, x | y << 10 | z << 20) of a
+// non-solid cell of that throat's box; boxes are at most 512 cells along an axis.
+struct CellAt {
+    int id, x, y, z, cell;
+};
+__device__ __forceinline__ CellAt decode_cell(int2 it, const Geom& g) {
+    CellAt c;
+    c.id = it.x;
+    c.x = it.y & 1023;
+    c.y = (it.y >> 10) & 1023;
+    c.z = it.y >> 20;
+    c.cell = c.z * g.nxy + c.y * g.nx + c.x;
+    return c;
+}
+
+constexpr int CELL_THREADS = 256;
+
+// (rho_w, rho_nw) of every listed cell (Eq. 2 after the pull of Eq. 1), summed
+// in four interleaved partial sums as the staged kernel sums its density ring.
+// Cells off the list (grain) keep the 0 they were given.
+__global__ void __launch_bounds__(CELL_THREADS)
+    throat_cell_density_kernel(const ThroatRec* __restrict__ recs, const int2* __restrict__ items, int n_items,
+                               const float* __restrict__ fin, const uint32_t* __restrict__ nbr,
+                               const uint32_t* __restrict__ nbr_nw, float2* __restrict__ rho2) {
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i >= n_items) return;
+    const int2 it = __ldg(items + i);
+    const ThroatRec& r = recs[it.x];
+    const Geom g = r.g;
+    const CellAt c = decode_cell(it, g);
+    const long long c_off = r.c_off;
+    const uint32_t w = __ldg(nbr + c_off + c.cell);
+    const Column col = make_column(c.x, c.y, g);
+    float unused[2][Q];
+    float rw, rn;
+    pull_known<false, true>(fin + r.f_off, nbr_nw + c_off, g, col, c.z, c.cell, w, unused, rw, rn);
+    rho2[c_off + c.cell] = make_float2(rw, rn);
+}
+
+// One time step of every listed cell: pull, neighbour densities from the field
+// of the density pass (0 beyond the closed box), collide_core, store.
+__global__ void __launch_bounds__(CELL_THREADS, 2)
+    throat_cell_step_kernel(const ThroatRec* __restrict__ recs, const int2* __restrict__ items, int n_items,
+                            const float* __restrict__ fin, float* __restrict__ fout, const float2* __restrict__ rho2,
+                            const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
+                            const uint32_t* __restrict__ adh, Phys P, const float* __restrict__ bc_all,
+                            int ladder_stride, const int* __restrict__ incr_now) {
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i >= n_items) return;
+    const int2 it = __ldg(items + i);
+    const ThroatRec& r = recs[it.x];
+    const Geom g = r.g;
+    const CellAt c = decode_cell(it, g);
+    const long long c_off = r.c_off, f_off = r.f_off;
+    const uint32_t w = __ldg(nbr + c_off + c.cell);
+    const Column col = make_column(c.x, c.y, g);
+    float f[2][Q];
+    float rw, rn;
+    pull_known<true, false>(fin + f_off, nbr_nw + c_off, g, col, c.z, c.cell, w, f, rw, rn);
+    const uint32_t a = (w & BIT_ADH) ? __ldg(adh + c_off + c.cell) : 0u;
+    const float2* rh = rho2 + c_off;
+    auto rho_at = [&](int k) {
+        const int nx = c.x + EX(k), ny = c.y + EY(k), nz = c.z + EZ(k);
+        if (nx < 0 || nx >= g.nx || ny < 0 || ny >= g.ny || nz < 0 || nz >= g.nz) return make_float2(0.f, 0.f);
+        return __ldg(rh + c.cell + EX(k) + EY(k) * g.nx + EZ(k) * g.nxy);
+    };
+    Phys Pt = P;
+    Pt.bc = bc_all + 4 * ((size_t)it.x * ladder_stride + *incr_now);
+    float* __restrict__ out0 = fout + f_off + c.cell;
+    float* __restrict__ out1 = out0 + (size_t)Q * g.plane;
+    collide_core(f, w, a, Pt, rho_at,
+                 [&](int s, int k, float v) { (s == 0 ? out0 : out1)[(size_t)k * g.plane] = v; });
+}
+
 // Rest-equilibrium start of every throat: wetting fluid (rho_major, rho_minor)
 // everywhere, (rho_minor, rho_major) on the inlet layer; stored so that the first
 // pull yields exactly that (as init_kernel).
@@ -321,7 +396,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                                     void* stream_ptr) {
     if (!throats || n < 1 || !params || !sched || !results || !rows || !sched->rho_in_nw || sched->n_incr < 1 ||
         sched->n_steps < 0 || (sched->per_throat != 0 && sched->per_throat != 1) || sched->batch_form < 0 ||
-        sched->batch_form > LBM_BATCH_PER_STEP) {
+        sched->batch_form > LBM_BATCH_CELLS) {
         set_error("lbm_run_throat_batch: NULL argument or empty batch/schedule");
         return LBM_ERR_ARG;
     }
@@ -400,6 +475,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         ThroatRec* d_recs = nullptr;
         int *d_order = nullptr, *d_counter = nullptr, *d_tiles = nullptr, *d_incr = nullptr;
         int4* d_items = nullptr;
+        int2* d_cells = nullptr;
+        float2* d_rho2 = nullptr;
         cudaGraphExec_t exec2[2] = {nullptr, nullptr};
         double* d_rin = nullptr;
         lbm_increment* d_rows = nullptr;
@@ -412,6 +489,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             cudaFree(d_rin);
             cudaFree(d_incr);
             cudaFree(d_items);
+            cudaFree(d_cells);
+            cudaFree(d_rho2);
             if (exec) cudaGraphExecDestroy(exec);
             for (cudaGraphExec_t& e : exec2)
                 if (e) cudaGraphExecDestroy(e);
@@ -487,10 +566,78 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         BATCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem));
         const int grid = std::max(1, std::min(n, sms * std::max(1, per_sm)));
-        const int form = sched->batch_form == LBM_BATCH_PERSISTENT ? LBM_BATCH_PERSISTENT : LBM_BATCH_PER_STEP;
+        const int form = sched->batch_form == LBM_BATCH_AUTO ? LBM_BATCH_CELLS : sched->batch_form;
         BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
 
-        if (form == LBM_BATCH_PER_STEP) {
+        if (form == LBM_BATCH_CELLS) {
+            // every non-solid cell of every throat (largest throats first,
+            // memory order inside a throat)
+            std::vector<int2> cells;
+            for (int t : order) {
+                const Geom& g = recs[t].g;
+                for (int z = 0; z < g.nz; ++z)
+                    for (int y = 0; y < g.ny; ++y)
+                        for (int x = 0; x < g.nx; ++x)
+                            if (!(masks[t][(size_t)z * g.nxy + (size_t)y * g.nx + x] & LBM_MASK_SOLID))
+                                cells.push_back(make_int2(t, x | (y << 10) | (z << 20)));
+            }
+            if (cells.size() > (size_t)INT_MAX) {
+                cleanup();
+                set_error("lbm_run_throat_batch: too many cells for the cell-list form");
+                return LBM_ERR_ARG;
+            }
+            const int n_cells = (int)cells.size();
+            BATCH_CUDA(cudaMalloc(&d_cells, sizeof(int2) * std::max<size_t>(1, cells.size())));
+            BATCH_CUDA(cudaMalloc(&d_rho2, sizeof(float2) * (size_t)c_tot));
+            BATCH_CUDA(cudaMalloc(&d_incr, sizeof(int) * 2));
+            BATCH_CUDA(cudaMemsetAsync(d_incr, 0, sizeof(int) * 2, stream));
+            BATCH_CUDA(cudaMemsetAsync(d_rho2, 0, sizeof(float2) * (size_t)c_tot, stream));
+            if (n_cells)
+                BATCH_CUDA(cudaMemcpyAsync(d_cells, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice,
+                                           stream));
+            BATCH_CUDA(cudaStreamSynchronize(stream));
+            const unsigned blocks = (unsigned)((n_cells + CELL_THREADS - 1) / CELL_THREADS);
+            const int n_graphs = (sched->n_steps & 1) ? 2 : 1;
+            for (int gi = 0; gi < n_graphs; ++gi) {
+                BATCH_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+                cudaError_t cerr = cudaSuccess;
+                for (int st = 0; st < sched->n_steps && cerr == cudaSuccess && n_cells; ++st) {
+                    const int c = (gi + st) & 1;
+                    const float* fin = c ? a1 : a0;
+                    throat_cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_recs, d_cells, n_cells, fin, d_nbr,
+                                                                                d_nbr_nw, d_rho2);
+                    cerr = cudaGetLastError();
+                    if (cerr != cudaSuccess) break;
+                    throat_cell_step_kernel<<<blocks, CELL_THREADS, 0, cap>>>(
+                        d_recs, d_cells, n_cells, fin, c ? a0 : a1, d_rho2, d_nbr, d_nbr_nw, d_adh, P, d_bc,
+                        sched->per_throat ? I : 0, d_incr);
+                    cerr = cudaGetLastError();
+                }
+                if (cerr == cudaSuccess) {
+                    const int c = (gi + sched->n_steps) & 1;
+                    throat_item_measure_kernel<<<n, dim3(32, BATCH_BY), 0, cap>>>(
+                        d_recs, n, c ? a1 : a0, d_nbr, d_nbr_nw, params->G, d_rin, sched->per_throat ? I : 0, d_rows,
+                        I, d_incr, d_incr + 1);
+                    cerr = cudaGetLastError();
+                }
+                cudaGraph_t graph = nullptr;
+                cudaError_t eend = cudaStreamEndCapture(cap, &graph);
+                if (cerr != cudaSuccess || eend != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    cleanup();
+                    return fail_cuda(cerr != cudaSuccess ? cerr : eend, "capture of the throat batch");
+                }
+                cudaError_t einst = cudaGraphInstantiate(&exec2[gi], graph, 0);
+                cudaGraphDestroy(graph);
+                if (einst != cudaSuccess) {
+                    exec2[gi] = nullptr;
+                    cleanup();
+                    return fail_cuda(einst, "cudaGraphInstantiate");
+                }
+            }
+            for (int i = 0; i < I; ++i)
+                BATCH_CUDA(cudaGraphLaunch(exec2[(int)(((long long)i * sched->n_steps) & 1) % n_graphs], stream));
+        } else if (form == LBM_BATCH_PER_STEP) {
             // work list: every active tile of every throat, its column cut into
             // z segments of at most 32 planes (largest throats first)
             std::vector<int4> items;

@@ -149,20 +149,28 @@ def test_batch_with_per_throat_ladders(lbm):
 
 @pytest.mark.parametrize("n_steps", [25, 0])
 def test_batch_forms_agree(lbm, n_steps):
-    """The persistent form (a CTA per throat per increment) and the per-step form
-    (a launch per step over every throat's tiles and z segments) run the same
-    step on the same cells: their rows are equal bit for bit.  An odd number of
-    steps swaps the arenas from one increment to the next (two graphs in the
-    per-step form); per-throat ladders select each throat's reservoir densities."""
+    """The persistent form (a CTA per throat per increment), the per-step form
+    (a launch per step over every throat's tiles and z segments) and the
+    cell-list form (a density launch and a step launch per time step over every
+    non-solid cell) run the same arithmetic on the same cells: their rows are
+    equal bit for bit.  An odd number of steps swaps the arenas from one
+    increment to the next (two graphs in the per-step forms); per-throat ladders
+    select each throat's reservoir densities."""
     from paper_1906_04722_gb300 import surrogate as S
     spheres = W.sample_spheres(128)
     throats = W.delaunay_throats(spheres, 9, seed=13)
     ladders = S.pressure_ladder(S.throat_incircle(throats), 4, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
     out = {}
-    for form in (lbm.BATCH_PERSISTENT, lbm.BATCH_PER_STEP):
+    for form in (lbm.BATCH_PERSISTENT, lbm.BATCH_PER_STEP, lbm.BATCH_CELLS):
         out[form] = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, n_steps, W.RHO_MAJOR, form=form)
-    (ra, rowsa), (rb, rowsb) = out[lbm.BATCH_PERSISTENT], out[lbm.BATCH_PER_STEP]
-    for t in range(len(throats)):
+    ra, rowsa = out[lbm.BATCH_PERSISTENT]
+    for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS):
+        rb, rowsb = out[form]
+        _rows_equal(ra, rowsa, rb, rowsb, ladders)
+
+
+def _rows_equal(ra, rowsa, rb, rowsb, ladders):
+    for t in range(len(ra)):
         assert ra[t]["invaded_at"] == rb[t]["invaded_at"]
         assert ra[t]["p_ce"] == rb[t]["p_ce"] or (math.isnan(ra[t]["p_ce"]) and math.isnan(rb[t]["p_ce"]))
         for i in range(ladders.shape[1]):
