@@ -68,6 +68,11 @@ def parse():
                          "or staged2:BY:LZ:2")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
+    ap.add_argument("--throat-batch", choices=["cells", "tiles", "persistent"], default="",
+                    help="instead of the benchmark: one batch of the 1024 held-out throats in the given form "
+                         "(32 increments), and the same batch with no time steps (the set-up cost)")
+    ap.add_argument("--throat-count", type=int, default=1024,
+                    help="with --throat-batch: every (1024 // count)-th throat of the packing (profiling captures)")
     ap.add_argument("--size", type=int, default=192,
                     help="box edge of the drainage sample (192 = the benchmark workload; smaller edges "
                          "scale the sphere count with the volume, for profiling captures)")
@@ -296,7 +301,8 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
     t_batch = tmax(time.perf_counter() - t0)
     truth = np.array([r["p_ce"] for r in res_ref])
     out["batched"] = world * n / t_batch
-    out["batch_form"] = "cell list: a density launch and a step launch per time step over every non-solid cell"
+    out["batch_form"] = ("cell list: compact storage of every non-solid cell, a density launch and a push-streaming "
+                         "step launch per time step")
     # the same batch in the other two forms, for context
     out["other_forms"] = {}
     agree = True
@@ -544,10 +550,41 @@ def run_drainage(args):
     return 0
 
 
+def run_throat_batch(args):
+    """One lbm_run_throat_batch of the throat benchmark's held-out packing in one
+    form, then the same call with zero steps per increment (geometry, lists,
+    arenas and the measurements only)."""
+    import torch
+    import paper_1906_04722_gb300 as lbm
+    import workloads as W
+
+    form = {"cells": lbm.BATCH_CELLS, "tiles": lbm.BATCH_PER_STEP, "persistent": lbm.BATCH_PERSISTENT}[args.throat_batch]
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR)
+    ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
+    tri = W.delaunay_throats(W.sample_spheres(192, seed=3), 1024, seed=3)
+    tri = tri[::max(1, len(tri) // max(1, args.throat_count))][:args.throat_count]
+    out = {"workload": f"{len(tri)} Delaunay throats of a 300-sphere 192^3 RSA packing, 32 increments x "
+                       f"{args.throat_steps} steps", "form": args.throat_batch}
+    for key, steps in (("full", args.throat_steps), ("no_steps", 0)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, _ = lbm.lbm_run_throat_batch(tri, params, ladder, steps, W.RHO_MAJOR, form=form)
+        torch.cuda.synchronize()
+        out[key + "_s"] = time.perf_counter() - t0
+    out["throats_per_s"] = len(tri) / out["full_s"]
+    out["fluid_cells"] = int(sum(r["n_fluid"] for r in res))
+    out["fluid_updates_per_s"] = out["fluid_cells"] * 32 * args.throat_steps / (out["full_s"] - out["no_steps_s"])
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.drainage:
         return run_drainage(args)
+    if args.throat_batch:
+        return run_throat_batch(args)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

@@ -179,11 +179,12 @@ typedef struct {
  * on it (no grid-wide synchronisation; best when the throats outnumber the CTAs
  * that fit on the GPU).  PER_STEP: one launch per time step over a work list of
  * every throat's active tiles and z segments, so that a few large throats still
- * fill the GPU.  CELLS: two launches per time step over a list of every
- * throat's non-solid cells, one thread per cell (a density pass, then the step
- * reading the neighbour densities it stored), so that the grain inside the
- * throat boxes costs neither lanes nor traffic.  All forms give bit-identical
- * rows.  AUTO is CELLS. */
+ * fill the GPU.  CELLS: the populations of the non-solid cells only, stored
+ * compactly after streaming; two launches per time step over that cell list,
+ * one thread per cell (a density pass, then the collision, which pushes each
+ * value to the cell it streams to), so that the grain inside the throat boxes
+ * (most of a box) costs neither lanes, traffic nor memory.  All forms give
+ * bit-identical rows.  AUTO is CELLS. */
 #define LBM_BATCH_AUTO 0
 #define LBM_BATCH_PERSISTENT 1
 #define LBM_BATCH_PER_STEP 2

@@ -19,6 +19,12 @@
 // z segment) items, the kernel boundary ordering the steps, then one
 // measurement launch with a CTA per throat.  One increment is captured as a
 // graph and relaunched; the increment index lives in device memory.
+//
+// Both forms keep each throat's whole box, and a throat box is mostly grain.
+// The cell-list form (the default) stores the populations of the non-solid
+// cells only, after streaming, and runs two launches per time step over that
+// list: densities, then the collision, which pushes every value to the cell it
+// streams to.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -60,23 +66,19 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Measurements of one throat box (definitions of lbm_measure), into row.
-__device__ void measure_throat(const float* __restrict__ f, const uint32_t* __restrict__ nbr,
-                               const uint32_t* __restrict__ nbr_nw, const Geom& g, double G, int probe,
-                               double rho_in_nw, double* red, lbm_increment* row) {
+// state(c, rw, rn) returns the geometry word of box cell c (class CLS_SOLID for
+// grain) and its densities after streaming, summed in k order.
+template <class CellState>
+__device__ void measure_cells(const Geom& g, double G, int probe, double rho_in_nw, double* red, lbm_increment* row,
+                              CellState&& state) {
     double acc[NMEAS];
 #pragma unroll
     for (int i = 0; i < NMEAS; ++i) acc[i] = 0.0;
     const int N = g.nxy * g.nz;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int c = tid; c < N; c += BATCH_THREADS) {
-        const int x = c % g.nx;
-        const int y = (c / g.nx) % g.ny;
-        const int z = c / g.nxy;
-        const Column col = make_column(x, y, g);
-        float dummy[2][Q];
         float rwf, rnf;
-        int cell;
-        const uint32_t w = pull_cell<false>(f, nbr, nbr_nw, g, col, z, dummy, rwf, rnf, cell);
+        const uint32_t w = state(c, rwf, rnf);
         const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
         if (cls == CLS_SOLID) continue;
         const double rw = rwf, rn = rnf;
@@ -97,13 +99,7 @@ __device__ void measure_throat(const float* __restrict__ f, const uint32_t* __re
 #pragma unroll
     for (int i = 0; i < NMEAS; ++i) tot[i] = block_sum(acc[i], red);
     float pr[2] = {0.f, 0.f};
-    if (tid == 0 && probe >= 0) {
-        const int x = probe % g.nx, y = (probe / g.nx) % g.ny, z = probe / g.nxy;
-        const Column col = make_column(x, y, g);
-        float dummy[2][Q];
-        int cell;
-        pull_cell<false>(f, nbr, nbr_nw, g, col, z, dummy, pr[0], pr[1], cell);
-    }
+    if (tid == 0 && probe >= 0) state(probe, pr[0], pr[1]);
     if (tid == 0) {
         lbm_increment r;
         r.rho_in_nw = rho_in_nw;
@@ -119,6 +115,21 @@ __device__ void measure_throat(const float* __restrict__ f, const uint32_t* __re
         r.n_interface = (long long)tot[MS_N_INTERFACE];
         *row = r;
     }
+}
+
+// The same on the box layout: densities pulled from the post-collision arrays.
+__device__ void measure_throat(const float* __restrict__ f, const uint32_t* __restrict__ nbr,
+                               const uint32_t* __restrict__ nbr_nw, const Geom& g, double G, int probe,
+                               double rho_in_nw, double* red, lbm_increment* row) {
+    measure_cells(g, G, probe, rho_in_nw, red, row, [&](int c, float& rw, float& rn) {
+        const int x = c % g.nx;
+        const int y = (c / g.nx) % g.ny;
+        const int z = c / g.nxy;
+        const Column col = make_column(x, y, g);
+        float dummy[2][Q];
+        int cell;
+        return pull_cell<false>(f, nbr, nbr_nw, g, col, z, dummy, rw, rn, cell);
+    });
 }
 
 template <int BY, int LEAD>
@@ -217,6 +228,17 @@ __global__ void __launch_bounds__(BATCH_THREADS)
 
 // The cell-list form.  A list item is (throat, x | y << 10 | z << 20) of a
 // non-solid cell of that throat's box; boxes are at most 512 cells along an axis.
+// Items are ordered by throat and, inside a throat, in memory order, so that the
+// +x neighbour of item i, when it is not grain, is item i + 1.
+//
+// Storage is compact: population (s, k) of item i lives at fc[(s Q + k) cp + i]
+// (cp: item count rounded up to 32), and the stored value is the population
+// after streaming -- what the pull of Eq. 1 would deliver to the cell.  Both
+// passes of a step read a cell's own values only; the collision pushes each
+// post-collision value f*_k to the slot (k) of the cell x + e_k, or, where
+// x + e_k is not fluid for the component, back into the cell's own slot
+// (opposite k) -- half-way bounce-back, decided by the bits the pull uses (bit
+// k' of a word: x - e_k' is not fluid).  Every slot is written exactly once.
 struct CellAt {
     int id, x, y, z, cell;
 };
@@ -231,62 +253,150 @@ __device__ __forceinline__ CellAt decode_cell(int2 it, const Geom& g) {
 }
 
 constexpr int CELL_THREADS = 256;
+constexpr int NB_DIRS = Q - 3;  // directions 3..18 leave the x row; 1 and 2 are +x and -x
 
-// (rho_w, rho_nw) of every listed cell (Eq. 2 after the pull of Eq. 1), summed
-// in four interleaved partial sums as the staged kernel sums its density ring.
-// Cells off the list (grain) keep the 0 they were given.
+// Compact copies of the geometry words and the push table: nbp[(k - 3) cp + i]
+// is the item of x + e_k, -1 where that cell is grain or beyond the box.
 __global__ void __launch_bounds__(CELL_THREADS)
-    throat_cell_density_kernel(const ThroatRec* __restrict__ recs, const int2* __restrict__ items, int n_items,
-                               const float* __restrict__ fin, const uint32_t* __restrict__ nbr,
-                               const uint32_t* __restrict__ nbr_nw, float2* __restrict__ rho2) {
+    cell_gather_kernel(const ThroatRec* __restrict__ recs, const int2* __restrict__ items, int n_items, int cp,
+                       const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
+                       const uint32_t* __restrict__ adh, const int* __restrict__ box_to_item,
+                       uint32_t* __restrict__ wc, uint32_t* __restrict__ wnc, uint32_t* __restrict__ adhc,
+                       int* __restrict__ nbp) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i >= n_items) return;
-    const int2 it = __ldg(items + i);
+    const int2 it = items[i];
     const ThroatRec& r = recs[it.x];
     const Geom g = r.g;
     const CellAt c = decode_cell(it, g);
     const long long c_off = r.c_off;
-    const uint32_t w = __ldg(nbr + c_off + c.cell);
-    const Column col = make_column(c.x, c.y, g);
-    float unused[2][Q];
-    float rw, rn;
-    pull_known<false, true>(fin + r.f_off, nbr_nw + c_off, g, col, c.z, c.cell, w, unused, rw, rn);
-    rho2[c_off + c.cell] = make_float2(rw, rn);
+    const uint32_t w = nbr[c_off + c.cell];
+    wc[i] = w;
+    wnc[i] = (w & BIT_NW_DIFF) ? nbr_nw[c_off + c.cell] : w;
+    adhc[i] = (w & BIT_ADH) ? adh[c_off + c.cell] : 0u;
+#pragma unroll
+    for (int k = 3; k < Q; ++k) {
+        const int x = c.x + EX(k), y = c.y + EY(k), z = c.z + EZ(k);
+        const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
+        nbp[(size_t)(k - 3) * cp + i] = in ? box_to_item[c_off + (long long)z * g.nxy + y * g.nx + x] : -1;
+    }
 }
 
-// One time step of every listed cell: pull, neighbour densities from the field
-// of the density pass (0 beyond the closed box), collide_core, store.
-__global__ void __launch_bounds__(CELL_THREADS, 2)
-    throat_cell_step_kernel(const ThroatRec* __restrict__ recs, const int2* __restrict__ items, int n_items,
-                            const float* __restrict__ fin, float* __restrict__ fout, const float2* __restrict__ rho2,
-                            const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
-                            const uint32_t* __restrict__ adh, Phys P, const float* __restrict__ bc_all,
-                            int ladder_stride, const int* __restrict__ incr_now) {
+// Rest equilibrium at the start (as throat_init_kernel: wetting fluid
+// everywhere, the non-wetting fluid on the inlet layer), stored after streaming.
+__global__ void __launch_bounds__(CELL_THREADS)
+    cell_init_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, float* __restrict__ fc, float rho_major,
+                     float rho_minor) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i >= n_items) return;
-    const int2 it = __ldg(items + i);
-    const ThroatRec& r = recs[it.x];
-    const Geom g = r.g;
-    const CellAt c = decode_cell(it, g);
-    const long long c_off = r.c_off, f_off = r.f_off;
-    const uint32_t w = __ldg(nbr + c_off + c.cell);
-    const Column col = make_column(c.x, c.y, g);
+    const uint32_t cls = (wc[i] >> CLS_SHIFT) & CLS_MASK;
+    const bool inlet = cls == CLS_INLET;
+    for (int s = 0; s < 2; ++s) {
+        const bool fl = !(s == 1 && cls == CLS_MEMBRANE);
+        const float r = !fl ? 0.f : s == 0 ? (inlet ? rho_minor : rho_major) : (inlet ? rho_major : rho_minor);
+        float sum = 0.f;
+        for (int k = 1; k < Q; ++k) sum += WK(k) * r;
+        float* fs = fc + (size_t)s * Q * cp + i;
+        fs[0] = fl ? r - sum : 0.f;
+        for (int k = 1; k < Q; ++k) fs[(size_t)k * cp] = fl ? WK(k) * r : 0.f;
+    }
+}
+
+// (rho_w, rho_nw) of every item (Eq. 2), in four interleaved partial sums as the
+// staged kernel sums its density ring; 0 for the non-wetting fluid on a membrane.
+__global__ void __launch_bounds__(CELL_THREADS)
+    cell_density_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, const float* __restrict__ fc,
+                        float2* __restrict__ rho2) {
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i >= n_items) return;
+    const uint32_t cls = (__ldg(wc + i) >> CLS_SHIFT) & CLS_MASK;
+    float r[2] = {0.f, 0.f};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (s == 1 && cls == CLS_MEMBRANE) break;
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < Q; ++k) a[k & 3] += __ldg(fc + (size_t)(s * Q + k) * cp + i);
+        r[s] = (a[0] + a[1]) + (a[2] + a[3]);
+    }
+    rho2[i] = make_float2(r[0], r[1]);
+}
+
+// One time step of every item: own populations, neighbour densities of the
+// density pass (0 where x + e_k is not fluid for the wetting component, i.e.
+// grain or beyond the box), collide_core, push.
+__global__ void __launch_bounds__(CELL_THREADS, 2)
+    cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float* __restrict__ fin,
+                     float* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
+                     const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const int* __restrict__ nbp,
+                     Phys P, const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i >= n_items) return;
+    const uint32_t w = __ldg(wc + i);
+    const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+    const bool has_nw = cls != CLS_MEMBRANE;
     float f[2][Q];
-    float rw, rn;
-    pull_known<true, false>(fin + f_off, nbr_nw + c_off, g, col, c.z, c.cell, w, f, rw, rn);
-    const uint32_t a = (w & BIT_ADH) ? __ldg(adh + c_off + c.cell) : 0u;
-    const float2* rh = rho2 + c_off;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) f[s][k] = (s == 0 || has_nw) ? __ldg(fin + (size_t)(s * Q + k) * cp + i) : 0.f;
+    const uint32_t wn = has_nw ? __ldg(wnc + i) : 0u;
+    const uint32_t a = (w & BIT_ADH) ? __ldg(adhc + i) : 0u;
+    auto dest = [&](int k) { return k == 1 ? i + 1 : k == 2 ? i - 1 : __ldg(nbp + (size_t)(k - 3) * cp + i); };
     auto rho_at = [&](int k) {
-        const int nx = c.x + EX(k), ny = c.y + EY(k), nz = c.z + EZ(k);
-        if (nx < 0 || nx >= g.nx || ny < 0 || ny >= g.ny || nz < 0 || nz >= g.nz) return make_float2(0.f, 0.f);
-        return __ldg(rh + c.cell + EX(k) + EY(k) * g.nx + EZ(k) * g.nxy);
+        if (k == 0) return __ldg(rho2 + i);
+        if ((w >> OPP(k)) & 1u) return make_float2(0.f, 0.f);
+        return __ldg(rho2 + dest(k));
     };
     Phys Pt = P;
-    Pt.bc = bc_all + 4 * ((size_t)it.x * ladder_stride + *incr_now);
-    float* __restrict__ out0 = fout + f_off + c.cell;
-    float* __restrict__ out1 = out0 + (size_t)Q * g.plane;
-    collide_core(f, w, a, Pt, rho_at,
-                 [&](int s, int k, float v) { (s == 0 ? out0 : out1)[(size_t)k * g.plane] = v; });
+    Pt.bc = bc_all + 4 * ((size_t)__ldg(&items[i].x) * ladder_stride + *incr_now);
+    collide_core(f, w, a, Pt, rho_at, [&](int s, int k, float v) {
+        if (s == 1 && !has_nw) return;
+        float* fs = fout + (size_t)s * Q * cp;
+        if (k == 0) {
+            fs[i] = v;
+            return;
+        }
+        const uint32_t bits = s == 0 ? w : wn;
+        if ((bits >> OPP(k)) & 1u) fs[(size_t)OPP(k) * cp + i] = v;
+        else fs[(size_t)k * cp + dest(k)] = v;
+    });
+}
+
+// Measurements of throat blockIdx.x from the compact populations, walking its
+// box in the order of the box-layout forms (the same sums, the same rounding);
+// the last CTA to finish advances the increment index.
+__global__ void __launch_bounds__(BATCH_THREADS)
+    cell_measure_kernel(const ThroatRec* __restrict__ recs, int n, const int* __restrict__ box_to_item, int cp,
+                        const float* __restrict__ fc, const uint32_t* __restrict__ wc, double G,
+                        const double* __restrict__ rin_all, int ladder_stride, lbm_increment* __restrict__ rows,
+                        int n_incr, int* incr_now, int* done) {
+    __shared__ double red[32];
+    const int id = blockIdx.x;
+    const int incr = *incr_now;
+    const Geom g = recs[id].g;
+    const int* map = box_to_item + recs[id].c_off;
+    measure_cells(g, G, recs[id].probe, rin_all[(size_t)id * ladder_stride + incr], red,
+                  rows + (size_t)id * n_incr + incr, [&](int c, float& rw, float& rn) {
+                      rw = 0.f;
+                      rn = 0.f;
+                      const int j = map[c];
+                      if (j < 0) return (uint32_t)CLS_SOLID << CLS_SHIFT;
+                      const uint32_t w = wc[j];
+                      const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+                      for (int k = 0; k < Q; ++k) rw += fc[(size_t)k * cp + j];
+                      if (cls != CLS_MEMBRANE)
+                          for (int k = 0; k < Q; ++k) rn += fc[(size_t)(Q + k) * cp + j];
+                      return w;
+                  });
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1) == n - 1) {  // every CTA has read the index
+            *done = 0;
+            *incr_now = incr + 1;
+        }
+    }
 }
 
 // Rest-equilibrium start of every throat: wetting fluid (rho_major, rho_minor)
@@ -477,6 +587,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         int4* d_items = nullptr;
         int2* d_cells = nullptr;
         float2* d_rho2 = nullptr;
+        int *d_map = nullptr, *d_nbp = nullptr;
+        uint32_t* d_wc = nullptr;
         cudaGraphExec_t exec2[2] = {nullptr, nullptr};
         double* d_rin = nullptr;
         lbm_increment* d_rows = nullptr;
@@ -491,6 +603,9 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             cudaFree(d_items);
             cudaFree(d_cells);
             cudaFree(d_rho2);
+            cudaFree(d_map);
+            cudaFree(d_nbp);
+            cudaFree(d_wc);
             if (exec) cudaGraphExecDestroy(exec);
             for (cudaGraphExec_t& e : exec2)
                 if (e) cudaGraphExecDestroy(e);
@@ -504,8 +619,12 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             return fail_cuda(e_, #call);               \
         }                                              \
     } while (0)
-        BATCH_CUDA(cudaMalloc(&a0, sizeof(float) * (size_t)f_tot));
-        BATCH_CUDA(cudaMalloc(&a1, sizeof(float) * (size_t)f_tot));
+        const int form = sched->batch_form == LBM_BATCH_AUTO ? LBM_BATCH_CELLS : sched->batch_form;
+        const bool box_layout = form != LBM_BATCH_CELLS;  // the cell-list form keeps compact arenas only
+        if (box_layout) {
+            BATCH_CUDA(cudaMalloc(&a0, sizeof(float) * (size_t)f_tot));
+            BATCH_CUDA(cudaMalloc(&a1, sizeof(float) * (size_t)f_tot));
+        }
         BATCH_CUDA(cudaMalloc(&d_mask, (size_t)c_tot));
         BATCH_CUDA(cudaMalloc(&d_nbr, sizeof(uint32_t) * (size_t)c_tot));
         BATCH_CUDA(cudaMalloc(&d_nbr_nw, sizeof(uint32_t) * (size_t)c_tot));
@@ -518,8 +637,10 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         const int L = sched->per_throat ? n : 1;  // ladders
         BATCH_CUDA(cudaMalloc(&d_bc, sizeof(float) * 4 * (size_t)I * L));
         BATCH_CUDA(cudaMalloc(&d_rin, sizeof(double) * (size_t)I * L));
-        BATCH_CUDA(cudaMemsetAsync(a0, 0, sizeof(float) * (size_t)f_tot, stream));
-        BATCH_CUDA(cudaMemsetAsync(a1, 0, sizeof(float) * (size_t)f_tot, stream));
+        if (box_layout) {
+            BATCH_CUDA(cudaMemsetAsync(a0, 0, sizeof(float) * (size_t)f_tot, stream));
+            BATCH_CUDA(cudaMemsetAsync(a1, 0, sizeof(float) * (size_t)f_tot, stream));
+        }
         {
             std::vector<uint8_t> all((size_t)c_tot);
             for (int t = 0; t < n; ++t) std::memcpy(all.data() + recs[t].c_off, masks[t].data(), masks[t].size());
@@ -543,7 +664,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             BATCH_CUDA(cudaMemcpyAsync(d_bc, bc.data(), sizeof(float) * bc.size(), cudaMemcpyHostToDevice, stream));
             BATCH_CUDA(cudaMemcpyAsync(d_rin, sched->rho_in_nw, sizeof(double) * (size_t)I * L,
                                        cudaMemcpyHostToDevice, stream));
-            throat_init_kernel<<<n, 256, 0, stream>>>(d_recs, n, a0, d_nbr, d_nbr_nw, (float)params->rho_major,
+            if (box_layout)
+                throat_init_kernel<<<n, 256, 0, stream>>>(d_recs, n, a0, d_nbr, d_nbr_nw, (float)params->rho_major,
                                                       (float)params->rho_minor);
             BATCH_CUDA(cudaGetLastError());
             BATCH_CUDA(cudaStreamSynchronize(stream));  // host staging buffers go out of scope
@@ -566,37 +688,61 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         BATCH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BATCH_THREADS, smem));
         const int grid = std::max(1, std::min(n, sms * std::max(1, per_sm)));
-        const int form = sched->batch_form == LBM_BATCH_AUTO ? LBM_BATCH_CELLS : sched->batch_form;
         BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
 
         if (form == LBM_BATCH_CELLS) {
             // every non-solid cell of every throat (largest throats first,
-            // memory order inside a throat)
+            // memory order inside a throat), and the box -> item map
             std::vector<int2> cells;
+            std::vector<int> box_to_item((size_t)c_tot, -1);
             for (int t : order) {
                 const Geom& g = recs[t].g;
+                const uint8_t* m = masks[t].data();
+                int* map = box_to_item.data() + recs[t].c_off;
                 for (int z = 0; z < g.nz; ++z)
                     for (int y = 0; y < g.ny; ++y)
-                        for (int x = 0; x < g.nx; ++x)
-                            if (!(masks[t][(size_t)z * g.nxy + (size_t)y * g.nx + x] & LBM_MASK_SOLID))
-                                cells.push_back(make_int2(t, x | (y << 10) | (z << 20)));
-            }
-            if (cells.size() > (size_t)INT_MAX) {
-                cleanup();
-                set_error("lbm_run_throat_batch: too many cells for the cell-list form");
-                return LBM_ERR_ARG;
+                        for (int x = 0; x < g.nx; ++x) {
+                            const size_t c = (size_t)z * g.nxy + (size_t)y * g.nx + x;
+                            if (m[c] & LBM_MASK_SOLID) continue;
+                            if (cells.size() >= (size_t)INT_MAX - 64) {
+                                cleanup();
+                                set_error("lbm_run_throat_batch: too many cells for the cell-list form");
+                                return LBM_ERR_ARG;
+                            }
+                            map[c] = (int)cells.size();
+                            cells.push_back(make_int2(t, x | (y << 10) | (z << 20)));
+                        }
             }
             const int n_cells = (int)cells.size();
+            const int cp = (n_cells + 31) / 32 * 32;
+            const size_t fc_floats = (size_t)2 * Q * std::max(cp, 32);
             BATCH_CUDA(cudaMalloc(&d_cells, sizeof(int2) * std::max<size_t>(1, cells.size())));
-            BATCH_CUDA(cudaMalloc(&d_rho2, sizeof(float2) * (size_t)c_tot));
+            BATCH_CUDA(cudaMalloc(&d_map, sizeof(int) * (size_t)std::max<long long>(1, c_tot)));
+            BATCH_CUDA(cudaMalloc(&d_rho2, sizeof(float2) * (size_t)std::max(cp, 32)));
+            BATCH_CUDA(cudaMalloc(&d_wc, sizeof(uint32_t) * 3 * (size_t)std::max(cp, 32)));
+            BATCH_CUDA(cudaMalloc(&d_nbp, sizeof(int) * (size_t)NB_DIRS * std::max(cp, 32)));
+            BATCH_CUDA(cudaMalloc(&a0, sizeof(float) * fc_floats));
+            BATCH_CUDA(cudaMalloc(&a1, sizeof(float) * fc_floats));
             BATCH_CUDA(cudaMalloc(&d_incr, sizeof(int) * 2));
             BATCH_CUDA(cudaMemsetAsync(d_incr, 0, sizeof(int) * 2, stream));
-            BATCH_CUDA(cudaMemsetAsync(d_rho2, 0, sizeof(float2) * (size_t)c_tot, stream));
-            if (n_cells)
+            uint32_t* d_wnc = d_wc + std::max(cp, 32);
+            uint32_t* d_adhc = d_wnc + std::max(cp, 32);
+            if (c_tot)
+                BATCH_CUDA(cudaMemcpyAsync(d_map, box_to_item.data(), sizeof(int) * box_to_item.size(),
+                                           cudaMemcpyHostToDevice, stream));
+            const unsigned blocks = (unsigned)((n_cells + CELL_THREADS - 1) / CELL_THREADS);
+            if (n_cells) {
                 BATCH_CUDA(cudaMemcpyAsync(d_cells, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice,
                                            stream));
-            BATCH_CUDA(cudaStreamSynchronize(stream));
-            const unsigned blocks = (unsigned)((n_cells + CELL_THREADS - 1) / CELL_THREADS);
+                cell_gather_kernel<<<blocks, CELL_THREADS, 0, stream>>>(d_recs, d_cells, n_cells, cp, d_nbr, d_nbr_nw,
+                                                                       d_adh, d_map, d_wc, d_wnc, d_adhc, d_nbp);
+                BATCH_CUDA(cudaGetLastError());
+                cell_init_kernel<<<blocks, CELL_THREADS, 0, stream>>>(d_wc, n_cells, cp, a0,
+                                                                     (float)params->rho_major,
+                                                                     (float)params->rho_minor);
+                BATCH_CUDA(cudaGetLastError());
+            }
+            BATCH_CUDA(cudaStreamSynchronize(stream));  // host lists go out of scope
             const int n_graphs = (sched->n_steps & 1) ? 2 : 1;
             for (int gi = 0; gi < n_graphs; ++gi) {
                 BATCH_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -604,20 +750,19 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                 for (int st = 0; st < sched->n_steps && cerr == cudaSuccess && n_cells; ++st) {
                     const int c = (gi + st) & 1;
                     const float* fin = c ? a1 : a0;
-                    throat_cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_recs, d_cells, n_cells, fin, d_nbr,
-                                                                                d_nbr_nw, d_rho2);
+                    cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
                     cerr = cudaGetLastError();
                     if (cerr != cudaSuccess) break;
-                    throat_cell_step_kernel<<<blocks, CELL_THREADS, 0, cap>>>(
-                        d_recs, d_cells, n_cells, fin, c ? a0 : a1, d_rho2, d_nbr, d_nbr_nw, d_adh, P, d_bc,
-                        sched->per_throat ? I : 0, d_incr);
+                    cell_step_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_cells, n_cells, cp, fin, c ? a0 : a1, d_rho2,
+                                                                       d_wc, d_wnc, d_adhc, d_nbp, P, d_bc,
+                                                                       sched->per_throat ? I : 0, d_incr);
                     cerr = cudaGetLastError();
                 }
                 if (cerr == cudaSuccess) {
                     const int c = (gi + sched->n_steps) & 1;
-                    throat_item_measure_kernel<<<n, dim3(32, BATCH_BY), 0, cap>>>(
-                        d_recs, n, c ? a1 : a0, d_nbr, d_nbr_nw, params->G, d_rin, sched->per_throat ? I : 0, d_rows,
-                        I, d_incr, d_incr + 1);
+                    cell_measure_kernel<<<n, dim3(32, BATCH_BY), 0, cap>>>(d_recs, n, d_map, cp, c ? a1 : a0, d_wc,
+                                                                           params->G, d_rin, sched->per_throat ? I : 0,
+                                                                           d_rows, I, d_incr, d_incr + 1);
                     cerr = cudaGetLastError();
                 }
                 cudaGraph_t graph = nullptr;
