@@ -324,7 +324,9 @@ __global__ void __launch_bounds__(CELL_THREADS)
 
 // One time step of every item: own populations, neighbour densities of the
 // density pass (0 where x + e_k is not fluid for the wetting component, i.e.
-// grain or beyond the box), collide_core, push.
+// grain or beyond the box), collide_core, push.  The bounce-back choice selects
+// an address rather than a branch: one load or store instruction per value for
+// the whole warp, whichever way each lane goes.
 __global__ void __launch_bounds__(CELL_THREADS, 2)
     cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float* __restrict__ fin,
                      float* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
@@ -345,8 +347,10 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
     auto dest = [&](int k) { return k == 1 ? i + 1 : k == 2 ? i - 1 : __ldg(nbp + (size_t)(k - 3) * cp + i); };
     auto rho_at = [&](int k) {
         if (k == 0) return __ldg(rho2 + i);
-        if ((w >> OPP(k)) & 1u) return make_float2(0.f, 0.f);
-        return __ldg(rho2 + dest(k));
+        const bool wall = (w >> OPP(k)) & 1u;
+        const int j = dest(k);
+        const float2 v = __ldg(rho2 + (wall ? i : j));
+        return wall ? make_float2(0.f, 0.f) : v;
     };
     Phys Pt = P;
     Pt.bc = bc_all + 4 * ((size_t)__ldg(&items[i].x) * ladder_stride + *incr_now);
@@ -358,8 +362,9 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
             return;
         }
         const uint32_t bits = s == 0 ? w : wn;
-        if ((bits >> OPP(k)) & 1u) fs[(size_t)OPP(k) * cp + i] = v;
-        else fs[(size_t)k * cp + dest(k)] = v;
+        const bool wall = (bits >> OPP(k)) & 1u;
+        const int j = dest(k);
+        fs[wall ? (size_t)OPP(k) * cp + i : (size_t)k * cp + j] = v;
     });
 }
 
