@@ -26,11 +26,14 @@
 // list: densities, then the collision, which pushes every value to the cell it
 // streams to.
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lbm_step_core.cuh"
@@ -454,6 +457,31 @@ __global__ void throat_init_kernel(const ThroatRec* __restrict__ recs, int n, fl
     }
 }
 
+// f(t) for t in [0, n) on the host cores.  Returns false if an iteration threw
+// (host allocation failure).
+template <class F>
+bool host_parallel_for(int n, F&& f) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::max(1, std::min(n, (int)std::min(32u, hw)));
+    std::atomic<int> next{0};
+    std::atomic<bool> ok{true};
+    auto work = [&]() {
+        for (int t; (t = next.fetch_add(1)) < n;) {
+            try {
+                f(t);
+            } catch (...) {
+                ok = false;
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    pool.reserve((size_t)nt - 1);
+    for (int i = 0; i + 1 < nt; ++i) pool.emplace_back(work);
+    work();
+    for (std::thread& th : pool) th.join();
+    return ok;
+}
+
 size_t batch_smem() {
     return sizeof(float) * (size_t)((BATCH_LEAD + 1) * 2 * Q + 4 * 2 + 2 * (BATCH_LEAD + 1)) * BATCH_THREADS;
 }
@@ -523,64 +551,90 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
     cudaStream_t stream = (cudaStream_t)stream_ptr;
     const int I = sched->n_incr;
     try {
-        // host geometry: frames, masks, probes
+        const int form = sched->batch_form == LBM_BATCH_AUTO ? LBM_BATCH_CELLS : sched->batch_form;
+        const bool box_layout = form != LBM_BATCH_CELLS;  // the cell-list form keeps compact arenas only
+        // host geometry: frames and sizes first (validation, on this thread), then
+        // masks, probes and per-throat lists on all host cores
         std::vector<ThroatRec> recs((size_t)n);
         std::vector<std::vector<uint8_t>> masks((size_t)n);
-        long long f_tot = 0, c_tot = 0;
+        std::vector<std::array<int, 3>> dims((size_t)n), probes((size_t)n);
         for (int t = 0; t < n; ++t) {
-            int dims[3], probe[3];
-            int rc = lbm_throat_geometry(throats + 12 * t, dims, nullptr, nullptr);
+            int rc = lbm_throat_geometry(throats + 12 * t, dims[t].data(), nullptr, nullptr);
             if (rc) return rc;
-            const long long N = (long long)dims[0] * dims[1] * dims[2];
-            masks[t].resize((size_t)N);
-            lbm_throat_geometry(throats + 12 * t, dims, masks[t].data(), probe);
+        }
+        std::vector<std::vector<int>> tiles_of((size_t)n), cells_of((size_t)n);
+        if (!host_parallel_for(n, [&](int t) {
+                const int nx = dims[t][0], ny = dims[t][1], nz = dims[t][2];
+                const size_t nxy = (size_t)nx * ny;
+                masks[t].resize(nxy * nz);
+                int d[3];
+                lbm_throat_geometry(throats + 12 * t, d, masks[t].data(), probes[t].data());
+                const uint8_t* m = masks[t].data();
+                long long nf = 0;
+                for (size_t c = 0; c < masks[t].size(); ++c) nf += m[c] == 0;
+                results[t].n_fluid = nf;
+                if (!box_layout) {
+                    // non-solid cells in memory order: x | y << 10 | z << 20
+                    std::vector<int>& cl = cells_of[t];
+                    for (int z = 0; z < nz; ++z)
+                        for (int y = 0; y < ny; ++y)
+                            for (int x = 0; x < nx; ++x)
+                                if (!(m[(size_t)z * nxy + (size_t)y * nx + x] & LBM_MASK_SOLID))
+                                    cl.push_back(x | (y << 10) | (z << 20));
+                    return;
+                }
+                // active tiles: the (30 x 4)-column tiles of the step kernel that
+                // hold a non-solid cell at some height
+                std::vector<uint8_t> col(nxy, 0);
+                for (int z = 0; z < nz; ++z)
+                    for (size_t c = 0; c < nxy; ++c)
+                        if (!(m[(size_t)z * nxy + c] & LBM_MASK_SOLID)) col[c] = 1;
+                const int TYB = BATCH_BY - 2;
+                for (int ty = 0; ty * TYB < ny; ++ty)
+                    for (int tx = 0; tx * 30 < nx; ++tx) {
+                        bool any = false;
+                        for (int y = ty * TYB; y < std::min(ny, ty * TYB + TYB) && !any; ++y)
+                            for (int x = tx * 30; x < std::min(nx, tx * 30 + 30); ++x)
+                                if (col[(size_t)y * nx + x]) { any = true; break; }
+                        if (any) tiles_of[t].push_back(tx | (ty << 16));
+                    }
+            })) {
+            set_error("host allocation failed");
+            return LBM_ERR_OOM;
+        }
+        long long f_tot = 0, c_tot = 0;
+        std::vector<int> tiles;
+        for (int t = 0; t < n; ++t) {
+            const int* dm = dims[t].data();
+            const int* probe = probes[t].data();
+            const long long N = (long long)dm[0] * dm[1] * dm[2];
             Geom& g = recs[t].g;
             std::memset(&g, 0, sizeof(g));
-            g.nx = dims[0];
-            g.ny = dims[1];
-            g.nz = dims[2];
-            g.nxy = dims[0] * dims[1];
+            g.nx = dm[0];
+            g.ny = dm[1];
+            g.nz = dm[2];
+            g.nxy = dm[0] * dm[1];
             g.plane = (int)((N + 31) / 32 * 32);
             fill_pull_offsets(g);
             recs[t].f_off = f_tot;
             recs[t].c_off = c_tot;
-            recs[t].probe = probe[0] < 0 ? -1 : (probe[2] * dims[1] + probe[1]) * dims[0] + probe[0];
+            recs[t].probe = probe[0] < 0 ? -1 : (probe[2] * dm[1] + probe[1]) * dm[0] + probe[0];
             f_tot += (long long)g.plane * 2 * Q;
             c_tot += N;
-            lbm_throat_result& r = results[t];
-            r.dims[0] = dims[0];
-            r.dims[1] = dims[1];
-            r.dims[2] = dims[2];
-            std::memcpy(r.probe, probe, sizeof(probe));
-            long long nf = 0;
-            for (uint8_t m : masks[t]) nf += m == 0;
-            r.n_fluid = nf;
-        }
-        // active tiles of each throat: the (30 x 4)-column tiles of the step
-        // kernel that hold a non-solid cell at some height
-        std::vector<int> tiles;
-        for (int t = 0; t < n; ++t) {
-            const Geom& g = recs[t].g;
-            std::vector<uint8_t> col((size_t)g.nxy, 0);
-            for (int z = 0; z < g.nz; ++z)
-                for (int c = 0; c < g.nxy; ++c)
-                    if (!(masks[t][(size_t)z * g.nxy + c] & LBM_MASK_SOLID)) col[(size_t)c] = 1;
-            const int TYB = BATCH_BY - 2;
             recs[t].tile_begin = (int)tiles.size();
-            for (int ty = 0; ty * TYB < g.ny; ++ty)
-                for (int tx = 0; tx * 30 < g.nx; ++tx) {
-                    bool any = false;
-                    for (int y = ty * TYB; y < std::min(g.ny, ty * TYB + TYB) && !any; ++y)
-                        for (int x = tx * 30; x < std::min(g.nx, tx * 30 + 30); ++x)
-                            if (col[(size_t)y * g.nx + x]) { any = true; break; }
-                    if (any) tiles.push_back(tx | (ty << 16));
-                }
-            recs[t].tile_count = (int)tiles.size() - recs[t].tile_begin;
+            tiles.insert(tiles.end(), tiles_of[t].begin(), tiles_of[t].end());
+            recs[t].tile_count = (int)tiles_of[t].size();
+            lbm_throat_result& r = results[t];
+            r.dims[0] = dm[0];
+            r.dims[1] = dm[1];
+            r.dims[2] = dm[2];
+            std::memcpy(r.probe, probe, sizeof(int) * 3);
         }
-        // most work first (active tiles x planes)
+        // most work first (active tiles x planes; non-solid cells in the cell-list form)
         std::vector<int> order((size_t)n);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (!box_layout) return cells_of[a].size() > cells_of[b].size();
             return (long long)recs[a].tile_count * recs[a].g.nz > (long long)recs[b].tile_count * recs[b].g.nz;
         });
 
@@ -624,8 +678,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             return fail_cuda(e_, #call);               \
         }                                              \
     } while (0)
-        const int form = sched->batch_form == LBM_BATCH_AUTO ? LBM_BATCH_CELLS : sched->batch_form;
-        const bool box_layout = form != LBM_BATCH_CELLS;  // the cell-list form keeps compact arenas only
         if (box_layout) {
             BATCH_CUDA(cudaMalloc(&a0, sizeof(float) * (size_t)f_tot));
             BATCH_CUDA(cudaMalloc(&a1, sizeof(float) * (size_t)f_tot));
@@ -698,26 +750,31 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         if (form == LBM_BATCH_CELLS) {
             // every non-solid cell of every throat (largest throats first,
             // memory order inside a throat), and the box -> item map
-            std::vector<int2> cells;
-            std::vector<int> box_to_item((size_t)c_tot, -1);
+            std::vector<long long> item0((size_t)n);
+            long long n_items = 0;
             for (int t : order) {
-                const Geom& g = recs[t].g;
-                const uint8_t* m = masks[t].data();
-                int* map = box_to_item.data() + recs[t].c_off;
-                for (int z = 0; z < g.nz; ++z)
-                    for (int y = 0; y < g.ny; ++y)
-                        for (int x = 0; x < g.nx; ++x) {
-                            const size_t c = (size_t)z * g.nxy + (size_t)y * g.nx + x;
-                            if (m[c] & LBM_MASK_SOLID) continue;
-                            if (cells.size() >= (size_t)INT_MAX - 64) {
-                                cleanup();
-                                set_error("lbm_run_throat_batch: too many cells for the cell-list form");
-                                return LBM_ERR_ARG;
-                            }
-                            map[c] = (int)cells.size();
-                            cells.push_back(make_int2(t, x | (y << 10) | (z << 20)));
-                        }
+                item0[t] = n_items;
+                n_items += (long long)cells_of[t].size();
             }
+            if (n_items > (long long)INT_MAX - 64) {
+                cleanup();
+                set_error("lbm_run_throat_batch: too many cells for the cell-list form");
+                return LBM_ERR_ARG;
+            }
+            std::vector<int2> cells((size_t)n_items);
+            std::vector<int> box_to_item((size_t)c_tot);
+            host_parallel_for(n, [&](int t) {
+                const Geom& g = recs[t].g;
+                int* map = box_to_item.data() + recs[t].c_off;
+                std::fill(map, map + (size_t)g.nxy * g.nz, -1);
+                const std::vector<int>& cl = cells_of[t];
+                for (size_t j = 0; j < cl.size(); ++j) {
+                    const int v = cl[j];
+                    const int item = (int)(item0[t] + (long long)j);
+                    cells[(size_t)item] = make_int2(t, v);
+                    map[(size_t)(v >> 20) * g.nxy + (size_t)((v >> 10) & 1023) * g.nx + (v & 1023)] = item;
+                }
+            });
             const int n_cells = (int)cells.size();
             const int cp = (n_cells + 31) / 32 * 32;
             const size_t fc_floats = (size_t)2 * Q * std::max(cp, 32);
