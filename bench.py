@@ -261,7 +261,7 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
 
     The ladder is 32 increments of the nw reservoir density (2.0 + 0.02 i) with
     n_steps time steps each, for every arm.  The surrogate is trained first on
-    two other seeded packings (its cost is reported, not counted in throats/s:
+    six other seeded packings (its cost is reported, not counted in throats/s:
     it is paid once for all throats of a network).  Every rank works on its own
     held-out packing; tmax(t) is the maximum of t over ranks, and the rates
     are whole-job: world x throats per rank / that maximum."""
@@ -273,13 +273,13 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
     out = {"workload": "1024 Delaunay throats of a 300-sphere 192^3 RSA packing, boxes 24^3..64^3, "
                        f"32 increments x {n_steps} steps", "unit": "throats/s"}
-    # training set from two other packings
+    # training set from six other packings
     t0 = time.perf_counter()
     Xs, Ys = [], []
-    for seed in (10 + 2 * rank, 11 + 2 * rank):
+    for seed in range(10 + 6 * rank, 16 + 6 * rank):
         tri = W.delaunay_throats(W.sample_spheres(192, seed=100 + seed), 1024, seed=100 + seed)
         res, rows = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
-        X, R = S.throat_features(tri, theta)
+        X, R = S.surrogate_inputs(tri, theta)
         Y, ok = S.ThroatSurrogate.targets(res, rows, R)
         Xs.append(X[ok])
         Ys.append(Y[ok])

@@ -211,6 +211,28 @@ typedef struct {
  * is detected).  LBM_ERR_ARG for collinear centres or boxes beyond 512. */
 int lbm_throat_geometry(const double* spheres3, int dims_out[3], unsigned char* mask_out, int probe_out[3]);
 
+/* lbm_throat_lattice_features -- what the lattice makes of each throat, for the
+ * surrogate: the throat boxes of lbm_throat_geometry are voxelised (host, all
+ * cores) and described by LBM_THROAT_LATTICE_FEATURES numbers each (row t of
+ * out, n x 14 doubles, caller-owned).  With A(k) the non-solid cells of plane k
+ * and the interior planes k = 1 .. nz - 2 (all planes when nz < 3), ordered by
+ * (A, k) ascending, k* the first of them:
+ *    0-2  nx, ny, nz
+ *    3    non-solid fraction of the box
+ *    4    A(k*)                       5  sqrt(A(k*) / pi)
+ *    6    mean A over interior planes 7  k* / nz
+ *    8    lattice incircle of plane k*: the largest Euclidean distance from a
+ *         non-solid cell to the nearest solid cell of the same plane
+ *    9-10 max and mean of that incircle over the first three planes
+ *    11   A(k*) / max(P, 1)           12 P: non-solid cells of plane k* with a
+ *         solid or out-of-plane 4-neighbour
+ *    13   mean of the first three A
+ * The entry pressure of a throat follows its narrowest section (Young-Laplace);
+ * these say how the lattice resolves that section.  Errors as
+ * lbm_throat_geometry (LBM_ERR_ARG for a bad throat; nothing is written). */
+#define LBM_THROAT_LATTICE_FEATURES 14
+int lbm_throat_lattice_features(const double* throats, int n, double* out);
+
 /* lbm_run_throat_batch -- the per-throat simulations of the hybrid method
  * (Sec. 2.2.2: one LBM run per pore throat, p_c^e from its drainage ladder) for
  * n throats at once: each throat's box (lbm_throat_geometry) starts filled with

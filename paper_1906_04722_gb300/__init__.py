@@ -127,6 +127,7 @@ SIGNATURES = {
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_tune_result)]),
     "lbm_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, _IP]),
     "lbm_throat_geometry": (ctypes.c_int, [_DP, _IP, _U8P, _IP]),
+    "lbm_throat_lattice_features": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
                                             ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
                                             ctypes.POINTER(lbm_increment), _VP]),
@@ -370,6 +371,18 @@ def lbm_throat_geometry(spheres3):
     _check(load().lbm_throat_geometry(sp.ctypes.data_as(_DP), dims, mask.ctypes.data_as(_U8P), probe),
            "lbm_throat_geometry")
     return mask, tuple(probe)
+
+
+THROAT_LATTICE_FEATURES = 14
+
+
+def lbm_throat_lattice_features(throats) -> np.ndarray:
+    """n x 14 lattice description of each throat box (lbm_throat_lattice_features)."""
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
+    out = np.empty((th.shape[0], THROAT_LATTICE_FEATURES), dtype=np.float64)
+    _check(load().lbm_throat_lattice_features(th.ctypes.data_as(_DP), th.shape[0], out.ctypes.data_as(_DP)),
+           "lbm_throat_lattice_features")
+    return out
 
 
 def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None,

@@ -27,13 +27,11 @@
 // streams to.
 #include <algorithm>
 #include <array>
-#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "lbm_step_core.cuh"
@@ -455,31 +453,6 @@ __global__ void throat_init_kernel(const ThroatRec* __restrict__ recs, int n, fl
             }
         }
     }
-}
-
-// f(t) for t in [0, n) on the host cores.  Returns false if an iteration threw
-// (host allocation failure).
-template <class F>
-bool host_parallel_for(int n, F&& f) {
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int nt = std::max(1, std::min(n, (int)std::min(32u, hw)));
-    std::atomic<int> next{0};
-    std::atomic<bool> ok{true};
-    auto work = [&]() {
-        for (int t; (t = next.fetch_add(1)) < n;) {
-            try {
-                f(t);
-            } catch (...) {
-                ok = false;
-            }
-        }
-    };
-    std::vector<std::thread> pool;
-    pool.reserve((size_t)nt - 1);
-    for (int i = 0; i + 1 < nt; ++i) pool.emplace_back(work);
-    work();
-    for (std::thread& th : pool) th.join();
-    return ok;
 }
 
 size_t batch_smem() {

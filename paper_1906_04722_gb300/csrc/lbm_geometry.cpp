@@ -204,3 +204,141 @@ void voxelise_throat(const double* sph, uint8_t* mask, int probe[3]) {
 }
 
 }  // namespace lbmk
+
+namespace lbmk {
+
+namespace {
+
+// Squared Euclidean distance transform of one line: d[i] = min_j (f[j] + (i - j)^2),
+// by the lower envelope of the parabolas rooted at every j (Felzenszwalb and
+// Huttenlocher, "Distance transforms of sampled functions", 2012).  f holds 0
+// at background cells and a large finite value (far above any squared distance
+// of the plane) elsewhere.  v, zb: scratch of n and n + 1 entries.
+void edt_line(const double* f, int n, double* d, int* v, double* zb) {
+    int k = 0;
+    v[0] = 0;
+    zb[0] = -1e300;
+    zb[1] = 1e300;
+    for (int q = 1; q < n; ++q) {
+        double s;
+        while (true) {
+            const int p = v[k];
+            s = ((f[q] + (double)q * q) - (f[p] + (double)p * p)) / (2.0 * (q - p));
+            if (s > zb[k]) break;  // zb[0] is below any s: the loop ends at k = 0 at the latest
+            --k;
+        }
+        ++k;
+        v[k] = q;
+        zb[k] = s;
+        zb[k + 1] = 1e300;
+    }
+    k = 0;
+    for (int q = 0; q < n; ++q) {
+        while (zb[k + 1] < q) ++k;
+        const double dq = (double)(q - v[k]);
+        d[q] = dq * dq + f[v[k]];
+    }
+}
+
+// Largest distance from a non-solid cell of plane (nx x ny, x fastest) to the
+// nearest solid cell of that plane; the plane diagonal where it has no solid cell.
+double plane_incircle(const uint8_t* m, int nx, int ny) {
+    const double big = 1e12;  // "no solid cell yet": far above (2 x 512)^2
+    const int nmax = std::max(nx, ny);
+    std::vector<double> g((size_t)nx * ny), f((size_t)nmax), d((size_t)nmax), zb((size_t)nmax + 1);
+    std::vector<int> v((size_t)nmax);
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) f[(size_t)x] = (m[(size_t)y * nx + x] & LBM_MASK_SOLID) ? 0.0 : big;
+        edt_line(f.data(), nx, d.data(), v.data(), zb.data());
+        for (int x = 0; x < nx; ++x) g[(size_t)y * nx + x] = d[(size_t)x];
+    }
+    double best = 0.0;
+    for (int x = 0; x < nx; ++x) {
+        for (int y = 0; y < ny; ++y) f[(size_t)y] = g[(size_t)y * nx + x];
+        edt_line(f.data(), ny, d.data(), v.data(), zb.data());
+        for (int y = 0; y < ny; ++y)
+            if (!(m[(size_t)y * nx + x] & LBM_MASK_SOLID)) best = std::max(best, d[(size_t)y]);
+    }
+    const double diag = (double)nx * nx + (double)ny * ny;
+    return std::sqrt(std::min(best, diag));
+}
+
+void lattice_features(const uint8_t* m, int nx, int ny, int nz, double* o) {
+    const size_t nxy = (size_t)nx * ny;
+    std::vector<long long> area((size_t)nz, 0);
+    long long nonsolid = 0;
+    for (int k = 0; k < nz; ++k) {
+        long long a = 0;
+        for (size_t c = 0; c < nxy; ++c) a += !(m[(size_t)k * nxy + c] & LBM_MASK_SOLID);
+        area[(size_t)k] = a;
+        nonsolid += a;
+    }
+    std::vector<int> planes;
+    for (int k = nz < 3 ? 0 : 1; k < (nz < 3 ? nz : nz - 1); ++k) planes.push_back(k);
+    std::stable_sort(planes.begin(), planes.end(),
+                     [&](int a, int b) { return area[(size_t)a] < area[(size_t)b]; });
+    const int ks = planes[0];
+    const int nsel = std::min<int>(3, (int)planes.size());
+    double inc[3] = {0.0, 0.0, 0.0}, amean3 = 0.0, ainner = 0.0;
+    for (int i = 0; i < nsel; ++i) {
+        inc[i] = plane_incircle(m + (size_t)planes[(size_t)i] * nxy, nx, ny);
+        amean3 += (double)area[(size_t)planes[(size_t)i]];
+    }
+    for (int k : planes) ainner += (double)area[(size_t)k];
+    long long perim = 0;
+    const uint8_t* p = m + (size_t)ks * nxy;
+    auto solid = [&](int x, int y) {
+        return x < 0 || y < 0 || x >= nx || y >= ny || (p[(size_t)y * nx + x] & LBM_MASK_SOLID);
+    };
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            if (!solid(x, y) && (solid(x - 1, y) || solid(x + 1, y) || solid(x, y - 1) || solid(x, y + 1))) ++perim;
+    const double amin = (double)area[(size_t)ks];
+    double imax = 0.0, imean = 0.0;
+    for (int i = 0; i < nsel; ++i) {
+        imax = std::max(imax, inc[i]);
+        imean += inc[i] / nsel;
+    }
+    o[0] = nx;
+    o[1] = ny;
+    o[2] = nz;
+    o[3] = (double)nonsolid / ((double)nxy * nz);
+    o[4] = amin;
+    o[5] = std::sqrt(amin / 3.14159265358979323846);
+    o[6] = ainner / (double)planes.size();
+    o[7] = (double)ks / nz;
+    o[8] = inc[0];
+    o[9] = imax;
+    o[10] = imean;
+    o[11] = amin / (double)std::max<long long>(perim, 1);
+    o[12] = (double)perim;
+    o[13] = amean3 / nsel;
+}
+
+}  // namespace
+
+}  // namespace lbmk
+
+using namespace lbmk;
+
+extern "C" int lbm_throat_lattice_features(const double* throats, int n, double* out) {
+    if (!throats || !out || n < 1) {
+        set_error("lbm_throat_lattice_features: NULL argument or empty batch");
+        return LBM_ERR_ARG;
+    }
+    std::vector<int> dims((size_t)3 * n);
+    for (int t = 0; t < n; ++t)
+        if (int rc = lbm_throat_geometry(throats + 12 * t, dims.data() + 3 * t, nullptr, nullptr)) return rc;
+    const bool ok = host_parallel_for(n, [&](int t) {
+        const int* d = dims.data() + 3 * t;
+        std::vector<uint8_t> mask((size_t)d[0] * d[1] * d[2]);
+        int dd[3], probe[3];
+        lbm_throat_geometry(throats + 12 * t, dd, mask.data(), probe);
+        lattice_features(mask.data(), d[0], d[1], d[2], out + (size_t)LBM_THROAT_LATTICE_FEATURES * t);
+    });
+    if (!ok) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    }
+    return LBM_OK;
+}

@@ -9,11 +9,15 @@ spread threshold back to the batched LBM (the fallback that also judges the
 network's error).  Host-side glue only: the LBM runs in lbm_run_throat_batch and
 the network in the lbm_surrogate_* kernels.
 
-Features per throat (7): the three radii and the three centre distances divided
+Inputs per throat (24): the three radii and the three centre distances divided
 by the mean radius R, spheres ordered by decreasing radius, and the contact
-angle in radians.  Outputs (1 + n_incr): p_c^e R (the capillary pressure made
-dimensionless by the throat size, standardised) and the throat's S_w after each
-pressure increment.
+angle in radians (7); what the lattice makes of the throat box
+(lbm_throat_lattice_features: its size, fluid fraction, the narrowest sections'
+areas, lattice incircles and perimeter, 14); and three of those lengths over R.
+The lattice part matters: the entry pressure follows the narrowest section as
+the voxelised box resolves it, which the continuous geometry alone does not fix.
+Outputs (1 + n_incr): p_c^e R (the capillary pressure made dimensionless by the
+throat size, standardised) and the throat's S_w after each pressure increment.
 """
 from __future__ import annotations
 
@@ -22,7 +26,7 @@ import time
 
 import numpy as np
 
-from . import Surrogate, lbm_run_throat_batch
+from . import Surrogate, lbm_run_throat_batch, lbm_throat_lattice_features
 
 
 def contact_angle_estimate(g_ads_w: float, g_ads_nw: float, G: float, rho_major: float, rho_minor: float) -> float:
@@ -45,6 +49,16 @@ def throat_features(triples: np.ndarray, theta: float) -> np.ndarray:
     d02 = np.linalg.norm(c[:, 0] - c[:, 2], axis=1)
     X = np.c_[r / R[:, None], d01 / R, d12 / R, d02 / R, np.full(len(t), theta)]
     return X.astype(np.float32), R
+
+
+N_INPUTS = 24
+
+
+def surrogate_inputs(triples, theta: float):
+    """n x N_INPUTS network inputs (see the module docstring) and the mean radii."""
+    X, R = throat_features(triples, theta)
+    L = lbm_throat_lattice_features(triples)
+    return np.c_[X, L, L[:, [5, 8, 9]] / R[:, None]].astype(np.float32), R
 
 
 def throat_incircle(triples) -> np.ndarray:
@@ -108,7 +122,7 @@ class ThroatSurrogate:
     def __init__(self, n_incr: int, n_members: int = 5, n_hidden: int = 256, n_layers: int = 4, half: bool = False,
                  seed: int = 0, spread_tol: float = 0.02):
         self.n_incr = n_incr
-        self.net = Surrogate(7, 1 + n_incr, n_hidden=n_hidden, n_layers=n_layers, n_members=n_members, half=half,
+        self.net = Surrogate(N_INPUTS, 1 + n_incr, n_hidden=n_hidden, n_layers=n_layers, n_members=n_members, half=half,
                              seed=seed)
         self.spread_tol = spread_tol
         self.x_mu = self.x_sd = None
@@ -146,8 +160,8 @@ class ThroatSurrogate:
     def predict_with_fallback(self, triples, theta, params, rho_in_nw, n_steps, rho_out_w):
         """Surrogate for confident throats, batched LBM for the rest.  Returns
         (p_ce, used_lbm mask, seconds in the network, seconds in the LBM)."""
-        X, R = throat_features(triples, theta)
         t0 = time.perf_counter()
+        X, R = surrogate_inputs(triples, theta)
         pce, rel, _ = self.predict(X, R)
         t_net = time.perf_counter() - t0
         fall = rel > self.spread_tol

@@ -6,9 +6,10 @@ members disagree on p_c^e by more than a relative spread (2 %, the design value,
 and 5 %).  The LBM result of every held-out throat judges the network.  Shown: the
 p_c^e error of the throats the network answers, the fallback fraction, and the
 throats per second gained over running the LBM for every held-out throat.  The
-LBM's p_c^e is read off a 32-step pressure ladder and depends on how the spheres
-fall on the lattice, so it is not a smooth function of the seven features: the
-bars are a median error below 8 % and more than half the throats answered at 5 %.
+LBM's p_c^e is read off a 32-step pressure ladder (about 6 % apart near invasion)
+and depends on how the spheres fall on the lattice; the inputs carry a lattice
+description of each box for that reason.  Bars: a median error below 8 % and more
+than half the throats answered at 5 %.
 """
 import json
 import os
@@ -47,7 +48,7 @@ def test_surrogate_gain_over_lbm(lbm):
     for seed in (10, 11, 12):
         tri = W.delaunay_throats(W.sample_spheres(192, seed=seed), 1024, seed=seed)
         res, rows = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
-        X, R = S.throat_features(tri, theta)
+        X, R = S.surrogate_inputs(tri, theta)
         Y, ok = S.ThroatSurrogate.targets(res, rows, R)
         Xs.append(X[ok])
         Ys.append(Y[ok])

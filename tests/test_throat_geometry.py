@@ -53,3 +53,55 @@ def test_throat_incircle_closed_forms():
     # the brute force's grid (about 0.06 cells apart) can only fall short of the maximum
     got = S.throat_incircle(t[None])[0]
     assert best - 1e-9 <= got <= best + 0.06
+
+
+def _lattice_features_reference(mask):
+    """The 14 numbers of lbm_throat_lattice_features, from their definitions in
+    lbm.h, with scipy's exact Euclidean distance transform."""
+    from scipy import ndimage
+    nz, ny, nx = mask.shape
+    fl = (mask & 1) == 0
+    area = fl.reshape(nz, -1).sum(axis=1)
+    planes = np.arange(1, nz - 1) if nz >= 3 else np.arange(nz)
+    planes = planes[np.argsort(area[planes], kind="stable")]
+    first = planes[:3]
+    inc = [float(ndimage.distance_transform_edt(fl[k]).max()) for k in first]
+    p = np.pad(fl[planes[0]], 1, constant_values=False)
+    edge = (~p[:-2, 1:-1]) | (~p[2:, 1:-1]) | (~p[1:-1, :-2]) | (~p[1:-1, 2:])
+    perim = int((fl[planes[0]] & edge).sum())
+    amin = float(area[planes[0]])
+    return np.array([nx, ny, nz, fl.mean(), amin, np.sqrt(amin / np.pi), area[planes].mean(), planes[0] / nz,
+                     inc[0], max(inc), np.mean(inc), amin / max(perim, 1), perim, area[first].mean()])
+
+
+def test_throat_lattice_features_match_reference(lbm):
+    """Host lattice description of throat boxes (surrogate inputs) against the
+    definitions in lbm.h computed with numpy and scipy.ndimage."""
+    pytest.importorskip("scipy")
+    throats = W.delaunay_throats(W.sample_spheres(192, seed=3), 40, seed=5)
+    F = lbm.lbm_throat_lattice_features(throats)
+    assert F.shape == (len(throats), lbm.THROAT_LATTICE_FEATURES)
+    for t, th in enumerate(throats):
+        mask, _ = lbm.lbm_throat_geometry(th)
+        np.testing.assert_allclose(F[t], _lattice_features_reference(mask), rtol=1e-12, atol=1e-9)
+
+
+def test_lattice_reference_against_brute_force(lbm):
+    """Pin the reference itself on hand-made planes: its incircle equals the brute
+    force max over fluid cells of the min distance to a solid cell, and its
+    perimeter the count of fluid cells with a solid 4-neighbour."""
+    rng = np.random.default_rng(4)
+    for r in (3, 6, 8.5):
+        y, x = np.mgrid[-10:11, -12:13]
+        plane = np.where(x * x + (1.3 * y) ** 2 <= r * r, 0, 1).astype(np.uint8)
+        plane[rng.random(plane.shape) < 0.03] = 1  # a few grains inside
+        mask = np.stack([np.ones_like(plane)] + [plane] * 3 + [np.ones_like(plane)])
+        f = _lattice_features_reference(mask)
+        fy, fx = np.nonzero(plane == 0)
+        sy, sx = np.nonzero(plane == 1)
+        d2 = (fy[:, None] - sy[None]) ** 2 + (fx[:, None] - sx[None]) ** 2
+        assert f[8] == pytest.approx(np.sqrt(d2.min(axis=1).max()))
+        solid = np.pad(plane == 1, 1, constant_values=True)
+        edge = solid[:-2, 1:-1] | solid[2:, 1:-1] | solid[1:-1, :-2] | solid[1:-1, 2:]
+        assert f[12] == ((plane == 0) & edge).sum()
+        assert f[4] == (plane == 0).sum()
