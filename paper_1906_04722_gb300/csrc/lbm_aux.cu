@@ -12,14 +12,15 @@ __device__ __forceinline__ bool fluid_nw(uint8_t m) { return !(m & (LBM_MASK_SOL
 // Geometry words (layout in lbm_internal.h).  For every direction k the pull
 // source x - e_k decides the bounce bit of each component; the neighbour
 // x + e_k contributes 36 w_k e_k to the adhesion vector when it is grain.
-__global__ void geometry_kernel(const uint8_t* __restrict__ mask, uint32_t* __restrict__ nbr,
-                                uint32_t* __restrict__ nbr_nw, uint32_t* __restrict__ adh, Geom g) {
-    const long long N = (long long)g.nxy * g.nz;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % g.nx);
-        const int y = (int)((c / g.nx) % g.ny);
-        const int z = (int)(c / g.nxy);
-        const uint8_t m = mask[c];
+// One thread per cell: x and y from the block and thread, z from blockIdx.z.
+__global__ void __launch_bounds__(256) geometry_kernel(const uint8_t* __restrict__ mask, uint32_t* __restrict__ nbr,
+                                                       uint32_t* __restrict__ nbr_nw, uint32_t* __restrict__ adh,
+                                                       Geom g) {
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y, z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    {
+        const long long c = (long long)z * g.nxy + (long long)y * g.nx + x;
+        const uint8_t m = __ldg(mask + c);
         uint32_t cls;
         if (m & LBM_MASK_SOLID) cls = CLS_SOLID;
         else if (m & LBM_MASK_INLET) cls = CLS_INLET;
@@ -37,7 +38,7 @@ __global__ void geometry_kernel(const uint8_t* __restrict__ mask, uint32_t* __re
                 bw |= 1u << k;
                 bn |= 1u << k;
             } else {
-                const uint8_t ms = mask[(long long)sz * g.nxy + (long long)sy * g.nx + sx];
+                const uint8_t ms = __ldg(mask + (long long)sz * g.nxy + (long long)sy * g.nx + sx);
                 if (!fluid_w(ms)) bw |= 1u << k;
                 if (!fluid_nw(ms)) bn |= 1u << k;
             }
@@ -46,7 +47,7 @@ __global__ void geometry_kernel(const uint8_t* __restrict__ mask, uint32_t* __re
             const int ty = wrap1(y + EY(k), g.ny, g.py, ok2);
             const int tz = wrap1(z + EZ(k), g.nz, g.pz, ok2);
             if (ok2) {
-                const uint8_t mt = mask[(long long)tz * g.nxy + (long long)ty * g.nx + tx];
+                const uint8_t mt = __ldg(mask + (long long)tz * g.nxy + (long long)ty * g.nx + tx);
                 if ((mt & LBM_MASK_SOLID) && (mt & LBM_MASK_ADHESIVE)) {
                     ax += W36(k) * EX(k);
                     ay += W36(k) * EY(k);
@@ -71,9 +72,10 @@ __global__ void init_kernel(const float* __restrict__ rho0, float* __restrict__ 
                             const uint32_t* __restrict__ nbr_nw, Geom g) {
     const long long N = (long long)g.nxy * g.nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % g.nx);
-        const int y = (int)((c / g.nx) % g.ny);
-        const int z = (int)(c / g.nxy);
+        const int ci = (int)c;  // a domain holds fewer than 2^31 cells (lbm_create_domain)
+        const int x = ci % g.nx;
+        const int y = (ci / g.nx) % g.ny;
+        const int z = ci / g.nxy;
         const uint32_t w = nbr[c];
         const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
         for (int s = 0; s < 2; ++s) {
@@ -112,9 +114,10 @@ __global__ void density_kernel(const float* __restrict__ f, float* __restrict__ 
                                const uint32_t* __restrict__ nbr_nw, Geom g) {
     const long long N = (long long)g.nxy * g.nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % g.nx);
-        const int y = (int)((c / g.nx) % g.ny);
-        const int z = (int)(c / g.nxy);
+        const int ci = (int)c;  // a domain holds fewer than 2^31 cells (lbm_create_domain)
+        const int x = ci % g.nx;
+        const int y = (ci / g.nx) % g.ny;
+        const int z = ci / g.nxy;
         Column col = make_column(x, y, g);
         float dummy[2][Q];
         float rw, rn;
@@ -144,9 +147,10 @@ __global__ void __launch_bounds__(MEAS_THREADS) measure_kernel(const float* __re
     for (int i = 0; i < NMEAS; ++i) acc[i] = 0.0;
     const long long N = (long long)g.nxy * g.nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % g.nx);
-        const int y = (int)((c / g.nx) % g.ny);
-        const int z = (int)(c / g.nxy);
+        const int ci = (int)c;  // a domain holds fewer than 2^31 cells (lbm_create_domain)
+        const int x = ci % g.nx;
+        const int y = (ci / g.nx) % g.ny;
+        const int z = ci / g.nxy;
         Column col = make_column(x, y, g);
         float dummy[2][Q];
         float rwf, rnf;
@@ -189,8 +193,8 @@ int grid_for(long long n, int threads) {
 
 cudaError_t launch_geometry(const uint8_t* mask, uint32_t* nbr, uint32_t* nbr_nw, uint32_t* adh, const Geom& g,
                             cudaStream_t s) {
-    const long long N = (long long)g.nxy * g.nz;
-    geometry_kernel<<<grid_for(N, 256), 256, 0, s>>>(mask, nbr, nbr_nw, adh, g);
+    const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    geometry_kernel<<<grid, dim3(32, 8), 0, s>>>(mask, nbr, nbr_nw, adh, g);
     return cudaGetLastError();
 }
 

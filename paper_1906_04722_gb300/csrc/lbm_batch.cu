@@ -34,6 +34,7 @@
 #include <string>
 #include <vector>
 
+#include "lbm_host.h"
 #include "lbm_step_core.cuh"
 
 namespace lbmk {

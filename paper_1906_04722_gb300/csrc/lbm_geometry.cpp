@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "lbm_host.h"
 #include "lbm_internal.h"
 
 namespace lbmk {
@@ -73,40 +74,44 @@ struct Prism {
 
 void voxelise_box(int nx, int ny, int nz, const double* spheres, int n_spheres, int prism_clip, int reservoirs,
                   int membrane_layers, uint8_t* mask) {
-    const long long N = (long long)nx * ny * nz;
-    std::memset(mask, 0, (size_t)N);
-    // grain: visit each sphere's bounding box only
-    for (int i = 0; i < n_spheres; ++i) {
-        const double* s = spheres + 4 * i;
-        const int x0 = std::max(0, (int)std::floor(s[0] - s[3]) - 1), x1 = std::min(nx - 1, (int)std::ceil(s[0] + s[3]) + 1);
-        const int y0 = std::max(0, (int)std::floor(s[1] - s[3]) - 1), y1 = std::min(ny - 1, (int)std::ceil(s[1] + s[3]) + 1);
-        const int z0 = std::max(0, (int)std::floor(s[2] - s[3]) - 1), z1 = std::min(nz - 1, (int)std::ceil(s[2] + s[3]) + 1);
-        for (int z = z0; z <= z1; ++z)
+    const bool clip = prism_clip && n_spheres >= 3 && spheres != nullptr;
+    const Prism prism = clip ? Prism(spheres, spheres + 4, spheres + 8) : Prism();
+    const size_t nxy = (size_t)nx * ny;
+    // one plane per task on the host cores; every cell's value depends on that
+    // cell alone, so the result does not depend on the order
+    host_parallel_for(nz, [&](int z) {
+        uint8_t* m = mask + (size_t)z * nxy;
+        std::memset(m, 0, nxy);
+        // grain: each sphere's bounding box within this plane
+        for (int i = 0; i < n_spheres; ++i) {
+            const double* s = spheres + 4 * i;
+            const int z0 = (int)std::floor(s[2] - s[3]) - 1, z1 = (int)std::ceil(s[2] + s[3]) + 1;
+            if (z < z0 || z > z1) continue;
+            const int x0 = std::max(0, (int)std::floor(s[0] - s[3]) - 1), x1 = std::min(nx - 1, (int)std::ceil(s[0] + s[3]) + 1);
+            const int y0 = std::max(0, (int)std::floor(s[1] - s[3]) - 1), y1 = std::min(ny - 1, (int)std::ceil(s[1] + s[3]) + 1);
             for (int y = y0; y <= y1; ++y)
                 for (int x = x0; x <= x1; ++x)
                     if (ball_contains((double)x, (double)y, (double)z, s))
-                        mask[((long long)z * ny + y) * nx + x] = LBM_MASK_SOLID | LBM_MASK_ADHESIVE;
-    }
-    const bool clip = prism_clip && n_spheres >= 3 && spheres != nullptr;
-    const Prism prism = clip ? Prism(spheres, spheres + 4, spheres + 8) : Prism();
-    for (int z = 0; z < nz; ++z)
+                        m[(size_t)y * nx + x] = LBM_MASK_SOLID | LBM_MASK_ADHESIVE;
+        }
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
-                const long long c = ((long long)z * ny + y) * nx + x;
-                if (mask[c]) continue;
+                uint8_t& c = m[(size_t)y * nx + x];
+                if (c) continue;
                 if (clip) {
                     const double p[3] = {(double)x, (double)y, (double)z};
                     if (!prism.contains(p)) {
-                        mask[c] = LBM_MASK_SOLID;
+                        c = LBM_MASK_SOLID;
                         continue;
                     }
                 }
                 if (reservoirs) {
-                    if (z == 0) mask[c] = LBM_MASK_INLET;
-                    else if (z == nz - 1) mask[c] = LBM_MASK_OUTLET;
-                    else if (z >= nz - 1 - membrane_layers) mask[c] = LBM_MASK_MEMBRANE;
+                    if (z == 0) c = LBM_MASK_INLET;
+                    else if (z == nz - 1) c = LBM_MASK_OUTLET;
+                    else if (z >= nz - 1 - membrane_layers) c = LBM_MASK_MEMBRANE;
                 }
             }
+    });
 }
 
 // Throat frame of Sec. 2.2.2 for centres c0, c1, c2: e1 along c1 - c0, e3 the
