@@ -286,6 +286,15 @@ int lbm_surrogate_train(lbm_surrogate* s, const float* X, const float* T, int n,
 /* lbm_surrogate_predict -- ensemble mean and standard deviation per output. */
 int lbm_surrogate_predict(lbm_surrogate* s, const float* X, int n, float* mean, float* spread);
 void lbm_surrogate_destroy(lbm_surrogate* s);
+/* lbm_surrogate_selftest_wait -- checks the failure path of the surrogate GEMM's
+ * waits for its tensor-core MMAs: one CTA runs the GEMM kernel with the MMA issue
+ * switched off, so that its completion barrier never completes, and its bounded
+ * waits limited to limit_us microseconds (1 .. 1e7; two waits run out).  *gave_up
+ * is set to 1 when the kernel gave up and reported it through its error flag (the
+ * expected outcome), 0 otherwise; it frees its tensor memory either way and the
+ * context stays usable.  Synchronising (legacy default stream).  No counterpart
+ * in the paper. */
+int lbm_surrogate_selftest_wait(int limit_us, int* gave_up);
 
 /* lbm_get_density -- densities of the current state, 2 x N doubles
  * (component-major), 0 where a component is not fluid. Synchronising. */

@@ -126,6 +126,7 @@ SIGNATURES = {
     "lbm_get_step_kernel": (ctypes.c_int, [_VP, _IP, _IP]),
     "lbm_autotune": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(lbm_tune_result)]),
     "lbm_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int, _IP]),
+    "lbm_surrogate_selftest_wait": (ctypes.c_int, [ctypes.c_int, _IP]),
     "lbm_throat_geometry": (ctypes.c_int, [_DP, _IP, _U8P, _IP]),
     "lbm_throat_lattice_features": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
@@ -358,6 +359,13 @@ def lbm_selftest_bounded_wait(limit_us: int) -> bool:
     flag = ctypes.c_int(0)
     _check(load().lbm_selftest_bounded_wait(int(limit_us), ctypes.byref(flag)), "lbm_selftest_bounded_wait")
     return flag.value == 1
+
+def lbm_surrogate_selftest_wait(limit_us: int) -> bool:
+    """True when the surrogate GEMM's bounded wait for its MMAs, run with no MMA
+    issued, gave up after limit_us and reported it (lbm_surrogate_selftest_wait)."""
+    flag = ctypes.c_int(0)
+    _check(load().lbm_surrogate_selftest_wait(int(limit_us), ctypes.byref(flag)), "lbm_surrogate_selftest_wait")
+    return bool(flag.value)
 
 
 def lbm_throat_geometry(spheres3):

@@ -65,7 +65,9 @@ struct GemmArgs {
     int epi;
     // per ensemble member (grid z): element offsets of A, B, C, bias, mask
     long long zA, zB, zC, zBias, zMask;
-    int* err;  // set to 1 when a wait for the tensor cores ran out
+    int* err;                    // set to 1 when a wait for the tensor cores ran out
+    unsigned long long wait_ns;  // limit of each such wait
+    int skip_mma;                // self-test only: issue no MMA, so that the waits run out
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -102,14 +104,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Wait for the phase of the given parity to complete, at most GEMM_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Wait for the phase of the given parity to complete, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
     if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
         for (int i = 0; i < 64; ++i)
             if (mbar_test(bar, parity)) return true;
-        if (global_ns() - t0 > GEMM_WAIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(GemmArgs p) {
         unsigned char* sa = smem + b * STAGE;
         unsigned char* sb = sa + A_TILE;
         if (c >= 2) {  // chunk c - 2 used this stage: its MMAs must have finished reading it
-            const bool ok = mbar_wait_bounded(b ? bar1 : bar0, (uint32_t)(((c - 2) >> 1) & 1));
+            const bool ok = mbar_wait_bounded(b ? bar1 : bar0, (uint32_t)(((c - 2) >> 1) & 1), p.wait_ns);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(GemmArgs p) {
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (tid == 0) {
+        if (tid == 0 && !p.skip_mma) {
             const uint32_t a_addr = smem_u32(sa), b_addr = smem_u32(sb);
 #pragma unroll
             for (int kk = 0; kk < TK / 16; ++kk) {  // K = 16 per MMA: two core matrices along K
@@ -229,11 +231,11 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(GemmArgs p) {
     // The commit of the last chunk issued covers every MMA before it.
     const int last = issued - 1;
     const uint32_t last_bar = (last & 1) ? bar1 : bar0, last_parity = (uint32_t)((last >> 1) & 1);
-    if (!failed && issued > 0) failed = __syncthreads_or(!mbar_wait_bounded(last_bar, last_parity));
+    if (!failed && issued > 0) failed = __syncthreads_or(!mbar_wait_bounded(last_bar, last_parity, p.wait_ns));
     if (failed) {
         if (tid == 0) atomicOr(p.err, 1);
         // give the MMAs already issued a second bounded wait before their accumulator is freed
-        if (issued > 0) mbar_wait_bounded(last_bar, last_parity);
+        if (issued > 0) mbar_wait_bounded(last_bar, last_parity, p.wait_ns);
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncthreads();
         if (warp == 0)
@@ -452,6 +454,8 @@ int predict_chunk(const lbm_surrogate* s) {
 cudaError_t gemm(const lbm_surrogate* s, GemmArgs a, int members) {
     if (a.M < 1 || a.N < 1 || a.K < 1 || members < 1) return cudaErrorInvalidValue;
     a.err = s->d_err;
+    a.wait_ns = GEMM_WAIT_NS;
+    a.skip_mma = 0;
     dim3 grid((a.N + TN - 1) / TN, (a.M + TM - 1) / TM, members);
     if (s->cfg.half) gemm_kernel<__half><<<grid, GEMM_THREADS, GEMM_SMEM, s->stream>>>(a);
     else gemm_kernel<__nv_bfloat16><<<grid, GEMM_THREADS, GEMM_SMEM, s->stream>>>(a);
@@ -815,6 +819,44 @@ int lbm_surrogate_predict(lbm_surrogate* s, const float* X, int n, float* mean, 
     }
     cleanup();
     return check_gemm_flag(s);
+}
+
+int lbm_surrogate_selftest_wait(int limit_us, int* gave_up) {
+    if (!gave_up || limit_us < 1 || limit_us > 10000000) {
+        set_error("lbm_surrogate_selftest_wait: limit_us in [1, 1e7] and a result pointer");
+        return LBM_ERR_ARG;
+    }
+    *gave_up = 0;
+    float* buf = nullptr;
+    int* d_flag = nullptr;
+    SUR_CUDA(cudaMalloc(&buf, sizeof(float) * 4));
+    cudaError_t e = cudaMalloc(&d_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, sizeof(float) * 4);
+    if (e == cudaSuccess) e = cudaMemset(d_flag, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+    if (e == cudaSuccess) {
+        GemmArgs a{};
+        a.A = buf;
+        a.B = buf + 1;
+        a.C = buf + 2;
+        a.M = a.N = a.K = 1;
+        a.sam = a.sak = a.sbk = a.sbn = a.ldc = 1;
+        a.epi = EPI_NONE;
+        a.err = d_flag;
+        a.wait_ns = 1000ull * (unsigned long long)limit_us;
+        a.skip_mma = 1;  // no MMA and no commit: the completion barrier never completes
+        gemm_kernel<__nv_bfloat16><<<1, GEMM_THREADS, GEMM_SMEM>>>(a);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    cudaFree(d_flag);
+    if (e != cudaSuccess) return sur_fail(e, "lbm_surrogate_selftest_wait");
+    *gave_up = flag != 0;
+    return LBM_OK;
 }
 
 void lbm_surrogate_destroy(lbm_surrogate* s) {

@@ -105,3 +105,15 @@ def test_members_train_independently(lbm):
     assert np.array_equal(alone.get_params(0), pair.get_params(0))
     assert not np.array_equal(pair.get_params(0), pair.get_params(1))
     assert np.allclose(la[0], lp[0], rtol=1e-12, atol=0)
+
+
+def test_gemm_wait_gives_up_and_context_survives(lbm):
+    """The surrogate GEMM's bounded wait for its MMAs, run with no MMA issued
+    (a completion barrier nothing completes, limit 20 ms): the kernel gives up,
+    reports it, frees its tensor memory, and the context runs a forward pass
+    afterwards."""
+    assert lbm.lbm_surrogate_selftest_wait(20000)
+    rng = np.random.default_rng(12)
+    sur = lbm.Surrogate(7, 3, n_hidden=64, n_layers=2, n_members=1, half=0, seed=5)
+    y = sur.forward(0, rng.standard_normal((50, 7)))
+    assert y.shape == (50, 3) and np.all(np.isfinite(y))
