@@ -5,8 +5,8 @@ p_c^e and the drainage curve of that throat (Sec. 2.2.2), each from one LBM run.
 This module learns the map from a throat's geometry to those outputs on throats
 the batched LBM has simulated, predicts new throats with an ensemble, and sends
 every throat whose ensemble members disagree on p_c^e by more than a relative
-spread threshold back to the batched LBM (the fallback that also judges the
-network's error).  Host-side glue only: the LBM runs in lbm_run_throat_batch and
+spread threshold back to the batched LBM (the fallback against which the
+network's error is also measured).  Host-side glue only: the LBM runs in lbm_run_throat_batch and
 the network in the lbm_surrogate_* kernels.
 
 Inputs per throat (24): the three radii and the three centre distances divided

@@ -3,7 +3,7 @@
 Training throats come from the batched LBM on seeded packings; held-out throats
 from another packing are predicted by the ensemble with LBM fallback where the
 members disagree on p_c^e by more than a relative spread (2 %, the design value,
-and 5 %).  The LBM result of every held-out throat judges the network.  Shown: the
+and 5 %).  The network's error is measured against the LBM result of every held-out throat.  Shown: the
 p_c^e error of the throats the network answers, the fallback fraction, and the
 throats per second gained over running the LBM for every held-out throat.  The
 LBM's p_c^e is read off a 32-step pressure ladder (about 6 % apart near invasion)
@@ -21,7 +21,8 @@ import pytest
 import workloads as W
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+# reports (JSON) go to the directory named by LBM_REPORT_DIR, when it is set
+OUT = os.environ.get("LBM_REPORT_DIR", "")
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +60,7 @@ def test_surrogate_gain_over_lbm(lbm):
     t0 = time.perf_counter()
     losses = sur.fit(X, Y, epochs=300, batch=256, lr=1e-3, seed=2)
     t_train = time.perf_counter() - t0
-    # held-out throats from another packing, judged by the LBM
+    # held-out throats from another packing, with the LBM result of each
     tri = W.delaunay_throats(W.sample_spheres(192, seed=20), 1024, seed=20)
     t0 = time.perf_counter()
     res_ref, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
@@ -81,9 +82,10 @@ def test_surrogate_gain_over_lbm(lbm):
                              "pce_rel_err_all_median": float(np.median(err)),
                              "throats_per_s_surrogate_with_fallback": len(tri) / (t_net + t_fb)}
     print(json.dumps(rep))
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "surrogate_report.json"), "w") as fh:
-        json.dump(rep, fh, indent=1)
+    if OUT:
+        os.makedirs(OUT, exist_ok=True)
+        with open(os.path.join(OUT, "surrogate_report.json"), "w") as fh:
+            json.dump(rep, fh, indent=1)
     assert losses[:, -1].mean() < 0.2 * losses[:, 0].mean()
     r5 = rep["tol_0.05"]
     assert r5["fallback_fraction"] < 0.5
