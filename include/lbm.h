@@ -237,8 +237,12 @@ int lbm_throat_lattice_features(const double* throats, int n, double* out);
  * (Sec. 2.2.2: one LBM run per pore throat, p_c^e from its drainage ladder) for
  * n throats at once: each throat's box (lbm_throat_geometry) starts filled with
  * wetting fluid, then runs the schedule's ladder exactly as lbm_run_drainage
- * would on that box alone.  All throats share one device arena; one persistent
- * launch per increment processes them largest first, one CTA per throat.
+ * would on that box alone.  All throats run together in one device arena, in the
+ * form sched->batch_form selects (LBM_BATCH_CELLS by default: the throats'
+ * non-solid cells as one list, two launches per time step; see the forms
+ * above); one increment is captured as a CUDA graph and relaunched.  Every form
+ * gives the same rows bit for bit.  The host set-up (voxelising the boxes,
+ * building the lists) runs on all host cores.
  *   throats   n x 3 x 4 doubles (host)
  *   params    tau, G, G_ads, body_force, rho_major, rho_minor are used
  *   results   n entries (host, caller-owned)
