@@ -19,11 +19,13 @@ Printed JSON line (rank 0):
   throats    pore throats per second on 1024 Delaunay throats of the sample
              packing (boxes 24^3..64^3): the plain per-throat loop (create,
              ladder of set_pressure_bc + steps + measure, destroy) on a strided
-             subset, the batched persistent launch, and the trained surrogate with
-             batched-LBM fallback where the ensemble spread exceeds 2 % (and 5 %),
-             with the surrogate's p_c^e error against the batched LBM.
+             subset, the batch (cell-list form, with the tile and persistent
+             forms beside it), and the surrogate (trained on six other packings)
+             with batched-LBM fallback where the ensemble spread exceeds 2 % (and
+             5 %), with the surrogate's p_c^e error against the batched LBM.
 --impl reference times that oracle alone (the method has no other reference
-implementation): rank 0 only.
+implementation): rank 0 only.  --drainage runs the sample's full drainage;
+--throat-batch FORM times one 1024-throat batch in one form.
 """
 from __future__ import annotations
 
