@@ -479,7 +479,7 @@ def run_ours(args, rank, world, local):
         d2.close()
         N = box[0] * box[1] * box[2]
         e2e_val = world * n_upd * E2E_SUBSTEPS * args.e2e_steps / dt / 1e6
-        h2d = int((N + 2 * N * 4 + spheres.nbytes) / args.e2e_steps) + 16
+        h2d = int((N + spheres.nbytes) / args.e2e_steps) + 16  # mask (voxelised on the host), spheres, BC values
         d2h = 16 * 8
 
     clocks = clk.summary()

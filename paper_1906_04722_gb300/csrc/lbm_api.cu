@@ -237,13 +237,19 @@ int wait_domain(lbm_domain* d) {
     }
 }
 
-// Upload rest-equilibrium densities (host doubles, 2 x N) and build the stored
-// populations from them.
-int upload_densities(lbm_domain* d, const double* rho) {
-    const long long N = d->N;
-    std::vector<float> tmp((size_t)(2 * N));
-    for (long long i = 0; i < 2 * N; ++i) tmp[(size_t)i] = (float)rho[i];
-    LBM_CUDA(cudaMemcpyAsync(d->d_rho, tmp.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, d->stream));
+// The default initial densities (2 x N floats): wetting fluid everywhere, the
+// non-wetting reservoir on the inlet layer, from the mask on the device.
+__global__ void rest_density_kernel(const uint8_t* __restrict__ mask, float* __restrict__ rho, long long N,
+                                    float rho_major, float rho_minor) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const bool inlet = mask[c] & LBM_MASK_INLET;
+        rho[c] = inlet ? rho_minor : rho_major;
+        rho[N + c] = inlet ? rho_major : rho_minor;
+    }
+}
+
+// Build the stored populations from the densities in d->d_rho.
+int init_from_densities(lbm_domain* d) {
     if (d->params.precision == 0) {
         LBM_CUDA(launch_init(d->d_rho, d->f[0], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
     } else {
@@ -254,6 +260,16 @@ int upload_densities(lbm_domain* d, const double* rho) {
     d->step = 0;
     d->ghosts_ok = false;
     return wait_domain(d);
+}
+
+// Upload rest-equilibrium densities (host doubles, 2 x N) and build the stored
+// populations from them.
+int upload_densities(lbm_domain* d, const double* rho) {
+    const long long N = d->N;
+    std::vector<float> tmp((size_t)(2 * N));
+    for (long long i = 0; i < 2 * N; ++i) tmp[(size_t)i] = (float)rho[i];
+    LBM_CUDA(cudaMemcpyAsync(d->d_rho, tmp.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, d->stream));
+    return init_from_densities(d);
 }
 
 int create_common(const lbm_params* params, const uint8_t* mask_host, const int box[3], void* stream,
@@ -333,13 +349,13 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     d->n_fluid = nf;
 
     // default initial state: wetting fluid everywhere, non-wetting reservoir on the inlet layer
-    std::vector<double> rho((size_t)(2 * d->N));
-    for (long long c = 0; c < d->N; ++c) {
-        const bool inlet = mask_host[c] & LBM_MASK_INLET;
-        rho[(size_t)c] = inlet ? params->rho_minor : params->rho_major;
-        rho[(size_t)(d->N + c)] = inlet ? params->rho_major : params->rho_minor;
+    rest_density_kernel<<<1216, 256, 0, d->stream>>>(d->d_mask, d->d_rho, d->N, (float)params->rho_major,
+                                                     (float)params->rho_minor);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) {
+        set_error(std::string("rest_density_kernel: ") + cudaGetErrorString(e));
+        return fail(LBM_ERR_CUDA);
     }
-    int rc = upload_densities(d, rho.data());
+    int rc = init_from_densities(d);
     if (rc != LBM_OK) return fail(rc);
     *out = d;
     return LBM_OK;
