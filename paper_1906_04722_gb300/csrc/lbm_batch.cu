@@ -1,30 +1,30 @@
-// lbm_batch.cu -- many pore throats in one persistent launch per pressure increment.
+// lbm_batch.cu -- many pore throats per call (lbm_run_throat_batch), in three
+// forms that give the same rows bit for bit.
 //
 // The hybrid method runs one small LBM simulation per pore throat (Sec. 2.2.2)
 // and the paper assigns one throat per CPU core (Sec. 4).  Here all throats of
-// a batch live in one device arena (each with its own box, plane stride and
-// geometry words, found through a record table) and a persistent grid of CTAs
-// pulls throats off a work counter, largest first.  A CTA owns its throat for a
-// whole increment: it runs the increment's time steps on the throat box tile by
-// tile (step_column, the same fused step as the single-domain kernel), over the
-// tiles whose columns hold a non-solid cell (the box is the bounding box of a
-// triangular prism: the columns outside the triangle are solid), with a
-// CTA barrier between steps as the only synchronisation, then measures the throat
-// (FP64 CTA reduction) and reads the probe cell.  One launch per increment; the
-// launches of all increments are captured in one CUDA graph.
+// a batch run together on the GPU, each with its own box, geometry words and
+// reservoir ladder, found through a record table.
 //
-// A batch of few throats leaves most SMs idle in that form and waits on its
-// largest throat.  The per-step form spreads every throat over many CTAs
-// instead: one launch per time step over a work list of (throat, active tile,
-// z segment) items, the kernel boundary ordering the steps, then one
-// measurement launch with a CTA per throat.  One increment is captured as a
-// graph and relaunched; the increment index lives in device memory.
+// Cell list (the default).  A throat box is mostly grain: it is the bounding box
+// of a triangular prism whose corners the spheres fill.  This form stores the
+// populations of the non-solid cells only, compactly and after streaming, and
+// runs two launches per time step over that list: densities, then the
+// collision, which pushes every value to the cell it streams to.  A measurement
+// launch (a CTA per throat) ends each increment.
 //
-// Both forms keep each throat's whole box, and a throat box is mostly grain.
-// The cell-list form (the default) stores the populations of the non-solid
-// cells only, after streaming, and runs two launches per time step over that
-// list: densities, then the collision, which pushes every value to the cell it
-// streams to.
+// Tiles.  One launch per time step over a work list of (throat, active tile,
+// z segment) items of the box layout, the step_column of the single-domain
+// staged kernel; the kernel boundary orders the steps.
+//
+// Persistent.  One launch per increment: a CTA takes a whole throat off a work
+// counter (largest first) and runs the increment's steps on its box tile by
+// tile, with a CTA barrier between steps, then measures it.  A batch of few
+// throats leaves most SMs idle in this form and waits on its largest throat.
+//
+// In the cell-list and tile forms one increment is captured as a CUDA graph and
+// relaunched, the increment index living in device memory; the persistent form
+// captures all increments in one graph.
 #include <algorithm>
 #include <array>
 #include <climits>
