@@ -105,3 +105,19 @@ def test_lattice_reference_against_brute_force(lbm):
         edge = solid[:-2, 1:-1] | solid[2:, 1:-1] | solid[1:-1, :-2] | solid[1:-1, 2:]
         assert f[12] == ((plane == 0) & edge).sum()
         assert f[4] == (plane == 0).sum()
+
+
+def test_surrogate_inputs_layout(lbm):
+    """The surrogate's 24 inputs: the 7 geometric features, the 14 lattice
+    numbers of each box, then three of those lengths over the mean radius."""
+    from paper_1906_04722_gb300 import surrogate as S
+    throats = W.delaunay_throats(W.sample_spheres(128), 12, seed=3)
+    X, R = S.surrogate_inputs(throats, 0.8)
+    assert X.shape == (len(throats), S.N_INPUTS) and X.dtype == np.float32
+    G, R2 = S.throat_features(throats, 0.8)
+    L = lbm.lbm_throat_lattice_features(throats)
+    np.testing.assert_array_equal(R, R2)
+    np.testing.assert_array_equal(X[:, :7], G)
+    np.testing.assert_allclose(X[:, 7:21], L, rtol=1e-6)
+    np.testing.assert_allclose(X[:, 21:], L[:, [5, 8, 9]] / R[:, None], rtol=1e-6)
+    assert np.all(X[:, 6] == np.float32(0.8))
