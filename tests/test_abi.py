@@ -47,12 +47,39 @@ def test_library_exports_every_declared_symbol(lib):
     assert declared_symbols() <= set(lib.SIGNATURES)
 
 
-def test_library_is_built_for_sm_103a(lib):
-    lib.load()
-    out = subprocess.run(["cuobjdump", "--list-elf", lib.library_path()], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
+def test_library_is_built_for_sm_103a_only():
+    """The build compiles every source for sm_103a and nothing else (checked on the
+    build configuration; no tool reads the compiled code)."""
+    from paper_1906_04722_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_new_entry_points_reject_bad_arguments_before_device_work(lib):
+    """Lattice features, the GEMM wait self-test and the batch form are checked
+    on the host before any device work (documented in lbm.h)."""
+    L = lib.load()
+    out = np.zeros(14)
+    assert L.lbm_throat_lattice_features(None, 1, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == lib.LBM_ERR_ARG
+    collinear = np.array([[0, 0, 0, 5], [10, 0, 0, 5], [20, 0, 0, 5]], dtype=np.float64)
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_throat_lattice_features(collinear)
+    assert e.value.code == lib.LBM_ERR_ARG
+    flag = ctypes.c_int(7)
+    assert L.lbm_surrogate_selftest_wait(0, ctypes.byref(flag)) == lib.LBM_ERR_ARG
+    assert L.lbm_surrogate_selftest_wait(20000000, ctypes.byref(flag)) == lib.LBM_ERR_ARG
+    with pytest.raises(ValueError):
+        lib.lbm_run_throat_batch(collinear, lib.make_params(), [2.0], 1, 2.0, form=7)
+    # the C check itself, past the binding
+    ladder = np.array([2.0])
+    sch = lib.lbm_schedule()
+    sch.n_incr, sch.n_steps, sch.rho_out_w, sch.batch_form = 1, 1, 2.0, 7
+    sch.rho_in_nw = ladder.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    res = (lib.lbm_throat_result * 1)()
+    rows = (lib.lbm_increment * 1)()
+    tri = np.array([[0, 0, 0, 5], [10, 0, 0, 5], [5, 9, 0, 5]], dtype=np.float64)
+    rc = L.lbm_run_throat_batch(tri.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, ctypes.byref(lib.make_params()),
+                                ctypes.byref(sch), res, rows, None)
+    assert rc == lib.LBM_ERR_ARG
 
 
 @pytest.mark.parametrize("field,value", [("tau", (0.5, 1.0)), ("precision", 3), ("membrane_layers", -1),
