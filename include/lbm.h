@@ -321,25 +321,27 @@ int lbm_set_state(lbm_domain* d, const float* f_in, long long step);
 
 /* lbm_measure_state_noalloc -- the observables of lbm_measure for a state that
  * lives in caller-owned device memory, computed without allocating any device
- * memory.  The paper has no counterpart: this serves callers that cannot
- * allocate, such as code running while a stream is captured, plug-ins whose
- * host application owns all device memory through its own pool, or loops that
- * cannot absorb the device synchronisation of cudaMalloc/cudaFree.
+ * memory.  The paper has no counterpart: this serves callers that must not
+ * allocate, such as plug-ins whose host application owns all device memory
+ * through its own pool and accounts for every byte, or loops that cannot absorb
+ * the device synchronisation of cudaMalloc/cudaFree.
  *   params    model parameters (only G and periodic are read).
  *   box       (nx, ny, nz), each in [1, 4096], at most 56,000,000 cells in all;
  *             larger states are rejected with LBM_ERR_ARG.
  *   f_dev     DEVICE pointer to the stored populations in the lbm_get_state
  *             layout: 2 x 19 x N floats, f[(s*19 + k) * N + cell].
- *   mask_dev  DEVICE pointer to the N mask bytes (layout above).
- *   stream    cudaStream_t to run on (NULL = legacy stream); the call waits for
- *             it before returning.
+ *   mask_dev  DEVICE pointer to the N mask bytes (layout above); a cell's class
+ *             follows the priority solid > inlet > outlet > membrane, as in a
+ *             domain created from the same mask.
+ *   stream    cudaStream_t to run on (NULL = legacy stream); the call copies its
+ *             sums into host memory and waits for the stream before returning.
  *   out       HOST pointer, filled as by lbm_measure.
  * The reduction scratch is a fixed device array inside the library (about
- * 128 KiB, held by every GPU that loads the library until the process exits).
+ * 128 KiB, held by every GPU that loads the library until the process exits);
+ * each call looks up its device address on the current device (no allocation).
  * All calls share it: calls whose device work overlaps in time race on it.
- * The first call on each device looks up the array's device address; make that
- * first call before any stream capture begins.  Returns LBM_ERR_NONFINITE like
- * lbm_measure, LBM_ERR_CUDA when a CUDA call fails. */
+ * Returns LBM_ERR_NONFINITE like lbm_measure, LBM_ERR_CUDA when a CUDA call
+ * fails. */
 int lbm_measure_state_noalloc(const lbm_params* params, const int box[3], const float* f_dev,
                               const unsigned char* mask_dev, void* stream, lbm_measurement* out);
 

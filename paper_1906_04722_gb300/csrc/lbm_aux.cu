@@ -184,12 +184,20 @@ __global__ void finalize_kernel(const double* __restrict__ partials, int nblocks
 
 int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
-    if (b > 152LL * 16) b = 152LL * 16;
+    const long long cap = 16LL * device_sm_count();
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
 }
 
 }  // namespace
+
+int device_sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    return sms;
+}
 
 cudaError_t launch_geometry(const uint8_t* mask, uint32_t* nbr, uint32_t* nbr_nw, uint32_t* adh, const Geom& g,
                             cudaStream_t s) {
@@ -220,7 +228,8 @@ cudaError_t launch_finalize(const double* partials, int nblocks, double* result,
 int measure_blocks(const Geom& g) {
     const long long N = (long long)g.nxy * g.nz;
     long long b = (N + MEAS_THREADS * 8 - 1) / (MEAS_THREADS * 8);
-    if (b > 152LL * 8) b = 152LL * 8;
+    const long long cap = 8LL * device_sm_count();
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -83,6 +83,9 @@ enum {
 };
 
 // ---------------------------------------------------------------- launchers
+// Streaming multiprocessors of the current device (1 when the query fails:
+// grid-stride kernels stay correct with any grid).
+int device_sm_count();
 struct StepTile {
     int by;    // block rows including the two halo rows (6, 8, 10 or 12)
     int lz;    // z-segment length per CTA

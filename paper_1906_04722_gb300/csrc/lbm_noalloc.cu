@@ -2,21 +2,19 @@
 // allocation.
 //
 // lbm_measure pulls its per-block FP64 partial sums through scratch memory that
-// lbm_create_domain allocated.  Some callers cannot allocate device memory at
-// all: code running while a stream is being captured, plug-ins whose host
-// application owns every device byte through its own pool (a framework's
-// caching allocator that must account for all memory), or control loops that
-// cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.
-// They keep the populations in their own buffers and call
-// lbm_measure_state_noalloc, which takes its scratch from the file-scope
-// device array below instead.
+// lbm_create_domain allocated.  Some callers must not allocate device memory:
+// plug-ins whose host application owns every device byte through its own pool
+// (a framework's caching allocator that must account for all memory), and
+// control loops that cannot afford the implicit device synchronisation of
+// cudaMalloc/cudaFree.  They keep the populations in their own buffers and call
+// lbm_measure_state_noalloc, which takes its scratch from the file-scope device
+// array below instead.  The call still copies its 16 sums to the host and waits
+// for its stream before it returns.
 //
 // The array is a fixed part of the library image: every GPU that loads the
 // library holds it (MAX_BLOCKS x 16 doubles + 16 doubles, about 128 KiB) until
 // the process exits.  All calls share it, so calls whose device work overlaps
 // (on different streams or host threads) race on it.
-#include <mutex>
-
 #include "lbm_device.cuh"
 
 namespace lbmk {
@@ -37,9 +35,22 @@ __device__ __forceinline__ double na_warp_sum(double v) {
     return v;
 }
 
+// Fluid-ness of a pull source for component s, from its raw mask bits (as the
+// geometry words decide bounce-back): solid stops both components, membrane
+// stops the non-wetting one.
 __device__ __forceinline__ bool na_fluid(uint8_t m, int s) {
     if (m & LBM_MASK_SOLID) return false;
     return !(s == 1 && (m & LBM_MASK_MEMBRANE));
+}
+
+// Class of a cell from its mask byte, in the priority order the geometry words
+// use: solid, then inlet, outlet, membrane, fluid.
+__device__ __forceinline__ uint32_t na_class(uint8_t m) {
+    if (m & LBM_MASK_SOLID) return CLS_SOLID;
+    if (m & LBM_MASK_INLET) return CLS_INLET;
+    if (m & LBM_MASK_OUTLET) return CLS_OUTLET;
+    if (m & LBM_MASK_MEMBRANE) return CLS_MEMBRANE;
+    return CLS_FLUID;
 }
 
 // The measurements of lbm_measure, with bounce-back decided from the mask bytes
@@ -54,13 +65,15 @@ __global__ void __launch_bounds__(NA_THREADS) na_measure_kernel(const float* __r
     const long long N = (long long)g.nxy * g.nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const uint8_t m = mask[c];
-        if (m & LBM_MASK_SOLID) continue;
+        const uint32_t cls = na_class(m);
+        if (cls == CLS_SOLID) continue;
         const int x = (int)(c % g.nx);
         const int y = (int)((c / g.nx) % g.ny);
         const int z = (int)(c / g.nxy);
         float rho[2] = {0.f, 0.f};
         for (int s = 0; s < 2; ++s) {
-            if (!na_fluid(m, s)) continue;
+            // a membrane cell holds no non-wetting fluid; every other class holds both
+            if (s == 1 && cls == CLS_MEMBRANE) continue;
             const float* fs = f + (size_t)s * Q * g.plane;
             float r = 0.f;
 #pragma unroll
@@ -78,25 +91,8 @@ __global__ void __launch_bounds__(NA_THREADS) na_measure_kernel(const float* __r
             }
             rho[s] = r;
         }
-        const double rw = rho[0], rn = rho[1];
-        acc[MS_MASS_W] += rw;
-        if (!isfinite(rw)) acc[MS_N_NONFINITE] += 1.0;
-        else if (rw < 0.0) acc[MS_N_NEGATIVE] += 1.0;
-        if (!(m & LBM_MASK_MEMBRANE)) {
-            acc[MS_MASS_NW] += rn;
-            if (!isfinite(rn)) acc[MS_N_NONFINITE] += 1.0;
-            else if (rn < 0.0) acc[MS_N_NEGATIVE] += 1.0;
-        }
-        const double p = (rw + rn) / 3.0 + G * rw * rn / 3.0;  // Eq. 5
-        if (m & LBM_MASK_INLET) { acc[MS_PIN] += p; acc[MS_N_IN] += 1.0; continue; }
-        if (m & LBM_MASK_OUTLET) { acc[MS_POUT] += p; acc[MS_N_OUT] += 1.0; continue; }
-        if (m & LBM_MASK_MEMBRANE) continue;
-        acc[MS_N_FLUID] += 1.0;
-        if (rw > rn) acc[MS_N_W] += 1.0;
-        const double phi = (rw - rn) / (rw + rn);
-        if (fabs(phi) < 0.5) acc[MS_N_INTERFACE] += 1.0;
-        if (phi > 0.9) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
-        if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
+        // the same accumulation as lbm_measure
+        measure_accumulate(acc, cls, (double)rho[0], (double)rho[1], G);
     }
     __shared__ double red[NA_THREADS / 32][NMEAS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -122,33 +118,18 @@ __global__ void na_finalize_kernel(const double* __restrict__ partials, int nblo
     }
 }
 
-// Device address of g_noalloc_scratch, looked up once per device with that
-// device current (the host-side name of the array is only a stand-in).
-std::mutex g_na_mutex;
-double* g_na_ptr[64] = {};
-
+// Device address of g_noalloc_scratch on the current device.  The host-side
+// name of the array is only a stand-in; its device address is looked up on
+// every call (a lookup in the loaded module, no allocation), so that a module
+// reloaded into a new context is never reached through a stale address.
 int scratch_address(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
         return LBM_ERR_CUDA;
     }
-    if (dev < 0 || dev >= 64) {
-        set_error("lbm_measure_state_noalloc supports devices 0..63");
-        return LBM_ERR_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-            return LBM_ERR_CUDA;
-        }
-        g_na_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_na_ptr[dev];
+    *out = static_cast<double*>(p);
     return LBM_OK;
 }
 

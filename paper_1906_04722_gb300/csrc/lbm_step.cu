@@ -168,8 +168,7 @@ StepTile default_tile(const Geom& g) {
     StepTile t;
     t.by = 6;
     t.lead = 2;
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sm_count();
     const long long tiles_xy = (long long)((g.nx + 29) / 30) * ((g.ny + (t.by - 2) - 1) / (t.by - 2));
     long long lz = (g.nz * tiles_xy + 2LL * sms - 1) / (2LL * sms);
     if (lz < 2) lz = 2;

@@ -389,7 +389,8 @@ cudaError_t configure16() {
 
 int grid_cells(long long n) {
     long long b = (n + 255) / 256;
-    if (b > 152LL * 16) b = 152LL * 16;
+    const long long cap = 16LL * device_sm_count();
+    if (b > cap) b = cap;
     return (int)std::max(1LL, b);
 }
 

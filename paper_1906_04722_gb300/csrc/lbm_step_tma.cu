@@ -440,8 +440,7 @@ int tma_default_lz(const Geom& g) {
     // tiles work on the same planes and their halo re-reads hit L2 (a CTA that
     // marched a whole column would drift away from its neighbours).  Small
     // boxes get enough segments to fill the SMs.
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sm_count();
     const long long tiles = (long long)((g.nx + TT_X - 1) / TT_X) * ((g.ny + TT_Y - 1) / TT_Y);
     long long segs = sms / tiles;
     if (segs < 1) segs = 1;

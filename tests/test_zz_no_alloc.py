@@ -1,10 +1,11 @@
-"""lbm_measure_state_noalloc: measurements for callers that cannot allocate
-device memory (stream capture in progress, a host application that owns every
-device byte through its own pool, loops that cannot absorb cudaMalloc's
-synchronisation).  The state lives in caller-owned device buffers (torch
-tensors here); the entry point's only scratch is a fixed device array inside
-the library.  Its results must equal those of lbm_measure on the same state, on
-two calls in a row (the second call must not see leftovers of the first).
+"""lbm_measure_state_noalloc: measurements for callers that must not allocate
+device memory (a host application that owns every device byte through its own
+pool, loops that cannot absorb cudaMalloc's synchronisation).  The state lives
+in caller-owned device buffers (torch tensors here); the entry point's only
+scratch is a fixed device array inside the library.  Its results must equal
+those of lbm_measure on the same state, call after call: a smaller state
+measured after a larger one must not pick up the larger one's leftovers in the
+shared array.
 
 This file is collected last on purpose: a run that stops at the first failure
 has already run every other test.
@@ -43,6 +44,21 @@ def _same(a, b):
     assert a["status_flags"] == b["status_flags"]
 
 
+def _measure_both(torch, lbm, dom, params, box, mask_dev, stream=None):
+    """lbm_measure of the domain, and the no-alloc call on a device copy of its state."""
+    ref = dom.measure()
+    f, _ = dom.state()
+    f_dev = torch.from_numpy(f).cuda()
+    torch.cuda.synchronize()
+    if stream is None:
+        got = lbm.lbm_measure_state_noalloc(params, box, f_dev.data_ptr(), mask_dev.data_ptr())
+    else:
+        with torch.cuda.stream(stream):
+            got = lbm.lbm_measure_state_noalloc(params, box, f_dev.data_ptr(), mask_dev.data_ptr(),
+                                                stream=lbm.ctypes.c_void_p(stream.cuda_stream))
+    return got, ref
+
+
 def test_noalloc_measure_matches_lbm_measure_twice(env):
     torch, lbm = env
     shape = (44, 36, 40)
@@ -58,14 +74,27 @@ def test_noalloc_measure_matches_lbm_measure_twice(env):
     mask_dev = torch.from_numpy(dom.mask()).cuda()
     for n_steps in (30, 20):
         dom.step(n_steps)
-        ref = dom.measure()
-        f, _ = dom.state()
-        f_dev = torch.from_numpy(f).cuda()
-        torch.cuda.synchronize()
-        got = lbm.lbm_measure_state_noalloc(params, (nx, ny, nz), f_dev.data_ptr(), mask_dev.data_ptr())
+        got, ref = _measure_both(torch, lbm, dom, params, (nx, ny, nz), mask_dev)
         _same(got, ref)
         assert got["n_bulk_nw"] > 0 and got["n_interface"] > 0
     dom.close()
+
+    # a smaller, periodic state right after: fewer blocks write partials, so any
+    # slot of the shared array that the larger call left behind and this call
+    # reads would show; measured on a non-default stream
+    shape2 = (10, 12, 14)
+    nz2, ny2, nx2 = shape2
+    params2 = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=(0.0, 0.0), rho_major=W.RHO_MAJOR,
+                              rho_minor=W.RHO_MINOR, periodic=(1, 1, 1))
+    dom2 = lbm.Domain(params2, np.zeros((0, 4)), (nx2, ny2, nz2))
+    dom2.set_densities(W.droplet_densities(shape2, (7, 6, 5), 3.5, seed=22))
+    dom2.step(15)
+    mask2 = torch.from_numpy(dom2.mask()).cuda()
+    side = torch.cuda.Stream()
+    got, ref = _measure_both(torch, lbm, dom2, params2, (nx2, ny2, nz2), mask2, stream=side)
+    _same(got, ref)
+    assert got["n_fluid"] == nx2 * ny2 * nz2 and got["n_bulk_nw"] > 0
+    dom2.close()
 
 
 def test_noalloc_rejects_states_beyond_its_maximum(env):
