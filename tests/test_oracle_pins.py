@@ -417,3 +417,128 @@ def test_throat_frame(orc):
         mask = orc.voxelise_throat(sph)
         assert mask.shape == (dims[2], dims[1], dims[0])
         assert (mask == orc.M_INLET).any() and (mask == orc.M_OUTLET).any()
+
+
+# ------------------------------------------------- reservoirs and membrane
+@pytest.mark.parametrize("layer", ["inlet", "outlet"])
+def test_reservoir_layer_imposes_its_pair_in_one_step(orc, layer):
+    """Sec. 2.2.2 reservoirs, read as Dirichlet layers: after collision every
+    reservoir cell holds the rest equilibrium of its imposed (w, nw) pair.  In a
+    periodic box made only of such cells, one step from any state leaves that
+    pair everywhere, component by component; the inlet pair and the outlet pair
+    are distinct, so a swapped (w, nw) order or a swapped inlet/outlet role fails."""
+    shape = (5, 4, 6)
+    bit = orc.M_INLET if layer == "inlet" else orc.M_OUTLET
+    mask = np.full(shape, bit, dtype=np.uint8)
+    rho_in, rho_out = (0.31, 1.17), (1.93, 0.071)
+    cfg = orc.Config(shape=shape, G=0.9, G_ads=(-0.3, 0.3), periodic=(1, 1, 1), rho_in=rho_in, rho_out=rho_out)
+    rng = np.random.default_rng(5)
+    f = orc.init(cfg, mask, rng.uniform(0.05, 2.0, (2,) + shape))
+    orc.step(cfg, mask, f, 1)
+    rho = orc.density(cfg, mask, f)
+    want = rho_in if layer == "inlet" else rho_out
+    for s in range(2):
+        assert np.allclose(rho[s], want[s], rtol=1e-14, atol=0), (layer, s)
+
+
+def test_inlet_layer_drives_a_closed_box_to_its_pair(orc):
+    """With G = G_ads = 0 the components only share their common velocity, and a
+    closed box whose one open face is an inlet reservoir layer relaxes, for each
+    component separately, to the density the layer imposes: the override drives
+    the box (it is not only written into the layer)."""
+    shape = (8, 4, 4)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[0] = orc.M_INLET
+    cfg = orc.Config(shape=shape, G=0.0, G_ads=(0.0, 0.0), rho_in=(0.3, 1.1), rho_out=(1.9, 0.07))
+    rho0 = np.stack([np.full(shape, 2.0), np.full(shape, 0.06)])
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 6000)
+    rho = orc.density(cfg, mask, f)
+    assert np.abs(rho[0] - 0.3).max() < 1e-12
+    assert np.abs(rho[1] - 1.1).max() < 1e-12
+    m = orc.measure(cfg, mask, f)
+    assert m["n_in"] == 16 and m["n_out"] == 0 and m["n_fluid"] == 7 * 16
+
+
+def test_membrane_passes_only_the_wetting_fluid(orc):
+    """Sec. 3.1.1's porous membrane, read as fluid for the wetting component and a
+    wall for the non-wetting one.  A closed box split by a membrane band: the
+    non-wetting fluid, present on one side only, never reaches the band or the
+    far side (exactly zero there), while the wetting fluid crosses the band and
+    evens out its density difference between the two sides; each component's
+    mass is conserved."""
+    shape = (12, 5, 6)
+    mask = np.zeros(shape, dtype=np.uint8)
+    mask[5:7] = orc.M_MEMBRANE
+    cfg = orc.Config(shape=shape, G=0.0, G_ads=(0.0, 0.0))
+    rho0 = np.zeros((2,) + shape)
+    rho0[0, :5], rho0[1, :5] = 0.5, 1.5      # side A: both fluids
+    rho0[0, 5:7] = 1.0                       # membrane: wetting fluid only
+    rho0[0, 7:], rho0[1, 7:] = 2.0, 0.0      # side B: wetting fluid only
+    f = orc.init(cfg, mask, rho0)
+    m0 = orc.measure(cfg, mask, f)
+    wA0 = orc.density(cfg, mask, f)[0, :5].sum()
+    orc.step(cfg, mask, f, 400)
+    rho = orc.density(cfg, mask, f)
+    assert np.all(f[1][:, 5:] == 0.0)                  # no non-wetting population at or beyond the band
+    assert np.all(rho[1, 5:] == 0.0)
+    m1 = orc.measure(cfg, mask, f)
+    for s in range(2):
+        assert abs(m1["mass"][s] - m0["mass"][s]) <= 1e-12 * m0["mass"][s]
+    wA1 = rho[0, :5].sum()
+    assert wA1 - wA0 > 0.5 * 5 * 30 * 0.25           # wetting mass crossed into side A
+    assert np.abs(rho[0, 8:] - rho[0, 8:].mean()).max() < 0.2
+
+
+# -------------------------------------------------------------------- probe
+def _equilateral(side, r, z=0.0):
+    h = side * math.sqrt(3.0) / 2.0
+    return np.array([[0.0, 0.0, z, r], [side, 0.0, z, r], [side / 2.0, h, z, r]])
+
+
+def _global_of_cell(orc, spheres3, cell):
+    """Global position of throat-box cell (i, j, k) from the frame's definition:
+    e1 along c1 - c0, e3 along (c1 - c0) x (c2 - c0), e2 = e3 x e1, origin c0."""
+    _, org, _ = orc.throat_frame(spheres3)
+    c0, c1, c2 = (spheres3[i, :3] for i in range(3))
+    e1 = (c1 - c0) / np.linalg.norm(c1 - c0)
+    e3 = np.cross(c1 - c0, c2 - c0)
+    e3 /= np.linalg.norm(e3)
+    e2 = np.cross(e3, e1)
+    loc = org + np.asarray(cell, dtype=float)
+    return c0 + loc[0] * e1 + loc[1] * e2 + loc[2] * e3
+
+
+@pytest.mark.parametrize("side,r", [(20.0, 10.0), (24.0, 10.5), (27.0, 12.0)])
+def test_probe_sits_on_the_symmetry_axis(orc, side, r):
+    """The invasion probe is the fluid cell of plane nz - 3 farthest from the three
+    sphere surfaces.  For three equal spheres on an equilateral triangle the
+    distance to the nearest surface peaks on the axis through the centroid: near
+    it, min_s |p - c_s| drops by between d/2 and d at distance d from the axis
+    (the three centre directions are 120 degrees apart), so the best lattice
+    cell lies within sqrt(2) of the axis (a cell within sqrt(2)/2 always exists).
+    A rule that took the nearest cell instead would sit against a sphere."""
+    sp = _equilateral(side, r)
+    sp[:, :2] += (0.37, 0.61)  # off the lattice
+    mask = orc.voxelise_throat(sp)
+    nz = mask.shape[0]
+    i, j, k = orc.throat_probe(sp, mask)
+    assert k == nz - 3
+    assert mask[k, j, i] == 0
+    p = _global_of_cell(orc, sp, (i, j, k))
+    centroid = sp[:, :3].mean(axis=0)
+    assert np.hypot(p[0] - centroid[0], p[1] - centroid[1]) <= math.sqrt(2.0) + 1e-9
+    assert abs(p[2] - (k - (nz - 1) / 2.0)) < 1e-9  # local height of plane k above the centres
+
+
+def test_probe_moves_towards_the_smaller_sphere(orc):
+    """With one sphere smaller than the other two, the point farthest from the
+    three surfaces moves off the centroid towards the smaller sphere's centre."""
+    sp = _equilateral(26.0, 11.0)
+    sp[2, 3] = 7.0
+    mask = orc.voxelise_throat(sp)
+    i, j, k = orc.throat_probe(sp, mask)
+    p = _global_of_cell(orc, sp, (i, j, k))
+    centroid = sp[:, :3].mean(axis=0)
+    c_small = sp[2, :3]
+    assert np.hypot(*(p[:2] - c_small[:2])) < np.hypot(*(centroid[:2] - c_small[:2])) - 1.0
