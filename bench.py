@@ -66,8 +66,8 @@ def parse():
                          "one JSON line with the p_c - S_w curve")
     ap.add_argument("--no-tune", action="store_true", help="time the default kernel instead of the autotuned one")
     ap.add_argument("--shape", default="",
-                    help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD "
-                         "or staged2:BY:LZ:2")
+                    help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD, "
+                         "staged2:BY:LZ:2 or push:ROWS:LZ:STAGES")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--throat-batch", choices=["cells", "tiles", "persistent"], default="",
@@ -138,11 +138,15 @@ def read_peaks():
 KERNEL_SOURCES = {
     "sc_step_kernel": ("lbm_step.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
     "sc_step_tma_kernel": ("lbm_step_tma.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
+    "sc_step_push_kernel": ("lbm_step_push.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
 }
+# push kernel shapes (box rows, plane stages) -> lbm_set_push_shape index, CTAs per SM
+PUSH_SHAPES = {(8, 4): (0, 1), (8, 3): (1, 1), (6, 3): (2, 2), (10, 3): (3, 1), (4, 4): (4, 2)}
 
 
 def kernel_hash(kernel_name="sc_step_kernel"):
-    key = "sc_step_tma_kernel" if kernel_name.startswith("sc_step_tma") else "sc_step_kernel"
+    key = next((k for k in ("sc_step_tma_kernel", "sc_step_push_kernel") if kernel_name.startswith(k)),
+               "sc_step_kernel")
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[key]:
         h.update(open(os.path.join(ROOT, "paper_1906_04722_gb300", "csrc", f), "rb").read())
@@ -406,13 +410,17 @@ def run_ours(args, rank, world, local):
         f = args.shape.split(":")
         tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
                  {"kind": f[0], "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
+        if f[0] == "push":  # push:rows:lz:stages
+            tuned = {"kind": "push", "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])}
     else:
         tuned = dom.autotune(trial_steps=20) if not args.no_tune else None
 
     def apply_tuned(d):
         if tuned is None:
             return
-        if tuned["kind"] == "tma":
+        if tuned["kind"] == "push":
+            d.set_push_shape(PUSH_SHAPES[(tuned["by"], tuned["lead"])][0], tuned["lz"])
+        elif tuned["kind"] == "tma":
             d.set_step_kernel(lbm.KERNEL_TMA, tuned["lz"])
         elif tuned["kind"] == "split":
             d.set_step_kernel(lbm.KERNEL_SPLIT)
@@ -428,6 +436,9 @@ def run_ours(args, rank, world, local):
     if args.precision:
         by, _, lead = lbm.lbm_get_tile(dom.h)
         kernel_name = "sc_step16_kernel<%s,%d,%d>" % ("half2" if args.precision == 1 else "bfloat162", by, lead)
+    elif kind == lbm.KERNEL_PUSH:
+        rows, stages = tuned["by"], tuned["lead"]
+        kernel_name = "sc_step_push_kernel<%d,%d,%d>" % (rows, stages, PUSH_SHAPES[(rows, stages)][1])
     elif kind == lbm.KERNEL_TMA:
         kernel_name = "sc_step_tma_kernel"
     elif kind == lbm.KERNEL_SPLIT:

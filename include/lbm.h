@@ -371,24 +371,51 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  *   LBM_KERNEL_STAGED2 the staged kernel with two threads per cell, one per
  *                      fluid component (any box; FP32 only; by 6 or 8, lead 2,
  *                      lz planes per z segment, lz <= 0: keep the current).
- * New domains use LBM_KERNEL_STAGED (the faster one on small boxes; lbm_autotune
- * times both on the domain).  Both give the same results up to rounding (not
- * bit for bit: the TMA kernel folds omega w_k into its equilibrium constants).  LBM_ERR_ARG
+ *   LBM_KERNEL_PUSH    the state is kept in a paired push layout (the two
+ *                      components of a direction side by side, each cell's
+ *                      populations at the current time level at its own
+ *                      address; streaming with bounce-back happens at the
+ *                      store); one thread per CTA loads each plane of a
+ *                      32-column tile, all 19 directions, with one tensor
+ *                      memory accelerator copy (FP32; boxes without periodic x
+ *                      or y and with an even nx); lz planes per z segment
+ *                      (lz <= 0: keep the current); shape by lbm_set_push_shape.
+ *                      Results equal the staged kernel's bit for bit.  The
+ *                      state is converted between the layouts when the kind
+ *                      changes, and read-outs (lbm_measure, lbm_get_density,
+ *                      lbm_get_density_at, lbm_get_state, lbm_run_drainage)
+ *                      convert a copy into the other buffer; callers see the
+ *                      pull layout only.
+ * New domains use LBM_KERNEL_STAGED (lbm_autotune times every kind that applies
+ * on the domain).  All give the same results up to rounding (not bit for bit:
+ * the TMA kernel folds omega w_k into its equilibrium constants).  LBM_ERR_ARG
  * for an unknown kind, LBM_ERR_STATE when the kernel does not apply to the
  * domain.  lbm_set_tile switches the domain to LBM_KERNEL_STAGED. */
 #define LBM_KERNEL_STAGED 0
 #define LBM_KERNEL_TMA 1
 #define LBM_KERNEL_SPLIT 2
 #define LBM_KERNEL_STAGED2 3
+#define LBM_KERNEL_PUSH 4
 int lbm_set_step_kernel(lbm_domain* d, int kind, int lz);
 int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
+
+/* lbm_set_push_shape -- switches the domain to LBM_KERNEL_PUSH with a CTA shape:
+ *   shape  0: 8 box rows (6 interior), 4 plane stages, one CTA per SM;
+ *          1: 8 rows, 3 stages, one CTA;  2: 6 rows, 3 stages, two CTAs;
+ *          3: 10 rows, 3 stages, one CTA; 4: 4 rows, 4 stages, two CTAs.
+ *          A CTA of 32 x rows threads advances 28 x (rows - 2) columns.
+ *   lz     planes per CTA z segment (lz <= 0: a default for the box).
+ * Results do not depend on the shape (bit for bit).  LBM_ERR_ARG for an unknown
+ * shape, LBM_ERR_STATE when the push kernel does not apply to the domain. */
+int lbm_set_push_shape(lbm_domain* d, int shape, int lz);
 
 /* lbm_autotune -- time the step kernels and launch shapes that apply to the
  * domain on the domain itself and keep the fastest.
  *   trial_steps  time steps timed per candidate (>= 1), after one untimed step;
  *   out          optional: the chosen shape and its time per step.
- * Candidates: for FP32 domains the TMA kernel (where it applies) with z
- * segments of 8 .. 48 planes, the two-launch kernel, the two-threads-per-cell
+ * Candidates: for FP32 domains the push kernel (where it applies) in every
+ * shape with z segments of 8, 16 and 32 planes, the TMA kernel (where it
+ * applies) with z segments of 8 .. 48 planes, the two-launch kernel, the two-threads-per-cell
  * staged kernel (by 6 or 8, z segments of 8 .. 32), and the staged kernel with
  * by in {6, 8, 10}, lead in {0, 1, 2, 3} (0 and 1: the double-pull variant) and
  * z segments of 8 .. 32 planes; for 16-bit storage by in {6, 8, 10} with lead 2.
@@ -398,8 +425,9 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
  * it stood.  Needs one extra population buffer of device memory while it runs
  * (LBM_ERR_OOM otherwise).  Synchronising. */
 typedef struct {
-    int kind;           /* LBM_KERNEL_STAGED or LBM_KERNEL_TMA */
-    int by, lz, lead;   /* the shape (by and lead: staged kernel only) */
+    int kind;           /* LBM_KERNEL_* of the chosen kernel */
+    int by, lz, lead;   /* the shape: staged kernels by and lead; push kernel box
+                           rows (by) and plane stages (lead); lz the z segment */
     double ms_per_step; /* its measured time per step */
     int n_candidates;   /* shapes timed */
 } lbm_tune_result;

@@ -86,7 +86,8 @@ class lbm_tune_result(ctypes.Structure):
                 ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int)]
 
     def as_dict(self) -> dict:
-        return {"kind": {0: "staged", 1: "tma", 2: "split", 3: "staged2"}.get(self.kind, "?"), "by": self.by, "lz": self.lz, "lead": self.lead,
+        return {"kind": {0: "staged", 1: "tma", 2: "split", 3: "staged2", 4: "push"}.get(self.kind, "?"),
+                "by": self.by, "lz": self.lz, "lead": self.lead,
                 "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates}
 
 
@@ -121,6 +122,7 @@ SIGNATURES = {
     "lbm_measure_state_noalloc": (ctypes.c_int, [ctypes.POINTER(lbm_params), _IP, _VP, _VP, _VP,
                                                  ctypes.POINTER(lbm_measurement)]),
     "lbm_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lbm_set_push_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "lbm_get_tile": (ctypes.c_int, [_VP, _IP, _IP, _IP]),
     "lbm_set_step_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "lbm_get_step_kernel": (ctypes.c_int, [_VP, _IP, _IP]),
@@ -331,6 +333,8 @@ KERNEL_STAGED = 0
 KERNEL_TMA = 1
 KERNEL_SPLIT = 2
 KERNEL_STAGED2 = 3
+KERNEL_PUSH = 4
+PUSH_SHAPES = 5  # lbm_set_push_shape: (rows, stages) = (8, 4), (8, 3), (6, 3), (10, 3), (4, 4)
 BATCH_AUTO = 0
 BATCH_PERSISTENT = 1
 BATCH_PER_STEP = 2
@@ -339,6 +343,10 @@ BATCH_CELLS = 3
 
 def lbm_set_step_kernel(h, kind: int, lz: int = 0):
     _check(load().lbm_set_step_kernel(h, int(kind), int(lz)), "lbm_set_step_kernel")
+
+
+def lbm_set_push_shape(h, shape: int, lz: int = 0):
+    _check(load().lbm_set_push_shape(h, int(shape), int(lz)), "lbm_set_push_shape")
 
 
 def lbm_get_step_kernel(h):
@@ -486,6 +494,9 @@ class Domain:
 
     def step_kernel(self):
         return lbm_get_step_kernel(self.h)
+
+    def set_push_shape(self, shape, lz=0):
+        lbm_set_push_shape(self.h, shape, lz)
 
     def autotune(self, trial_steps=20):
         return lbm_autotune(self.h, trial_steps)

@@ -98,6 +98,9 @@ void drop_graphs(lbm_domain* d) {
 
 // One step from buffer `cur` to buffer cur ^ 1 on stream s.
 cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH)
+        return launch_step_push(d->tile.push_shape, d->push_maps[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh,
+                                d->geom, d->phys, d->tile.push_lz, d->d_err, s);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA)
         return launch_step_tma(d->tma, cur, d->f[cur], d->f[cur ^ 1], d->d_nbr_nw, d->d_adh, d->geom, d->phys,
                                d->tile.tma_lz, d->d_err, s);
@@ -114,10 +117,58 @@ cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
 }
 
 cudaError_t prepare_one(lbm_domain* d) {
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH) return prepare_step_push(d->tile.push_shape);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA) return prepare_step_tma();
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_SPLIT) return cudaSuccess;
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_STAGED2) return prepare_step2(d->tile);
     return d->params.precision == 0 ? prepare_step(d->tile) : prepare_step16(d->params.precision, d->tile);
+}
+
+// The layout the current kernel kind steps on: the push kernel keeps the FP32
+// state in the paired push layout, every other kernel in the pull layout.
+int wanted_layout(const lbm_domain* d) {
+    return (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH) ? 1 : 0;
+}
+
+// Converts the state into the given layout (into the other buffer, which then
+// becomes the current one).  The step counter is unchanged.
+int set_layout(lbm_domain* d, int layout) {
+    if (d->params.precision != 0 || d->layout == layout) return LBM_OK;
+    if (layout == 1)
+        LBM_CUDA(launch_pull_to_push(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+    else
+        LBM_CUDA(launch_push_to_pull(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+    d->cur ^= 1;
+    d->layout = layout;
+    d->ghosts_ok = false;
+    return LBM_OK;
+}
+
+// The current FP32 state in the pull layout, for the read-out kernels: f[cur]
+// itself, or (paired push layout) its conversion into the other buffer, which
+// the next step overwrites anyway.
+int pull_view(lbm_domain* d, const float** out) {
+    if (d->layout == 0) {
+        *out = d->f[d->cur];
+        return LBM_OK;
+    }
+    LBM_CUDA(launch_push_to_pull(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+    *out = d->f[d->cur ^ 1];
+    return LBM_OK;
+}
+
+// Tensor maps of both buffers for the push kernel's current shape.
+int ensure_push_maps(lbm_domain* d) {
+    const int rows = push_shape_rows(d->tile.push_shape);
+    if (d->push_maps_rows == rows) return LBM_OK;
+    cudaError_t e = encode_push_maps(d->geom, d->f[0], d->f[1], rows, d->push_maps);
+    if (e != cudaSuccess) {
+        d->push_maps_rows = 0;
+        set_error(std::string("tensor maps of the push kernel: ") + cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    d->push_maps_rows = rows;
+    return LBM_OK;
 }
 
 // Capture GRAPH_STEPS step launches that start from buffer `parity` on the
@@ -153,6 +204,11 @@ int capture_graph(lbm_domain* d, int parity) {
 // n steps: whole chunks replay a captured graph, the remainder is launched one by one.
 int run_steps(lbm_domain* d, int n) {
     if (n <= 0) return LBM_OK;
+    if (int rc = set_layout(d, wanted_layout(d))) return rc;
+    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH) {
+        if (int rc = ensure_push_maps(d)) return rc;
+        d->tma_pending = true;  // the push kernel reports a wait that ran out through d_err
+    }
     const bool tma = d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA;
     if (tma && !d->ghosts_ok) {
         LBM_CUDA(launch_ghost_fill(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
@@ -259,6 +315,7 @@ int init_from_densities(lbm_domain* d) {
     d->cur = 0;
     d->step = 0;
     d->ghosts_ok = false;
+    d->layout = 0;
     return wait_domain(d);
 }
 
@@ -291,6 +348,10 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     g.pz = params->periodic[2] ? 1 : 0;
     fill_pull_offsets(g);
     d->tile = default_tile(g);
+    d->tile.push_shape = 0;
+    d->tile.push_lz = push_default_lz(g, 0);
+    d->layout = 0;
+    d->push_maps_rows = 0;
 
     auto fail = [&](int rc) { free_domain(d); return rc; };
 #define LBM_CUDA_D(call)                                                                  \
@@ -449,8 +510,11 @@ int lbm_get_density_at(lbm_domain* d, int x, int y, int z, double rho_out[2]) {
         set_error("probe cell outside the box");
         return LBM_ERR_ARG;
     }
-    if (d->params.precision == 0)
-        LBM_CUDA(launch_probe(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
+    if (d->params.precision == 0) {
+        const float* fp = nullptr;
+        if (int rc = pull_view(d, &fp)) return rc;
+        LBM_CUDA(launch_probe(fp, d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
+    }
     else
         LBM_CUDA(launch_probe16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
                                 d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
@@ -508,9 +572,12 @@ int lbm_run_drainage(lbm_domain* d, const double* rho_in_nw, int n_incr, int n_s
 
 int lbm_measure(lbm_domain* d, lbm_measurement* out) {
     if (!d || !out) { set_error("domain or out is NULL"); return LBM_ERR_ARG; }
-    if (d->params.precision == 0)
-        LBM_CUDA(launch_measure(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials,
-                                d->meas_blocks, d->d_result, d->stream));
+    if (d->params.precision == 0) {
+        const float* fp = nullptr;
+        if (int rc = pull_view(d, &fp)) return rc;
+        LBM_CUDA(launch_measure(fp, d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials, d->meas_blocks,
+                                d->d_result, d->stream));
+    }
     else
         LBM_CUDA(launch_measure16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
                                   d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials, d->meas_blocks,
@@ -549,8 +616,11 @@ int lbm_measure(lbm_domain* d, lbm_measurement* out) {
 int lbm_get_density(lbm_domain* d, double* rho_out) {
     if (!d || !rho_out) { set_error("domain or rho_out is NULL"); return LBM_ERR_ARG; }
     try {
-        if (d->params.precision == 0)
-            LBM_CUDA(launch_density(d->f[d->cur], d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        if (d->params.precision == 0) {
+            const float* fp = nullptr;
+            if (int rc = pull_view(d, &fp)) return rc;
+            LBM_CUDA(launch_density(fp, d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        }
         else
             LBM_CUDA(launch_density16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]),
                                       d->R[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->d_rho, d->stream));
@@ -585,8 +655,10 @@ int lbm_get_state(lbm_domain* d, float* f_out, long long* step_out) {
     if (!d || !f_out) { set_error("domain or f_out is NULL"); return LBM_ERR_ARG; }
     if (d->params.precision != 0) { set_error("checkpoints are available for FP32 domains only"); return LBM_ERR_STATE; }
     const long long N = d->N;
+    const float* fp = nullptr;
+    if (int rc = pull_view(d, &fp)) return rc;
     for (int p = 0; p < 2 * Q; ++p)
-        LBM_CUDA(cudaMemcpyAsync(f_out + (size_t)p * N, d->f[d->cur] + (size_t)p * d->geom.plane, sizeof(float) * N,
+        LBM_CUDA(cudaMemcpyAsync(f_out + (size_t)p * N, fp + (size_t)p * d->geom.plane, sizeof(float) * N,
                                  cudaMemcpyDeviceToHost, d->stream));
     int rc = wait_domain(d);
     if (rc) return rc;
@@ -603,6 +675,7 @@ int lbm_set_state(lbm_domain* d, const float* f_in, long long step) {
                                  cudaMemcpyHostToDevice, d->stream));
     d->step = step;
     d->ghosts_ok = false;
+    d->layout = 0;
     return wait_domain(d);
 }
 
@@ -623,9 +696,19 @@ int lbm_set_tile(lbm_domain* d, int by, int lz, int lead) {
 int lbm_set_step_kernel(lbm_domain* d, int kind, int lz) {
     if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
     if (kind != LBM_KERNEL_STAGED && kind != LBM_KERNEL_TMA && kind != LBM_KERNEL_SPLIT &&
-        kind != LBM_KERNEL_STAGED2) {
+        kind != LBM_KERNEL_STAGED2 && kind != LBM_KERNEL_PUSH) {
         set_error("unknown step kernel");
         return LBM_ERR_ARG;
+    }
+    if (kind == LBM_KERNEL_PUSH) {
+        if (d->params.precision != 0 || !push_step_applicable(d->geom)) {
+            set_error("the push step kernel needs an FP32 domain without periodic x or y and with an even nx");
+            return LBM_ERR_STATE;
+        }
+        if (lz > 0) d->tile.push_lz = lz > d->geom.nz ? d->geom.nz : lz;
+        d->tile.kind = kind;
+        drop_graphs(d);
+        return ensure_push_maps(d);
     }
     if ((kind == LBM_KERNEL_SPLIT || kind == LBM_KERNEL_STAGED2) && d->params.precision != 0) {
         set_error("the two-launch and two-threads-per-cell step kernels need an FP32 domain");
@@ -651,8 +734,24 @@ int lbm_set_step_kernel(lbm_domain* d, int kind, int lz) {
 int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz) {
     if (!d || !kind || !lz) { set_error("NULL argument"); return LBM_ERR_ARG; }
     *kind = d->tile.kind;
-    *lz = d->tile.kind == LBM_KERNEL_TMA ? d->tile.tma_lz : d->tile.lz;  // staged kinds: the z segment
+    *lz = d->tile.kind == LBM_KERNEL_TMA ? d->tile.tma_lz
+          : d->tile.kind == LBM_KERNEL_PUSH ? d->tile.push_lz
+                                            : d->tile.lz;  // staged kinds: the z segment
     return LBM_OK;
+}
+
+int lbm_set_push_shape(lbm_domain* d, int shape, int lz) {
+    if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
+    if (shape < 0 || shape >= push_shape_count()) { set_error("unknown push kernel shape"); return LBM_ERR_ARG; }
+    if (d->params.precision != 0 || !push_step_applicable(d->geom)) {
+        set_error("the push step kernel needs an FP32 domain without periodic x or y and with an even nx");
+        return LBM_ERR_STATE;
+    }
+    d->tile.push_shape = shape;
+    d->tile.push_lz = lz > 0 ? (lz > d->geom.nz ? d->geom.nz : lz) : push_default_lz(d->geom, shape);
+    d->tile.kind = LBM_KERNEL_PUSH;
+    drop_graphs(d);
+    return ensure_push_maps(d);
 }
 
 int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead) {
@@ -674,6 +773,7 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     const StepTile orig = d->tile;
     const int cur = d->cur;
     const long long step = d->step;
+    const int layout = d->layout;
     // candidates
     std::vector<StepTile> cand;
     auto add = [&](int kind, int by, int lz, int lead) {
@@ -682,9 +782,19 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
         t.by = by;
         t.lead = lead;
         if (kind == LBM_KERNEL_TMA) t.tma_lz = lz > g.nz ? g.nz : lz;
+        else if (kind == LBM_KERNEL_PUSH) t.push_lz = lz > g.nz ? g.nz : lz;
         else t.lz = lz > g.nz ? g.nz : lz;
         cand.push_back(t);
     };
+    if (fp32 && push_step_applicable(g))
+        for (int sh = 0; sh < push_shape_count(); ++sh)
+            for (int lz : {8, 16, 32}) {
+                StepTile t = orig;
+                t.kind = LBM_KERNEL_PUSH;
+                t.push_shape = sh;
+                t.push_lz = lz > g.nz ? g.nz : lz;
+                cand.push_back(t);
+            }
     if (fp32 && d->tma_ok)
         for (int lz : {8, 12, 16, 24, 32, 48}) add(LBM_KERNEL_TMA, orig.by, lz, orig.lead);
     if (fp32) add(LBM_KERNEL_SPLIT, orig.by, orig.lz, orig.lead);
@@ -711,6 +821,7 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
         if (rbytes) LBM_CUDA(cudaMemcpyAsync(d->R[cur], rsave, rbytes, cudaMemcpyDeviceToDevice, d->stream));
         d->cur = cur;
         d->step = step;
+        d->layout = layout;
         d->ghosts_ok = false;
         return LBM_OK;
     };
@@ -763,9 +874,11 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     if (rc) return rc;
     if (out) {
         out->kind = best_t.kind;
-        out->by = best_t.by;
-        out->lz = best_t.kind == LBM_KERNEL_TMA ? best_t.tma_lz : best_t.lz;
-        out->lead = best_t.lead;
+        out->by = best_t.kind == LBM_KERNEL_PUSH ? push_shape_rows(best_t.push_shape) : best_t.by;
+        out->lz = best_t.kind == LBM_KERNEL_TMA ? best_t.tma_lz
+                  : best_t.kind == LBM_KERNEL_PUSH ? best_t.push_lz
+                                                   : best_t.lz;
+        out->lead = best_t.kind == LBM_KERNEL_PUSH ? push_shape_stages(best_t.push_shape) : best_t.lead;
         out->ms_per_step = best;
         out->n_candidates = (int)cand.size();
     }

@@ -90,8 +90,10 @@ struct StepTile {
     int by;    // block rows including the two halo rows (6, 8, 10 or 12)
     int lz;    // z-segment length per CTA
     int lead;  // planes queued ahead of the collided plane (2, 3 or 4)
-    int kind;  // LBM_KERNEL_STAGED, LBM_KERNEL_TMA, LBM_KERNEL_SPLIT or LBM_KERNEL_STAGED2
+    int kind;  // LBM_KERNEL_STAGED, _TMA, _SPLIT, _STAGED2 or _PUSH
     int tma_lz;  // z-segment length of the TMA kernel
+    int push_shape;  // shape index of the push kernel (push_shape_rows / _stages)
+    int push_lz;     // z-segment length of the push kernel
 };
 
 // Tensor maps of the TMA step kernel (lbm_step_tma.cu): the two population
@@ -150,6 +152,22 @@ cudaError_t launch_step2(const float* fin, float* fout, const uint32_t* nbr, con
 cudaError_t launch_step_split(const float* fin, float* fout, float2* rho2, const uint32_t* nbr,
                               const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p,
                               cudaStream_t s);
+// paired push-form step (lbm_step_push.cu): float2 F[19][plane] of the current
+// time level; TMA box loads of whole planes (no periodic x / y, nx even)
+int push_shape_count();
+int push_shape_rows(int shape);
+int push_shape_stages(int shape);
+bool push_step_applicable(const Geom& g);
+int push_default_lz(const Geom& g, int shape);
+cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtensorMap (&maps)[2]);
+cudaError_t prepare_step_push(int shape);
+cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, const uint32_t* nbr,
+                             const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p, int lz,
+                             int* err, cudaStream_t s);
+cudaError_t launch_pull_to_push(const float* fin, float* F, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                const Geom& g, cudaStream_t s);
+cudaError_t launch_push_to_pull(const float* F, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                const Geom& g, cudaStream_t s);
 // one CTA waiting, bounded, on an mbarrier that nothing completes (self-test)
 cudaError_t launch_wait_selftest(long long limit_ns, int* gave_up, cudaStream_t s);
 // ghost stores (the reflected populations the TMA kernel pulls from wall cells) of a state
@@ -203,6 +221,9 @@ struct lbm_domain {
     int* h_err;         // pinned copy of d_err, read after a wait
     bool tma_pending;   // a TMA step ran since d_err was last read
     float2* d_rho2;     // FP32 domains: (rho_w, rho_nw) per cell for the two-launch step
+    int layout;         // FP32 state in f[cur]: 0 = pull layout, 1 = paired push layout
+    CUtensorMap push_maps[2];  // tensor maps of f[0], f[1] for the push kernel's shape
+    int push_maps_rows;        // box rows the push maps were encoded for (0: none)
 };
 
 constexpr int GRAPH_STEPS = 64;  // steps per captured graph (even: the buffer parity is unchanged)

@@ -1,0 +1,468 @@
+// lbm_step_push.cu -- the fused two-component Shan-Chen D3Q19 step (FP32) on
+// paired push-form storage, with population planes loaded by the tensor memory
+// accelerator.
+//
+// Storage ("paired push" layout, a domain's alternative to the pull layout of
+// the other FP32 kernels): float2 F[19][plane], F[k][cell] = (f_k^w, f_k^nw) of
+// the cell at the current time level, i.e. the populations after streaming and
+// before collision.  A cell's own 19 pairs are all it needs for its moments
+// (Eqs. 2-3); streaming with half-way bounce-back (Eq. 1, left-hand side)
+// happens at the store: the post-collision f*_k of cell x goes to slot k of
+// x + e_k, or, when x + e_k is not fluid for the component, to slot kbar of x
+// itself.  Nothing is ever stored into a solid cell or into the non-wetting
+// half of a membrane cell, so those slots stay zero and every density sum can
+// run over a cell's 19 pairs without looking at its class.
+//
+// Data movement.  A CTA of 32 x BY threads owns a box of 32 x BY columns whose
+// interior, 28 x (BY - 2) columns, it advances; it marches along z through a
+// segment of planes.  For every plane one thread issues a single 4-D TMA box
+// load (x as 64 floats, y, z, k: all 19 pair arrays at once, 19 x BY x 256
+// bytes) into one of NS stage buffers, completing on that stage's mbarrier.
+// The box starts two cells left of the interior so that its x coordinate stays
+// 16-byte aligned; the cells two columns out are loaded and not used.  When a
+// plane has landed every thread sums its cell's two densities (four interleaved
+// partial sums, as the staged kernel) into a 4-plane density ring.  After one
+// CTA barrier per plane the interior threads collide the plane behind with the
+// 18 neighbour densities at hand (collide_core, the arithmetic of the staged
+// kernel, so the results are the staged kernel's bit for bit) and store the
+// pairs to global memory: one 8-byte store per direction where both components
+// stream alike, separate stores next to a membrane.  The loads of the next
+// NS - 2 planes are in flight meanwhile.
+//
+// DRAM sees each population read once (whole boxes: grain columns of a tile
+// ride along) and written once; the box halos, re-read by neighbouring tiles
+// that march in step, are served by L2.
+//
+// Waits on the mbarriers are bounded in time: a wait that runs out sets *err,
+// waits (bounded again) for the copies in flight and ends the CTA.
+//
+// Requirements (checked on the host): no periodic x or y axis, nx even (the
+// tensor map's row pitch must be a multiple of 16 bytes).  z may be periodic.
+#include <cuda.h>
+
+#include "lbm_step_core.cuh"
+
+namespace lbmk {
+
+namespace {
+
+constexpr int PX = 32;        // box columns (x)
+constexpr int PXI = 28;       // interior columns: box lanes 2 .. 29
+constexpr long long PUSH_WAIT_NS = 2000000000LL;  // 2 s
+constexpr uint32_t PUSH_BOUNCE_BITS = 0x7fffeu;   // bits 1..18
+
+__device__ __forceinline__ uint32_t p_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void p_mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(p_smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void p_mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(p_smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void p_mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(p_smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool p_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(p_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long p_global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity, for at most PUSH_WAIT_NS.
+__device__ __forceinline__ bool p_mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (p_mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = p_global_ns();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (p_mbar_try_wait(bar, parity)) return true;
+        if ((long long)(p_global_ns() - t0) > PUSH_WAIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void p_tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(p_smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(p_smem_u32(bar))
+        : "memory");
+}
+
+// Swaps the bits of each opposite pair: pull bounce bits (x - e_k not fluid)
+// become push bounce bits (x + e_k not fluid).
+__device__ __forceinline__ uint32_t p_swap_pairs(uint32_t m) {
+    return ((m & 0x2aaaau) << 1) | ((m & 0x55554u) >> 1);
+}
+
+template <int BY>
+constexpr uint32_t stage_bytes() {
+    return (uint32_t)(Q * BY * PX * sizeof(float2));
+}
+template <int BY, int NS>
+constexpr size_t push_smem_bytes() {
+    return (size_t)NS * stage_bytes<BY>() + sizeof(float2) * 4 * BY * PX + sizeof(uint64_t) * NS;
+}
+
+template <int BY, int NS, int MINB>
+__global__ void __launch_bounds__(PX * BY, MINB)
+    sc_step_push_kernel(const __grid_constant__ CUtensorMap tm, float2* __restrict__ fout,
+                        const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
+                        const uint32_t* __restrict__ adh, Geom g, Phys P, int lz, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (*reinterpret_cast<volatile int*>(err) != 0) return;  // an earlier launch gave up
+    constexpr int TY = BY - 2;
+    constexpr int NT = PX * BY;
+    float2* stages = reinterpret_cast<float2*>(smem);  // [NS][Q][BY][PX]
+    float2* ring = reinterpret_cast<float2*>(smem + NS * stage_bytes<BY>());  // [4][BY][PX]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * stage_bytes<BY>() + sizeof(float2) * 4 * NT);
+    const int lane = threadIdx.x, row = threadIdx.y;
+    const int tid = row * PX + lane;
+    const int xb = blockIdx.x * PXI - 2;  // box column of lane 0
+    const int yb = blockIdx.y * TY - 1;   // box row of row 0
+    const int gx = xb + lane, gy = yb + row;
+    const int z0 = blockIdx.z * lz;
+    const int z1 = min(z0 + lz, g.nz);
+    const bool interior = lane >= 2 && lane < 2 + PXI && row >= 1 && row <= TY && gx < g.nx && gy < g.ny;
+    const int col = gy * g.nx + gx;  // valid for interior threads
+
+    auto slot = [&](int p) { return (p - z0 + 1) % NS; };
+    auto parity = [&](int p) { return (uint32_t)(((p - z0 + 1) / NS) & 1); };
+    // plane p of every pair array into its stage; a plane beyond a closed z
+    // face is not loaded (its densities are zero) and only completes the phase
+    auto issue = [&](int p) {
+        uint64_t* b = bar + slot(p);
+        int zc = p;
+        if (zc < 0 || zc >= g.nz) {
+            if (!g.pz) {
+                p_mbar_arrive(b);
+                return;
+            }
+            zc = zc < 0 ? zc + g.nz : zc - g.nz;
+        }
+        p_mbar_arrive_expect_tx(b, stage_bytes<BY>());
+        p_tma_load_4d(stages + (size_t)slot(p) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
+    };
+    auto outside_z = [&](int p) { return !g.pz && (p < 0 || p >= g.nz); };
+    // the two densities of this thread's box cell on plane p, into the ring
+    auto publish = [&](int p) {
+        float2 r = make_float2(0.f, 0.f);
+        if (!outside_z(p)) {
+            const float2* st = stages + (size_t)slot(p) * (Q * NT) + tid;
+            float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const float2 v = st[k * NT];
+                a[k & 3] += v.x;
+                b[k & 3] += v.y;
+            }
+            r.x = (a[0] + a[1]) + (a[2] + a[3]);
+            r.y = (b[0] + b[1]) + (b[2] + b[3]);
+        }
+        ring[(p & 3) * NT + tid] = r;
+    };
+
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) p_mbar_init(bar + i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int p = z0 - 1; p <= z1 && p < z0 - 1 + NS; ++p) issue(p);
+
+    // geometry of the interior cell on plane z (prefetched a plane ahead)
+    uint32_t w_next = 0u;
+    if (interior) w_next = __ldg(nbr + (size_t)z0 * g.nxy + col);
+
+    bool ok = p_mbar_wait_bounded(bar + slot(z0 - 1), parity(z0 - 1));
+    if (ok) publish(z0 - 1);
+    ok = ok && p_mbar_wait_bounded(bar + slot(z0), parity(z0));
+    if (ok) publish(z0);
+    // a failed wait here is reported by the first iteration's barrier below
+    for (int z = z0; z < z1; ++z) {
+        const uint32_t w = w_next;
+        if (interior && z + 1 < z1) w_next = __ldg(nbr + (size_t)(z + 1) * g.nxy + col);
+        uint32_t a = 0u, nwb = 0u;
+        if (interior) {
+            if (w & BIT_ADH) a = __ldg(adh + (size_t)z * g.nxy + col);
+            if (w & BIT_NW_DIFF) nwb = __ldg(nbr_nw + (size_t)z * g.nxy + col);
+        }
+        const bool okz = ok && p_mbar_wait_bounded(bar + slot(z + 1), parity(z + 1));
+        if (okz) publish(z + 1);
+        if (__syncthreads_or(!okz)) {
+            if (tid == 0) {
+                atomicOr(err, 1);
+                // bounded waits for every copy still in flight
+                for (int p = max(z0 - 1, z - 1); p <= z1 && p < z - 1 + NS; ++p)
+                    p_mbar_wait_bounded(bar + slot(p), parity(p));
+            }
+            __syncthreads();
+            return;
+        }
+        if (tid == 0 && z + NS - 1 <= z1) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            issue(z + NS - 1);  // into the stage of plane z - 1, read by everyone before the barrier
+        }
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE) {
+            const float2* st = stages + (size_t)slot(z) * (Q * NT) + tid;
+            float f[2][Q];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const float2 v = st[k * NT];
+                f[0][k] = v.x;
+                f[1][k] = v.y;
+            }
+            float o[2][Q];
+            collide_core(
+                f, w, a, P,
+                [&](int k) { return ring[((z + EZ(k)) & 3) * NT + (row + EY(k)) * PX + (lane + EX(k))]; },
+                [&](int s, int k, float v) { o[s][k] = v; });
+            // push streaming with half-way bounce-back
+            const int zz = z;  // z in [0, nz): the plane itself needs no wrap
+            const int dzp = (zz == g.nz - 1) ? (1 - g.nz) * g.nxy : g.nxy;
+            const int dzm = (zz == 0) ? (g.nz - 1) * g.nxy : -g.nxy;
+            const int cell = zz * g.nxy + col;
+            const uint32_t pw = p_swap_pairs(w & PUSH_BOUNCE_BITS);
+            auto dst = [&](int k, uint32_t bits) -> int {
+                const int off = EX(k) + EY(k) * g.nx + (EZ(k) > 0 ? dzp : (EZ(k) < 0 ? dzm : 0));
+                return ((bits >> k) & 1u) ? (OPP(k) * g.plane + cell) : (k * g.plane + cell + off);
+            };
+            if (cls == CLS_MEMBRANE) {
+                // the wetting fluid only; the non-wetting half of every slot stays zero
+                float* fo = reinterpret_cast<float*>(fout);
+                fo[2 * (size_t)cell] = o[0][0];
+#pragma unroll
+                for (int k = 1; k < Q; ++k) fo[2 * (size_t)dst(k, pw)] = o[0][k];
+            } else if (w & BIT_NW_DIFF) {
+                const uint32_t pn = p_swap_pairs(nwb & PUSH_BOUNCE_BITS);
+                float* fo = reinterpret_cast<float*>(fout);
+                fout[cell] = make_float2(o[0][0], o[1][0]);
+#pragma unroll
+                for (int k = 1; k < Q; ++k) {
+                    fo[2 * (size_t)dst(k, pw)] = o[0][k];
+                    fo[2 * (size_t)dst(k, pn) + 1] = o[1][k];
+                }
+            } else {
+                fout[cell] = make_float2(o[0][0], o[1][0]);
+#pragma unroll
+                for (int k = 1; k < Q; ++k) fout[dst(k, pw)] = make_float2(o[0][k], o[1][k]);
+            }
+        }
+    }
+}
+
+// Pull layout -> paired push layout: F_k(x) = the pull of x (source x - e_k if
+// it is fluid for the component, else the cell's own slot kbar); zero where a
+// component is not fluid.
+__global__ void pull_to_push_kernel(const float* __restrict__ fin, float2* __restrict__ F,
+                                    const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw, Geom g) {
+    const long long N = (long long)g.nxy * g.nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)c;
+        const int x = ci % g.nx, y = (ci / g.nx) % g.ny, z = ci / g.nxy;
+        const Column colm = make_column(x, y, g);
+        float f[2][Q];
+        float rw, rn;
+        int cell;
+        const uint32_t w = pull_cell<true>(fin, nbr, nbr_nw, g, colm, z, f, rw, rn, cell);
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        const bool fw = cls != CLS_SOLID && cls != CLS_OUTSIDE;
+        const bool fn = fw && cls != CLS_MEMBRANE;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) F[(size_t)k * g.plane + ci] = make_float2(fw ? f[0][k] : 0.f, fn ? f[1][k] : 0.f);
+    }
+}
+
+// Paired push layout -> pull layout: slot k of cell y holds what y + e_k pulls
+// from it, F_k(y + e_k), when y + e_k is fluid for the component and pulls from
+// y; otherwise what y pulls from itself in direction kbar, F_kbar(y).  Zero
+// where the component is not fluid.
+__global__ void push_to_pull_kernel(const float2* __restrict__ F, float* __restrict__ fout,
+                                    const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw, Geom g) {
+    const long long N = (long long)g.nxy * g.nz;
+    const float* Fs = reinterpret_cast<const float*>(F);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)c;
+        const int x = ci % g.nx, y = (ci / g.nx) % g.ny, z = ci / g.nxy;
+        const uint32_t w = nbr[ci];
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        for (int s = 0; s < 2; ++s) {
+            const bool fl = cls != CLS_SOLID && !(s == 1 && cls == CLS_MEMBRANE);
+            // push bits: bit k set when y + e_k is not fluid for s (or beyond a closed face)
+            const uint32_t bits = s == 0 ? w : ((w & BIT_NW_DIFF) ? nbr_nw[ci] : w);
+            const uint32_t pb = p_swap_pairs(bits & PUSH_BOUNCE_BITS);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                float v = 0.f;
+                if (fl) {
+                    if (k == 0 || ((pb >> k) & 1u)) {
+                        v = Fs[2 * ((size_t)OPP(k) * g.plane + ci) + s];  // OPP(0) = 0: the rest slot
+                    } else {
+                        bool okk = true;
+                        const int tx = wrap1(x + EX(k), g.nx, g.px, okk);
+                        const int ty = wrap1(y + EY(k), g.ny, g.py, okk);
+                        const int tz = wrap1(z + EZ(k), g.nz, g.pz, okk);
+                        v = Fs[2 * ((size_t)k * g.plane + (size_t)tz * g.nxy + (size_t)ty * g.nx + tx) + s];
+                    }
+                }
+                fout[((size_t)s * Q + k) * g.plane + ci] = v;
+            }
+        }
+    }
+}
+
+typedef CUresult (*PushEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PushEncodeFn push_encode_fn() {
+    static PushEncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PushEncodeFn>(p);
+    }
+    return fn;
+}
+
+template <int BY, int NS, int MINB>
+cudaError_t configure_push() {
+    static unsigned long long configured = 0;  // one bit per device: the attribute is per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(sc_step_push_kernel<BY, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)push_smem_bytes<BY, NS>());
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    return cudaSuccess;
+}
+
+template <int BY, int NS, int MINB>
+cudaError_t launch_push_shape(const CUtensorMap& tm, float2* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                              const uint32_t* adh, const Geom& g, const Phys& p, int lz, int* err, cudaStream_t s) {
+    constexpr int TY = BY - 2;
+    const dim3 grid((g.nx + PXI - 1) / PXI, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
+    sc_step_push_kernel<BY, NS, MINB><<<grid, dim3(PX, BY), push_smem_bytes<BY, NS>(), s>>>(
+        tm, fout, nbr, nbr_nw, adh, g, p, lz, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Shapes of the push kernel: (rows BY, stages NS, CTAs per SM) by index.
+//   0: 8 rows, 4 stages, 1 CTA    1: 8 rows, 3 stages, 1 CTA
+//   2: 6 rows, 3 stages, 2 CTAs   3: 10 rows, 3 stages, 1 CTA
+//   4: 4 rows, 4 stages, 2 CTAs
+int push_shape_count() { return 5; }
+
+bool push_step_applicable(const Geom& g) { return !g.px && !g.py && g.nx % 2 == 0; }
+
+cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtensorMap (&maps)[2]) {
+    if (!push_step_applicable(g)) return cudaErrorInvalidValue;
+    PushEncodeFn enc = push_encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    // (component-interleaved x as floats, y, z, direction)
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 8, (cuuint64_t)g.nxy * 8, (cuuint64_t)g.plane * 8};
+    const cuuint32_t box[4] = {2 * PX, (cuuint32_t)by, 1, (cuuint32_t)Q};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    float* bufs[2] = {f0, f1};
+    for (int i = 0; i < 2; ++i)
+        if (enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bufs[i], dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+int push_shape_rows(int shape) {
+    static const int rows[5] = {8, 8, 6, 10, 4};
+    return (shape >= 0 && shape < 5) ? rows[shape] : 0;
+}
+
+int push_shape_stages(int shape) {
+    static const int stages[5] = {4, 3, 3, 3, 4};
+    return (shape >= 0 && shape < 5) ? stages[shape] : 0;
+}
+
+int push_default_lz(const Geom& g, int shape) {
+    // Short z segments keep neighbouring tiles on the same planes, so that the
+    // box halos they share are re-read from L2; small boxes get enough segments
+    // to give every SM a CTA.
+    const int ty = push_shape_rows(shape) - 2;
+    if (ty <= 0) return 1;
+    const long long tiles = (long long)((g.nx + PXI - 1) / PXI) * ((g.ny + ty - 1) / ty);
+    long long segs = device_sm_count() / tiles;
+    if (segs < 1) segs = 1;
+    int lz = (int)((g.nz + segs - 1) / segs);
+    if (lz > 16) lz = 16;
+    if (lz < 4) lz = 4;
+    if (lz > g.nz) lz = g.nz;
+    return lz;
+}
+
+cudaError_t prepare_step_push(int shape) {
+    switch (shape) {
+        case 0: return configure_push<8, 4, 1>();
+        case 1: return configure_push<8, 3, 1>();
+        case 2: return configure_push<6, 3, 2>();
+        case 3: return configure_push<10, 3, 1>();
+        case 4: return configure_push<4, 4, 2>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, const uint32_t* nbr,
+                             const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p, int lz,
+                             int* err, cudaStream_t s) {
+    if (lz < 1) return cudaErrorInvalidValue;
+    float2* fo = reinterpret_cast<float2*>(fout);
+    switch (shape) {
+        case 0: return launch_push_shape<8, 4, 1>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 1: return launch_push_shape<8, 3, 1>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 2: return launch_push_shape<6, 3, 2>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 3: return launch_push_shape<10, 3, 1>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 4: return launch_push_shape<4, 4, 2>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pull_to_push(const float* fin, float* F, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                const Geom& g, cudaStream_t s) {
+    const long long N = (long long)g.nxy * g.nz;
+    long long blocks = (N + 255) / 256;
+    const long long cap = 16LL * device_sm_count();
+    if (blocks > cap) blocks = cap;
+    pull_to_push_kernel<<<(int)blocks, 256, 0, s>>>(fin, reinterpret_cast<float2*>(F), nbr, nbr_nw, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push_to_pull(const float* F, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                const Geom& g, cudaStream_t s) {
+    const long long N = (long long)g.nxy * g.nz;
+    long long blocks = (N + 255) / 256;
+    const long long cap = 16LL * device_sm_count();
+    if (blocks > cap) blocks = cap;
+    push_to_pull_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<const float2*>(F), fout, nbr, nbr_nw, g);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -1,5 +1,6 @@
 """The FP32 step kernels (staged cp.async, its double-pull variant, TMA plane
-loads, the two-launch form) against the FP64 oracle and against each other.
+loads, the two-launch form, the paired push-form kernel) against the FP64
+oracle and against each other.
 
 Boxes are chosen so that the TMA kernel's 32 x 8 tiles have ragged tails in x
 and y and its z segments ragged ends; grains carry adhesion, the closed-z case
@@ -143,7 +144,7 @@ def test_autotune_restores_state_and_keeps_parity(lbm, orc):
     assert res["n_candidates"] >= 10 and res["ms_per_step"] > 0
     kind, lz = dom.step_kernel()
     assert kind == {"staged": lbm.KERNEL_STAGED, "tma": lbm.KERNEL_TMA, "split": lbm.KERNEL_SPLIT,
-                    "staged2": lbm.KERNEL_STAGED2}[res["kind"]]
+                    "staged2": lbm.KERNEL_STAGED2, "push": lbm.KERNEL_PUSH}[res["kind"]]
     if res["kind"] != "split":
         assert lz == res["lz"]
     dom.step(65)
@@ -223,7 +224,7 @@ def test_staged2_periodic_xy(lbm, orc):
     assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
 
 
-@pytest.mark.parametrize("kernel", ["staged", "tma", "split", "staged2"])
+@pytest.mark.parametrize("kernel", ["staged", "tma", "split", "staged2", "push"])
 def test_unequal_tau_and_body_force_every_kernel(lbm, orc, kernel):
     """tau = (0.8, 1.2) with a body force (weakly damped, the most rounding
     sensitive case of the suite) for every FP32 kernel."""
@@ -239,6 +240,8 @@ def test_unequal_tau_and_body_force_every_kernel(lbm, orc, kernel):
         dom.set_step_kernel(lbm.KERNEL_SPLIT)
     elif kernel == "staged2":
         dom.set_step_kernel(lbm.KERNEL_STAGED2, 8)
+    elif kernel == "push":
+        dom.set_push_shape(2, 9)
     dom.set_densities(rho0)
     dom.step(80)
     mask = orc.voxelise(shape, spheres)
@@ -272,3 +275,86 @@ def test_bounded_wait_gives_up_and_reports(lbm):
     dom.set_step_kernel(lbm.KERNEL_TMA, 8)
     dom.step(3)
     assert dom.measure()["n_nonfinite"] == 0
+
+
+# ------------------------------------------------------- paired push kernel
+def _push_run(lbm, flags, rho0, steps, shape, lz):
+    nz, ny, nx = SHAPE
+    dom = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
+    dom.set_push_shape(shape, lz)
+    assert dom.step_kernel() == (lbm.KERNEL_PUSH, lz)
+    dom.set_densities(rho0)
+    if not flags.get("periodic"):
+        dom.set_pressure_bc(2.08, W.RHO_MAJOR)
+    dom.step(steps)
+    return dom
+
+
+@pytest.mark.parametrize("shape,lz", [(0, 13), (1, 7), (2, 16), (3, 45), (4, 5)])
+@pytest.mark.parametrize("periodic_z", [0, 1])
+def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, periodic_z):
+    """The push kernel reads each cell's own populations and streams at the
+    store, the staged kernel pulls; both sum the densities in the same order and
+    share the collision, so after 60 steps the states (read back in the pull
+    layout) are the same bit for bit -- every shape, ragged x, y and z tiles,
+    reservoirs and a membrane (closed z) or a wrapped z axis."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
+    a = _push_run(lbm, flags, rho0, 60, shape, lz).state()[0]
+    b = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED).state()[0]
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("periodic_z", [0, 1])
+def test_push_kernel_matches_oracle(lbm, orc, periodic_z):
+    flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
+    dom = _push_run(lbm, flags, rho0, 70, 0, 13)
+    assert np.array_equal(dom.mask(), mask)
+    f = orc.init(cfg, mask, rho0)
+    orc.step(cfg, mask, f, 70)
+    assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
+    m, mo = dom.measure(), orc.measure(cfg, mask, f)
+    for key in ("n_fluid", "n_w", "n_in", "n_out"):
+        assert m[key] == mo[key], key
+    for s in range(2):
+        assert abs(m["mass"][s] - mo["mass"][s]) <= 1e-6 * mo["mass"][s]
+
+
+def test_push_kernel_switches_and_checkpoints_bitwise(lbm, orc):
+    """The state changes layout when the kernel kind changes and when it is read
+    out; neither changes a bit: push 25 steps, read the density (a converted
+    copy), staged 20, push 15 more, checkpoint, resume on a new domain with the
+    push kernel, equals 60 staged steps."""
+    flags, mask, cfg, rho0 = _case(lbm, orc, 0)
+    nz, ny, nx = SHAPE
+    ref = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED).state()[0]
+    dom = _push_run(lbm, flags, rho0, 25, 1, 8)
+    dom.density()
+    dom.set_tile(6, 16, 2)
+    dom.step(20)
+    dom.set_push_shape(4, 11)
+    dom.step(10)
+    f, st = dom.state()
+    assert st == 55
+    dom2 = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
+    dom2.set_push_shape(2, 0)
+    dom2.set_pressure_bc(2.08, W.RHO_MAJOR)
+    dom2.set_state(f, st)
+    dom2.step(5)
+    got, st2 = dom2.state()
+    assert st2 == 60
+    assert np.array_equal(got, ref)
+
+
+def test_push_kernel_applicability(lbm):
+    nz, ny, nx = SHAPE
+    d1 = lbm.Domain(_params(lbm, periodic=(1, 0, 0)), SPHERES, (nx, ny, nz))
+    with pytest.raises(lbm.LbmError):
+        d1.set_step_kernel(lbm.KERNEL_PUSH)
+    d2 = lbm.Domain(_params(lbm), SPHERES, (nx - 1, ny, nz))  # odd nx
+    with pytest.raises(lbm.LbmError):
+        d2.set_push_shape(0)
+    d3 = lbm.Domain(_params(lbm), SPHERES, (nx, ny, nz))
+    with pytest.raises(lbm.LbmError):
+        d3.set_push_shape(lbm.PUSH_SHAPES)
+    d3.set_step_kernel(lbm.KERNEL_PUSH, 9)
+    assert d3.step_kernel() == (lbm.KERNEL_PUSH, 9)
