@@ -253,6 +253,77 @@ int lbm_run_throat_batch(const double* throats, int n, const lbm_params* params,
                          lbm_throat_result* results, lbm_increment* rows, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Pore network (Sec. 2.2.1 pore-space decomposition, Sec. 2.2.2 fluid
+ * displacement, Sec. 3.1.1 drainage of the sample).  Host computations; the
+ * entry pressures they consume come from lbm_run_throat_batch (or the
+ * surrogate, or the incircle estimate).
+ * ------------------------------------------------------------------------- */
+#define LBM_PN_INLET (-1)   /* throat_pores second entry: the non-wetting reservoir */
+#define LBM_PN_OUTLET (-2)  /* throat_pores second entry: the wetting reservoir (behind the membrane) */
+
+/* lbm_regular_triangulation -- the regular triangulation of the sphere centres
+ * weighted by the squared radii (Sec. 2.2.1: tetrahedra are pore bodies, their
+ * facets pore throats; for equal radii it is the Delaunay tetrahedralisation),
+ * by Bowyer-Watson insertion in double precision.
+ *   spheres   n x (cx, cy, cz, r), n >= 4, non-overlapping spheres (then every
+ *             centre is a vertex; a redundant weighted point would be skipped).
+ *   tets_out  capacity x 4 sphere indices (host, caller-owned), each
+ *             tetrahedron positively oriented; may be NULL when capacity = 0,
+ *             which only counts.
+ *   n_tets    the number of tetrahedra.
+ * LBM_ERR_ARG for bad input, a degenerate (flat) configuration, or a capacity
+ * below the count (*n_tets still holds it). */
+int lbm_regular_triangulation(const double* spheres, int n, int* tets_out, int capacity, int* n_tets);
+
+/* lbm_pn_build -- the pore network of a lattice sample: pore i is tetrahedron i
+ * of tets (n_tets x 4 sphere indices).  Every interior void cell of the mask
+ * (mask byte 0: not grain, not a reservoir or membrane layer) belongs to the
+ * tetrahedron holding its centre (the lowest index on shared faces); cells
+ * outside every tetrahedron join the pore of the nearest such cell through the
+ * void (6-neighbour flood).  pore_volume[i] = its cell count.  Throats: every
+ * facet shared by two tetrahedra (throat_pores = the two pores, throat_spheres
+ * = the facet's three sphere indices), then a link (pore, LBM_PN_INLET) for
+ * each pore with a cell next to the inlet layer and (pore, LBM_PN_OUTLET) for
+ * each pore with a cell next to the first membrane or outlet layer (spheres
+ * -1 -1 -1).  capacity = 0 (arrays may be NULL) only counts into *n_throats.
+ *   mask, box  the sample's mask (lbm_get_mask layout) and (nx, ny, nz).
+ * LBM_ERR_ARG for bad input or a capacity below the count. */
+int lbm_pn_build(const double* spheres, int n_spheres, const int* tets, int n_tets, const unsigned char* mask,
+                 const int box[3], double* pore_volume, int* n_throats, int* throat_pores, int* throat_spheres,
+                 int capacity);
+
+/* lbm_pn_drainage -- quasi-static primary drainage of a pore network.  Level l
+ * imposes capillary pressure p_c[l]; the non-wetting fluid then passes every
+ * throat with entry pressure below p_c[l] (strictly) from a non-wetting pore or
+ * the non-wetting reservoir into a wetting pore, lowest entry pressure first
+ * (ties: lower throat index), until no such throat is left.  A wetting pore
+ * without a path of wetting pores to the wetting reservoir is trapped and keeps
+ * its fluid ("disconnected regions remain saturated", Sec. 3.1.1); nothing
+ * enters the wetting reservoir (membrane).
+ *   throat_pores  n_throats x 2: a pore, then a pore or LBM_PN_INLET / _OUTLET.
+ *   throat_pce    entry pressures (+inf: never passed).
+ *   S_w           n_levels outputs: wetting volume fraction after each level.
+ *   pore_invaded_at, pore_trapped_at (n_pores each, may be NULL): the level a
+ *                 pore was invaded / trapped at, -1 if never (pores cut off
+ *                 from the start are trapped at level 0).
+ * LBM_ERR_ARG for bad input. */
+int lbm_pn_drainage(int n_pores, const double* pore_volume, int n_throats, const int* throat_pores,
+                    const double* throat_pce, int n_levels, const double* p_c, double* S_w,
+                    int* pore_invaded_at, int* pore_trapped_at);
+
+/* lbm_throat_incircle -- for n throats (n x 3 x (cx, cy, cz, r)), the radius of
+ * the circle in the plane of the three centres that touches the three sphere
+ * sections from outside with its centre inside their triangle (the throat's
+ * inscribed circle); -1 when the spheres close the throat.  r_out: n doubles. */
+int lbm_throat_incircle(const double* throats, int n, double* r_out);
+
+/* lbm_throat_pce_incircle -- the incircle estimate of the entry pressure (the
+ * approximation Sec. 1 cites): a meniscus of radius r_i / cos(theta) spanning
+ * the inscribed circle, p_c^e = 2 sigma cos(theta) / r_i (+inf for a closed
+ * throat).  sigma: interfacial tension, cos_theta: of the contact angle. */
+int lbm_throat_pce_incircle(const double* throats, int n, double sigma, double cos_theta, double* pce_out);
+
+/* ---------------------------------------------------------------------------
  * Surrogate network.  The paper reads p_c^e off one LBM run per throat; the
  * surrogate learns that map from LBM-generated throats so that most throats of a
  * large packing need no LBM run, with the LBM as fallback where the ensemble

@@ -131,6 +131,13 @@ SIGNATURES = {
     "lbm_surrogate_selftest_wait": (ctypes.c_int, [ctypes.c_int, _IP]),
     "lbm_throat_geometry": (ctypes.c_int, [_DP, _IP, _U8P, _IP]),
     "lbm_throat_lattice_features": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
+    "lbm_regular_triangulation": (ctypes.c_int, [_DP, ctypes.c_int, _IP, ctypes.c_int, _IP]),
+    "lbm_pn_build": (ctypes.c_int, [_DP, ctypes.c_int, _IP, ctypes.c_int, _U8P, _IP, _DP, _IP, _IP, _IP,
+                                    ctypes.c_int]),
+    "lbm_pn_drainage": (ctypes.c_int, [ctypes.c_int, _DP, ctypes.c_int, _IP, _DP, ctypes.c_int, _DP, _DP, _IP,
+                                       _IP]),
+    "lbm_throat_incircle": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
+    "lbm_throat_pce_incircle": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP]),
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
                                             ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
                                             ctypes.POINTER(lbm_increment), _VP]),
@@ -390,6 +397,76 @@ def lbm_throat_geometry(spheres3):
 
 
 THROAT_LATTICE_FEATURES = 14
+
+
+PN_INLET, PN_OUTLET = -1, -2
+
+
+def lbm_regular_triangulation(spheres) -> np.ndarray:
+    """Tetrahedra (m x 4 sphere indices) of the regular triangulation of the
+    sphere centres weighted by r^2 (Sec. 2.2.1)."""
+    sp = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+    n = ctypes.c_int()
+    L = load()
+    _check(L.lbm_regular_triangulation(sp.ctypes.data_as(_DP), sp.shape[0], None, 0, ctypes.byref(n)),
+           "lbm_regular_triangulation")
+    out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+    _check(L.lbm_regular_triangulation(sp.ctypes.data_as(_DP), sp.shape[0], out.ctypes.data_as(_IP), out.shape[0],
+                                       ctypes.byref(n)), "lbm_regular_triangulation")
+    return out[:n.value]
+
+
+def lbm_pn_build(spheres, tets, mask: np.ndarray):
+    """Pore network of a lattice sample: (pore_volume[m], throat_pores[t, 2],
+    throat_spheres[t, 3]) with reservoir links as PN_INLET / PN_OUTLET."""
+    sp = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+    tt = np.ascontiguousarray(np.asarray(tets, dtype=np.int32).reshape(-1, 4))
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    nz, ny, nx = m.shape
+    bx = (ctypes.c_int * 3)(nx, ny, nz)
+    vol = np.zeros(tt.shape[0])
+    n = ctypes.c_int()
+    L = load()
+    args = (sp.ctypes.data_as(_DP), sp.shape[0], tt.ctypes.data_as(_IP), tt.shape[0], m.ctypes.data_as(_U8P), bx,
+            vol.ctypes.data_as(_DP), ctypes.byref(n))
+    _check(L.lbm_pn_build(*args, None, None, 0), "lbm_pn_build")
+    tp = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+    ts = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    _check(L.lbm_pn_build(*args, tp.ctypes.data_as(_IP), ts.ctypes.data_as(_IP), tp.shape[0]), "lbm_pn_build")
+    return vol, tp[:n.value], ts[:n.value]
+
+
+def lbm_pn_drainage(pore_volume, throat_pores, throat_pce, p_c_levels):
+    """Quasi-static drainage of a pore network: (S_w per level, invaded_at per
+    pore, trapped_at per pore)."""
+    vol = np.ascontiguousarray(pore_volume, dtype=np.float64)
+    tp = np.ascontiguousarray(np.asarray(throat_pores, dtype=np.int32).reshape(-1, 2))
+    pce = np.ascontiguousarray(throat_pce, dtype=np.float64)
+    lev = np.ascontiguousarray(p_c_levels, dtype=np.float64)
+    sw = np.zeros(lev.shape[0])
+    inv = np.zeros(vol.shape[0], dtype=np.int32)
+    trap = np.zeros(vol.shape[0], dtype=np.int32)
+    _check(load().lbm_pn_drainage(vol.shape[0], vol.ctypes.data_as(_DP), tp.shape[0], tp.ctypes.data_as(_IP),
+                                  pce.ctypes.data_as(_DP), lev.shape[0], lev.ctypes.data_as(_DP),
+                                  sw.ctypes.data_as(_DP), inv.ctypes.data_as(_IP), trap.ctypes.data_as(_IP)),
+           "lbm_pn_drainage")
+    return sw, inv, trap
+
+
+def lbm_throat_incircle(throats) -> np.ndarray:
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 12))
+    out = np.zeros(th.shape[0])
+    _check(load().lbm_throat_incircle(th.ctypes.data_as(_DP), th.shape[0], out.ctypes.data_as(_DP)),
+           "lbm_throat_incircle")
+    return out
+
+
+def lbm_throat_pce_incircle(throats, sigma: float, cos_theta: float) -> np.ndarray:
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 12))
+    out = np.zeros(th.shape[0])
+    _check(load().lbm_throat_pce_incircle(th.ctypes.data_as(_DP), th.shape[0], float(sigma), float(cos_theta),
+                                          out.ctypes.data_as(_DP)), "lbm_throat_pce_incircle")
+    return out
 
 
 def lbm_throat_lattice_features(throats) -> np.ndarray:

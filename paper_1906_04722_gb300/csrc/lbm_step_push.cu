@@ -10,8 +10,9 @@
 // happens at the store: the post-collision f*_k of cell x goes to slot k of
 // x + e_k, or, when x + e_k is not fluid for the component, to slot kbar of x
 // itself.  Nothing is ever stored into a solid cell or into the non-wetting
-// half of a membrane cell, so those slots stay zero and every density sum can
-// run over a cell's 19 pairs without looking at its class.
+// half of a membrane cell; those slots are never read either (they may hold
+// values of the pull layout the buffer held before), the densities being taken
+// as zero there from the cell's class.
 //
 // Data movement.  A CTA of 32 x BY threads owns a box of 32 x BY columns whose
 // interior, 28 x (BY - 2) columns, it advances; it marches along z through a
@@ -21,7 +22,8 @@
 // The box starts two cells left of the interior so that its x coordinate stays
 // 16-byte aligned; the cells two columns out are loaded and not used.  When a
 // plane has landed every thread sums its cell's two densities (four interleaved
-// partial sums, as the staged kernel) into a 4-plane density ring.  After one
+// partial sums, as the staged kernel; its geometry word, loaded a plane ahead,
+// zeroes a component that is not fluid there) into a 4-plane density ring.  After one
 // CTA barrier per plane the interior threads collide the plane behind with the
 // 18 neighbour densities at hand (collide_core, the arithmetic of the staged
 // kernel, so the results are the staged kernel's bit for bit) and store the
@@ -150,11 +152,25 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         p_mbar_arrive_expect_tx(b, stage_bytes<BY>());
         p_tma_load_4d(stages + (size_t)slot(p) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
     };
-    auto outside_z = [&](int p) { return !g.pz && (p < 0 || p >= g.nz); };
-    // the two densities of this thread's box cell on plane p, into the ring
-    auto publish = [&](int p) {
+    // geometry word of this thread's box cell on plane p (class CLS_OUTSIDE
+    // beyond the box or a closed z face)
+    const bool in_xy = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
+    auto word = [&](int p) -> uint32_t {
+        if (!in_xy || p > z1) return CLS_OUTSIDE << CLS_SHIFT;
+        int zc = p;
+        if (zc < 0 || zc >= g.nz) {
+            if (!g.pz) return CLS_OUTSIDE << CLS_SHIFT;
+            zc = zc < 0 ? zc + g.nz : zc - g.nz;
+        }
+        return __ldg(nbr + (size_t)zc * g.nxy + col);
+    };
+    // the two densities of this thread's box cell on plane p (geometry word wp)
+    // into the ring: 0 where a component is not fluid, whatever the slots hold
+    // (a buffer's grain slots may hold another layout's values)
+    auto publish = [&](int p, uint32_t wp) {
         float2 r = make_float2(0.f, 0.f);
-        if (!outside_z(p)) {
+        const uint32_t c = (wp >> CLS_SHIFT) & CLS_MASK;
+        if (c != CLS_SOLID && c != CLS_OUTSIDE) {
             const float2* st = stages + (size_t)slot(p) * (Q * NT) + tid;
             float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -164,7 +180,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
                 b[k & 3] += v.y;
             }
             r.x = (a[0] + a[1]) + (a[2] + a[3]);
-            r.y = (b[0] + b[1]) + (b[2] + b[3]);
+            if (c != CLS_MEMBRANE) r.y = (b[0] + b[1]) + (b[2] + b[3]);
         }
         ring[(p & 3) * NT + tid] = r;
     };
@@ -178,25 +194,25 @@ __global__ void __launch_bounds__(PX * BY, MINB)
     if (tid == 0)
         for (int p = z0 - 1; p <= z1 && p < z0 - 1 + NS; ++p) issue(p);
 
-    // geometry of the interior cell on plane z (prefetched a plane ahead)
-    uint32_t w_next = 0u;
-    if (interior) w_next = __ldg(nbr + (size_t)z0 * g.nxy + col);
+    // geometry words of planes z0 - 1 .. z0 + 1, then one plane further per iteration
+    const uint32_t w_m = word(z0 - 1);
+    uint32_t w_0 = word(z0), w_1 = word(z0 + 1);
 
     bool ok = p_mbar_wait_bounded(bar + slot(z0 - 1), parity(z0 - 1));
-    if (ok) publish(z0 - 1);
+    if (ok) publish(z0 - 1, w_m);
     ok = ok && p_mbar_wait_bounded(bar + slot(z0), parity(z0));
-    if (ok) publish(z0);
+    if (ok) publish(z0, w_0);
     // a failed wait here is reported by the first iteration's barrier below
     for (int z = z0; z < z1; ++z) {
-        const uint32_t w = w_next;
-        if (interior && z + 1 < z1) w_next = __ldg(nbr + (size_t)(z + 1) * g.nxy + col);
+        const uint32_t w = w_0;
+        const uint32_t w_2 = word(z + 2);  // for the next iteration's publish
         uint32_t a = 0u, nwb = 0u;
         if (interior) {
             if (w & BIT_ADH) a = __ldg(adh + (size_t)z * g.nxy + col);
             if (w & BIT_NW_DIFF) nwb = __ldg(nbr_nw + (size_t)z * g.nxy + col);
         }
         const bool okz = ok && p_mbar_wait_bounded(bar + slot(z + 1), parity(z + 1));
-        if (okz) publish(z + 1);
+        if (okz) publish(z + 1, w_1);
         if (__syncthreads_or(!okz)) {
             if (tid == 0) {
                 atomicOr(err, 1);
@@ -211,15 +227,18 @@ __global__ void __launch_bounds__(PX * BY, MINB)
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             issue(z + NS - 1);  // into the stage of plane z - 1, read by everyone before the barrier
         }
+        w_0 = w_1;
+        w_1 = w_2;
         const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
         if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE) {
             const float2* st = stages + (size_t)slot(z) * (Q * NT) + tid;
             float f[2][Q];
 #pragma unroll
+            const bool has_nw = cls != CLS_MEMBRANE;
             for (int k = 0; k < Q; ++k) {
                 const float2 v = st[k * NT];
                 f[0][k] = v.x;
-                f[1][k] = v.y;
+                f[1][k] = has_nw ? v.y : 0.f;
             }
             float o[2][Q];
             collide_core(
