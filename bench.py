@@ -65,6 +65,10 @@ def parse():
                     help="instead of the benchmark: the full drainage of the sample (20 increments x 5000 steps), "
                          "one JSON line with the p_c - S_w curve")
     ap.add_argument("--no-tune", action="store_true", help="time the default kernel instead of the autotuned one")
+    ap.add_argument("--pore-network", action="store_true",
+                    help="drainage of the sample by the pore network (throat entry pressures from the batched "
+                         "LBM and the incircle estimate) next to the full LBM drainage, one JSON line")
+    ap.add_argument("--pn-steps", type=int, default=5000, help="full-LBM steps per increment for --pore-network")
     ap.add_argument("--shape", default="",
                     help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD, "
                          "staged2:BY:LZ:2 or push:ROWS:LZ:STAGES")
@@ -563,6 +567,106 @@ def run_drainage(args):
     return 0
 
 
+def laplace_sigma(lbm, W, edge=48, radii=(8.0, 12.0), steps=4000):
+    """Interfacial tension of the model from Laplace's law on the GPU: static
+    non-wetting drops of two radii in a periodic box, dp = p_nw - p_w of the bulk
+    phases (Eq. 5), R from the drop's volume; sigma = dp R / 2 averaged."""
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=(0.0, 0.0), rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR, periodic=(1, 1, 1))
+    shape = (edge, edge, edge)
+    out = []
+    for R0 in radii:
+        with lbm.Domain(params, None, shape) as d:
+            d.set_densities(W.droplet_densities(shape, (edge / 2, edge / 2, edge / 2), R0, seed=1, noise=0.0))
+            d.step(steps)
+            m = d.measure()
+        vol = m["n_fluid"] - m["n_w"]
+        R = (3.0 * vol / (4.0 * math.pi)) ** (1.0 / 3.0)
+        out.append((R, m["p_nw"] - m["p_w"]))
+    return float(np.mean([dp * R / 2.0 for R, dp in out])), out
+
+
+def run_pore_network(args):
+    """Row f1: drainage of the 192^3 sample by the pore network (Sec. 2.2.1 -
+    2.2.2, Sec. 3.1.1) next to the fully resolved LBM drainage.  The network is
+    the regular triangulation of the packing; every interior throat's entry
+    pressure comes from the batched throat LBM (and, as the cheap baseline, from
+    the incircle estimate with sigma from Laplace's law and the contact angle of
+    the adhesion estimate); the levels are the reservoir capillary pressures the
+    full LBM reached at each of its increments."""
+    import torch
+    import paper_1906_04722_gb300 as lbm
+    import workloads as W
+
+    spheres, box = sample_geometry(args.size)
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR, reservoirs=True, membrane_layers=3)
+    t_all = time.perf_counter()
+    dom = lbm.Domain(params, spheres, box)
+    mask = dom.mask()
+    dom.autotune(trial_steps=10)
+    ladder = [W.RHO_MAJOR + 0.02 * i for i in range(20)]
+    probe = (box[0] // 2, box[1] // 2, box[2] - 6)
+    t0 = time.perf_counter()
+    full = dom.drainage(ladder, args.pn_steps, W.RHO_MAJOR, probe)
+    torch.cuda.synchronize()
+    t_full = time.perf_counter() - t0
+    dom.close()
+
+    t0 = time.perf_counter()
+    tets = lbm.lbm_regular_triangulation(spheres)
+    vol, tp, ts = lbm.lbm_pn_build(spheres, tets, mask)
+    inner = tp[:, 1] >= 0
+    tri = spheres[ts[inner]]
+    t_net = time.perf_counter() - t0
+
+    tparams = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                              rho_minor=W.RHO_MINOR)
+    tl = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, _ = lbm.lbm_run_throat_batch(tri, tparams, tl, args.throat_steps, W.RHO_MAJOR)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    pce_lbm = np.array([r["p_ce"] for r in res])
+    sigma, drops = laplace_sigma(lbm, W)
+    cos_t = (W.G_ADS[1] - W.G_ADS[0]) / (W.G_COHESION * (W.RHO_MAJOR - W.RHO_MINOR) / 2.0)
+    pce_inc = lbm.lbm_throat_pce_incircle(tri, sigma, cos_t)
+
+    levels = np.array([r["p_c_res"] for r in full["rows"]])
+    sw_full = np.array([r["S_w"] for r in full["rows"]])
+
+    def network_curve(pce_inner):
+        pce = np.zeros(len(tp))
+        pce[inner] = pce_inner
+        pce[tp[:, 1] == lbm.PN_OUTLET] = np.inf
+        sw, inv, trap = lbm.lbm_pn_drainage(vol, tp, pce, levels)
+        return sw, int((trap >= 0).sum())
+
+    sw_lbm, trapped_lbm = network_curve(pce_lbm)
+    sw_inc, trapped_inc = network_curve(pce_inc)
+    rows = [{"increment": i, "rho_in_nw": ladder[i], "p_c_res": float(levels[i]), "S_w_full_lbm": float(sw_full[i]),
+             "S_w_network_lbm_pce": float(sw_lbm[i]), "S_w_network_incircle": float(sw_inc[i])}
+            for i in range(len(levels))]
+    print(json.dumps({
+        "workload": f"sample{args.size}: full LBM drainage 20 x {args.pn_steps} steps vs pore-network drainage "
+                    f"on its regular triangulation ({len(tets)} pores, {int(inner.sum())} interior throats)",
+        "seconds": {"full_lbm": t_full, "network_build": t_net, "throat_batch": t_batch,
+                    "total": time.perf_counter() - t_all},
+        "throats": {"n": int(inner.sum()), "invaded_in_ladder": int(np.isfinite(pce_lbm).sum()),
+                    "p_ce_median": float(np.median(pce_lbm[np.isfinite(pce_lbm)])),
+                    "incircle_p_ce_median": float(np.median(pce_inc[np.isfinite(pce_inc)])),
+                    "incircle_vs_lbm_median_ratio": float(np.median((pce_inc / pce_lbm)[np.isfinite(pce_lbm)]))},
+        "sigma": sigma, "laplace_drops": drops, "cos_theta": cos_t,
+        "trapped_pores": {"lbm_pce": trapped_lbm, "incircle": trapped_inc},
+        "S_w_abs_error": {"lbm_pce_max": float(np.abs(sw_lbm - sw_full).max()),
+                          "lbm_pce_mean": float(np.abs(sw_lbm - sw_full).mean()),
+                          "incircle_max": float(np.abs(sw_inc - sw_full).max()),
+                          "incircle_mean": float(np.abs(sw_inc - sw_full).mean())},
+        "rows": rows}))
+    return 0
+
+
 def run_throat_batch(args):
     """One lbm_run_throat_batch of the throat benchmark's held-out packing in one
     form, then the same call with zero steps per increment (geometry, lists,
@@ -596,6 +700,8 @@ def main():
     args = parse()
     if args.drainage:
         return run_drainage(args)
+    if args.pore_network:
+        return run_pore_network(args)
     if args.throat_batch:
         return run_throat_batch(args)
     rank, world, local = dist_env()

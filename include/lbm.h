@@ -371,6 +371,80 @@ void lbm_surrogate_destroy(lbm_surrogate* s);
  * in the paper. */
 int lbm_surrogate_selftest_wait(int limit_us, int* gave_up);
 
+/* ---------------------------------------------------------------------------
+ * Throat surrogate: the network above applied to pore throats (no counterpart
+ * in the paper, which reads p_c^e off one LBM run per throat, Sec. 2.2.2).
+ * Inputs per throat (LBM_SURROGATE_INPUTS): the three radii and the three
+ * centre distances over the mean radius R (spheres ordered by decreasing
+ * radius, ties in input order) and the contact angle (7); the throat box's
+ * lbm_throat_lattice_features (14); their entries 5, 8 and 9 over R (3).
+ * Outputs (1 + n_incr): p_c^e R and the throat's S_w after each increment of
+ * the training ladder.  Inputs and targets are standardised by the training
+ * means and standard deviations (+1e-6).
+ * ------------------------------------------------------------------------- */
+#define LBM_SURROGATE_INPUTS 24
+typedef struct lbm_throat_surrogate lbm_throat_surrogate;
+typedef struct {
+    int n_incr;               /* increments of the ladder the targets come from      */
+    int n_members, n_hidden, n_layers, half;  /* the ensemble (lbm_surrogate_config) */
+    unsigned long long seed;  /* initialisation seed                                  */
+    double theta;             /* contact angle (radians) in every throat's inputs     */
+} lbm_throat_surrogate_config;
+
+/* lbm_contact_angle_estimate -- contact angle of the wall adhesion by the
+ * estimate cos(theta) = (G_ads,nw - G_ads,w) / (G (rho_major - rho_minor) / 2)
+ * (Huang et al. 2007), clamped to [0, pi]; radians. */
+int lbm_contact_angle_estimate(double G_ads_w, double G_ads_nw, double G, double rho_major, double rho_minor,
+                               double* theta_out);
+
+/* lbm_pressure_ladder -- per-throat reservoir ladders: n_incr inlet densities
+ * per throat (out: n x n_incr, throat-major) whose reservoir capillary pressure
+ * p_c,res = (rho_in - rho_major)(1 + G rho_minor)/3 (Eq. 5 on the reservoir
+ * layers at rest) runs from lo / r to hi / r in equal steps, r = r_in[i]
+ * (floored at 0.5), e.g. the throat's incircle radius. */
+int lbm_pressure_ladder(const double* r_in, int n, int n_incr, double lo, double hi, double rho_major,
+                        double rho_minor, double G, double* out);
+
+/* lbm_throat_surrogate_inputs -- the inputs of n throats (n x 3 x 4 doubles):
+ * X_out n x LBM_SURROGATE_INPUTS floats, R_out (may be NULL) the mean radii. */
+int lbm_throat_surrogate_inputs(const double* throats, int n, double theta, float* X_out, double* R_out);
+
+int lbm_throat_surrogate_create(const lbm_throat_surrogate_config* cfg, void* stream, lbm_throat_surrogate** out);
+
+/* lbm_throat_surrogate_fit -- trains on n throats and their batched-LBM outcome
+ * (results: n entries, rows: n x n_incr, as lbm_run_throat_batch returns them);
+ * throats never invaded within the ladder are left out (*n_used counts the
+ * rest).  Sets the standardisation, then lbm_surrogate_train (epochs, batch, lr,
+ * shuffle_seed, epoch_loss as there).  LBM_ERR_ARG with fewer than 2 throats. */
+int lbm_throat_surrogate_fit(lbm_throat_surrogate* ts, const double* throats, int n, const lbm_throat_result* results,
+                             const lbm_increment* rows, int epochs, int batch, float lr, unsigned long long shuffle_seed,
+                             double* epoch_loss, int* n_used);
+
+/* lbm_throat_surrogate_predict -- ensemble mean p_c^e (lattice pressure units),
+ * its relative spread |std(p_c^e R)| / |mean(p_c^e R)|, and (curves, may be
+ * NULL; n x n_incr) the mean S_w curve of n throats.  LBM_ERR_STATE before a fit. */
+int lbm_throat_surrogate_predict(lbm_throat_surrogate* ts, const double* throats, int n, double* p_ce,
+                                 double* rel_spread, float* curves);
+
+/* lbm_throat_surrogate_predict_with_fallback -- p_c^e of n throats: the
+ * ensemble's where its relative spread is at most spread_tol, otherwise the
+ * batched LBM's (lbm_run_throat_batch with params and sched on the surrogate's
+ * stream; with sched->per_throat the ladders are n x n_incr).  used_lbm[i] = 1
+ * for the throats that went to the LBM.  seconds (may be NULL): [network time,
+ * LBM time]. */
+int lbm_throat_surrogate_predict_with_fallback(lbm_throat_surrogate* ts, const double* throats, int n,
+                                               double spread_tol, const lbm_params* params,
+                                               const lbm_schedule* sched, double* p_ce, int* used_lbm,
+                                               double* seconds);
+
+/* lbm_throat_surrogate_scaling -- the standardisation (LBM_SURROGATE_INPUTS and
+ * 1 + n_incr doubles each).  lbm_throat_surrogate_network -- the underlying
+ * network (owned by the throat surrogate). */
+int lbm_throat_surrogate_scaling(const lbm_throat_surrogate* ts, double* x_mu, double* x_sd, double* y_mu,
+                                 double* y_sd);
+lbm_surrogate* lbm_throat_surrogate_network(lbm_throat_surrogate* ts);
+void lbm_throat_surrogate_destroy(lbm_throat_surrogate* ts);
+
 /* lbm_get_density -- densities of the current state, 2 x N doubles
  * (component-major), 0 where a component is not fluid. Synchronising. */
 int lbm_get_density(lbm_domain* d, double* rho_out);
