@@ -285,20 +285,19 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
                        f"32 increments x {n_steps} steps", "unit": "throats/s"}
     # training set from six other packings
     t0 = time.perf_counter()
-    Xs, Ys = [], []
+    tris, ress, rowss = [], [], []
     for seed in range(10 + 6 * rank, 16 + 6 * rank):
         tri = W.delaunay_throats(W.sample_spheres(192, seed=100 + seed), 1024, seed=100 + seed)
         res, rows = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
-        X, R = S.surrogate_inputs(tri, theta)
-        Y, ok = S.ThroatSurrogate.targets(res, rows, R)
-        Xs.append(X[ok])
-        Ys.append(Y[ok])
+        tris.append(tri)
+        ress += res
+        rowss += rows
     t_gen = time.perf_counter() - t0
-    sur = S.ThroatSurrogate(n_incr=len(ladder), n_members=5, seed=1)
+    sur = S.ThroatSurrogate(n_incr=len(ladder), theta=theta, n_members=5, seed=1)
     t0 = time.perf_counter()
-    losses = sur.fit(np.concatenate(Xs), np.concatenate(Ys), epochs=300, batch=256, lr=1e-3, seed=2)
+    losses, used = sur.fit(np.concatenate(tris), ress, rowss, epochs=300, batch=256, lr=1e-3, seed=2)
     t_train = time.perf_counter() - t0
-    out["surrogate_training"] = {"throats": int(sum(len(x) for x in Xs)), "lbm_s": t_gen, "train_s": t_train,
+    out["surrogate_training"] = {"throats": int(used), "lbm_s": t_gen, "train_s": t_train,
                                  "loss_first_last": [float(losses[:, 0].mean()), float(losses[:, -1].mean())]}
 
     tri = W.delaunay_throats(W.sample_spheres(192, seed=3 + 1000 * rank), 1024, seed=3 + 1000 * rank)
@@ -343,7 +342,7 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
         sur.spread_tol = tol
         sync()
         t0 = time.perf_counter()
-        pce, fell, _, _ = sur.predict_with_fallback(tri, theta, params, ladder, n_steps, W.RHO_MAJOR)
+        pce, fell, _, _ = sur.predict_with_fallback(tri, params, ladder, n_steps, W.RHO_MAJOR)
         sync()
         dt = tmax(time.perf_counter() - t0)
         ans = ok & ~fell
@@ -352,7 +351,7 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
             "value": world * n / dt, "vs_plain": world * n / dt / out["plain"], "fallback_fraction": float(fell.mean()),
             "pce_rel_err_answered_median": float(np.median(err)) if err.size else None,
             "pce_rel_err_answered_p90": float(np.percentile(err, 90)) if err.size else None}
-    sur.net.close()
+    sur.close()
     return out
 
 

@@ -81,6 +81,12 @@ class lbm_throat_result(ctypes.Structure):
                 "probe": tuple(self.probe), "n_fluid": self.n_fluid}
 
 
+class lbm_throat_surrogate_config(ctypes.Structure):
+    _fields_ = [("n_incr", ctypes.c_int), ("n_members", ctypes.c_int), ("n_hidden", ctypes.c_int),
+                ("n_layers", ctypes.c_int), ("half", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("theta", ctypes.c_double)]
+
+
 class lbm_tune_result(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("by", ctypes.c_int), ("lz", ctypes.c_int), ("lead", ctypes.c_int),
                 ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int)]
@@ -138,6 +144,21 @@ SIGNATURES = {
                                        _IP]),
     "lbm_throat_incircle": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
     "lbm_throat_pce_incircle": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP]),
+    "lbm_contact_angle_estimate": (ctypes.c_int, [ctypes.c_double] * 5 + [_DP]),
+    "lbm_pressure_ladder": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [_DP]),
+    "lbm_throat_surrogate_inputs": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _FP, _DP]),
+    "lbm_throat_surrogate_create": (ctypes.c_int, [ctypes.POINTER(lbm_throat_surrogate_config), _VP,
+                                                   ctypes.POINTER(_VP)]),
+    "lbm_throat_surrogate_fit": (ctypes.c_int, [_VP, _DP, ctypes.c_int, ctypes.POINTER(lbm_throat_result),
+                                                ctypes.POINTER(lbm_increment), ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_float, ctypes.c_ulonglong, _DP, _IP]),
+    "lbm_throat_surrogate_predict": (ctypes.c_int, [_VP, _DP, ctypes.c_int, _DP, _DP, _FP]),
+    "lbm_throat_surrogate_predict_with_fallback": (ctypes.c_int, [_VP, _DP, ctypes.c_int, ctypes.c_double,
+                                                                  ctypes.POINTER(lbm_params),
+                                                                  ctypes.POINTER(lbm_schedule), _DP, _IP, _DP]),
+    "lbm_throat_surrogate_scaling": (ctypes.c_int, [_VP, _DP, _DP, _DP, _DP]),
+    "lbm_throat_surrogate_network": (_VP, [_VP]),
+    "lbm_throat_surrogate_destroy": (None, [_VP]),
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
                                             ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
                                             ctypes.POINTER(lbm_increment), _VP]),

@@ -44,21 +44,18 @@ def test_surrogate_gain_over_lbm(lbm):
     ladder = [2.0 + 0.02 * i for i in range(32)]
     n_steps = 100
     # training throats: three seeded packings, 1024 facets each
-    Xs, Ys = [], []
+    tris, ress, rowss = [], [], []
     t0 = time.perf_counter()
     for seed in (10, 11, 12):
         tri = W.delaunay_throats(W.sample_spheres(192, seed=seed), 1024, seed=seed)
         res, rows = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
-        X, R = S.surrogate_inputs(tri, theta)
-        Y, ok = S.ThroatSurrogate.targets(res, rows, R)
-        Xs.append(X[ok])
-        Ys.append(Y[ok])
+        tris.append(tri)
+        ress += res
+        rowss += rows
     t_gen = time.perf_counter() - t0
-    X = np.concatenate(Xs)
-    Y = np.concatenate(Ys)
-    sur = S.ThroatSurrogate(n_incr=len(ladder), n_members=5, seed=1)
+    sur = S.ThroatSurrogate(n_incr=len(ladder), theta=theta, n_members=5, seed=1)
     t0 = time.perf_counter()
-    losses = sur.fit(X, Y, epochs=300, batch=256, lr=1e-3, seed=2)
+    losses, n_used = sur.fit(np.concatenate(tris), ress, rowss, epochs=300, batch=256, lr=1e-3, seed=2)
     t_train = time.perf_counter() - t0
     # held-out throats from another packing, with the LBM result of each
     tri = W.delaunay_throats(W.sample_spheres(192, seed=20), 1024, seed=20)
@@ -66,13 +63,13 @@ def test_surrogate_gain_over_lbm(lbm):
     res_ref, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
     t_lbm_all = time.perf_counter() - t0
     truth = np.array([r["p_ce"] for r in res_ref])
-    rep = {"train_throats": int(len(X)), "generate_s": t_gen, "train_s": t_train,
+    rep = {"train_throats": int(n_used), "generate_s": t_gen, "train_s": t_train,
            "loss_first_last": [float(losses[:, 0].mean()), float(losses[:, -1].mean())],
            "held_out": int(len(tri)), "throats_per_s_lbm_batched": len(tri) / t_lbm_all}
     ok = np.isfinite(truth)
     for tol in (0.02, 0.05):
         sur.spread_tol = tol
-        pce, fell, t_net, t_fb = sur.predict_with_fallback(tri, theta, params, ladder, n_steps, W.RHO_MAJOR)
+        pce, fell, t_net, t_fb = sur.predict_with_fallback(tri, params, ladder, n_steps, W.RHO_MAJOR)
         answered = ok & ~fell
         err = np.abs(pce[ok] - truth[ok]) / truth[ok]
         err_ans = np.abs(pce[answered] - truth[answered]) / truth[answered]

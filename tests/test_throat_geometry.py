@@ -42,7 +42,7 @@ def test_throat_incircle_closed_forms():
         t2 = t.copy()
         t2[:, :3] = t[:, :3] @ rot.T + np.array([3.3, -7.1, 12.9])
         got = S.throat_incircle(np.stack([t, t2]))
-        assert np.allclose(got, a / math.sqrt(3) - r, atol=1e-6)
+        assert np.allclose(got, a / math.sqrt(3) - r, atol=1e-9)
     t = np.array([[0, 0, 0, 9.0], [24, 0, 0, 12.0], [9, 19, 0, 10.5]])
     q = t[:, :2]
     best = 0.0
@@ -108,16 +108,44 @@ def test_lattice_reference_against_brute_force(lbm):
 
 
 def test_surrogate_inputs_layout(lbm):
-    """The surrogate's 24 inputs: the 7 geometric features, the 14 lattice
-    numbers of each box, then three of those lengths over the mean radius."""
+    """The surrogate's 24 inputs (lbm_throat_surrogate_inputs): the three radii
+    and three centre distances over the mean radius, spheres ordered by
+    decreasing radius, and the contact angle; the 14 lattice numbers of each
+    box; then three of those lengths over the mean radius -- each recomputed
+    here from that definition."""
     from paper_1906_04722_gb300 import surrogate as S
     throats = W.delaunay_throats(W.sample_spheres(128), 12, seed=3)
+    throats[0, 1, 3] = throats[0, 2, 3]  # a tie keeps the input order
     X, R = S.surrogate_inputs(throats, 0.8)
     assert X.shape == (len(throats), S.N_INPUTS) and X.dtype == np.float32
-    G, R2 = S.throat_features(throats, 0.8)
     L = lbm.lbm_throat_lattice_features(throats)
-    np.testing.assert_array_equal(R, R2)
-    np.testing.assert_array_equal(X[:, :7], G)
-    np.testing.assert_allclose(X[:, 7:21], L, rtol=1e-6)
-    np.testing.assert_allclose(X[:, 21:], L[:, [5, 8, 9]] / R[:, None], rtol=1e-6)
-    assert np.all(X[:, 6] == np.float32(0.8))
+    for i, t in enumerate(throats):
+        order = sorted(range(3), key=lambda j: -t[j, 3])  # stable: ties in input order
+        c, r = t[order, :3], t[order, 3]
+        Ri = r.mean()
+        d = [np.linalg.norm(c[0] - c[1]), np.linalg.norm(c[1] - c[2]), np.linalg.norm(c[0] - c[2])]
+        want = np.r_[r / Ri, np.array(d) / Ri, 0.8, L[i], L[i, [5, 8, 9]] / Ri].astype(np.float32)
+        assert R[i] == pytest.approx(Ri, rel=1e-15)
+        np.testing.assert_array_equal(X[i], want)
+
+
+def test_pressure_ladder_closed_form(lbm):
+    """Per-throat ladders: the reservoir capillary pressure of Eq. 5 at rest,
+    p_c,res = (rho_in - rho_major)(1 + G rho_minor)/3, runs from lo/r to hi/r in
+    equal steps; radii below 0.5 count as 0.5."""
+    from paper_1906_04722_gb300 import surrogate as S
+    r = np.array([2.0, 4.0, 0.1])
+    lad = S.pressure_ladder(r, 5, 0.4, 1.6, 2.0, 0.06, 0.9)
+    pc = (lad - 2.0) * (1 + 0.9 * 0.06) / 3.0
+    for i, ri in enumerate([2.0, 4.0, 0.5]):
+        np.testing.assert_allclose(pc[i], np.linspace(0.4, 1.6, 5) / ri, rtol=1e-13)
+
+
+def test_contact_angle_estimate(lbm):
+    """cos(theta) = (G_ads,nw - G_ads,w) / (G (rho_major - rho_minor) / 2), clamped."""
+    import math
+    from paper_1906_04722_gb300 import surrogate as S
+    th = S.contact_angle_estimate(-0.3, 0.3, 0.9, 2.0, 0.06)
+    assert math.cos(th) == pytest.approx(0.6 / (0.9 * 0.97), rel=1e-14)
+    assert S.contact_angle_estimate(0.0, 0.0, 0.9, 2.0, 0.06) == pytest.approx(math.pi / 2)
+    assert S.contact_angle_estimate(-5.0, 5.0, 0.9, 2.0, 0.06) == 0.0
