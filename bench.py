@@ -145,7 +145,7 @@ KERNEL_SOURCES = {
     "sc_step_push_kernel": ("lbm_step_push.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
 }
 # push kernel shapes (box rows, plane stages) -> lbm_set_push_shape index, CTAs per SM
-PUSH_SHAPES = {(8, 4): (0, 1), (8, 3): (1, 1), (6, 3): (2, 2), (10, 3): (3, 1), (4, 4): (4, 2)}
+PUSH_SHAPES = {(8, 4): (0, 1), (6, 3): (1, 2), (10, 3): (2, 1)}
 
 
 def kernel_hash(kernel_name="sc_step_kernel"):
@@ -441,7 +441,8 @@ def run_ours(args, rank, world, local):
         kernel_name = "sc_step16_kernel<%s,%d,%d>" % ("half2" if args.precision == 1 else "bfloat162", by, lead)
     elif kind == lbm.KERNEL_PUSH:
         rows, stages = tuned["by"], tuned["lead"]
-        kernel_name = "sc_step_push_kernel<%d,%d,%d>" % (rows, stages, PUSH_SHAPES[(rows, stages)][1])
+        kernel_name = "sc_step_push_kernel<%d,%d,%d,%s>" % (rows, stages, PUSH_SHAPES[(rows, stages)][1],
+                                                             "true" if tuple(W.TAU) == (1.0, 1.0) else "false")
     elif kind == lbm.KERNEL_TMA:
         kernel_name = "sc_step_tma_kernel"
     elif kind == lbm.KERNEL_SPLIT:

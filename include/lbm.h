@@ -312,9 +312,11 @@ int lbm_pn_drainage(int n_pores, const double* pore_volume, int n_throats, const
                     int* pore_invaded_at, int* pore_trapped_at);
 
 /* lbm_throat_incircle -- for n throats (n x 3 x (cx, cy, cz, r)), the radius of
- * the circle in the plane of the three centres that touches the three sphere
- * sections from outside with its centre inside their triangle (the throat's
- * inscribed circle); -1 when the spheres close the throat.  r_out: n doubles. */
+ * the throat's inscribed circle: in the plane of the three centres, the largest
+ * clearance min_i(|p - c_i| - r_i) over points p of their triangle (the circle
+ * touching the three sphere sections when its centre lies in the triangle,
+ * else a circle centred on an edge); 0 when the spheres close the throat.
+ * r_out: n doubles. */
 int lbm_throat_incircle(const double* throats, int n, double* r_out);
 
 /* lbm_throat_pce_incircle -- the incircle estimate of the entry pressure (the
@@ -546,12 +548,13 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
 
 /* lbm_set_push_shape -- switches the domain to LBM_KERNEL_PUSH with a CTA shape:
  *   shape  0: 8 box rows (6 interior), 4 plane stages, one CTA per SM;
- *          1: 8 rows, 3 stages, one CTA;  2: 6 rows, 3 stages, two CTAs;
- *          3: 10 rows, 3 stages, one CTA; 4: 4 rows, 4 stages, two CTAs.
+ *          1: 6 rows, 3 stages, two CTAs per SM; 2: 10 rows, 3 stages, one CTA.
  *          A CTA of 32 x rows threads advances 28 x (rows - 2) columns.
  *   lz     planes per CTA z segment (lz <= 0: a default for the box).
- * Results do not depend on the shape (bit for bit).  LBM_ERR_ARG for an unknown
- * shape, LBM_ERR_STATE when the push kernel does not apply to the domain. */
+ * Results do not depend on the shape (bit for bit); with tau = 1 in both
+ * components a compile-time tau = 1 form of the collision runs (the same bits).
+ * LBM_ERR_ARG for an unknown shape, LBM_ERR_STATE when the push kernel does not
+ * apply to the domain. */
 int lbm_set_push_shape(lbm_domain* d, int shape, int lz);
 
 /* lbm_autotune -- time the step kernels and launch shapes that apply to the

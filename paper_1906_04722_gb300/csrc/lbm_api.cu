@@ -348,8 +348,8 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     g.pz = params->periodic[2] ? 1 : 0;
     fill_pull_offsets(g);
     d->tile = default_tile(g);
-    d->tile.push_shape = 0;
-    d->tile.push_lz = push_default_lz(g, 0);
+    d->tile.push_shape = 1;  // 6 rows, 3 stages, two CTAs per SM
+    d->tile.push_lz = push_default_lz(g, 1);
     d->layout = 0;
     d->push_maps_rows = 0;
 

@@ -333,11 +333,16 @@ class Regular {
     }
 };
 
-// Largest circle in the plane of three sphere centres that touches the three
-// sphere sections (radius r_i each) from outside: |c - c_i| = r + r_i.  In the
-// plane, subtracting the first equation from the others gives c linear in r;
-// the first equation is then a quadratic in r.  Returns -1 when the spheres
-// close the throat (no such circle with its centre inside the triangle).
+// Inscribed circle of a throat: in the plane of the three centres, the largest
+// clearance f(p) = min_i (|p - c_i| - r_i) over points p of their triangle (the
+// widest circle centred in the triangle that the three sphere sections leave
+// free).  Along a curve where two clearances are equal f grows away from their
+// centres, so its maximum is either the point where all three are equal (the
+// circle touching the three sections, |c - c_i| = r + r_i, when its centre lies
+// in the triangle) or lies on an edge.  Subtracting the first tangency equation
+// from the others makes c linear in r, the first is then a quadratic in r; each
+// edge is sampled and the best sample refined by golden-section search.
+// Returns 0 when the spheres close the throat (no positive clearance).
 double incircle3(const double* s3) {
     V3 c[3];
     double r[3];
@@ -345,18 +350,30 @@ double incircle3(const double* s3) {
         c[i] = {s3[4 * i], s3[4 * i + 1], s3[4 * i + 2]};
         r[i] = s3[4 * i + 3];
     }
-    // frame of the plane: origin c0, e1 along c1 - c0, e2 in the plane
     const V3 a = sub(c[1], c[0]), b = sub(c[2], c[0]);
     const double la = std::sqrt(dot(a, a));
-    if (!(la > 0)) return -1;
+    if (!(la > 0)) return 0;
     const V3 e1{a.x / la, a.y / la, a.z / la};
     V3 n = cross(a, b);
     const double ln = std::sqrt(dot(n, n));
-    if (!(ln > 0)) return -1;
+    if (!(ln > 0)) return 0;
     n = {n.x / ln, n.y / ln, n.z / ln};
     const V3 e2 = cross(n, e1);
-    double P[3][2] = {{0, 0}, {la, 0}, {dot(b, e1), dot(b, e2)}};
-    // 2 (P_i - P_0) . c = |P_i|^2 - |P_0|^2 - (r_i^2 - r_0^2) - 2 r (r_i - r_0), i = 1, 2
+    const double P[3][2] = {{0, 0}, {la, 0}, {dot(b, e1), dot(b, e2)}};
+    auto clearance = [&](double x, double y) {
+        double m = std::numeric_limits<double>::infinity();
+        for (int i = 0; i < 3; ++i) m = std::min(m, std::hypot(x - P[i][0], y - P[i][1]) - r[i]);
+        return m;
+    };
+    auto inside = [&](double x, double y) {
+        auto side = [&](int i, int j) {
+            return (P[j][0] - P[i][0]) * (y - P[i][1]) - (P[j][1] - P[i][1]) * (x - P[i][0]);
+        };
+        const double s0 = side(0, 1), s1 = side(1, 2), s2 = side(2, 0);
+        return (s0 >= 0 && s1 >= 0 && s2 >= 0) || (s0 <= 0 && s1 <= 0 && s2 <= 0);
+    };
+    double best = -std::numeric_limits<double>::infinity();
+    // 1. the circle touching the three sections: c = g + h r
     double A[2][2], u[2], v[2];
     for (int i = 1; i <= 2; ++i) {
         A[i - 1][0] = 2 * (P[i][0] - P[0][0]);
@@ -366,39 +383,56 @@ double incircle3(const double* s3) {
         v[i - 1] = -2 * (r[i] - r[0]);
     }
     const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-    if (!(std::fabs(det) > 0)) return -1;
-    // c = g + h r
-    const double g0 = (u[0] * A[1][1] - A[0][1] * u[1]) / det, g1 = (A[0][0] * u[1] - u[0] * A[1][0]) / det;
-    const double h0 = (v[0] * A[1][1] - A[0][1] * v[1]) / det, h1 = (A[0][0] * v[1] - v[0] * A[1][0]) / det;
-    // |g + h r - P0|^2 = (r + r0)^2
-    const double dx = g0 - P[0][0], dy = g1 - P[0][1];
-    const double qa = h0 * h0 + h1 * h1 - 1.0;
-    const double qb = 2 * (dx * h0 + dy * h1) - 2 * r[0];
-    const double qc = dx * dx + dy * dy - r[0] * r[0];
-    double best = -1;
-    auto consider = [&](double rr) {
-        if (!(rr > 0) || !std::isfinite(rr)) return;
-        const double cx = g0 + h0 * rr, cy = g1 + h1 * rr;
-        // the centre must lie inside the triangle of the centres
-        auto side = [&](int i, int j) {
-            return (P[j][0] - P[i][0]) * (cy - P[i][1]) - (P[j][1] - P[i][1]) * (cx - P[i][0]);
-        };
-        const double s0 = side(0, 1), s1 = side(1, 2), s2 = side(2, 0);
-        const bool inside = (s0 >= 0 && s1 >= 0 && s2 >= 0) || (s0 <= 0 && s1 <= 0 && s2 <= 0);
-        if (!inside) return;
-        if (best < 0 || rr < best) best = rr;
-    };
-    if (std::fabs(qa) < 1e-14) {
-        if (std::fabs(qb) > 0) consider(-qc / qb);
-    } else {
-        const double disc = qb * qb - 4 * qa * qc;
-        if (disc >= 0) {
-            const double sq = std::sqrt(disc);
-            consider((-qb - sq) / (2 * qa));
-            consider((-qb + sq) / (2 * qa));
+    if (std::fabs(det) > 0) {
+        const double g0 = (u[0] * A[1][1] - A[0][1] * u[1]) / det, g1 = (A[0][0] * u[1] - u[0] * A[1][0]) / det;
+        const double h0 = (v[0] * A[1][1] - A[0][1] * v[1]) / det, h1 = (A[0][0] * v[1] - v[0] * A[1][0]) / det;
+        // |g + h r - P0|^2 = (r + r0)^2
+        const double dx = g0 - P[0][0], dy = g1 - P[0][1];
+        const double qa = h0 * h0 + h1 * h1 - 1.0;
+        const double qb = 2 * (dx * h0 + dy * h1) - 2 * r[0];
+        const double qc = dx * dx + dy * dy - r[0] * r[0];
+        double roots[2];
+        int nr = 0;
+        if (std::fabs(qa) < 1e-14) {
+            if (std::fabs(qb) > 0) roots[nr++] = -qc / qb;
+        } else {
+            const double disc = qb * qb - 4 * qa * qc;
+            if (disc >= 0) {
+                const double sq = std::sqrt(disc);
+                roots[nr++] = (-qb - sq) / (2 * qa);
+                roots[nr++] = (-qb + sq) / (2 * qa);
+            }
+        }
+        for (int k = 0; k < nr; ++k) {
+            const double rr = roots[k];
+            if (!std::isfinite(rr) || rr + std::max({r[0], r[1], r[2]}) < 0) continue;
+            const double cx = g0 + h0 * rr, cy = g1 + h1 * rr;
+            if (inside(cx, cy)) best = std::max(best, clearance(cx, cy));
         }
     }
-    return best;
+    // 2. the edges
+    for (int e = 0; e < 3; ++e) {
+        const double* p0 = P[e];
+        const double* p1 = P[(e + 1) % 3];
+        auto at = [&](double t) { return clearance(p0[0] + t * (p1[0] - p0[0]), p0[1] + t * (p1[1] - p0[1])); };
+        const int M = 512;
+        int bi = 0;
+        double bv = at(0.0);
+        for (int i = 1; i <= M; ++i) {
+            const double fv = at((double)i / M);
+            if (fv > bv) { bv = fv; bi = i; }
+        }
+        double lo = std::max(0.0, (bi - 1.0) / M), hi = std::min(1.0, (bi + 1.0) / M);
+        const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+        double x1 = hi - gr * (hi - lo), x2 = lo + gr * (hi - lo);
+        double f1 = at(x1), f2 = at(x2);
+        for (int it = 0; it < 80; ++it) {
+            if (f1 < f2) { lo = x1; x1 = x2; f1 = f2; x2 = lo + gr * (hi - lo); f2 = at(x2); }
+            else { hi = x2; x2 = x1; f2 = f1; x1 = hi - gr * (hi - lo); f1 = at(x1); }
+        }
+        best = std::max({best, bv, f1, f2});
+    }
+    return best > 0 ? best : 0.0;
 }
 
 }  // namespace
@@ -465,7 +499,7 @@ int lbm_throat_pce_incircle(const double* throats, int n, double sigma, double c
     }
     for (int i = 0; i < n; ++i) {
         const double r = incircle3(throats + 12 * (size_t)i);
-        pce_out[i] = r > 0 ? 2.0 * sigma * cos_theta / r : INFINITY;
+        pce_out[i] = r > 0 ? 2.0 * sigma * cos_theta / r : INFINITY;  // a closed throat is never passed
     }
     return LBM_OK;
 }

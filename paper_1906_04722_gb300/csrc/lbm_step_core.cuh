@@ -121,8 +121,12 @@ __device__ __forceinline__ void plane_density(uint32_t w, const float* st, int t
 // f^eq are shared by a pair).  The rest population is rho_s - sum_{k>=1} f*_k.
 //
 // collide_core is the general form: rho_at(k) returns (rho_w, rho_nw) at x + e_k
-// (k = 0: the cell itself), 0 where that cell is not fluid.
-template <class RhoAt, class Sink>
+// (k = 0: the cell itself), 0 where that cell is not fluid.  TAU1 = true is the
+// form for tau = 1 in both components, with omega = 1 and 1 - omega = 0 known
+// at compile time: for finite populations it gives the same bits as the
+// general form run with tau = 1 (multiplying by 1 and adding 0 times a finite
+// value are exact), with the multiplications left out.
+template <bool TAU1 = false, class RhoAt, class Sink>
 __device__ __forceinline__ void collide_core(const float (&f)[2][Q], uint32_t w, uint32_t a, const Phys& P,
                                              RhoAt&& rho_at, Sink&& sink) {
     const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
@@ -183,10 +187,11 @@ __device__ __forceinline__ void collide_core(const float (&f)[2][Q], uint32_t w,
     // common velocity u' = (j_w/tau_w + j_nw/tau_nw) / (rho_w/tau_w + rho_nw/tau_nw)
     float up[3];
     {
-        const float den = rw * P.omega[0] + (has_nw ? rn * P.omega[1] : 0.f);
+        const float om0 = TAU1 ? 1.0f : P.omega[0], om1 = TAU1 ? 1.0f : P.omega[1];
+        const float den = rw * om0 + (has_nw ? rn * om1 : 0.f);
         const float inv = den != 0.f ? 1.0f / den : 0.f;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) up[d] = (j[0][d] * P.omega[0] + (has_nw ? j[1][d] * P.omega[1] : 0.f)) * inv;
+        for (int d = 0; d < 3; ++d) up[d] = (j[0][d] * om0 + (has_nw ? j[1][d] * om1 : 0.f)) * inv;
     }
 
 #pragma unroll
@@ -198,11 +203,11 @@ __device__ __forceinline__ void collide_core(const float (&f)[2][Q], uint32_t w,
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const float F = -P.G * rs * coh[d] - P.Gads[s] * rs * ad[d] + rs * P.g[d];
-            ueq[d] = up[d] + (rs != 0.f ? P.tau[s] * F / rs : 0.f);
+            ueq[d] = up[d] + (rs != 0.f ? (TAU1 ? F : P.tau[s] * F) / rs : 0.f);
         }
         const float uu = ueq[0] * ueq[0] + ueq[1] * ueq[1] + ueq[2] * ueq[2];
-        const float om = P.omega[s];
-        const float keep = 1.0f - om;
+        const float om = TAU1 ? 1.0f : P.omega[s];
+        const float keep = TAU1 ? 0.0f : 1.0f - om;
         const float base = rs * (1.0f - 1.5f * uu);
         const float r45 = 4.5f * rs;
         const float r3 = 3.0f * rs;
@@ -213,8 +218,8 @@ __device__ __forceinline__ void collide_core(const float (&f)[2][Q], uint32_t w,
             // f^eq_k = w rho (1 + 3 eu + 4.5 eu^2 - 1.5 uu), f^eq_{k+1} with -eu
             const float sym = WK(k) * (base + r45 * eu * eu);
             const float asym = WK(k) * (r3 * eu);
-            const float v0 = keep * f[s][k] + om * (sym + asym);
-            const float v1 = keep * f[s][k + 1] + om * (sym - asym);
+            const float v0 = TAU1 ? sym + asym : keep * f[s][k] + om * (sym + asym);
+            const float v1 = TAU1 ? sym - asym : keep * f[s][k + 1] + om * (sym - asym);
             part[(k >> 1) % 3] += v0 + v1;
             sink(s, k, v0);
             sink(s, k + 1, v1);

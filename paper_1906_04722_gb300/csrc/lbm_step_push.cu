@@ -113,7 +113,7 @@ constexpr size_t push_smem_bytes() {
     return (size_t)NS * stage_bytes<BY>() + sizeof(float2) * 4 * BY * PX + sizeof(uint64_t) * NS;
 }
 
-template <int BY, int NS, int MINB>
+template <int BY, int NS, int MINB, bool TAU1>
 __global__ void __launch_bounds__(PX * BY, MINB)
     sc_step_push_kernel(const __grid_constant__ CUtensorMap tm, float2* __restrict__ fout,
                         const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
@@ -194,9 +194,20 @@ __global__ void __launch_bounds__(PX * BY, MINB)
     if (tid == 0)
         for (int p = z0 - 1; p <= z1 && p < z0 - 1 + NS; ++p) issue(p);
 
-    // geometry words of planes z0 - 1 .. z0 + 1, then one plane further per iteration
+    // geometry words of planes z0 - 1 .. z0 + 1, then one plane further per
+    // iteration; the adhesion and non-wetting bounce words of an interior cell a
+    // plane ahead of its collision
     const uint32_t w_m = word(z0 - 1);
     uint32_t w_0 = word(z0), w_1 = word(z0 + 1);
+    auto extra = [&](int p, uint32_t wp, uint32_t& ap, uint32_t& np) {
+        ap = 0u;
+        np = 0u;
+        if (!interior || p >= z1) return;
+        if (wp & BIT_ADH) ap = __ldg(adh + (size_t)p * g.nxy + col);
+        if (wp & BIT_NW_DIFF) np = __ldg(nbr_nw + (size_t)p * g.nxy + col);
+    };
+    uint32_t a_0, nwb_0;
+    extra(z0, w_0, a_0, nwb_0);
 
     bool ok = p_mbar_wait_bounded(bar + slot(z0 - 1), parity(z0 - 1));
     if (ok) publish(z0 - 1, w_m);
@@ -204,13 +215,9 @@ __global__ void __launch_bounds__(PX * BY, MINB)
     if (ok) publish(z0, w_0);
     // a failed wait here is reported by the first iteration's barrier below
     for (int z = z0; z < z1; ++z) {
-        const uint32_t w = w_0;
+        const uint32_t w = w_0, a = a_0, nwb = nwb_0;
         const uint32_t w_2 = word(z + 2);  // for the next iteration's publish
-        uint32_t a = 0u, nwb = 0u;
-        if (interior) {
-            if (w & BIT_ADH) a = __ldg(adh + (size_t)z * g.nxy + col);
-            if (w & BIT_NW_DIFF) nwb = __ldg(nbr_nw + (size_t)z * g.nxy + col);
-        }
+        extra(z + 1, w_1, a_0, nwb_0);     // for the next iteration's collision
         const bool okz = ok && p_mbar_wait_bounded(bar + slot(z + 1), parity(z + 1));
         if (okz) publish(z + 1, w_1);
         if (__syncthreads_or(!okz)) {
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
                 f[1][k] = has_nw ? v.y : 0.f;
             }
             float o[2][Q];
-            collide_core(
+            collide_core<TAU1>(
                 f, w, a, P,
                 [&](int k) { return ring[((z + EZ(k)) & 3) * NT + (row + EY(k)) * PX + (lane + EX(k))]; },
                 [&](int s, int k, float v) { o[s][k] = v; });
@@ -358,7 +365,7 @@ PushEncodeFn push_encode_fn() {
     return fn;
 }
 
-template <int BY, int NS, int MINB>
+template <int BY, int NS, int MINB, bool TAU1>
 cudaError_t configure_push() {
     static unsigned long long configured = 0;  // one bit per device: the attribute is per device
     int dev = 0;
@@ -366,7 +373,7 @@ cudaError_t configure_push() {
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured & bit)) {
-        e = cudaFuncSetAttribute(sc_step_push_kernel<BY, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sc_step_push_kernel<BY, NS, MINB, TAU1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)push_smem_bytes<BY, NS>());
         if (e != cudaSuccess) return e;
         configured |= bit;
@@ -374,23 +381,25 @@ cudaError_t configure_push() {
     return cudaSuccess;
 }
 
-template <int BY, int NS, int MINB>
+template <int BY, int NS, int MINB, bool TAU1>
 cudaError_t launch_push_shape(const CUtensorMap& tm, float2* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
                               const uint32_t* adh, const Geom& g, const Phys& p, int lz, int* err, cudaStream_t s) {
     constexpr int TY = BY - 2;
     const dim3 grid((g.nx + PXI - 1) / PXI, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
-    sc_step_push_kernel<BY, NS, MINB><<<grid, dim3(PX, BY), push_smem_bytes<BY, NS>(), s>>>(
+    sc_step_push_kernel<BY, NS, MINB, TAU1><<<grid, dim3(PX, BY), push_smem_bytes<BY, NS>(), s>>>(
         tm, fout, nbr, nbr_nw, adh, g, p, lz, err);
     return cudaGetLastError();
 }
 
+// tau = 1 in both components selects the compile-time tau = 1 collision
+bool tau_one(const Phys& p) { return p.tau[0] == 1.0f && p.tau[1] == 1.0f; }
+
 }  // namespace
 
 // Shapes of the push kernel: (rows BY, stages NS, CTAs per SM) by index.
-//   0: 8 rows, 4 stages, 1 CTA    1: 8 rows, 3 stages, 1 CTA
-//   2: 6 rows, 3 stages, 2 CTAs   3: 10 rows, 3 stages, 1 CTA
-//   4: 4 rows, 4 stages, 2 CTAs
-int push_shape_count() { return 5; }
+//   0: 8 rows, 4 stages, 1 CTA    1: 6 rows, 3 stages, 2 CTAs    2: 10 rows, 3 stages, 1 CTA
+constexpr int N_PUSH_SHAPES = 3;
+int push_shape_count() { return N_PUSH_SHAPES; }
 
 bool push_step_applicable(const Geom& g) { return !g.px && !g.py && g.nx % 2 == 0; }
 
@@ -413,13 +422,13 @@ cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtens
 }
 
 int push_shape_rows(int shape) {
-    static const int rows[5] = {8, 8, 6, 10, 4};
-    return (shape >= 0 && shape < 5) ? rows[shape] : 0;
+    static const int rows[N_PUSH_SHAPES] = {8, 6, 10};
+    return (shape >= 0 && shape < N_PUSH_SHAPES) ? rows[shape] : 0;
 }
 
 int push_shape_stages(int shape) {
-    static const int stages[5] = {4, 3, 3, 3, 4};
-    return (shape >= 0 && shape < 5) ? stages[shape] : 0;
+    static const int stages[N_PUSH_SHAPES] = {4, 3, 3};
+    return (shape >= 0 && shape < N_PUSH_SHAPES) ? stages[shape] : 0;
 }
 
 int push_default_lz(const Geom& g, int shape) {
@@ -432,19 +441,18 @@ int push_default_lz(const Geom& g, int shape) {
     long long segs = device_sm_count() / tiles;
     if (segs < 1) segs = 1;
     int lz = (int)((g.nz + segs - 1) / segs);
-    if (lz > 16) lz = 16;
+    if (lz > 32) lz = 32;
     if (lz < 4) lz = 4;
     if (lz > g.nz) lz = g.nz;
     return lz;
 }
 
 cudaError_t prepare_step_push(int shape) {
+    cudaError_t e = cudaSuccess;
     switch (shape) {
-        case 0: return configure_push<8, 4, 1>();
-        case 1: return configure_push<8, 3, 1>();
-        case 2: return configure_push<6, 3, 2>();
-        case 3: return configure_push<10, 3, 1>();
-        case 4: return configure_push<4, 4, 2>();
+        case 0: e = configure_push<8, 4, 1, false>(); if (e == cudaSuccess) e = configure_push<8, 4, 1, true>(); return e;
+        case 1: e = configure_push<6, 3, 2, false>(); if (e == cudaSuccess) e = configure_push<6, 3, 2, true>(); return e;
+        case 2: e = configure_push<10, 3, 1, false>(); if (e == cudaSuccess) e = configure_push<10, 3, 1, true>(); return e;
     }
     return cudaErrorInvalidValue;
 }
@@ -454,12 +462,17 @@ cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, c
                              int* err, cudaStream_t s) {
     if (lz < 1) return cudaErrorInvalidValue;
     float2* fo = reinterpret_cast<float2*>(fout);
+    const bool t1 = tau_one(p);
     switch (shape) {
-        case 0: return launch_push_shape<8, 4, 1>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
-        case 1: return launch_push_shape<8, 3, 1>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
-        case 2: return launch_push_shape<6, 3, 2>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
-        case 3: return launch_push_shape<10, 3, 1>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
-        case 4: return launch_push_shape<4, 4, 2>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 0:
+            return t1 ? launch_push_shape<8, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
+                      : launch_push_shape<8, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 1:
+            return t1 ? launch_push_shape<6, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
+                      : launch_push_shape<6, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 2:
+            return t1 ? launch_push_shape<10, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
+                      : launch_push_shape<10, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -217,21 +217,26 @@ def test_incircle_equilateral(lbm, d, r):
 
 
 def test_incircle_matches_search(lbm):
-    """Separated unequal spheres: the largest circle between the three sections,
-    found by search, within the search's resolution."""
+    """Separated unequal spheres, acute and obtuse triangles (where the circle
+    touching the three sections has its centre outside the triangle and the
+    widest clearance lies on an edge): the search's value."""
     from oracle import pn
     rng = np.random.default_rng(5)
-    for _ in range(6):
+    for trial in range(12):
         r = rng.uniform(9.0, 14.0, 3)
-        ang = np.array([0.0, 2.1, 4.2]) + rng.uniform(-0.2, 0.2, 3)
-        rad = r.mean() * 1.35 + rng.uniform(0.5, 3.0, 3)
-        th = np.c_[np.cos(ang) * rad, np.sin(ang) * rad, np.zeros(3), r]
-        assert lbm.lbm_throat_incircle(th)[0] == pytest.approx(pn.incircle_search(th), abs=1e-6)
+        if trial < 6:
+            ang = np.array([0.0, 2.1, 4.2]) + rng.uniform(-0.2, 0.2, 3)
+            rad = r.mean() * 1.35 + rng.uniform(0.5, 3.0, 3)
+            xy = np.c_[np.cos(ang) * rad, np.sin(ang) * rad]
+        else:  # long, flat triangles
+            xy = np.array([[0.0, 0.0], [rng.uniform(40, 60), 0.0], [rng.uniform(5, 50), rng.uniform(4, 9)]])
+        th = np.c_[xy, np.zeros(3), r]
+        assert lbm.lbm_throat_incircle(th)[0] == pytest.approx(max(pn.incircle_search(th), 0.0), abs=1e-6), trial
 
 
 def test_incircle_closed_throat(lbm):
-    """Overlapping sections leave no circle between them: -1 and an infinite
-    entry pressure."""
+    """Overlapping sections leave no clearance anywhere in the triangle: 0 and an
+    infinite entry pressure."""
     th = np.array([[0, 0, 0, 10.0], [12, 0, 0, 10.0], [6, 10, 0, 10.0]])
-    assert lbm.lbm_throat_incircle(th)[0] == -1
+    assert lbm.lbm_throat_incircle(th)[0] == 0
     assert math.isinf(lbm.lbm_throat_pce_incircle(th, 0.1, 1.0)[0])
