@@ -145,7 +145,7 @@ KERNEL_SOURCES = {
     "sc_step_push_kernel": ("lbm_step_push.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
 }
 # push kernel shapes (box rows, plane stages) -> lbm_set_push_shape index, CTAs per SM
-PUSH_SHAPES = {(8, 4): (0, 1), (6, 3): (1, 2), (10, 3): (2, 1)}
+PUSH_SHAPES = {(8, 4): (0, 1), (6, 3): (1, 2), (10, 3): (2, 1), (7, 3): (3, 2), (10, 4): (4, 1), (12, 3): (5, 1)}
 
 
 def kernel_hash(kernel_name="sc_step_kernel"):

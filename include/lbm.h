@@ -548,7 +548,9 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
 
 /* lbm_set_push_shape -- switches the domain to LBM_KERNEL_PUSH with a CTA shape:
  *   shape  0: 8 box rows (6 interior), 4 plane stages, one CTA per SM;
- *          1: 6 rows, 3 stages, two CTAs per SM; 2: 10 rows, 3 stages, one CTA.
+ *          1: 6 rows, 3 stages, two CTAs per SM; 2: 10 rows, 3 stages, one CTA;
+ *          3: 7 rows, 3 stages, two CTAs per SM; 4: 10 rows, 4 stages, one CTA;
+ *          5: 12 rows, 3 stages, one CTA.
  *          A CTA of 32 x rows threads advances 28 x (rows - 2) columns.
  *   lz     planes per CTA z segment (lz <= 0: a default for the box).
  * Results do not depend on the shape (bit for bit); with tau = 1 in both

@@ -362,7 +362,7 @@ KERNEL_TMA = 1
 KERNEL_SPLIT = 2
 KERNEL_STAGED2 = 3
 KERNEL_PUSH = 4
-PUSH_SHAPES = 3  # lbm_set_push_shape: (rows, stages) = (8, 4), (6, 3), (10, 3)
+PUSH_SHAPES = 6  # lbm_set_push_shape: (rows, stages) = (8, 4), (6, 3), (10, 3), (7, 3), (10, 4), (12, 3)
 BATCH_AUTO = 0
 BATCH_PERSISTENT = 1
 BATCH_PER_STEP = 2

@@ -788,7 +788,7 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     };
     if (fp32 && push_step_applicable(g))
         for (int sh = 0; sh < push_shape_count(); ++sh)
-            for (int lz : {8, 16, 32}) {
+            for (int lz : {16, 32, 48, 64}) {
                 StepTile t = orig;
                 t.kind = LBM_KERNEL_PUSH;
                 t.push_shape = sh;

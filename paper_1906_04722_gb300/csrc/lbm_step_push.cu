@@ -398,7 +398,9 @@ bool tau_one(const Phys& p) { return p.tau[0] == 1.0f && p.tau[1] == 1.0f; }
 
 // Shapes of the push kernel: (rows BY, stages NS, CTAs per SM) by index.
 //   0: 8 rows, 4 stages, 1 CTA    1: 6 rows, 3 stages, 2 CTAs    2: 10 rows, 3 stages, 1 CTA
-constexpr int N_PUSH_SHAPES = 3;
+//   3: 7 rows, 3 stages, 2 CTAs (at most 144 registers a thread)
+//   4: 10 rows, 4 stages, 1 CTA   5: 12 rows, 3 stages, 1 CTA
+constexpr int N_PUSH_SHAPES = 6;
 int push_shape_count() { return N_PUSH_SHAPES; }
 
 bool push_step_applicable(const Geom& g) { return !g.px && !g.py && g.nx % 2 == 0; }
@@ -422,12 +424,12 @@ cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtens
 }
 
 int push_shape_rows(int shape) {
-    static const int rows[N_PUSH_SHAPES] = {8, 6, 10};
+    static const int rows[N_PUSH_SHAPES] = {8, 6, 10, 7, 10, 12};
     return (shape >= 0 && shape < N_PUSH_SHAPES) ? rows[shape] : 0;
 }
 
 int push_shape_stages(int shape) {
-    static const int stages[N_PUSH_SHAPES] = {4, 3, 3};
+    static const int stages[N_PUSH_SHAPES] = {4, 3, 3, 3, 4, 3};
     return (shape >= 0 && shape < N_PUSH_SHAPES) ? stages[shape] : 0;
 }
 
@@ -453,6 +455,9 @@ cudaError_t prepare_step_push(int shape) {
         case 0: e = configure_push<8, 4, 1, false>(); if (e == cudaSuccess) e = configure_push<8, 4, 1, true>(); return e;
         case 1: e = configure_push<6, 3, 2, false>(); if (e == cudaSuccess) e = configure_push<6, 3, 2, true>(); return e;
         case 2: e = configure_push<10, 3, 1, false>(); if (e == cudaSuccess) e = configure_push<10, 3, 1, true>(); return e;
+        case 3: e = configure_push<7, 3, 2, false>(); if (e == cudaSuccess) e = configure_push<7, 3, 2, true>(); return e;
+        case 4: e = configure_push<10, 4, 1, false>(); if (e == cudaSuccess) e = configure_push<10, 4, 1, true>(); return e;
+        case 5: e = configure_push<12, 3, 1, false>(); if (e == cudaSuccess) e = configure_push<12, 3, 1, true>(); return e;
     }
     return cudaErrorInvalidValue;
 }
@@ -473,6 +478,15 @@ cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, c
         case 2:
             return t1 ? launch_push_shape<10, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
                       : launch_push_shape<10, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 3:
+            return t1 ? launch_push_shape<7, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
+                      : launch_push_shape<7, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 4:
+            return t1 ? launch_push_shape<10, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
+                      : launch_push_shape<10, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+        case 5:
+            return t1 ? launch_push_shape<12, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
+                      : launch_push_shape<12, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
     }
     return cudaErrorInvalidValue;
 }

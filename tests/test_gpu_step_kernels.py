@@ -290,7 +290,7 @@ def _push_run(lbm, flags, rho0, steps, shape, lz):
     return dom
 
 
-@pytest.mark.parametrize("shape,lz", [(0, 13), (1, 7), (1, 45), (2, 16), (0, 5)])
+@pytest.mark.parametrize("shape,lz", [(0, 13), (1, 7), (1, 45), (2, 16), (3, 11), (4, 9), (5, 20), (0, 5)])
 @pytest.mark.parametrize("periodic_z", [0, 1])
 def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, periodic_z):
     """The push kernel reads each cell's own populations and streams at the
