@@ -5,7 +5,8 @@
 * lbm_run_drainage against the oracle's ladder (Sec. 2.2.2) on a throat that
   invades: S_w and p_c per increment, the invasion increment and p_c^e.
 * lbm_run_throat_batch: throat i of a batch equals throat i run alone through
-  lbm_create_domain_mask + lbm_run_drainage.
+  lbm_create_domain_mask + lbm_run_drainage, and the default cell-list form
+  matches the oracle's ladder on the oracle's own throat boxes.
 """
 import math
 
@@ -85,14 +86,25 @@ def test_drainage_matches_oracle(lbm, orc):
     ref = orc.drainage(cfg, mask, f, ladder, n_steps, probe)
     assert ref["invaded_at"] >= 0, "the test throat must invade"
     assert gpu["invaded_at"] == ref["invaded_at"]
-    pc_scale = max(abs(r["p_c"]) for r in ref["rows"] if r["p_c"] == r["p_c"])
     for i, (g, o) in enumerate(zip(gpu["rows"], ref["rows"])):
         if i > ref["invaded_at"]:
             break
         assert abs(g["S_w"] - o["S_w"]) <= 5e-3 * o["S_w"], (i, g["S_w"], o["S_w"])
-        if o["p_c"] == o["p_c"]:
-            assert abs(g["p_c"] - o["p_c"]) <= 5e-3 * pc_scale, (i, g["p_c"], o["p_c"])
+        _pc_close(g["p_c"], o["p_c"], i)
     assert abs(gpu["p_ce"] - ref["p_ce"]) <= 5e-3 * abs(ref["p_ce"])
+
+
+# p_c (bulk phases) within 0.5 % of its own value, with an absolute floor where
+# it comes near zero: an FP32 density held to 1e-5 of the oracle's moves each
+# Eq. 5 pressure (about 0.7 here) by up to 7e-6, their difference by 1.4e-5
+PC_FLOOR = 2e-5
+
+
+def _pc_close(g, o, where):
+    if o != o:  # no bulk phase on the oracle's side: none on the GPU's either
+        assert g != g, (where, g, o)
+        return
+    assert abs(g - o) <= 5e-3 * abs(o) + PC_FLOOR, (where, g, o)
 
 
 def test_batch_equals_single_throats(lbm, orc):
@@ -179,3 +191,36 @@ def _rows_equal(ra, rowsa, rb, rowsb, ladders):
             for k in ("S_w", "phi_probe", "p_c_res", "p_c", "p_w", "p_nw"):
                 assert a[k] == b[k] or (a[k] != a[k] and b[k] != b[k]), (t, i, k, a[k], b[k])
             assert a["n_interface"] == b["n_interface"]
+
+
+def test_batch_matches_oracle(lbm, orc):
+    """Delaunay throats of a seeded packing through lbm_run_throat_batch in its
+    default form (the cell list: compact storage, push streaming) against the
+    oracle's ladder on the oracle's voxelisation of each throat box and its
+    probe: invasion increment, S_w and p_c per increment, and p_c^e (Sec. 2.2.2)."""
+    spheres = W.sample_spheres(128, seed=4)
+    cand = W.delaunay_throats(spheres, 40, seed=21)
+    size = [np.prod(orc.throat_frame(t)[0]) for t in cand]
+    throats = cand[np.argsort(size, kind="stable")[:4]]  # the four smallest boxes keep the oracle quick
+    ladder = [2.0 + 0.04 * i for i in range(10)]
+    n_steps = 60
+    res, rows = lbm.lbm_run_throat_batch(throats, _params(lbm), ladder, n_steps, W.RHO_MAJOR)
+    invaded = 0
+    for t, sph in enumerate(throats):
+        mask = orc.voxelise_throat(sph)
+        probe = orc.throat_probe(sph, mask)
+        assert res[t]["probe"] == probe
+        cfg = orc.Config(shape=mask.shape, tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS,
+                         rho_out=(W.RHO_MAJOR, W.RHO_MINOR))
+        f = orc.init(cfg, mask, W.initial_densities(mask.shape))
+        ref = orc.drainage(cfg, mask, f, ladder, n_steps, probe)
+        assert res[t]["invaded_at"] == ref["invaded_at"], t
+        for i, (g, o) in enumerate(zip(rows[t], ref["rows"])):
+            assert abs(g["S_w"] - o["S_w"]) <= 5e-3 * o["S_w"] + 1e-12, (t, i, g["S_w"], o["S_w"])
+            _pc_close(g["p_c"], o["p_c"], (t, i))
+        if ref["invaded_at"] >= 0:
+            invaded += 1
+            assert abs(res[t]["p_ce"] - ref["p_ce"]) <= 5e-3 * abs(ref["p_ce"]) + PC_FLOOR, t
+        else:
+            assert math.isinf(res[t]["p_ce"])
+    assert invaded >= 2, "the ladder must invade most of the test throats"

@@ -94,3 +94,46 @@ def test_16bit_mass_conservation(lbm, precision):
     m1 = dom.measure()["mass"]
     for s in range(2):
         assert abs(m1[s] - m0[s]) <= 1e-4 * m0[s], (s, m0[s], m1[s])
+
+
+@pytest.mark.parametrize("precision,bound", [(1, 2e-3), (2, 2e-2)])
+def test_16bit_sample192_sampled_cells(lbm, orc, precision, bound):
+    """The 192^3 drainage sample with 16-bit storage in the launch shape the
+    autotuner picks for it (32 x 8 threads, 32-plane z segments): two steps from
+    a seeded noisy state, sampled cells against the oracle run on crops that
+    hold their whole dependency cone (2 cells per step)."""
+    shape = (192, 192, 192)
+    spheres = W.sample192_spheres()
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR, rho_minor=W.RHO_MINOR,
+                             reservoirs=True, membrane_layers=3, precision=precision)
+    dom = lbm.Domain(params, spheres, (192, 192, 192))
+    dom.set_tile(8, 32, 2)
+    assert dom.tile() == (8, 32, 2)
+    mask = orc.voxelise(shape, spheres, reservoirs=True, membrane_layers=3)
+    assert np.array_equal(dom.mask(), mask)
+    rho0 = W.initial_densities(shape, noise=2e-2, seed=8)
+    dom.set_densities(rho0)
+    K = 2
+    dom.step(K)
+    rho_g = dom.density()
+    rng = np.random.default_rng(14)
+    R = 2 * K + 2
+    fluid = np.argwhere(mask == 0)
+    picks = list(fluid[rng.choice(len(fluid), 24, replace=False)]) + [(0, 95, 1), (191, 100, 190), (188, 50, 60)]
+    worst = 0.0
+    for z, y, x in picks:
+        if mask[z, y, x] & orc.M_SOLID:
+            continue
+        zs, ys, xs = [slice(max(0, v - R), min(192, v + R + 1)) for v in (z, y, x)]
+        sub = mask[zs, ys, xs].copy()
+        cfg = orc.Config(shape=sub.shape, tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS,
+                         rho_in=(W.RHO_MINOR, W.RHO_MAJOR), rho_out=(W.RHO_MAJOR, W.RHO_MINOR))
+        f = orc.init(cfg, sub, np.ascontiguousarray(rho0[:, zs, ys, xs]))
+        orc.step(cfg, sub, f, K)
+        ro = orc.density(cfg, sub, f)[:, z - zs.start, y - ys.start, x - xs.start]
+        for s in range(2):
+            if s == 1 and mask[z, y, x] & orc.M_MEMBRANE:
+                continue
+            worst = max(worst, abs(rho_g[s, z, y, x] - ro[s]) / max(abs(ro[s]), W.RHO_MINOR))
+    print(json.dumps({"precision": {1: "fp16", 2: "bf16"}[precision], "sample192_max_rel_density_err_2_steps": worst}))
+    assert worst <= bound, worst

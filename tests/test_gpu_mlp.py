@@ -2,13 +2,18 @@
 
 Forward outputs, loss gradients and one Adam step of the tensor-core kernels
 (BF16 or FP16 operands rounded from FP32 masters, FP32 accumulation) are compared
-with oracle/mlp.py on the same parameters.  Bars, norm-wise relative: every GEMM
-rounds its operands once (unit roundoff u = 2^-11 for FP16, 2^-8 for BF16); the
-backward dot products over 256 hidden units cancel (terms of both signs), which
-amplifies that rounding by about sqrt(256) = 16 per layer, and the first layer's
-gradient passes through four of them: measured 1.1e-2 (FP16) and 3.1e-2 (BF16)
-there.  Bars 2e-2 (FP16) and 6e-2 (BF16); the outputs of the forward pass are held
-to 2e-3 / 1.5e-2.  Training must drive the loss of a smooth target down.
+with oracle/mlp.py on the same parameters, element by element, each element
+against its own bound.  The bounds follow the arithmetic: a GEMM rounds both of
+its operands once (unit roundoff u = 2^-11 for FP16, 2^-8 for BF16) and adds in
+FP32 (2^-24 per addition), so an output element is off by at most
+(2u + (n + 2) 2^-24) times the sum of the absolute values of its products, plus
+what its inputs were off by carried through |W|.  Carried layer by layer (ReLU
+does not amplify), and through the backward pass with the same rule, this bounds
+every output and every gradient element; where a hidden unit's pre-activation
+lies within its own bound of zero the two sides may disagree on its ReLU
+derivative, and the full size of that unit's term is added to the bound.  The
+norm-wise errors are printed as a report.  Training must drive the loss of a
+smooth target down.
 """
 import numpy as np
 import pytest
@@ -32,8 +37,84 @@ def _nrel(a, b):
     return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / max(1e-30, np.linalg.norm(b)))
 
 
+U32 = 2.0 ** -24
+
+
+def _elementwise_bounds(params, X, T, u):
+    """Per-element bounds on |GPU - oracle| of the outputs and of every (dW, db),
+    for GEMMs that round their operands to a 16-bit type of unit roundoff u and
+    accumulate in FP32 (first order in u; see the module docstring)."""
+    acts, zs, ez = [np.asarray(X, float)], [], []
+    eh = np.zeros_like(acts[0])
+    L = len(params)
+    for i, (W, b) in enumerate(params):
+        h = acts[-1]
+        n = W.shape[1]
+        z = h @ W.T + b
+        mag = np.abs(h) @ np.abs(W).T + np.abs(b)
+        e = eh @ np.abs(W).T * (1 + u) ** 2 + (2.01 * u + (n + 2) * U32) * mag
+        zs.append(z)
+        ez.append(e)
+        eh = e
+        acts.append(np.maximum(z, 0.0) if i < L - 1 else z)
+    y, ey = acts[-1], ez[-1]
+    N = y.size
+    d = 2.0 * (y - T) / N
+    ed = 2.0 * (ey + 4 * U32 * np.abs(y - T)) / N
+    bounds = [None] * L
+    for i in range(L - 1, -1, -1):
+        W, _ = params[i]
+        h = acts[i]
+        ehi = ez[i - 1] if i > 0 else np.zeros_like(h)
+        ns = h.shape[0]
+        gam = 2.01 * u + (ns + 2) * U32
+        bW = np.abs(ed).T @ np.abs(h) * (1 + u) ** 2 + np.abs(d).T @ ehi * (1 + u) ** 2 + gam * (np.abs(d).T @ np.abs(h))
+        bb = ed.sum(axis=0) + (ns + 2) * U32 * np.abs(d).sum(axis=0)
+        bounds[i] = (bW, bb)
+        if i > 0:
+            m = W.shape[0]
+            full = np.abs(d) @ np.abs(W)
+            back = np.abs(ed) @ np.abs(W) * (1 + u) ** 2 + (2.01 * u + (m + 2) * U32) * full
+            zprev = zs[i - 1]
+            certain = np.abs(zprev) > ez[i - 1]
+            alive = zprev > 0
+            ed = np.where(certain, np.where(alive, back, 0.0), back + full)
+            d = (d @ W) * alive
+    return y, ey, bounds
+
+
+@pytest.mark.parametrize("half", [1, 0])
+def test_forward_and_gradients_elementwise(lbm, half):
+    rng = np.random.default_rng(5)
+    sur = lbm.Surrogate(7, 17, n_hidden=256, n_layers=4, n_members=2, half=half, seed=3)
+    layers = omlp.init_params(sur.sizes, seed=9)
+    for W, b in layers:
+        b[:] = rng.standard_normal(b.shape) * 0.1
+    sur.set_params(1, sur.flatten(layers))
+    ref = [[W.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)] for W, b in layers]
+    X = rng.standard_normal((300, 7)).astype(np.float32).astype(np.float64)
+    T = rng.standard_normal((300, 17)).astype(np.float32).astype(np.float64)
+    u = 2.0 ** -11 if half else 2.0 ** -8
+    y_ref, ey, bounds = _elementwise_bounds(ref, X, T, u)
+    def ratio(err, bound):  # largest err / bound (an element whose bound is 0 must be exact)
+        assert np.all(err <= bound)
+        pos = bound > 0
+        return float((err[pos] / bound[pos]).max()) if pos.any() else 0.0
+
+    y = sur.forward(1, X)
+    worst = [ratio(np.abs(y - y_ref), ey)]
+    g, _ = sur.gradients(1, X, T)
+    g_ref = omlp.gradients(ref, X, T)
+    for (gW, gb), (rW, rb), (bW, bb) in zip(sur.layers(g), g_ref, bounds):
+        worst.append(max(ratio(np.abs(gW - rW), bW), ratio(np.abs(gb - rb), bb)))
+    print("half" if half else "bf16", "largest error / element bound: forward then layers", worst)
+
+
 @pytest.mark.parametrize("half,tol_fwd,tol", [(1, 2e-3, 2e-2), (0, 1.5e-2, 6e-2)])
 def test_forward_and_gradients_match_oracle(lbm, half, tol_fwd, tol):
+    """Norm-wise report: the backward dot products over 256 hidden units cancel,
+    which amplifies operand rounding by about sqrt(256) per layer; measured
+    1.1e-2 (FP16) and 3.1e-2 (BF16) on the first layer's gradient."""
     rng = np.random.default_rng(5)
     sur = lbm.Surrogate(7, 17, n_hidden=256, n_layers=4, n_members=2, half=half, seed=3)
     layers = omlp.init_params(sur.sizes, seed=9)
