@@ -266,7 +266,7 @@ def cpu_baseline():
             "sample": oc.sample_text(steps)}
 
 
-def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
+def throat_bench(lbm, W, n_steps, rank, world, sync, tmax, gather=None):
     """Throats per second: plain loop vs batched vs surrogate with fallback.
 
     The ladder is 32 increments of the nw reservoir density (2.0 + 0.02 i) with
@@ -323,19 +323,35 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax):
         out["other_forms"][name] = world * n / tmax(time.perf_counter() - t0)
         agree &= bool(np.array_equal(truth, np.array([r["p_ce"] for r in res_f]), equal_nan=True))
     out["forms_agree"] = agree
-    # plain per-throat loop on every 32nd throat
-    sub = tri[::32]
+    if world > 1 and gather is not None:
+        # one throat list over all ranks: LPT shards on the non-solid cells of
+        # each box, results gathered back into the list's order
+        shared = W.delaunay_throats(W.sample_spheres(192, seed=3), 1024, seed=3)
+        sync()
+        t0 = time.perf_counter()
+        res_s, _ = lbm.run_throat_batch_sharded(shared, params, ladder, n_steps, W.RHO_MAJOR, rank, world, gather)
+        sync()
+        out["sharded_one_list"] = {"throats": len(shared), "ranks": world,
+                                   "throats_per_s": len(shared) / tmax(time.perf_counter() - t0),
+                                   "all_gathered": all(r is not None for r in res_s)}
+    # plain per-throat loop on every 16th throat
+    sub = tri[::16]
+    per = []
     sync()
     t0 = time.perf_counter()
     for th in sub:
+        t1 = time.perf_counter()
         mask, probe = lbm.lbm_throat_geometry(th)
         d = lbm.Domain(params, mask=mask)
         d.drainage(ladder, n_steps, W.RHO_MAJOR, probe)
         d.close()
+        per.append(time.perf_counter() - t1)
     sync()
     t_plain = tmax(time.perf_counter() - t0)
     out["plain"] = world * len(sub) / t_plain
-    out["plain_sample"] = f"{len(sub)} throats (every 32nd)"
+    out["plain_sample"] = f"{len(sub)} throats (every 16th)"
+    out["plain_seconds_per_throat"] = {"p10": float(np.percentile(per, 10)), "median": float(np.median(per)),
+                                       "p90": float(np.percentile(per, 90)), "max": float(np.max(per))}
     out["batched_vs_plain"] = out["batched"] / out["plain"]
     ok = np.isfinite(truth)
     for tol in (0.02, 0.05):
@@ -506,7 +522,13 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         barrier()
 
-    throats = None if args.no_throats else throat_bench(lbm, W, args.throat_steps, rank, world, sync, tmax)
+    def gather(obj):
+        got = [None] * world
+        dist.all_gather_object(got, obj)
+        return got
+
+    throats = None if args.no_throats else throat_bench(lbm, W, args.throat_steps, rank, world, sync, tmax,
+                                                        gather if dist is not None else None)
     out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "f16 deviations, f32 math", 2: "bf16 deviations, f32 math"}[args.precision],

@@ -311,6 +311,15 @@ int lbm_pn_drainage(int n_pores, const double* pore_volume, int n_throats, const
                     const double* throat_pce, int n_levels, const double* p_c, double* S_w,
                     int* pore_invaded_at, int* pore_trapped_at);
 
+/* lbm_partition_lpt -- splits n work items (cost[i] >= 0, e.g. the non-solid
+ * cells of a throat box) over `parts` ranks, longest processing time first:
+ * items by decreasing cost (ties: lower index), each to the part with the least
+ * load so far (ties: lower part).  part_out: n part indices; load_out (may be
+ * NULL): the parts' total costs.  Used to shard a throat list over GPUs
+ * (Sec. 4: throats are independent, so the only exchange is the final gather
+ * of their results). */
+int lbm_partition_lpt(const double* cost, int n, int parts, int* part_out, double* load_out);
+
 /* lbm_throat_incircle -- for n throats (n x 3 x (cx, cy, cz, r)), the radius of
  * the throat's inscribed circle: in the plane of the three centres, the largest
  * clearance min_i(|p - c_i| - r_i) over points p of their triangle (the circle

@@ -145,6 +145,7 @@ SIGNATURES = {
     "lbm_throat_incircle": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
     "lbm_throat_pce_incircle": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP]),
     "lbm_contact_angle_estimate": (ctypes.c_int, [ctypes.c_double] * 5 + [_DP]),
+    "lbm_partition_lpt": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int, _IP, _DP]),
     "lbm_pressure_ladder": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [_DP]),
     "lbm_throat_surrogate_inputs": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _FP, _DP]),
     "lbm_throat_surrogate_create": (ctypes.c_int, [ctypes.POINTER(lbm_throat_surrogate_config), _VP,
@@ -472,6 +473,40 @@ def lbm_pn_drainage(pore_volume, throat_pores, throat_pce, p_c_levels):
                                   sw.ctypes.data_as(_DP), inv.ctypes.data_as(_IP), trap.ctypes.data_as(_IP)),
            "lbm_pn_drainage")
     return sw, inv, trap
+
+
+def lbm_partition_lpt(cost, parts: int):
+    """(part of each item, load of each part): longest-processing-time-first split."""
+    c = np.ascontiguousarray(np.asarray(cost, dtype=np.float64).reshape(-1))
+    part = np.empty(c.shape[0], dtype=np.int32)
+    lp = np.empty(int(parts))
+    _check(load().lbm_partition_lpt(c.ctypes.data_as(_DP), c.shape[0], int(parts), part.ctypes.data_as(_IP),
+                                    lp.ctypes.data_as(_DP)), "lbm_partition_lpt")
+    return part, lp
+
+
+def run_throat_batch_sharded(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, rank: int,
+                             world: int, gather, run=None):
+    """The throats of one list split over `world` ranks (lbm_partition_lpt on
+    the non-solid cells of each box), this rank's share run with
+    lbm_run_throat_batch (or `run`, same signature), and every rank's results
+    gathered back into the list's order.  gather(obj) -> list of every rank's obj
+    (torch.distributed.all_gather_object, for one).  Returns (results, rows)."""
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
+    F = lbm_throat_lattice_features(th)
+    cost = F[:, 0] * F[:, 1] * F[:, 2] * F[:, 3]
+    part, _ = lbm_partition_lpt(cost, world)
+    mine = np.flatnonzero(part == rank)
+    lad = np.asarray(rho_in_nw, dtype=np.float64)
+    my_lad = lad[mine] if lad.ndim == 2 else lad
+    res, rows = ([], []) if len(mine) == 0 else (run or lbm_run_throat_batch)(th[mine], params, my_lad, n_steps,
+                                                                                rho_out_w)
+    pieces = gather((mine.tolist(), res, rows))
+    out_res, out_rows = [None] * len(th), [None] * len(th)
+    for idx, r, w in pieces:
+        for j, t in enumerate(idx):
+            out_res[t], out_rows[t] = r[j], w[j]
+    return out_res, out_rows
 
 
 def lbm_throat_incircle(throats) -> np.ndarray:

@@ -285,53 +285,57 @@ __global__ void __launch_bounds__(CELL_THREADS)
 }
 
 // Rest equilibrium at the start (as throat_init_kernel: wetting fluid
-// everywhere, the non-wetting fluid on the inlet layer), stored after streaming.
+// everywhere, the non-wetting fluid on the inlet layer), stored after streaming
+// as pairs: fc[k cp + i] = (f_k^w, f_k^nw) of item i.
 __global__ void __launch_bounds__(CELL_THREADS)
-    cell_init_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, float* __restrict__ fc, float rho_major,
+    cell_init_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, float2* __restrict__ fc, float rho_major,
                      float rho_minor) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i >= n_items) return;
     const uint32_t cls = (wc[i] >> CLS_SHIFT) & CLS_MASK;
     const bool inlet = cls == CLS_INLET;
+    float v[2][Q];
     for (int s = 0; s < 2; ++s) {
         const bool fl = !(s == 1 && cls == CLS_MEMBRANE);
         const float r = !fl ? 0.f : s == 0 ? (inlet ? rho_minor : rho_major) : (inlet ? rho_major : rho_minor);
         float sum = 0.f;
         for (int k = 1; k < Q; ++k) sum += WK(k) * r;
-        float* fs = fc + (size_t)s * Q * cp + i;
-        fs[0] = fl ? r - sum : 0.f;
-        for (int k = 1; k < Q; ++k) fs[(size_t)k * cp] = fl ? WK(k) * r : 0.f;
+        v[s][0] = fl ? r - sum : 0.f;
+        for (int k = 1; k < Q; ++k) v[s][k] = fl ? WK(k) * r : 0.f;
     }
+    for (int k = 0; k < Q; ++k) fc[(size_t)k * cp + i] = make_float2(v[0][k], v[1][k]);
 }
 
 // (rho_w, rho_nw) of every item (Eq. 2), in four interleaved partial sums as the
 // staged kernel sums its density ring; 0 for the non-wetting fluid on a membrane.
 __global__ void __launch_bounds__(CELL_THREADS)
-    cell_density_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, const float* __restrict__ fc,
+    cell_density_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, const float2* __restrict__ fc,
                         float2* __restrict__ rho2) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i >= n_items) return;
     const uint32_t cls = (__ldg(wc + i) >> CLS_SHIFT) & CLS_MASK;
-    float r[2] = {0.f, 0.f};
+    float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        if (s == 1 && cls == CLS_MEMBRANE) break;
-        float a[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < Q; ++k) a[k & 3] += __ldg(fc + (size_t)(s * Q + k) * cp + i);
-        r[s] = (a[0] + a[1]) + (a[2] + a[3]);
+    for (int k = 0; k < Q; ++k) {
+        const float2 v = __ldg(fc + (size_t)k * cp + i);
+        a[k & 3] += v.x;
+        b[k & 3] += v.y;
     }
-    rho2[i] = make_float2(r[0], r[1]);
+    const float rn = cls == CLS_MEMBRANE ? 0.f : (b[0] + b[1]) + (b[2] + b[3]);
+    rho2[i] = make_float2((a[0] + a[1]) + (a[2] + a[3]), rn);
 }
 
-// One time step of every item: own populations, neighbour densities of the
+// One time step of every item: own population pairs, neighbour densities of the
 // density pass (0 where x + e_k is not fluid for the wetting component, i.e.
-// grain or beyond the box), collide_core, push.  The bounce-back choice selects
-// an address rather than a branch: one load or store instruction per value for
-// the whole warp, whichever way each lane goes.
+// grain or beyond the box), collide_core (the compile-time tau = 1 form when
+// TAU1), push: one 8-byte store per direction where both components stream
+// alike, separate stores where a membrane makes them differ.  The bounce-back
+// choice selects an address rather than a branch: one store instruction per
+// value for the whole warp, whichever way each lane goes.
+template <bool TAU1>
 __global__ void __launch_bounds__(CELL_THREADS, 2)
-    cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float* __restrict__ fin,
-                     float* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
+    cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float2* __restrict__ fin,
+                     float2* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
                      const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const int* __restrict__ nbp,
                      Phys P, const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
@@ -341,33 +345,46 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
     const bool has_nw = cls != CLS_MEMBRANE;
     float f[2][Q];
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int k = 0; k < Q; ++k) f[s][k] = (s == 0 || has_nw) ? __ldg(fin + (size_t)(s * Q + k) * cp + i) : 0.f;
+    for (int k = 0; k < Q; ++k) {
+        const float2 v = __ldg(fin + (size_t)k * cp + i);
+        f[0][k] = v.x;
+        f[1][k] = has_nw ? v.y : 0.f;
+    }
     const uint32_t wn = has_nw ? __ldg(wnc + i) : 0u;
     const uint32_t a = (w & BIT_ADH) ? __ldg(adhc + i) : 0u;
-    auto dest = [&](int k) { return k == 1 ? i + 1 : k == 2 ? i - 1 : __ldg(nbp + (size_t)(k - 3) * cp + i); };
+    int dst[Q];  // item of x + e_k
+#pragma unroll
+    for (int k = 1; k < Q; ++k) dst[k] = k == 1 ? i + 1 : k == 2 ? i - 1 : __ldg(nbp + (size_t)(k - 3) * cp + i);
     auto rho_at = [&](int k) {
         if (k == 0) return __ldg(rho2 + i);
         const bool wall = (w >> OPP(k)) & 1u;
-        const int j = dest(k);
-        const float2 v = __ldg(rho2 + (wall ? i : j));
+        const float2 v = __ldg(rho2 + (wall ? i : dst[k]));
         return wall ? make_float2(0.f, 0.f) : v;
     };
     Phys Pt = P;
     Pt.bc = bc_all + 4 * ((size_t)__ldg(&items[i].x) * ladder_stride + *incr_now);
-    collide_core(f, w, a, Pt, rho_at, [&](int s, int k, float v) {
-        if (s == 1 && !has_nw) return;
-        float* fs = fout + (size_t)s * Q * cp;
-        if (k == 0) {
-            fs[i] = v;
-            return;
+    float o[2][Q];
+    collide_core<TAU1>(f, w, a, Pt, rho_at, [&](int s, int k, float v) { o[s][k] = v; });
+    auto addr = [&](int k, uint32_t bits) {
+        return ((bits >> OPP(k)) & 1u) ? (size_t)OPP(k) * cp + i : (size_t)k * cp + dst[k];
+    };
+    float* fo = reinterpret_cast<float*>(fout);
+    if (!has_nw) {
+        fo[2 * (size_t)i] = o[0][0];
+#pragma unroll
+        for (int k = 1; k < Q; ++k) fo[2 * addr(k, w)] = o[0][k];
+    } else if (w & BIT_NW_DIFF) {
+        fout[i] = make_float2(o[0][0], o[1][0]);
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            fo[2 * addr(k, w)] = o[0][k];
+            fo[2 * addr(k, wn) + 1] = o[1][k];
         }
-        const uint32_t bits = s == 0 ? w : wn;
-        const bool wall = (bits >> OPP(k)) & 1u;
-        const int j = dest(k);
-        fs[wall ? (size_t)OPP(k) * cp + i : (size_t)k * cp + j] = v;
-    });
+    } else {
+        fout[i] = make_float2(o[0][0], o[1][0]);
+#pragma unroll
+        for (int k = 1; k < Q; ++k) fout[addr(k, w)] = make_float2(o[0][k], o[1][k]);
+    }
 }
 
 // Measurements of throat blockIdx.x from the compact populations, walking its
@@ -375,7 +392,7 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
 // the last CTA to finish advances the increment index.
 __global__ void __launch_bounds__(BATCH_THREADS)
     cell_measure_kernel(const ThroatRec* __restrict__ recs, int n, const int* __restrict__ box_to_item, int cp,
-                        const float* __restrict__ fc, const uint32_t* __restrict__ wc, double G,
+                        const float2* __restrict__ fc, const uint32_t* __restrict__ wc, double G,
                         const double* __restrict__ rin_all, int ladder_stride, lbm_increment* __restrict__ rows,
                         int n_incr, int* incr_now, int* done) {
     __shared__ double red[32];
@@ -391,9 +408,9 @@ __global__ void __launch_bounds__(BATCH_THREADS)
                       if (j < 0) return (uint32_t)CLS_SOLID << CLS_SHIFT;
                       const uint32_t w = wc[j];
                       const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
-                      for (int k = 0; k < Q; ++k) rw += fc[(size_t)k * cp + j];
+                      for (int k = 0; k < Q; ++k) rw += fc[(size_t)k * cp + j].x;
                       if (cls != CLS_MEMBRANE)
-                          for (int k = 0; k < Q; ++k) rn += fc[(size_t)(Q + k) * cp + j];
+                          for (int k = 0; k < Q; ++k) rn += fc[(size_t)k * cp + j].y;
                       return w;
                   });
     __syncthreads();
@@ -773,7 +790,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                 cell_gather_kernel<<<blocks, CELL_THREADS, 0, stream>>>(d_recs, d_cells, n_cells, cp, d_nbr, d_nbr_nw,
                                                                        d_adh, d_map, d_wc, d_wnc, d_adhc, d_nbp);
                 BATCH_CUDA(cudaGetLastError());
-                cell_init_kernel<<<blocks, CELL_THREADS, 0, stream>>>(d_wc, n_cells, cp, a0,
+                cell_init_kernel<<<blocks, CELL_THREADS, 0, stream>>>(d_wc, n_cells, cp, reinterpret_cast<float2*>(a0),
                                                                      (float)params->rho_major,
                                                                      (float)params->rho_minor);
                 BATCH_CUDA(cudaGetLastError());
@@ -785,18 +802,26 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                 cudaError_t cerr = cudaSuccess;
                 for (int st = 0; st < sched->n_steps && cerr == cudaSuccess && n_cells; ++st) {
                     const int c = (gi + st) & 1;
-                    const float* fin = c ? a1 : a0;
+                    const float2* fin = reinterpret_cast<const float2*>(c ? a1 : a0);
+                    float2* fout = reinterpret_cast<float2*>(c ? a0 : a1);
                     cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
                     cerr = cudaGetLastError();
                     if (cerr != cudaSuccess) break;
-                    cell_step_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_cells, n_cells, cp, fin, c ? a0 : a1, d_rho2,
-                                                                       d_wc, d_wnc, d_adhc, d_nbp, P, d_bc,
-                                                                       sched->per_throat ? I : 0, d_incr);
+                    if (P.tau[0] == 1.0f && P.tau[1] == 1.0f)
+                        cell_step_kernel<true><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, d_nbp, P, d_bc,
+                            sched->per_throat ? I : 0, d_incr);
+                    else
+                        cell_step_kernel<false><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, d_nbp, P, d_bc,
+                            sched->per_throat ? I : 0, d_incr);
                     cerr = cudaGetLastError();
                 }
                 if (cerr == cudaSuccess) {
                     const int c = (gi + sched->n_steps) & 1;
-                    cell_measure_kernel<<<n, dim3(32, BATCH_BY), 0, cap>>>(d_recs, n, d_map, cp, c ? a1 : a0, d_wc,
+                    cell_measure_kernel<<<n, dim3(32, BATCH_BY), 0, cap>>>(d_recs, n, d_map, cp,
+                                                                           reinterpret_cast<const float2*>(c ? a1 : a0),
+                                                                           d_wc,
                                                                            params->G, d_rin, sched->per_throat ? I : 0,
                                                                            d_rows, I, d_incr, d_incr + 1);
                     cerr = cudaGetLastError();

@@ -31,6 +31,7 @@
 #include <limits>
 #include <map>
 #include <new>
+#include <numeric>
 #include <queue>
 #include <string>
 #include <vector>
@@ -624,6 +625,40 @@ int lbm_pn_build(const double* spheres, int n_spheres, const int* tets, int n_te
             throat_pores[2 * i + 1] = th[i][1];
             for (int j = 0; j < 3; ++j) throat_spheres[3 * i + j] = th[i][2 + j];
         }
+        return LBM_OK;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    }
+}
+
+int lbm_partition_lpt(const double* cost, int n, int parts, int* part_out, double* load_out) {
+    if (!cost || !part_out || n < 0 || parts < 1) {
+        set_error("lbm_partition_lpt: NULL argument, n < 0 or parts < 1");
+        return LBM_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(cost[i]) || cost[i] < 0) { set_error("lbm_partition_lpt: costs must be finite and >= 0"); return LBM_ERR_ARG; }
+    try {
+        // longest processing time first: items by decreasing cost (ties: lower
+        // index), each to the part with the least load so far (ties: lower part)
+        std::vector<int> order((size_t)n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        using P = std::pair<double, int>;
+        std::priority_queue<P, std::vector<P>, std::greater<P>> heap;
+        for (int q = 0; q < parts; ++q) heap.push({0.0, q});
+        std::vector<double> load((size_t)parts, 0.0);
+        for (int i : order) {
+            P top = heap.top();
+            heap.pop();
+            part_out[i] = top.second;
+            top.first += cost[i];
+            load[(size_t)top.second] = top.first;
+            heap.push(top);
+        }
+        if (load_out)
+            for (int q = 0; q < parts; ++q) load_out[q] = load[(size_t)q];
         return LBM_OK;
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed");
