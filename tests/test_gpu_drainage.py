@@ -199,11 +199,12 @@ def test_batch_matches_oracle(lbm, orc):
     oracle's ladder on the oracle's voxelisation of each throat box and its
     probe: invasion increment, S_w and p_c per increment, and p_c^e (Sec. 2.2.2)."""
     spheres = W.sample_spheres(128, seed=4)
-    cand = W.delaunay_throats(spheres, 40, seed=21)
-    size = [np.prod(orc.throat_frame(t)[0]) for t in cand]
-    throats = cand[np.argsort(size, kind="stable")[:4]]  # the four smallest boxes keep the oracle quick
-    ladder = [2.0 + 0.04 * i for i in range(10)]
-    n_steps = 60
+    cand = W.delaunay_throats(spheres, 60, seed=21)
+    # five boxes of 15 k - 20 k cells (the oracle's ladder takes about 2 s each)
+    # with wide constrictions: four invade within the ladder, one does not
+    throats = cand[[49, 45, 47, 1, 31]]
+    ladder = [2.0 + 0.06 * i for i in range(12)]
+    n_steps = 100
     res, rows = lbm.lbm_run_throat_batch(throats, _params(lbm), ladder, n_steps, W.RHO_MAJOR)
     invaded = 0
     for t, sph in enumerate(throats):
@@ -223,4 +224,4 @@ def test_batch_matches_oracle(lbm, orc):
             assert abs(res[t]["p_ce"] - ref["p_ce"]) <= 5e-3 * abs(ref["p_ce"]) + PC_FLOOR, t
         else:
             assert math.isinf(res[t]["p_ce"])
-    assert invaded >= 2, "the ladder must invade most of the test throats"
+    assert invaded >= 3, "the ladder must invade most of the test throats"
