@@ -69,6 +69,9 @@ def parse():
                     help="drainage of the sample by the pore network (throat entry pressures from the batched "
                          "LBM and the incircle estimate) next to the full LBM drainage, one JSON line")
     ap.add_argument("--pn-steps", type=int, default=5000, help="full-LBM steps per increment for --pore-network")
+    ap.add_argument("--surrogate-config5", action="store_true",
+                    help="the throat surrogate at configuration 5's size (20 k training throats, 1e5 inference "
+                         "throats of 2000-sphere packings, LBM fallback at 2 %% spread), one JSON line")
     ap.add_argument("--shape", default="",
                     help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD, "
                          "staged2:BY:LZ:2 or push:ROWS:LZ:STAGES")
@@ -281,13 +284,13 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax, gather=None):
                              rho_minor=W.RHO_MINOR)
     theta = S.contact_angle_estimate(W.G_ADS[0], W.G_ADS[1], W.G_COHESION, W.RHO_MAJOR, W.RHO_MINOR)
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
-    out = {"workload": "1024 Delaunay throats of a 300-sphere 192^3 RSA packing, boxes 24^3..64^3, "
-                       f"32 increments x {n_steps} steps", "unit": "throats/s"}
+    out = {"workload": "1024 throats (facets of the regular triangulation, longest centre distance < 64) of a "
+                       f"300-sphere 192^3 RSA packing, 32 increments x {n_steps} steps", "unit": "throats/s"}
     # training set from six other packings
     t0 = time.perf_counter()
     tris, ress, rowss = [], [], []
     for seed in range(10 + 6 * rank, 16 + 6 * rank):
-        tri = W.delaunay_throats(W.sample_spheres(192, seed=100 + seed), 1024, seed=100 + seed)
+        tri = lbm.packing_throat_sample(W.sample_spheres(192, seed=100 + seed), 1024, seed=100 + seed)
         res, rows = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
         tris.append(tri)
         ress += res
@@ -300,7 +303,7 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax, gather=None):
     out["surrogate_training"] = {"throats": int(used), "lbm_s": t_gen, "train_s": t_train,
                                  "loss_first_last": [float(losses[:, 0].mean()), float(losses[:, -1].mean())]}
 
-    tri = W.delaunay_throats(W.sample_spheres(192, seed=3 + 1000 * rank), 1024, seed=3 + 1000 * rank)
+    tri = lbm.packing_throat_sample(W.sample_spheres(192, seed=3 + 1000 * rank), 1024, seed=3 + 1000 * rank)
     n = len(tri)
     # batched
     sync()
@@ -326,7 +329,7 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax, gather=None):
     if world > 1 and gather is not None:
         # one throat list over all ranks: LPT shards on the non-solid cells of
         # each box, results gathered back into the list's order
-        shared = W.delaunay_throats(W.sample_spheres(192, seed=3), 1024, seed=3)
+        shared = lbm.packing_throat_sample(W.sample_spheres(192, seed=3), 1024, seed=3)
         sync()
         t0 = time.perf_counter()
         res_s, _ = lbm.run_throat_batch_sharded(shared, params, ladder, n_steps, W.RHO_MAJOR, rank, world, gather)
@@ -689,6 +692,92 @@ def run_pore_network(args):
     return 0
 
 
+def run_surrogate_config5(args):
+    """Configuration 5 at its stated size: the throat surrogate trained on 20 k
+    throats the batched LBM ran (facets of the regular triangulations of seeded
+    300-sphere packings), then asked for 1e5 throats of four seeded 2000-sphere
+    packings, the batched LBM taking the throats whose ensemble spread exceeds
+    2 %.  The LBM judges a seeded random subset of 2000 of the 1e5 throats (all
+    of them would take about 5 min of GPU time); the fallback's cost for all
+    1e5 is its measured rate on that subset's fallback throats."""
+    import torch
+    import paper_1906_04722_gb300 as lbm
+    from paper_1906_04722_gb300 import surrogate as S
+    import workloads as W
+
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR)
+    theta = S.contact_angle_estimate(W.G_ADS[0], W.G_ADS[1], W.G_COHESION, W.RHO_MAJOR, W.RHO_MINOR)
+    ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
+    n_steps = args.throat_steps
+    out = {"workload": "configuration 5: 20 k training throats of seeded 300-sphere 192^3 packings; 1e5 throats of "
+                       "four seeded 2000-sphere 361^3 packings; 32 increments x %d steps; 5 members, 4 x 256, "
+                       "BF16 operands; fallback at 2 %% ensemble spread" % n_steps}
+    t0 = time.perf_counter()
+    tris, ress, rowss, seed = [], [], [], 110
+    while sum(len(t) for t in tris) < 20000:
+        th = lbm.packing_throat_sample(W.sample_spheres(192, seed=seed), None, seed)
+        res, rows = lbm.lbm_run_throat_batch(th, params, ladder, n_steps, W.RHO_MAJOR)
+        tris.append(th)
+        ress += res
+        rowss += rows
+        seed += 1
+    out["training_lbm_s"] = time.perf_counter() - t0
+    sur = S.ThroatSurrogate(n_incr=len(ladder), theta=theta, n_members=5, seed=1, spread_tol=0.02)
+    t0 = time.perf_counter()
+    losses, used = sur.fit(np.concatenate(tris), ress, rowss, epochs=300, batch=256, lr=1e-3, seed=2)
+    out["training"] = {"throats": int(sum(len(t) for t in tris)), "used": int(used), "packings": len(tris),
+                       "train_s": time.perf_counter() - t0,
+                       "loss_first_last": [float(losses[:, 0].mean()), float(losses[:, -1].mean())]}
+    inf = np.concatenate([lbm.packing_throat_sample(W.sample_spheres(361, seed=s), None, s) for s in (20, 21, 22, 23)])
+    inf = inf[:100000]
+    n = len(inf)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pce, rel, _ = sur.predict(inf)
+    torch.cuda.synchronize()
+    t_net = time.perf_counter() - t0
+    fall = rel > 0.02
+    sub = np.sort(np.random.default_rng(7).choice(n, 2000, replace=False))
+    t0 = time.perf_counter()
+    truth_res, _ = lbm.lbm_run_throat_batch(inf[sub], params, ladder, n_steps, W.RHO_MAJOR)
+    t_judge = time.perf_counter() - t0
+    truth = np.array([r["p_ce"] for r in truth_res])
+    fb = sub[fall[sub]]
+    t0 = time.perf_counter()
+    if len(fb):
+        lbm.lbm_run_throat_batch(inf[fb], params, ladder, n_steps, W.RHO_MAJOR)
+    t_fb_sub = time.perf_counter() - t0
+    rate_fb = len(fb) / t_fb_sub if len(fb) else float("inf")
+    t_fb_all = float(fall.sum()) / rate_fb if len(fb) else 0.0
+    answer = np.where(fall[sub], truth, pce[sub])  # fallback throats take the LBM's value
+    ok = np.isfinite(truth)
+    err_all = np.abs(answer[ok] - truth[ok]) / np.abs(truth[ok])
+    ans_ok = ok & ~fall[sub]
+    err_ans = np.abs(pce[sub][ans_ok] - truth[ans_ok]) / np.abs(truth[ans_ok])
+    plain_th = inf[sub[::63]]
+    t0 = time.perf_counter()
+    for th in plain_th:
+        mask, probe = lbm.lbm_throat_geometry(th)
+        d = lbm.Domain(params, mask=mask)
+        d.drainage(ladder, n_steps, W.RHO_MAJOR, probe)
+        d.close()
+    plain = len(plain_th) / (time.perf_counter() - t0)
+    value = n / (t_net + t_fb_all)
+    out.update({"inference_throats": n, "network_s_all": t_net, "fallback_fraction": float(fall.mean()),
+                "fallback_s_all_estimated": t_fb_all, "fallback_rate_throats_per_s": rate_fb,
+                "throats_per_s": value, "plain_throats_per_s": plain, "vs_plain": value / plain,
+                "batched_lbm_throats_per_s": len(sub) / t_judge,
+                "judged_subset": int(len(sub)), "judged_invaded": int(ok.sum()),
+                "pce_rel_err_all_median": float(np.median(err_all)), "pce_rel_err_all_p90": float(np.percentile(err_all, 90)),
+                "pce_rel_err_answered_median": float(np.median(err_ans)) if err_ans.size else None,
+                "pce_rel_err_answered_p90": float(np.percentile(err_ans, 90)) if err_ans.size else None,
+                "answered_in_subset": int(ans_ok.sum())})
+    sur.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_throat_batch(args):
     """One lbm_run_throat_batch of the throat benchmark's held-out packing in one
     form, then the same call with zero steps per increment (geometry, lists,
@@ -701,10 +790,10 @@ def run_throat_batch(args):
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
                              rho_minor=W.RHO_MINOR)
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
-    tri = W.delaunay_throats(W.sample_spheres(192, seed=3), 1024, seed=3)
+    tri = lbm.packing_throat_sample(W.sample_spheres(192, seed=3), None, 3)
     tri = tri[::max(1, len(tri) // max(1, args.throat_count))][:args.throat_count]
-    out = {"workload": f"{len(tri)} Delaunay throats of a 300-sphere 192^3 RSA packing, 32 increments x "
-                       f"{args.throat_steps} steps", "form": args.throat_batch}
+    out = {"workload": f"{len(tri)} throats (regular triangulation) of a 300-sphere 192^3 RSA packing, "
+                       f"32 increments x {args.throat_steps} steps", "form": args.throat_batch}
     for key, steps in (("full", args.throat_steps), ("no_steps", 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -724,6 +813,8 @@ def main():
         return run_drainage(args)
     if args.pore_network:
         return run_pore_network(args)
+    if args.surrogate_config5:
+        return run_surrogate_config5(args)
     if args.throat_batch:
         return run_throat_batch(args)
     rank, world, local = dist_env()

@@ -275,6 +275,15 @@ int lbm_run_throat_batch(const double* throats, int n, const lbm_params* params,
  * below the count (*n_tets still holds it). */
 int lbm_regular_triangulation(const double* spheres, int n, int* tets_out, int capacity, int* n_tets);
 
+/* lbm_packing_throats -- the pore throats of a packing (Sec. 2.2.1): the facets
+ * that two tetrahedra of lbm_regular_triangulation share, as sorted sphere
+ * triples in lexicographic order, keeping those whose longest centre distance
+ * is below max_edge (the throat boxes stay bounded).  facets_out: capacity x 3
+ * sphere indices (may be NULL when capacity = 0, which only counts).
+ * LBM_ERR_ARG as lbm_regular_triangulation, or for a capacity below the count. */
+int lbm_packing_throats(const double* spheres, int n, double max_edge, int* facets_out, int capacity,
+                        int* n_facets);
+
 /* lbm_pn_build -- the pore network of a lattice sample: pore i is tetrahedron i
  * of tets (n_tets x 4 sphere indices).  Every interior void cell of the mask
  * (mask byte 0: not grain, not a reservoir or membrane layer) belongs to the
@@ -538,10 +547,10 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  *                      (lz <= 0: keep the current); shape by lbm_set_push_shape.
  *                      Results equal the staged kernel's bit for bit.  The
  *                      state is converted between the layouts when the kind
- *                      changes, and read-outs (lbm_measure, lbm_get_density,
- *                      lbm_get_density_at, lbm_get_state, lbm_run_drainage)
- *                      convert a copy into the other buffer; callers see the
- *                      pull layout only.
+ *                      changes; lbm_measure, lbm_get_density and
+ *                      lbm_get_density_at read the paired layout directly (the
+ *                      same bits), lbm_get_state converts a copy into the other
+ *                      buffer; callers see the pull layout only.
  * New domains use LBM_KERNEL_STAGED (lbm_autotune times every kind that applies
  * on the domain).  All give the same results up to rounding (not bit for bit:
  * the TMA kernel folds omega w_k into its equilibrium constants).  LBM_ERR_ARG

@@ -146,6 +146,7 @@ SIGNATURES = {
     "lbm_throat_pce_incircle": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP]),
     "lbm_contact_angle_estimate": (ctypes.c_int, [ctypes.c_double] * 5 + [_DP]),
     "lbm_partition_lpt": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int, _IP, _DP]),
+    "lbm_packing_throats": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _IP, ctypes.c_int, _IP]),
     "lbm_pressure_ladder": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 5 + [_DP]),
     "lbm_throat_surrogate_inputs": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _FP, _DP]),
     "lbm_throat_surrogate_create": (ctypes.c_int, [ctypes.POINTER(lbm_throat_surrogate_config), _VP,
@@ -436,6 +437,32 @@ def lbm_regular_triangulation(spheres) -> np.ndarray:
     _check(L.lbm_regular_triangulation(sp.ctypes.data_as(_DP), sp.shape[0], out.ctypes.data_as(_IP), out.shape[0],
                                        ctypes.byref(n)), "lbm_regular_triangulation")
     return out[:n.value]
+
+
+def lbm_packing_throats(spheres, max_edge: float = 64.0) -> np.ndarray:
+    """Interior facets of the packing's regular triangulation with longest centre
+    distance below max_edge: m x 3 sphere indices (lbm_packing_throats)."""
+    sp = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+    n = ctypes.c_int()
+    L = load()
+    _check(L.lbm_packing_throats(sp.ctypes.data_as(_DP), sp.shape[0], float(max_edge), None, 0, ctypes.byref(n)),
+           "lbm_packing_throats")
+    out = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    _check(L.lbm_packing_throats(sp.ctypes.data_as(_DP), sp.shape[0], float(max_edge), out.ctypes.data_as(_IP),
+                                 out.shape[0], ctypes.byref(n)), "lbm_packing_throats")
+    return out[:n.value]
+
+
+def packing_throat_sample(spheres, n, seed: int, max_edge: float = 64.0) -> np.ndarray:
+    """n throats (n x 3 x 4 sphere records) of the packing's regular
+    triangulation, drawn without replacement (seeded); n = None: all of them."""
+    sp = np.asarray(spheres, dtype=np.float64).reshape(-1, 4)
+    f = lbm_packing_throats(sp, max_edge)
+    if n is not None:
+        if n > len(f):
+            raise ValueError(f"only {len(f)} throats, asked for {n}")
+        f = f[np.sort(np.random.default_rng(seed).choice(len(f), size=n, replace=False))]
+    return sp[f]
 
 
 def lbm_pn_build(spheres, tets, mask: np.ndarray):

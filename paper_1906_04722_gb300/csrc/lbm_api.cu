@@ -510,10 +510,10 @@ int lbm_get_density_at(lbm_domain* d, int x, int y, int z, double rho_out[2]) {
         set_error("probe cell outside the box");
         return LBM_ERR_ARG;
     }
-    if (d->params.precision == 0) {
-        const float* fp = nullptr;
-        if (int rc = pull_view(d, &fp)) return rc;
-        LBM_CUDA(launch_probe(fp, d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
+    if (d->params.precision == 0 && d->layout == 1) {
+        LBM_CUDA(launch_probe_push(d->f[d->cur], d->d_nbr, d->geom, x, y, z, d->d_probe, d->stream));
+    } else if (d->params.precision == 0) {
+        LBM_CUDA(launch_probe(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
     }
     else
         LBM_CUDA(launch_probe16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
@@ -572,11 +572,12 @@ int lbm_run_drainage(lbm_domain* d, const double* rho_in_nw, int n_incr, int n_s
 
 int lbm_measure(lbm_domain* d, lbm_measurement* out) {
     if (!d || !out) { set_error("domain or out is NULL"); return LBM_ERR_ARG; }
-    if (d->params.precision == 0) {
-        const float* fp = nullptr;
-        if (int rc = pull_view(d, &fp)) return rc;
-        LBM_CUDA(launch_measure(fp, d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials, d->meas_blocks,
-                                d->d_result, d->stream));
+    if (d->params.precision == 0 && d->layout == 1) {
+        LBM_CUDA(launch_measure_push(d->f[d->cur], d->d_nbr, d->geom, d->params.G, d->d_partials, d->meas_blocks,
+                                     d->d_result, d->stream));
+    } else if (d->params.precision == 0) {
+        LBM_CUDA(launch_measure(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials,
+                                d->meas_blocks, d->d_result, d->stream));
     }
     else
         LBM_CUDA(launch_measure16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
@@ -616,10 +617,10 @@ int lbm_measure(lbm_domain* d, lbm_measurement* out) {
 int lbm_get_density(lbm_domain* d, double* rho_out) {
     if (!d || !rho_out) { set_error("domain or rho_out is NULL"); return LBM_ERR_ARG; }
     try {
-        if (d->params.precision == 0) {
-            const float* fp = nullptr;
-            if (int rc = pull_view(d, &fp)) return rc;
-            LBM_CUDA(launch_density(fp, d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        if (d->params.precision == 0 && d->layout == 1) {
+            LBM_CUDA(launch_density_push(d->f[d->cur], d->d_nbr, d->geom, d->d_rho, d->stream));
+        } else if (d->params.precision == 0) {
+            LBM_CUDA(launch_density(d->f[d->cur], d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
         }
         else
             LBM_CUDA(launch_density16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]),

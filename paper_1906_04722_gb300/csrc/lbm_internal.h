@@ -168,6 +168,13 @@ cudaError_t launch_pull_to_push(const float* fin, float* F, const uint32_t* nbr,
                                 const Geom& g, cudaStream_t s);
 cudaError_t launch_push_to_pull(const float* F, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
                                 const Geom& g, cudaStream_t s);
+// read-outs straight from the paired push layout (a cell's densities are the
+// sums of its own pairs; the same bits as the pull read-outs)
+cudaError_t launch_measure_push(const float* F, const uint32_t* nbr, const Geom& g, double G, double* partials,
+                               int nblocks, double* result, cudaStream_t s);
+cudaError_t launch_density_push(const float* F, const uint32_t* nbr, const Geom& g, float* rho, cudaStream_t s);
+cudaError_t launch_probe_push(const float* F, const uint32_t* nbr, const Geom& g, int x, int y, int z, float* out,
+                              cudaStream_t s);
 // one CTA waiting, bounded, on an mbarrier that nothing completes (self-test)
 cudaError_t launch_wait_selftest(long long limit_ns, int* gave_up, cudaStream_t s);
 // ghost stores (the reflected populations the TMA kernel pulls from wall cells) of a state

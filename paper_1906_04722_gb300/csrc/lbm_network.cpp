@@ -484,6 +484,64 @@ int lbm_regular_triangulation(const double* spheres, int n, int* tets_out, int c
     }
 }
 
+int lbm_packing_throats(const double* spheres, int n, double max_edge, int* facets_out, int capacity,
+                        int* n_facets) {
+    if (!n_facets || capacity < 0 || (capacity > 0 && !facets_out) || !(max_edge > 0)) {
+        set_error("lbm_packing_throats: NULL argument, capacity < 0 or max_edge <= 0");
+        return LBM_ERR_ARG;
+    }
+    int nt = 0;
+    int rc = lbm_regular_triangulation(spheres, n, nullptr, 0, &nt);
+    if (rc) return rc;
+    try {
+        std::vector<int> tets((size_t)nt * 4);
+        rc = lbm_regular_triangulation(spheres, n, tets.data(), nt, &nt);
+        if (rc) return rc;
+        // facets shared by two tetrahedra, as sorted sphere triples
+        std::vector<std::array<int, 3>> all;
+        all.reserve((size_t)nt * 4);
+        for (int t = 0; t < nt; ++t)
+            for (int f = 0; f < 4; ++f) {
+                std::array<int, 3> key;
+                int m = 0;
+                for (int j = 0; j < 4; ++j)
+                    if (j != f) key[m++] = tets[4 * (size_t)t + j];
+                std::sort(key.begin(), key.end());
+                all.push_back(key);
+            }
+        std::sort(all.begin(), all.end());
+        std::vector<std::array<int, 3>> out;
+        for (size_t i = 0; i + 1 < all.size(); ++i) {
+            if (all[i] != all[i + 1]) continue;
+            const std::array<int, 3>& k = all[i];
+            double e = 0.0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = a + 1; b < 3; ++b) {
+                    const double* p = spheres + 4 * (size_t)k[a];
+                    const double* q = spheres + 4 * (size_t)k[b];
+                    e = std::max(e, std::sqrt((p[0] - q[0]) * (p[0] - q[0]) + (p[1] - q[1]) * (p[1] - q[1]) +
+                                              (p[2] - q[2]) * (p[2] - q[2])));
+                }
+            if (e < max_edge) out.push_back(k);
+            ++i;  // a facet appears at most twice
+        }
+        *n_facets = (int)out.size();
+        if (capacity < (int)out.size()) {
+            if (capacity > 0) {
+                set_error("lbm_packing_throats: capacity too small (*n_facets holds the count)");
+                return LBM_ERR_ARG;
+            }
+            return LBM_OK;
+        }
+        for (size_t i = 0; i < out.size(); ++i)
+            for (int j = 0; j < 3; ++j) facets_out[3 * i + j] = out[i][j];
+        return LBM_OK;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return LBM_ERR_OOM;
+    }
+}
+
 int lbm_throat_incircle(const double* throats, int n, double* r_out) {
     if (!throats || !r_out || n < 0) {
         set_error("lbm_throat_incircle: NULL argument or n < 0");

@@ -346,6 +346,79 @@ __global__ void push_to_pull_kernel(const float2* __restrict__ F, float* __restr
     }
 }
 
+// Densities of cell c from its own pairs, summed in k order (the order of the
+// pull read-outs, so the same bits); 0 where a component is not fluid.
+__device__ __forceinline__ uint32_t push_cell_density(const float* __restrict__ Fs, const uint32_t* __restrict__ nbr,
+                                                      const Geom& g, long long c, float& rw, float& rn) {
+    rw = 0.f;
+    rn = 0.f;
+    const uint32_t w = __ldg(nbr + c);
+    const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+    if (cls == CLS_SOLID || cls == CLS_OUTSIDE) return w;
+    const float2* F2 = reinterpret_cast<const float2*>(Fs);
+    float a = 0.f, b = 0.f;
+    for (int k = 0; k < Q; ++k) {
+        const float2 v = __ldg(F2 + (size_t)k * g.plane + c);
+        a += v.x;
+        b += v.y;
+    }
+    rw = a;
+    if (cls != CLS_MEMBRANE) rn = b;
+    return w;
+}
+
+constexpr int PUSH_MEAS_THREADS = 256;
+
+// lbm_measure on the paired push layout: per-block FP64 partials (a second
+// kernel adds them in block order).
+__global__ void __launch_bounds__(PUSH_MEAS_THREADS)
+    push_measure_kernel(const float* __restrict__ Fs, const uint32_t* __restrict__ nbr, Geom g, double G,
+                        double* __restrict__ partials) {
+    double acc[NMEAS];
+#pragma unroll
+    for (int i = 0; i < NMEAS; ++i) acc[i] = 0.0;
+    const long long N = (long long)g.nxy * g.nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        float rw, rn;
+        const uint32_t w = push_cell_density(Fs, nbr, g, c, rw, rn);
+        measure_accumulate(acc, (w >> CLS_SHIFT) & CLS_MASK, (double)rw, (double)rn, G);
+    }
+    __shared__ double red[PUSH_MEAS_THREADS / 32][NMEAS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NMEAS; ++i) {
+        double v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NMEAS) {
+        double v = 0.0;
+        for (int wv = 0; wv < PUSH_MEAS_THREADS / 32; ++wv) v += red[wv][threadIdx.x];
+        partials[(size_t)blockIdx.x * NMEAS + threadIdx.x] = v;
+    }
+}
+
+__global__ void push_density_kernel(const float* __restrict__ Fs, const uint32_t* __restrict__ nbr, Geom g,
+                                    float* __restrict__ rho) {
+    const long long N = (long long)g.nxy * g.nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        float rw, rn;
+        push_cell_density(Fs, nbr, g, c, rw, rn);
+        rho[c] = rw;
+        rho[N + c] = rn;
+    }
+}
+
+__global__ void push_probe_kernel(const float* __restrict__ Fs, const uint32_t* __restrict__ nbr, Geom g,
+                                  long long c, float* __restrict__ out) {
+    float rw, rn;
+    push_cell_density(Fs, nbr, g, c, rw, rn);
+    out[0] = rw;
+    out[1] = rn;
+}
+
 typedef CUresult (*PushEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -489,6 +562,30 @@ cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, c
                       : launch_push_shape<12, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_measure_push(const float* F, const uint32_t* nbr, const Geom& g, double G, double* partials,
+                               int nblocks, double* result, cudaStream_t s) {
+    push_measure_kernel<<<nblocks, PUSH_MEAS_THREADS, 0, s>>>(F, nbr, g, G, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_finalize(partials, nblocks, result, s);
+}
+
+cudaError_t launch_density_push(const float* F, const uint32_t* nbr, const Geom& g, float* rho, cudaStream_t s) {
+    const long long N = (long long)g.nxy * g.nz;
+    long long blocks = (N + 255) / 256;
+    const long long cap = 16LL * device_sm_count();
+    if (blocks > cap) blocks = cap;
+    push_density_kernel<<<(int)blocks, 256, 0, s>>>(F, nbr, g, rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_push(const float* F, const uint32_t* nbr, const Geom& g, int x, int y, int z, float* out,
+                              cudaStream_t s) {
+    const long long c = ((long long)z * g.ny + y) * g.nx + x;
+    push_probe_kernel<<<1, 1, 0, s>>>(F, nbr, g, c, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pull_to_push(const float* fin, float* F, const uint32_t* nbr, const uint32_t* nbr_nw,

@@ -240,3 +240,35 @@ def test_incircle_closed_throat(lbm):
     th = np.array([[0, 0, 0, 10.0], [12, 0, 0, 10.0], [6, 10, 0, 10.0]])
     assert lbm.lbm_throat_incircle(th)[0] == 0
     assert math.isinf(lbm.lbm_throat_pce_incircle(th, 0.1, 1.0)[0])
+
+
+def test_packing_throats_are_shared_facets(lbm):
+    """lbm_packing_throats: for equal radii the interior facets of the Delaunay
+    tetrahedralisation (qhull), for unequal ones those of the lifted lower hull,
+    each with its longest centre distance below the limit."""
+    from collections import Counter
+    from scipy.spatial import Delaunay
+    for equal in (True, False):
+        sp = W.sample_spheres(192, seed=6)
+        if equal:
+            sp[:, 3] = 12.0
+            simp = Delaunay(sp[:, :3]).simplices
+        else:
+            from scipy.spatial import ConvexHull
+            P = sp[:, :3]
+            h = ConvexHull(np.c_[P, (P ** 2).sum(1) - sp[:, 3] ** 2])
+            simp = h.simplices[h.equations[:, 3] < 0]
+        cnt = Counter()
+        for tet in np.asarray(simp).tolist():
+            for f in range(4):
+                cnt[tuple(sorted(tet[:f] + tet[f + 1:]))] += 1
+        want = set()
+        for k, v in cnt.items():
+            if v == 2:
+                c = sp[list(k), :3]
+                e = max(np.linalg.norm(c[a] - c[b]) for a in range(3) for b in range(a + 1, 3))
+                if e < 64.0:
+                    want.add(k)
+        got = lbm.lbm_packing_throats(sp, 64.0)
+        assert {tuple(x) for x in got.tolist()} == want
+        assert [tuple(x) for x in got.tolist()] == sorted(want)
