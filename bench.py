@@ -69,6 +69,8 @@ def parse():
                     help="drainage of the sample by the pore network (throat entry pressures from the batched "
                          "LBM and the incircle estimate) next to the full LBM drainage, one JSON line")
     ap.add_argument("--pn-steps", type=int, default=5000, help="full-LBM steps per increment for --pore-network")
+    ap.add_argument("--throat-convergence", action="store_true",
+                    help="p_c^e of 64 throats against the steps per pressure increment (100 .. 2000), one JSON line")
     ap.add_argument("--surrogate-config5", action="store_true",
                     help="the throat surrogate at configuration 5's size (20 k training throats, 1e5 inference "
                          "throats of 2000-sphere packings, LBM fallback at 2 %% spread), one JSON line")
@@ -778,6 +780,38 @@ def run_surrogate_config5(args):
     return 0
 
 
+def run_throat_convergence(args):
+    """Steps per increment for a quasi-static throat ladder (Sec. 2.2.2: the
+    density is raised gradually): 64 throats of the held-out packing run the
+    32-increment ladder at 100 .. 2000 steps per increment; each p_c^e and
+    invasion increment against the 2000-step run."""
+    import paper_1906_04722_gb300 as lbm
+    import workloads as W
+
+    params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
+                             rho_minor=W.RHO_MINOR)
+    ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
+    tri = lbm.packing_throat_sample(W.sample_spheres(192, seed=3), 64, seed=5)
+    runs = {}
+    for n_steps in (100, 250, 500, 1000, 2000):
+        t0 = time.perf_counter()
+        res, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
+        runs[n_steps] = ([r["p_ce"] for r in res], [r["invaded_at"] for r in res], time.perf_counter() - t0)
+    ref_p, ref_i, _ = runs[2000]
+    out = {"workload": "64 throats (regular triangulation) of a 300-sphere 192^3 packing, 32 increments of +0.02",
+           "rows": []}
+    for n_steps, (p, inv, dt) in runs.items():
+        both = [k for k in range(len(tri)) if math.isfinite(p[k]) and math.isfinite(ref_p[k])]
+        err = [abs(p[k] - ref_p[k]) / abs(ref_p[k]) for k in both]
+        out["rows"].append({"steps_per_increment": n_steps, "seconds": dt, "invaded": int(sum(math.isfinite(v) for v in p)),
+                            "same_increment_as_2000": int(sum(inv[k] == ref_i[k] for k in range(len(tri)))),
+                            "mean_increment_shift": float(np.mean([inv[k] - ref_i[k] for k in both])) if both else None,
+                            "pce_rel_diff_median": float(np.median(err)) if err else None,
+                            "pce_rel_diff_p90": float(np.percentile(err, 90)) if err else None})
+    print(json.dumps(out))
+    return 0
+
+
 def run_throat_batch(args):
     """One lbm_run_throat_batch of the throat benchmark's held-out packing in one
     form, then the same call with zero steps per increment (geometry, lists,
@@ -815,6 +849,8 @@ def main():
         return run_pore_network(args)
     if args.surrogate_config5:
         return run_surrogate_config5(args)
+    if args.throat_convergence:
+        return run_throat_convergence(args)
     if args.throat_batch:
         return run_throat_batch(args)
     rank, world, local = dist_env()
