@@ -70,13 +70,13 @@ def parse():
                          "LBM and the incircle estimate) next to the full LBM drainage, one JSON line")
     ap.add_argument("--pn-steps", type=int, default=5000, help="full-LBM steps per increment for --pore-network")
     ap.add_argument("--throat-convergence", action="store_true",
-                    help="p_c^e of 64 throats against the steps per pressure increment (100 .. 2000), one JSON line")
+                    help="p_c^e of 64 throats against the steps per pressure increment (100 .. 4000), one JSON line")
     ap.add_argument("--surrogate-config5", action="store_true",
                     help="the throat surrogate at configuration 5's size (20 k training throats, 1e5 inference "
                          "throats of 2000-sphere packings, LBM fallback at 2 %% spread), one JSON line")
     ap.add_argument("--shape", default="",
                     help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD, "
-                         "staged2:BY:LZ:2 or push:ROWS:LZ:STAGES")
+                         "staged2:BY:LZ:2 or push:ROWS:LZ:STAGES[:PREFETCH]")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--throat-batch", choices=["cells", "tiles", "persistent"], default="",
@@ -315,6 +315,18 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax, gather=None):
     t_batch = tmax(time.perf_counter() - t0)
     truth = np.array([r["p_ce"] for r in res_ref])
     out["batched"] = world * n / t_batch
+    # the analytic estimates Sec. 1 cites, on the same throats (sigma from
+    # Laplace's law on the GPU, the contact angle of the adhesion estimate)
+    sigma, _ = laplace_sigma(lbm, W)
+    cos_t = math.cos(theta)
+    fin = np.isfinite(truth)
+    out["baselines"] = {"sigma": sigma, "cos_theta": cos_t}
+    for name, est in (("incircle", lbm.lbm_throat_pce_incircle(tri, sigma, cos_t)),
+                      ("msp", lbm.lbm_throat_pce_msp(tri, sigma, cos_t))):
+        ok = fin & np.isfinite(est)
+        rel = np.abs(est[ok] - truth[ok]) / np.abs(truth[ok])
+        out["baselines"][name] = {"median_ratio_to_lbm": float(np.median(est[ok] / truth[ok])),
+                                  "rel_err_median": float(np.median(rel)), "rel_err_p90": float(np.percentile(rel, 90))}
     out["batch_form"] = ("cell list: compact storage of every non-solid cell, a density launch and a push-streaming "
                          "step launch per time step")
     # the same batch in the other two forms, for context
@@ -434,8 +446,9 @@ def run_ours(args, rank, world, local):
         f = args.shape.split(":")
         tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
                  {"kind": f[0], "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
-        if f[0] == "push":  # push:rows:lz:stages
-            tuned = {"kind": "push", "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])}
+        if f[0] == "push":  # push:rows:lz:stages[:prefetch planes]
+            tuned = {"kind": "push", "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3]),
+                     "prefetch": int(f[4]) if len(f) > 4 else 0}
     else:
         tuned = dom.autotune(trial_steps=20) if not args.no_tune else None
 
@@ -444,6 +457,7 @@ def run_ours(args, rank, world, local):
             return
         if tuned["kind"] == "push":
             d.set_push_shape(PUSH_SHAPES[(tuned["by"], tuned["lead"])][0], tuned["lz"])
+            d.set_push_prefetch(tuned.get("prefetch", 0))
         elif tuned["kind"] == "tma":
             d.set_step_kernel(lbm.KERNEL_TMA, tuned["lz"])
         elif tuned["kind"] == "split":
@@ -618,9 +632,9 @@ def run_pore_network(args):
     2.2.2, Sec. 3.1.1) next to the fully resolved LBM drainage.  The network is
     the regular triangulation of the packing; every interior throat's entry
     pressure comes from the batched throat LBM (and, as the cheap baseline, from
-    the incircle estimate with sigma from Laplace's law and the contact angle of
-    the adhesion estimate); the levels are the reservoir capillary pressures the
-    full LBM reached at each of its increments."""
+    incircle and Mayer-Stowe-Princen estimates with sigma from Laplace's law and
+    the contact angle of the adhesion estimate); the levels are the reservoir
+    capillary pressures the full LBM reached at each of its increments."""
     import torch
     import paper_1906_04722_gb300 as lbm
     import workloads as W
@@ -657,8 +671,10 @@ def run_pore_network(args):
     t_batch = time.perf_counter() - t0
     pce_lbm = np.array([r["p_ce"] for r in res])
     sigma, drops = laplace_sigma(lbm, W)
-    cos_t = (W.G_ADS[1] - W.G_ADS[0]) / (W.G_COHESION * (W.RHO_MAJOR - W.RHO_MINOR) / 2.0)
+    from paper_1906_04722_gb300 import surrogate as S
+    cos_t = math.cos(S.contact_angle_estimate(W.G_ADS[0], W.G_ADS[1], W.G_COHESION, W.RHO_MAJOR, W.RHO_MINOR))
     pce_inc = lbm.lbm_throat_pce_incircle(tri, sigma, cos_t)
+    pce_msp = lbm.lbm_throat_pce_msp(tri, sigma, cos_t)
 
     levels = np.array([r["p_c_res"] for r in full["rows"]])
     sw_full = np.array([r["S_w"] for r in full["rows"]])
@@ -672,24 +688,32 @@ def run_pore_network(args):
 
     sw_lbm, trapped_lbm = network_curve(pce_lbm)
     sw_inc, trapped_inc = network_curve(pce_inc)
+    sw_msp, trapped_msp = network_curve(pce_msp)
     rows = [{"increment": i, "rho_in_nw": ladder[i], "p_c_res": float(levels[i]), "S_w_full_lbm": float(sw_full[i]),
-             "S_w_network_lbm_pce": float(sw_lbm[i]), "S_w_network_incircle": float(sw_inc[i])}
+             "S_w_network_lbm_pce": float(sw_lbm[i]), "S_w_network_incircle": float(sw_inc[i]),
+             "S_w_network_msp": float(sw_msp[i])}
             for i in range(len(levels))]
+    fin = np.isfinite(pce_lbm)
     print(json.dumps({
         "workload": f"sample{args.size}: full LBM drainage 20 x {args.pn_steps} steps vs pore-network drainage "
-                    f"on its regular triangulation ({len(tets)} pores, {int(inner.sum())} interior throats)",
+                    f"on its regular triangulation ({len(tets)} pores, {int(inner.sum())} interior throats); "
+                    f"throat ladders 32 x {args.throat_steps} steps",
         "seconds": {"full_lbm": t_full, "network_build": t_net, "throat_batch": t_batch,
                     "total": time.perf_counter() - t_all},
         "throats": {"n": int(inner.sum()), "invaded_in_ladder": int(np.isfinite(pce_lbm).sum()),
                     "p_ce_median": float(np.median(pce_lbm[np.isfinite(pce_lbm)])),
                     "incircle_p_ce_median": float(np.median(pce_inc[np.isfinite(pce_inc)])),
-                    "incircle_vs_lbm_median_ratio": float(np.median((pce_inc / pce_lbm)[np.isfinite(pce_lbm)]))},
+                    "incircle_vs_lbm_median_ratio": float(np.median((pce_inc / pce_lbm)[fin])),
+                    "msp_p_ce_median": float(np.median(pce_msp[np.isfinite(pce_msp)])),
+                    "msp_vs_lbm_median_ratio": float(np.median((pce_msp / pce_lbm)[fin]))},
         "sigma": sigma, "laplace_drops": drops, "cos_theta": cos_t,
-        "trapped_pores": {"lbm_pce": trapped_lbm, "incircle": trapped_inc},
+        "trapped_pores": {"lbm_pce": trapped_lbm, "incircle": trapped_inc, "msp": trapped_msp},
         "S_w_abs_error": {"lbm_pce_max": float(np.abs(sw_lbm - sw_full).max()),
                           "lbm_pce_mean": float(np.abs(sw_lbm - sw_full).mean()),
                           "incircle_max": float(np.abs(sw_inc - sw_full).max()),
-                          "incircle_mean": float(np.abs(sw_inc - sw_full).mean())},
+                          "incircle_mean": float(np.abs(sw_inc - sw_full).mean()),
+                          "msp_max": float(np.abs(sw_msp - sw_full).max()),
+                          "msp_mean": float(np.abs(sw_msp - sw_full).mean())},
         "rows": rows}))
     return 0
 
@@ -783,8 +807,8 @@ def run_surrogate_config5(args):
 def run_throat_convergence(args):
     """Steps per increment for a quasi-static throat ladder (Sec. 2.2.2: the
     density is raised gradually): 64 throats of the held-out packing run the
-    32-increment ladder at 100 .. 2000 steps per increment; each p_c^e and
-    invasion increment against the 2000-step run."""
+    32-increment ladder at 100 .. 4000 steps per increment; each p_c^e and
+    invasion increment against the 4000-step run."""
     import paper_1906_04722_gb300 as lbm
     import workloads as W
 
@@ -793,18 +817,18 @@ def run_throat_convergence(args):
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
     tri = lbm.packing_throat_sample(W.sample_spheres(192, seed=3), 64, seed=5)
     runs = {}
-    for n_steps in (100, 250, 500, 1000, 2000):
+    for n_steps in (100, 250, 500, 1000, 2000, 4000):
         t0 = time.perf_counter()
         res, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR)
         runs[n_steps] = ([r["p_ce"] for r in res], [r["invaded_at"] for r in res], time.perf_counter() - t0)
-    ref_p, ref_i, _ = runs[2000]
+    ref_p, ref_i, _ = runs[4000]
     out = {"workload": "64 throats (regular triangulation) of a 300-sphere 192^3 packing, 32 increments of +0.02",
-           "rows": []}
+           "reference": "4000 steps per increment", "rows": []}
     for n_steps, (p, inv, dt) in runs.items():
         both = [k for k in range(len(tri)) if math.isfinite(p[k]) and math.isfinite(ref_p[k])]
         err = [abs(p[k] - ref_p[k]) / abs(ref_p[k]) for k in both]
         out["rows"].append({"steps_per_increment": n_steps, "seconds": dt, "invaded": int(sum(math.isfinite(v) for v in p)),
-                            "same_increment_as_2000": int(sum(inv[k] == ref_i[k] for k in range(len(tri)))),
+                            "same_increment_as_ref": int(sum(inv[k] == ref_i[k] for k in range(len(tri)))),
                             "mean_increment_shift": float(np.mean([inv[k] - ref_i[k] for k in both])) if both else None,
                             "pce_rel_diff_median": float(np.median(err)) if err else None,
                             "pce_rel_diff_p90": float(np.percentile(err, 90)) if err else None})

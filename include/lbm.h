@@ -343,6 +343,29 @@ int lbm_throat_incircle(const double* throats, int n, double* r_out);
  * throat).  sigma: interfacial tension, cos_theta: of the contact angle. */
 int lbm_throat_pce_incircle(const double* throats, int n, double sigma, double cos_theta, double* pce_out);
 
+/* lbm_throat_pce_msp -- the Mayer-Stowe-Princen estimate of the entry pressure
+ * (the other approximation Sec. 1 cites), with the throat taken as a prism:
+ * its section is the triangle of the three centres minus the sphere sections,
+ * its sides neutral walls (90 degrees, as the lattice throat domain's).  At
+ * p_c = sigma / r the wetting fluid holds arc menisci of radius r in the
+ * corners between grains (meeting the grains at theta, the walls at 90
+ * degrees); the non-wetting area A_nw, meniscus length L_nw and grain contact
+ * length L_ns of the section then satisfy at entry
+ *     p_c^e A_nw = sigma (L_nw + L_ns cos(theta)),
+ * solved for r by a scan from 0 in steps of r_i / 64 (r_i the incircle, up to
+ * 16 r_i) and bisection; p_c^e = sigma / r.  The non-wetting region is
+ * found exactly for any arrangement of the menisci (the part of the section
+ * within r of the meniscus centres allowed by the contact angles; its boundary
+ * from the arrangement of walls, grain circles and meniscus circles).
+ * pce_out[t] = +inf for a closed throat, NaN for collinear centres.
+ * cos_theta in (0, 1].  Host, all cores. */
+int lbm_throat_pce_msp(const double* throats, int n, double sigma, double cos_theta, double* pce_out);
+
+/* lbm_throat_msp_terms -- the MS-P terms of one throat (3 x (cx, cy, cz, r)) at
+ * meniscus radius r: out[0] = A_nw, out[1] = L_nw, out[2] = L_ns (lattice
+ * units).  LBM_ERR_ARG for collinear centres, r <= 0 or cos_theta <= 0. */
+int lbm_throat_msp_terms(const double* throat, double r, double cos_theta, double out[3]);
+
 /* ---------------------------------------------------------------------------
  * Surrogate network.  The paper reads p_c^e off one LBM run per throat; the
  * surrogate learns that map from LBM-generated throats so that most throats of a
@@ -577,12 +600,20 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
  * apply to the domain. */
 int lbm_set_push_shape(lbm_domain* d, int shape, int lz);
 
+/* lbm_set_push_prefetch -- how many planes (0 .. 4) the push kernel asks the
+ * tensor memory accelerator to bring into L2 beyond the planes whose loads
+ * are in flight; a hint that changes no result (bit for bit) and costs no
+ * shared memory.  New domains use 0.  Kept across lbm_set_push_shape;
+ * lbm_autotune sets it with the shape it picks.  LBM_ERR_ARG outside 0 .. 4. */
+int lbm_set_push_prefetch(lbm_domain* d, int planes);
+
 /* lbm_autotune -- time the step kernels and launch shapes that apply to the
  * domain on the domain itself and keep the fastest.
  *   trial_steps  time steps timed per candidate (>= 1), after one untimed step;
  *   out          optional: the chosen shape and its time per step.
  * Candidates: for FP32 domains the push kernel (where it applies) in every
- * shape with z segments of 8, 16 and 32 planes, the TMA kernel (where it
+ * shape with z segments of 16, 32, 48 and 64 planes, each without and with a
+ * two-plane L2 prefetch (lbm_set_push_prefetch), the TMA kernel (where it
  * applies) with z segments of 8 .. 48 planes, the two-launch kernel, the two-threads-per-cell
  * staged kernel (by 6 or 8, z segments of 8 .. 32), and the staged kernel with
  * by in {6, 8, 10}, lead in {0, 1, 2, 3} (0 and 1: the double-pull variant) and
@@ -598,6 +629,7 @@ typedef struct {
                            rows (by) and plane stages (lead); lz the z segment */
     double ms_per_step; /* its measured time per step */
     int n_candidates;   /* shapes timed */
+    int prefetch;       /* push kernel: its L2 prefetch distance in planes; else 0 */
 } lbm_tune_result;
 int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out);
 

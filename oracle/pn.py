@@ -110,3 +110,83 @@ def incircle_search(spheres3, grid: int = 400):
         lo = np.array(best_p) - span
         hi = np.array(best_p) + span
     return best_v
+
+
+def _throat_plane(spheres3):
+    """Centres of a throat in the plane through them (counter-clockwise) and radii."""
+    s = np.asarray(spheres3, dtype=float).reshape(3, 4)
+    c, r = s[:, :3], s[:, 3]
+    e1 = (c[1] - c[0]) / np.linalg.norm(c[1] - c[0])
+    n = np.cross(c[1] - c[0], c[2] - c[0])
+    n /= np.linalg.norm(n)
+    e2 = np.cross(n, e1)
+    P = np.stack([[(ci - c[0]) @ e1, (ci - c[0]) @ e2] for ci in c])
+    return P, r
+
+
+def msp_terms_raster(spheres3, r, cos_theta, h):
+    """A_nw, L_nw, L_ns of the Mayer-Stowe-Princen construction (Sec. 1 cites
+    MS-P) by brute force on a pixel grid of spacing h, for a throat taken as a
+    prism with neutral side walls: the section is the triangle T of the centres
+    minus the sphere sections; meniscus discs of radius r may be centred at any
+    point of T at a distance of at least sqrt(R_i^2 + r^2 + 2 R_i r cos(theta))
+    from every centre (so that a disc cuts grain i at the contact angle); the
+    non-wetting region is what those discs cover of the section.  A_nw counts
+    its pixels; L_nw is the length of the level set {distance to the allowed
+    centres = r} inside the section (coarea formula, a band of width 8 h);
+    L_ns the measure of grain-circle points inside T within r of an allowed
+    centre (circles sampled densely).  No arcs, no case analysis."""
+    from scipy import ndimage
+    from scipy.spatial import cKDTree
+
+    P, R = _throat_plane(spheres3)
+    lo, hi = P.min(axis=0) - 2 * h, P.max(axis=0) + 2 * h
+    xs = np.arange(lo[0], hi[0], h)
+    ys = np.arange(lo[1], hi[1], h)
+    X, Y = np.meshgrid(xs, ys)
+
+    def in_T(x, y):
+        def side(i, j):
+            return (P[j, 0] - P[i, 0]) * (y - P[i, 1]) - (P[j, 1] - P[i, 1]) * (x - P[i, 0])
+        return (side(0, 1) >= 0) & (side(1, 2) >= 0) & (side(2, 0) >= 0)
+
+    inT = in_T(X, Y)
+    dist_c = [np.hypot(X - P[i, 0], Y - P[i, 1]) for i in range(3)]
+    grain = (dist_c[0] < R[0]) | (dist_c[1] < R[1]) | (dist_c[2] < R[2])
+    rho = np.sqrt(R * R + r * r + 2 * R * r * cos_theta)
+    allowed = inT & (dist_c[0] >= rho[0]) & (dist_c[1] >= rho[1]) & (dist_c[2] >= rho[2])
+    if not allowed.any():
+        return 0.0, 0.0, 0.0
+    d = ndimage.distance_transform_edt(~allowed, sampling=h)
+    pore = inT & ~grain
+    a_nw = float((pore & (d <= r)).sum()) * h * h
+    eps = 8 * h
+    l_nw = float((pore & (np.abs(d - r) < eps / 2)).sum()) * h * h / eps
+    tree = cKDTree(np.column_stack([X[allowed], Y[allowed]]))
+    l_ns = 0.0
+    for i in range(3):
+        t = np.linspace(0.0, 2 * np.pi, 40000, endpoint=False)
+        px, py = P[i, 0] + R[i] * np.cos(t), P[i, 1] + R[i] * np.sin(t)
+        keep = in_T(px, py)
+        for j in range(3):
+            if j != i:
+                keep &= np.hypot(px - P[j, 0], py - P[j, 1]) >= R[j]
+        if not keep.any():
+            continue
+        dd, _ = tree.query(np.column_stack([px[keep], py[keep]]))
+        l_ns += R[i] * 2 * np.pi * float((dd <= r + 0.5 * h).sum()) / len(t)
+    return a_nw, l_nw, l_ns
+
+
+def msp_radius_raster(spheres3, cos_theta, h, r_hi):
+    """Meniscus radius of the MS-P condition A_nw = r (L_nw + L_ns cos(theta)),
+    by bisection on [0, r_hi] over msp_terms_raster."""
+    lo, hi = 0.0, float(r_hi)
+    for _ in range(22):
+        mid = 0.5 * (lo + hi)
+        a, lnw, lns = msp_terms_raster(spheres3, mid, cos_theta, h)
+        if a - mid * (lnw + lns * cos_theta) > 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)

@@ -89,12 +89,12 @@ class lbm_throat_surrogate_config(ctypes.Structure):
 
 class lbm_tune_result(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("by", ctypes.c_int), ("lz", ctypes.c_int), ("lead", ctypes.c_int),
-                ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int)]
+                ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int), ("prefetch", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"kind": {0: "staged", 1: "tma", 2: "split", 3: "staged2", 4: "push"}.get(self.kind, "?"),
                 "by": self.by, "lz": self.lz, "lead": self.lead,
-                "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates}
+                "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates, "prefetch": self.prefetch}
 
 
 class lbm_surrogate_config(ctypes.Structure):
@@ -129,6 +129,7 @@ SIGNATURES = {
                                                  ctypes.POINTER(lbm_measurement)]),
     "lbm_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_set_push_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "lbm_set_push_prefetch": (ctypes.c_int, [_VP, ctypes.c_int]),
     "lbm_get_tile": (ctypes.c_int, [_VP, _IP, _IP, _IP]),
     "lbm_set_step_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "lbm_get_step_kernel": (ctypes.c_int, [_VP, _IP, _IP]),
@@ -144,6 +145,8 @@ SIGNATURES = {
                                        _IP]),
     "lbm_throat_incircle": (ctypes.c_int, [_DP, ctypes.c_int, _DP]),
     "lbm_throat_pce_incircle": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP]),
+    "lbm_throat_pce_msp": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, ctypes.c_double, _DP]),
+    "lbm_throat_msp_terms": (ctypes.c_int, [_DP, ctypes.c_double, ctypes.c_double, _DP]),
     "lbm_contact_angle_estimate": (ctypes.c_int, [ctypes.c_double] * 5 + [_DP]),
     "lbm_partition_lpt": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_int, _IP, _DP]),
     "lbm_packing_throats": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.c_double, _IP, ctypes.c_int, _IP]),
@@ -379,6 +382,10 @@ def lbm_set_push_shape(h, shape: int, lz: int = 0):
     _check(load().lbm_set_push_shape(h, int(shape), int(lz)), "lbm_set_push_shape")
 
 
+def lbm_set_push_prefetch(h, planes: int):
+    _check(load().lbm_set_push_prefetch(h, int(planes)), "lbm_set_push_prefetch")
+
+
 def lbm_get_step_kernel(h):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(load().lbm_get_step_kernel(h, ctypes.byref(a), ctypes.byref(b)), "lbm_get_step_kernel")
@@ -544,6 +551,24 @@ def lbm_throat_incircle(throats) -> np.ndarray:
     return out
 
 
+def lbm_throat_pce_msp(throats, sigma: float, cos_theta: float) -> np.ndarray:
+    """Mayer-Stowe-Princen p_c^e of each throat (+inf closed, NaN no regular meniscus)."""
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 12))
+    out = np.zeros(th.shape[0])
+    _check(load().lbm_throat_pce_msp(th.ctypes.data_as(_DP), th.shape[0], float(sigma), float(cos_theta),
+                                     out.ctypes.data_as(_DP)), "lbm_throat_pce_msp")
+    return out
+
+
+def lbm_throat_msp_terms(throat, r: float, cos_theta: float):
+    """(A_nw, L_nw, L_ns) of one throat at meniscus radius r."""
+    th = np.ascontiguousarray(np.asarray(throat, dtype=np.float64).reshape(12))
+    out = np.zeros(3)
+    _check(load().lbm_throat_msp_terms(th.ctypes.data_as(_DP), float(r), float(cos_theta), out.ctypes.data_as(_DP)),
+           "lbm_throat_msp_terms")
+    return tuple(out)
+
+
 def lbm_throat_pce_incircle(throats, sigma: float, cos_theta: float) -> np.ndarray:
     th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 12))
     out = np.zeros(th.shape[0])
@@ -657,6 +682,9 @@ class Domain:
 
     def set_push_shape(self, shape, lz=0):
         lbm_set_push_shape(self.h, shape, lz)
+
+    def set_push_prefetch(self, planes):
+        lbm_set_push_prefetch(self.h, planes)
 
     def autotune(self, trial_steps=20):
         return lbm_autotune(self.h, trial_steps)

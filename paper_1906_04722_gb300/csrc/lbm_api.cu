@@ -100,7 +100,7 @@ void drop_graphs(lbm_domain* d) {
 cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH)
         return launch_step_push(d->tile.push_shape, d->push_maps[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh,
-                                d->geom, d->phys, d->tile.push_lz, d->d_err, s);
+                                d->geom, d->phys, d->tile.push_lz, d->tile.push_pf, d->d_err, s);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA)
         return launch_step_tma(d->tma, cur, d->f[cur], d->f[cur ^ 1], d->d_nbr_nw, d->d_adh, d->geom, d->phys,
                                d->tile.tma_lz, d->d_err, s);
@@ -350,6 +350,7 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     d->tile = default_tile(g);
     d->tile.push_shape = 1;  // 6 rows, 3 stages, two CTAs per SM
     d->tile.push_lz = push_default_lz(g, 1);
+    d->tile.push_pf = 0;
     d->layout = 0;
     d->push_maps_rows = 0;
 
@@ -755,6 +756,17 @@ int lbm_set_push_shape(lbm_domain* d, int shape, int lz) {
     return ensure_push_maps(d);
 }
 
+int lbm_set_push_prefetch(lbm_domain* d, int planes) {
+    if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
+    if (planes < 0 || planes > PUSH_MAX_PREFETCH) {
+        set_error("push prefetch distance outside [0, 4]");
+        return LBM_ERR_ARG;
+    }
+    d->tile.push_pf = planes;
+    drop_graphs(d);
+    return LBM_OK;
+}
+
 int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead) {
     if (!d || !by || !lz || !lead) { set_error("NULL argument"); return LBM_ERR_ARG; }
     *by = d->tile.by;
@@ -789,13 +801,15 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     };
     if (fp32 && push_step_applicable(g))
         for (int sh = 0; sh < push_shape_count(); ++sh)
-            for (int lz : {16, 32, 48, 64}) {
-                StepTile t = orig;
-                t.kind = LBM_KERNEL_PUSH;
-                t.push_shape = sh;
-                t.push_lz = lz > g.nz ? g.nz : lz;
-                cand.push_back(t);
-            }
+            for (int lz : {16, 32, 48, 64})
+                for (int pf : {0, 2}) {
+                    StepTile t = orig;
+                    t.kind = LBM_KERNEL_PUSH;
+                    t.push_shape = sh;
+                    t.push_lz = lz > g.nz ? g.nz : lz;
+                    t.push_pf = pf;
+                    cand.push_back(t);
+                }
     if (fp32 && d->tma_ok)
         for (int lz : {8, 12, 16, 24, 32, 48}) add(LBM_KERNEL_TMA, orig.by, lz, orig.lead);
     if (fp32) add(LBM_KERNEL_SPLIT, orig.by, orig.lz, orig.lead);
@@ -882,6 +896,7 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
         out->lead = best_t.kind == LBM_KERNEL_PUSH ? push_shape_stages(best_t.push_shape) : best_t.lead;
         out->ms_per_step = best;
         out->n_candidates = (int)cand.size();
+        out->prefetch = best_t.kind == LBM_KERNEL_PUSH ? best_t.push_pf : 0;
     }
     return LBM_OK;
 }

@@ -94,6 +94,7 @@ struct StepTile {
     int tma_lz;  // z-segment length of the TMA kernel
     int push_shape;  // shape index of the push kernel (push_shape_rows / _stages)
     int push_lz;     // z-segment length of the push kernel
+    int push_pf;     // planes the push kernel prefetches into L2 beyond its loads (0 .. PUSH_MAX_PREFETCH)
 };
 
 // Tensor maps of the TMA step kernel (lbm_step_tma.cu): the two population
@@ -154,6 +155,11 @@ cudaError_t launch_step_split(const float* fin, float* fout, float2* rho2, const
                               cudaStream_t s);
 // paired push-form step (lbm_step_push.cu): float2 F[19][plane] of the current
 // time level; TMA box loads of whole planes (no periodic x / y, nx even)
+// Inscribed circle of a throat (3 x (cx, cy, cz, r)): the largest clearance
+// over the triangle of the centres, 0 when the spheres close it.
+double throat_incircle(const double* s3);
+
+constexpr int PUSH_MAX_PREFETCH = 4;
 int push_shape_count();
 int push_shape_rows(int shape);
 int push_shape_stages(int shape);
@@ -163,7 +169,7 @@ cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtens
 cudaError_t prepare_step_push(int shape);
 cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, const uint32_t* nbr,
                              const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p, int lz,
-                             int* err, cudaStream_t s);
+                             int pf, int* err, cudaStream_t s);
 cudaError_t launch_pull_to_push(const float* fin, float* F, const uint32_t* nbr, const uint32_t* nbr_nw,
                                 const Geom& g, cudaStream_t s);
 cudaError_t launch_push_to_pull(const float* F, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,

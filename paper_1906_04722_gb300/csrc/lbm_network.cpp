@@ -438,6 +438,8 @@ double incircle3(const double* s3) {
 
 }  // namespace
 
+double throat_incircle(const double* s3) { return incircle3(s3); }
+
 }  // namespace lbmk
 
 using namespace lbmk;

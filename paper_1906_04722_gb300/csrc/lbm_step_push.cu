@@ -98,6 +98,15 @@ __device__ __forceinline__ void p_tma_load_4d(void* dst, const CUtensorMap* map,
         : "memory");
 }
 
+// A hint: the box at these coordinates into L2, nothing into shared memory and
+// no completion to wait for.
+__device__ __forceinline__ void p_tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+
 // Swaps the bits of each opposite pair: pull bounce bits (x - e_k not fluid)
 // become push bounce bits (x + e_k not fluid).
 __device__ __forceinline__ uint32_t p_swap_pairs(uint32_t m) {
@@ -117,7 +126,8 @@ template <int BY, int NS, int MINB, bool TAU1>
 __global__ void __launch_bounds__(PX * BY, MINB)
     sc_step_push_kernel(const __grid_constant__ CUtensorMap tm, float2* __restrict__ fout,
                         const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
-                        const uint32_t* __restrict__ adh, Geom g, Phys P, int lz, int* __restrict__ err) {
+                        const uint32_t* __restrict__ adh, Geom g, Phys P, int lz, int pf,
+                        int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (*reinterpret_cast<volatile int*>(err) != 0) return;  // an earlier launch gave up
     constexpr int TY = BY - 2;
@@ -151,6 +161,20 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         }
         p_mbar_arrive_expect_tx(b, stage_bytes<BY>());
         p_tma_load_4d(stages + (size_t)slot(p) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
+    };
+    // plane p into L2 ahead of its load (pf planes beyond the loads in flight);
+    // the box is moved inside the tensor where it sticks out, so that every
+    // coordinate is in range (the hint then covers a few other columns)
+    const int pfx = max(0, min(2 * xb, 2 * g.nx - 2 * PX));
+    const int pfy = max(0, min(yb, g.ny - BY));
+    auto prefetch = [&](int p) {
+        if (p > z1) return;
+        int zc = p;
+        if (zc < 0 || zc >= g.nz) {
+            if (!g.pz) return;
+            zc = zc < 0 ? zc + g.nz : zc - g.nz;
+        }
+        p_tma_prefetch_4d(&tm, pfx, pfy, zc, 0);
     };
     // geometry word of this thread's box cell on plane p (class CLS_OUTSIDE
     // beyond the box or a closed z face)
@@ -191,8 +215,10 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0)
+    if (tid == 0) {
         for (int p = z0 - 1; p <= z1 && p < z0 - 1 + NS; ++p) issue(p);
+        for (int p = z0 - 1 + NS; p < z0 - 1 + NS + pf; ++p) prefetch(p);
+    }
 
     // geometry words of planes z0 - 1 .. z0 + 1, then one plane further per
     // iteration; the adhesion and non-wetting bounce words of an interior cell a
@@ -233,6 +259,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         if (tid == 0 && z + NS - 1 <= z1) {
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             issue(z + NS - 1);  // into the stage of plane z - 1, read by everyone before the barrier
+            if (pf > 0) prefetch(z + NS - 1 + pf);
         }
         w_0 = w_1;
         w_1 = w_2;
@@ -456,11 +483,12 @@ cudaError_t configure_push() {
 
 template <int BY, int NS, int MINB, bool TAU1>
 cudaError_t launch_push_shape(const CUtensorMap& tm, float2* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
-                              const uint32_t* adh, const Geom& g, const Phys& p, int lz, int* err, cudaStream_t s) {
+                              const uint32_t* adh, const Geom& g, const Phys& p, int lz, int pf, int* err,
+                              cudaStream_t s) {
     constexpr int TY = BY - 2;
     const dim3 grid((g.nx + PXI - 1) / PXI, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
     sc_step_push_kernel<BY, NS, MINB, TAU1><<<grid, dim3(PX, BY), push_smem_bytes<BY, NS>(), s>>>(
-        tm, fout, nbr, nbr_nw, adh, g, p, lz, err);
+        tm, fout, nbr, nbr_nw, adh, g, p, lz, pf, err);
     return cudaGetLastError();
 }
 
@@ -537,29 +565,29 @@ cudaError_t prepare_step_push(int shape) {
 
 cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, const uint32_t* nbr,
                              const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p, int lz,
-                             int* err, cudaStream_t s) {
-    if (lz < 1) return cudaErrorInvalidValue;
+                             int pf, int* err, cudaStream_t s) {
+    if (lz < 1 || pf < 0 || pf > PUSH_MAX_PREFETCH) return cudaErrorInvalidValue;
     float2* fo = reinterpret_cast<float2*>(fout);
     const bool t1 = tau_one(p);
     switch (shape) {
         case 0:
-            return t1 ? launch_push_shape<8, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
-                      : launch_push_shape<8, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+            return t1 ? launch_push_shape<8, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
+                      : launch_push_shape<8, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
         case 1:
-            return t1 ? launch_push_shape<6, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
-                      : launch_push_shape<6, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+            return t1 ? launch_push_shape<6, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
+                      : launch_push_shape<6, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
         case 2:
-            return t1 ? launch_push_shape<10, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
-                      : launch_push_shape<10, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+            return t1 ? launch_push_shape<10, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
+                      : launch_push_shape<10, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
         case 3:
-            return t1 ? launch_push_shape<7, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
-                      : launch_push_shape<7, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+            return t1 ? launch_push_shape<7, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
+                      : launch_push_shape<7, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
         case 4:
-            return t1 ? launch_push_shape<10, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
-                      : launch_push_shape<10, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+            return t1 ? launch_push_shape<10, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
+                      : launch_push_shape<10, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
         case 5:
-            return t1 ? launch_push_shape<12, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s)
-                      : launch_push_shape<12, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, err, s);
+            return t1 ? launch_push_shape<12, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
+                      : launch_push_shape<12, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
     }
     return cudaErrorInvalidValue;
 }

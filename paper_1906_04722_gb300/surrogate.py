@@ -40,8 +40,9 @@ def surrogate_inputs(triples, theta: float):
 
 
 def throat_incircle(triples) -> np.ndarray:
-    """Inscribed-circle radius of each throat (lbm_throat_incircle; -1 where the
-    spheres close the throat)."""
+    """Inscribed-circle radius of each throat (lbm_throat_incircle): the largest
+    clearance over the triangle of the three centres, 0 where the spheres close
+    the throat."""
     return lbm_throat_incircle(triples)
 
 

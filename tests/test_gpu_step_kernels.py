@@ -278,10 +278,11 @@ def test_bounded_wait_gives_up_and_reports(lbm):
 
 
 # ------------------------------------------------------- paired push kernel
-def _push_run(lbm, flags, rho0, steps, shape, lz):
+def _push_run(lbm, flags, rho0, steps, shape, lz, prefetch=0):
     nz, ny, nx = SHAPE
     dom = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
     dom.set_push_shape(shape, lz)
+    dom.set_push_prefetch(prefetch)
     assert dom.step_kernel() == (lbm.KERNEL_PUSH, lz)
     dom.set_densities(rho0)
     if not flags.get("periodic"):
@@ -290,16 +291,18 @@ def _push_run(lbm, flags, rho0, steps, shape, lz):
     return dom
 
 
-@pytest.mark.parametrize("shape,lz", [(0, 13), (1, 7), (1, 45), (2, 16), (3, 11), (4, 9), (5, 20), (0, 5)])
+@pytest.mark.parametrize("shape,lz,prefetch", [(0, 13, 0), (1, 7, 2), (1, 45, 4), (2, 16, 1), (3, 11, 2), (4, 9, 3),
+                                               (5, 20, 0), (0, 5, 2)])
 @pytest.mark.parametrize("periodic_z", [0, 1])
-def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, periodic_z):
+def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, prefetch, periodic_z):
     """The push kernel reads each cell's own populations and streams at the
     store, the staged kernel pulls; both sum the densities in the same order and
     share the collision, so after 60 steps the states (read back in the pull
     layout) are the same bit for bit -- every shape, ragged x, y and z tiles,
-    reservoirs and a membrane (closed z) or a wrapped z axis."""
+    reservoirs and a membrane (closed z) or a wrapped z axis, with and without
+    the L2 prefetch (a hint that changes nothing)."""
     flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
-    a = _push_run(lbm, flags, rho0, 60, shape, lz).state()[0]
+    a = _push_run(lbm, flags, rho0, 60, shape, lz, prefetch).state()[0]
     b = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED).state()[0]
     assert np.array_equal(a, b)
 
@@ -356,5 +359,8 @@ def test_push_kernel_applicability(lbm):
     d3 = lbm.Domain(_params(lbm), SPHERES, (nx, ny, nz))
     with pytest.raises(lbm.LbmError):
         d3.set_push_shape(lbm.PUSH_SHAPES)
+    for bad in (-1, 5):
+        with pytest.raises(lbm.LbmError):
+            d3.set_push_prefetch(bad)
     d3.set_step_kernel(lbm.KERNEL_PUSH, 9)
     assert d3.step_kernel() == (lbm.KERNEL_PUSH, 9)

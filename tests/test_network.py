@@ -11,6 +11,12 @@
 * The throat incircle follows Descartes' theorem for touching circles, the
   closed form of three equal circles on an equilateral triangle, and a search
   for the largest circle between the sphere sections.
+* The Mayer-Stowe-Princen terms (non-wetting area, meniscus and grain-contact
+  lengths) follow the closed form of three touching equal circles at zero
+  contact angle and, at other contact angles and arrangements (unequal radii,
+  gaps, a meniscus disc reaching over a wall), a brute-force raster of the same
+  construction (oracle/pn.py); the MS-P radius likewise, and it lies below the
+  incircle at zero contact angle.
 """
 import math
 
@@ -272,3 +278,113 @@ def test_packing_throats_are_shared_facets(lbm):
         got = lbm.lbm_packing_throats(sp, 64.0)
         assert {tuple(x) for x in got.tolist()} == want
         assert [tuple(x) for x in got.tolist()] == sorted(want)
+
+
+# --------------------------------------------------------------- MS-P estimate
+def _touching_terms(R, r, cos_t=1.0):
+    """Three equal circles of radius R touching on an equilateral triangle.  A
+    corner meniscus cuts both circles at the contact angle: its centre V lies at
+    rho = sqrt(R^2 + r^2 + 2 R r cos(theta)) from both centres, above the touching
+    point T0; it meets circle i at polar angle alpha = phi - delta (phi the
+    direction of V, cos(delta) = (R^2 + rho^2 - r^2) / (2 R rho)).  The wet
+    corner is the triangle (T0, P_j, P_i) minus the two grain segments of angle
+    alpha and the meniscus segment of angle gamma (chord |P_i P_j|)."""
+    rho = math.sqrt(R * R + r * r + 2 * R * r * cos_t)
+    phi = math.atan2(math.sqrt(rho * rho - R * R), R)
+    alpha = phi - math.acos(min(1.0, (R * R + rho * rho - r * r) / (2 * R * rho)))
+    gamma = 2 * math.asin(R * (1 - math.cos(alpha)) / r)
+    wet = (R * R * (1 - math.cos(alpha)) * math.sin(alpha) - R * R * (alpha - math.sin(alpha))
+           - 0.5 * r * r * (gamma - math.sin(gamma)))
+    a_nw = (math.sqrt(3) - math.pi / 2) * R * R - 3 * wet
+    return a_nw, 3 * r * gamma, 3 * R * (math.pi / 3 - 2 * alpha)
+
+
+_TOUCH = np.array([[0, 0, 0, 1.0], [2, 0, 0, 1.0], [1, math.sqrt(3), 0, 1.0]])
+
+
+@pytest.mark.parametrize("r", [0.01, 0.05, 0.1, 0.14])
+@pytest.mark.parametrize("cos_t", [1.0, math.cos(math.radians(30)), math.cos(math.radians(50))])
+def test_msp_terms_touching_closed_form(lbm, r, cos_t):
+    got = lbm.lbm_throat_msp_terms(_TOUCH * 7.5, r * 7.5, cos_t)  # any scale
+    want = _touching_terms(7.5, r * 7.5, cos_t)
+    for g, w in zip(got, want):
+        assert abs(g - w) <= 1e-9 * max(1.0, abs(w))
+
+
+def test_msp_radius_touching_closed_form(lbm):
+    """The root of A_nw = r (L_nw + L_ns cos(theta)) of the closed form
+    (bisection here) against lbm_throat_pce_msp with sigma = 1."""
+    for cos_t in (1.0, math.cos(math.radians(40))):
+        lo, hi = 1e-6, 2 / math.sqrt(3) - 1
+        for _ in range(100):
+            mid = 0.5 * (lo + hi)
+            a, lnw, lns = _touching_terms(1.0, mid, cos_t)
+            lo, hi = (mid, hi) if a - mid * (lnw + lns * cos_t) > 0 else (lo, mid)
+        r_star = 0.5 * (lo + hi)
+        assert abs(1.0 / lbm.lbm_throat_pce_msp(_TOUCH, 1.0, cos_t)[0] - r_star) <= 1e-9
+
+
+def test_msp_raster_oracle_touching_closed_form():
+    """The brute-force raster of oracle/pn.py against the closed form of
+    touching circles at 50 degrees (where its meniscus band is well posed)."""
+    from oracle import pn
+    ct = math.cos(math.radians(50))
+    for r in (0.05, 0.12):
+        want = _touching_terms(1.0, r, ct)
+        got = pn.msp_terms_raster(_TOUCH, r, ct, 0.002)
+        assert abs(got[0] - want[0]) <= 0.01 * want[0]
+        assert abs(got[1] - want[1]) <= 0.04 * want[1]
+        assert abs(got[2] - want[2]) <= 0.015 * want[2]
+
+
+# (throat, cos theta, r): unequal radii; gaps on every edge; a wall corner where
+# the meniscus disc reaches over the edge and leaves two slivers; the same edge
+# with the disc covering both grains' edge points (a dry corner)
+_RASTER_CASES = [
+    (np.array([[0, 0, 0, 1.0], [2.3, 0.2, 0.1, 0.8], [0.9, 2.1, -0.2, 1.2]]), 0.7, 0.1),
+    (np.array([[0, 0, 0, 1.0], [2.3, 0.2, 0.1, 0.8], [0.9, 2.1, -0.2, 1.2]]), 0.7, 0.2),
+    (np.array([[0, 0, 0, 1.0], [2.2, 0, 0, 1.0], [1.1, 2.2 * math.sqrt(3) / 2, 0, 1.0]]), 0.8, 0.2),
+    (np.array([[0, 0, 0, 1.0], [2.6, 0, 0, 1.0], [1.3, 2.8, 0, 1.0]]), 0.5, 0.65),
+    (np.array([[0, 0, 0, 1.0], [2.6, 0, 0, 1.0], [1.3, 2.8, 0, 1.0]]), 0.5, 0.5),
+]
+
+
+@pytest.mark.parametrize("case", range(len(_RASTER_CASES)))
+def test_msp_terms_match_raster(lbm, case):
+    """Exact terms against the pixel count of the same construction (h = 0.002
+    on unit radii): area within 1 %, grain contact within 1.5 %, menisci within
+    4 % or 0.02 (the raster's level-set band)."""
+    from oracle import pn
+    th, ct, r = _RASTER_CASES[case]
+    a, lnw, lns = lbm.lbm_throat_msp_terms(th, r, ct)
+    ra, rlnw, rlns = pn.msp_terms_raster(th, r, ct, 0.002)
+    assert abs(a - ra) <= 0.01 * ra
+    assert abs(lns - rlns) <= 0.015 * rlns
+    assert abs(lnw - rlnw) <= max(0.04 * rlnw, 0.02)
+
+
+def test_msp_radius_matches_raster(lbm):
+    from oracle import pn
+    th, ct = _RASTER_CASES[0][0], 0.7
+    r_exact = 1.0 / lbm.lbm_throat_pce_msp(th, 1.0, ct)[0]
+    r_raster = pn.msp_radius_raster(th, ct, 0.003, 2 * lbm.lbm_throat_incircle(th)[0])
+    assert abs(r_exact - r_raster) <= 0.02 * r_raster
+
+
+def test_msp_packing_below_incircle_and_closed(lbm):
+    """On every throat of a packing the zero-contact-angle MS-P meniscus is no
+    wider than the incircle: beyond r_i no meniscus centre is allowed.  It
+    reaches r_i only where the walls, not the grains, bound the section (the
+    non-wetting region then spills over the neutral walls and F stays positive
+    until the allowed centres run out): a few throats.  All finite; a closed
+    throat gives +inf."""
+    tri = lbm.packing_throat_sample(W.sample_spheres(192, seed=3), None, 3)
+    p = lbm.lbm_throat_pce_msp(tri, 1.0, 1.0)
+    rin = lbm.lbm_throat_incircle(tri)
+    assert np.isfinite(p).all()
+    assert (1.0 / p <= rin * (1 + 1e-9)).all()
+    assert (1.0 / p < rin * (1 - 1e-6)).mean() > 0.99
+    th = np.array([[0, 0, 0, 10.0], [12, 0, 0, 10.0], [6, 10, 0, 10.0]])
+    assert math.isinf(lbm.lbm_throat_pce_msp(th, 0.1, 1.0)[0])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_throat_pce_msp(_TOUCH, 1.0, 0.0)
