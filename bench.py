@@ -74,9 +74,16 @@ def parse():
     ap.add_argument("--surrogate-config5", action="store_true",
                     help="the throat surrogate at configuration 5's size (20 k training throats, 1e5 inference "
                          "throats of 2000-sphere packings, LBM fallback at 2 %% spread), one JSON line")
+    ap.add_argument("--train-throats", type=int, default=20000,
+                    help="--surrogate-config5: LBM training throats (whole packings until reached)")
+    ap.add_argument("--judge", type=int, default=2000,
+                    help="--surrogate-config5: inference throats the LBM judges (seeded random subset)")
+    ap.add_argument("--refine", type=int, default=1,
+                    help="--surrogate-config5: entry pressures refined to 1/N of a ladder step "
+                         "(lbm_run_throat_batch_refined) for the labels and the judge; 1 = the ladder's own")
     ap.add_argument("--shape", default="",
                     help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD, "
-                         "staged2:BY:LZ:2 or push:ROWS:LZ:STAGES[:PREFETCH]")
+                         "staged2:BY:LZ:2 or push:SHAPE:LZ[:PREFETCH] (SHAPE an lbm_set_push_shape index)")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--throat-batch", choices=["cells", "tiles", "persistent"], default="",
@@ -149,8 +156,6 @@ KERNEL_SOURCES = {
     "sc_step_tma_kernel": ("lbm_step_tma.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
     "sc_step_push_kernel": ("lbm_step_push.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
 }
-# push kernel shapes (box rows, plane stages) -> lbm_set_push_shape index, CTAs per SM
-PUSH_SHAPES = {(8, 4): (0, 1), (6, 3): (1, 2), (10, 3): (2, 1), (7, 3): (3, 2), (10, 4): (4, 1), (12, 3): (5, 1)}
 
 
 def kernel_hash(kernel_name="sc_step_kernel"):
@@ -444,11 +449,13 @@ def run_ours(args, rank, world, local):
     # domain (state restored afterwards); untimed
     if args.shape:
         f = args.shape.split(":")
-        tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
-                 {"kind": f[0], "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
-        if f[0] == "push":  # push:rows:lz:stages[:prefetch planes]
-            tuned = {"kind": "push", "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3]),
-                     "prefetch": int(f[4]) if len(f) > 4 else 0}
+        if f[0] == "push":  # push:shape:lz[:prefetch planes]
+            sh = int(f[1])
+            tuned = {"kind": "push", "shape": sh, "by": lbm.PUSH_SHAPE_TABLE[sh][0], "lz": int(f[2]),
+                     "lead": lbm.PUSH_SHAPE_TABLE[sh][1], "prefetch": int(f[3]) if len(f) > 3 else 0}
+        else:
+            tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
+                     {"kind": f[0], "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
     else:
         tuned = dom.autotune(trial_steps=20) if not args.no_tune else None
 
@@ -456,7 +463,7 @@ def run_ours(args, rank, world, local):
         if tuned is None:
             return
         if tuned["kind"] == "push":
-            d.set_push_shape(PUSH_SHAPES[(tuned["by"], tuned["lead"])][0], tuned["lz"])
+            d.set_push_shape(tuned["shape"], tuned["lz"])
             d.set_push_prefetch(tuned.get("prefetch", 0))
         elif tuned["kind"] == "tma":
             d.set_step_kernel(lbm.KERNEL_TMA, tuned["lz"])
@@ -475,9 +482,9 @@ def run_ours(args, rank, world, local):
         by, _, lead = lbm.lbm_get_tile(dom.h)
         kernel_name = "sc_step16_kernel<%s,%d,%d>" % ("half2" if args.precision == 1 else "bfloat162", by, lead)
     elif kind == lbm.KERNEL_PUSH:
-        rows, stages = tuned["by"], tuned["lead"]
-        kernel_name = "sc_step_push_kernel<%d,%d,%d,%s>" % (rows, stages, PUSH_SHAPES[(rows, stages)][1],
-                                                             "true" if tuple(W.TAU) == (1.0, 1.0) else "false")
+        rows, stages, ctas, resident = lbm.PUSH_SHAPE_TABLE[tuned["shape"]]
+        kernel_name = "sc_step_push_kernel<%d,%d,%d,%s,%s>" % (
+            rows, stages, ctas, "true" if tuple(W.TAU) == (1.0, 1.0) else "false", "true" if resident else "false")
     elif kind == lbm.KERNEL_TMA:
         kernel_name = "sc_step_tma_kernel"
     elif kind == lbm.KERNEL_SPLIT:
@@ -666,10 +673,13 @@ def run_pore_network(args):
     tl = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res, _ = lbm.lbm_run_throat_batch(tri, tparams, tl, args.throat_steps, W.RHO_MAJOR)
+    if args.refine > 1:
+        _, _, pce_lbm = lbm.lbm_run_throat_batch_refined(tri, tparams, tl, args.throat_steps, W.RHO_MAJOR, args.refine)
+    else:
+        res, _ = lbm.lbm_run_throat_batch(tri, tparams, tl, args.throat_steps, W.RHO_MAJOR)
+        pce_lbm = np.array([r["p_ce"] for r in res])
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
-    pce_lbm = np.array([r["p_ce"] for r in res])
     sigma, drops = laplace_sigma(lbm, W)
     from paper_1906_04722_gb300 import surrogate as S
     cos_t = math.cos(S.contact_angle_estimate(W.G_ADS[0], W.G_ADS[1], W.G_COHESION, W.RHO_MAJOR, W.RHO_MINOR))
@@ -697,7 +707,8 @@ def run_pore_network(args):
     print(json.dumps({
         "workload": f"sample{args.size}: full LBM drainage 20 x {args.pn_steps} steps vs pore-network drainage "
                     f"on its regular triangulation ({len(tets)} pores, {int(inner.sum())} interior throats); "
-                    f"throat ladders 32 x {args.throat_steps} steps",
+                    f"throat ladders 32 x {args.throat_steps} steps"
+                    + (f", p_c^e refined to 1/{args.refine} of a ladder step" if args.refine > 1 else ""),
         "seconds": {"full_lbm": t_full, "network_build": t_net, "throat_batch": t_batch,
                     "total": time.perf_counter() - t_all},
         "throats": {"n": int(inner.sum()), "invaded_in_ladder": int(np.isfinite(pce_lbm).sum()),
@@ -723,9 +734,11 @@ def run_surrogate_config5(args):
     throats the batched LBM ran (facets of the regular triangulations of seeded
     300-sphere packings), then asked for 1e5 throats of four seeded 2000-sphere
     packings, the batched LBM taking the throats whose ensemble spread exceeds
-    2 %.  The LBM judges a seeded random subset of 2000 of the 1e5 throats (all
-    of them would take about 5 min of GPU time); the fallback's cost for all
-    1e5 is its measured rate on that subset's fallback throats."""
+    2 %.  The LBM judges a seeded random subset of the 1e5 throats (--judge,
+    2000 by default: all of them would take about 5 min of GPU time at 100
+    steps per increment); the fallback's cost for all 1e5 is its measured rate
+    on that subset's fallback throats.  --train-throats, --throat-steps and
+    --refine set the training size, the schedule and the label resolution."""
     import torch
     import paper_1906_04722_gb300 as lbm
     from paper_1906_04722_gb300 import surrogate as S
@@ -736,14 +749,27 @@ def run_surrogate_config5(args):
     theta = S.contact_angle_estimate(W.G_ADS[0], W.G_ADS[1], W.G_COHESION, W.RHO_MAJOR, W.RHO_MINOR)
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
     n_steps = args.throat_steps
-    out = {"workload": "configuration 5: 20 k training throats of seeded 300-sphere 192^3 packings; 1e5 throats of "
-                       "four seeded 2000-sphere 361^3 packings; 32 increments x %d steps; 5 members, 4 x 256, "
-                       "BF16 operands; fallback at 2 %% ensemble spread" % n_steps}
+    refine = max(1, args.refine)
+
+    def lbm_pce(th):
+        """(results, rows) of the batch; p_ce refined when asked."""
+        if refine == 1:
+            return lbm.lbm_run_throat_batch(th, params, ladder, n_steps, W.RHO_MAJOR)
+        res, rows, fine = lbm.lbm_run_throat_batch_refined(th, params, ladder, n_steps, W.RHO_MAJOR, refine)
+        for r, f in zip(res, fine):
+            r["p_ce"] = float(f)
+        return res, rows
+
+    out = {"workload": "configuration 5: %d training throats of seeded 300-sphere 192^3 packings; 1e5 throats of "
+                       "four seeded 2000-sphere 361^3 packings, %d judged by the LBM; 32 increments x %d steps%s; "
+                       "5 members, 4 x 256, BF16 operands; fallback at 2 %% ensemble spread"
+                       % (args.train_throats, args.judge, n_steps,
+                          "" if refine == 1 else ", p_c^e refined to 1/%d of a ladder step" % refine)}
     t0 = time.perf_counter()
     tris, ress, rowss, seed = [], [], [], 110
-    while sum(len(t) for t in tris) < 20000:
+    while sum(len(t) for t in tris) < args.train_throats:
         th = lbm.packing_throat_sample(W.sample_spheres(192, seed=seed), None, seed)
-        res, rows = lbm.lbm_run_throat_batch(th, params, ladder, n_steps, W.RHO_MAJOR)
+        res, rows = lbm_pce(th)
         tris.append(th)
         ress += res
         rowss += rows
@@ -764,15 +790,15 @@ def run_surrogate_config5(args):
     torch.cuda.synchronize()
     t_net = time.perf_counter() - t0
     fall = rel > 0.02
-    sub = np.sort(np.random.default_rng(7).choice(n, 2000, replace=False))
+    sub = np.sort(np.random.default_rng(7).choice(n, min(args.judge, n), replace=False))
     t0 = time.perf_counter()
-    truth_res, _ = lbm.lbm_run_throat_batch(inf[sub], params, ladder, n_steps, W.RHO_MAJOR)
+    truth_res, _ = lbm_pce(inf[sub])
     t_judge = time.perf_counter() - t0
     truth = np.array([r["p_ce"] for r in truth_res])
     fb = sub[fall[sub]]
     t0 = time.perf_counter()
     if len(fb):
-        lbm.lbm_run_throat_batch(inf[fb], params, ladder, n_steps, W.RHO_MAJOR)
+        lbm_pce(inf[fb])
     t_fb_sub = time.perf_counter() - t0
     rate_fb = len(fb) / t_fb_sub if len(fb) else float("inf")
     t_fb_all = float(fall.sum()) / rate_fb if len(fb) else 0.0
@@ -781,7 +807,7 @@ def run_surrogate_config5(args):
     err_all = np.abs(answer[ok] - truth[ok]) / np.abs(truth[ok])
     ans_ok = ok & ~fall[sub]
     err_ans = np.abs(pce[sub][ans_ok] - truth[ans_ok]) / np.abs(truth[ans_ok])
-    plain_th = inf[sub[::63]]
+    plain_th = inf[sub[::max(1, len(sub) // 32)]]
     t0 = time.perf_counter()
     for th in plain_th:
         mask, probe = lbm.lbm_throat_geometry(th)

@@ -252,6 +252,21 @@ int lbm_throat_lattice_features(const double* throats, int n, double* out);
 int lbm_run_throat_batch(const double* throats, int n, const lbm_params* params, const lbm_schedule* sched,
                          lbm_throat_result* results, lbm_increment* rows, void* stream);
 
+/* lbm_run_throat_batch_refined -- lbm_run_throat_batch (results, rows as
+ * there), then p_c^e below the ladder step: every throat invaded at increment
+ * k >= 1 runs again with the same levels up to k - 1 (the same state, the run
+ * being deterministic) followed by n_fine equal sub-steps from level k - 1 to
+ * level k (sched->n_steps each, the ladder padded with level k to a common
+ * length), and p_ce_fine[t] is that run's p_c^e (the rule of
+ * lbm_run_drainage).  Throats invaded at increment 0 keep the coarse p_c^e, and
+ * so does a throat the second run does not invade; +inf where the first run
+ * did not invade.  n_fine = 1 returns the coarse values.  Per-throat ladders
+ * (sched->per_throat) are refined each on its own levels.  p_ce_fine: n
+ * doubles (host, caller-owned).  LBM_ERR_ARG for n_fine < 1. */
+int lbm_run_throat_batch_refined(const double* throats, int n, const lbm_params* params, const lbm_schedule* sched,
+                                 int n_fine, lbm_throat_result* results, lbm_increment* rows, double* p_ce_fine,
+                                 void* stream);
+
 /* ---------------------------------------------------------------------------
  * Pore network (Sec. 2.2.1 pore-space decomposition, Sec. 2.2.2 fluid
  * displacement, Sec. 3.1.1 drainage of the sample).  Host computations; the
@@ -591,7 +606,12 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
  *   shape  0: 8 box rows (6 interior), 4 plane stages, one CTA per SM;
  *          1: 6 rows, 3 stages, two CTAs per SM; 2: 10 rows, 3 stages, one CTA;
  *          3: 7 rows, 3 stages, two CTAs per SM; 4: 10 rows, 4 stages, one CTA;
- *          5: 12 rows, 3 stages, one CTA.
+ *          5: 12 rows, 3 stages, one CTA;
+ *          6 .. 11 keep each cell's populations in registers from the density
+ *          pass to the collision, so that every stage holds a load in flight:
+ *          6: 6 rows, 3 stages, two CTAs; 7: 10 rows, 4 stages, one CTA;
+ *          8: 12 rows, 3 stages, one CTA; 9: 5 rows, 4 stages, two CTAs;
+ *          10: 8 rows, 4 stages, one CTA; 11: 7 rows, 3 stages, two CTAs.
  *          A CTA of 32 x rows threads advances 28 x (rows - 2) columns.
  *   lz     planes per CTA z segment (lz <= 0: a default for the box).
  * Results do not depend on the shape (bit for bit); with tau = 1 in both
@@ -630,6 +650,7 @@ typedef struct {
     double ms_per_step; /* its measured time per step */
     int n_candidates;   /* shapes timed */
     int prefetch;       /* push kernel: its L2 prefetch distance in planes; else 0 */
+    int shape;          /* push kernel: its lbm_set_push_shape index; else -1 */
 } lbm_tune_result;
 int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out);
 

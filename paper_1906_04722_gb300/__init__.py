@@ -89,12 +89,14 @@ class lbm_throat_surrogate_config(ctypes.Structure):
 
 class lbm_tune_result(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("by", ctypes.c_int), ("lz", ctypes.c_int), ("lead", ctypes.c_int),
-                ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int), ("prefetch", ctypes.c_int)]
+                ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int), ("prefetch", ctypes.c_int),
+                ("shape", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"kind": {0: "staged", 1: "tma", 2: "split", 3: "staged2", 4: "push"}.get(self.kind, "?"),
                 "by": self.by, "lz": self.lz, "lead": self.lead,
-                "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates, "prefetch": self.prefetch}
+                "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates, "prefetch": self.prefetch,
+                "shape": self.shape}
 
 
 class lbm_surrogate_config(ctypes.Structure):
@@ -167,6 +169,10 @@ SIGNATURES = {
     "lbm_run_throat_batch": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
                                             ctypes.POINTER(lbm_schedule), ctypes.POINTER(lbm_throat_result),
                                             ctypes.POINTER(lbm_increment), _VP]),
+    "lbm_run_throat_batch_refined": (ctypes.c_int, [_DP, ctypes.c_int, ctypes.POINTER(lbm_params),
+                                                    ctypes.POINTER(lbm_schedule), ctypes.c_int,
+                                                    ctypes.POINTER(lbm_throat_result), ctypes.POINTER(lbm_increment),
+                                                    _DP, _VP]),
     "lbm_surrogate_create": (ctypes.c_int, [ctypes.POINTER(lbm_surrogate_config), _VP, ctypes.POINTER(_VP)]),
     "lbm_surrogate_num_params": (ctypes.c_int, [_VP]),
     "lbm_surrogate_get_params": (ctypes.c_int, [_VP, ctypes.c_int, _FP]),
@@ -367,7 +373,11 @@ KERNEL_TMA = 1
 KERNEL_SPLIT = 2
 KERNEL_STAGED2 = 3
 KERNEL_PUSH = 4
-PUSH_SHAPES = 6  # lbm_set_push_shape: (rows, stages) = (8, 4), (6, 3), (10, 3), (7, 3), (10, 4), (12, 3)
+# lbm_set_push_shape index -> (box rows, plane stages, CTAs per SM, pairs held in registers)
+PUSH_SHAPE_TABLE = [(8, 4, 1, False), (6, 3, 2, False), (10, 3, 1, False), (7, 3, 2, False), (10, 4, 1, False),
+                    (12, 3, 1, False), (6, 3, 2, True), (10, 4, 1, True), (12, 3, 1, True), (5, 4, 2, True),
+                    (8, 4, 1, True), (7, 3, 2, True)]
+PUSH_SHAPES = len(PUSH_SHAPE_TABLE)
 BATCH_AUTO = 0
 BATCH_PERSISTENT = 1
 BATCH_PER_STEP = 2
@@ -586,13 +596,7 @@ def lbm_throat_lattice_features(throats) -> np.ndarray:
     return out
 
 
-def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None,
-                         form: int = 0):
-    """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
-    rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr).
-    form: BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP or BATCH_CELLS."""
-    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
-    n = th.shape[0]
+def _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form):
     lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
     sch = lbm_schedule()
     if lad.ndim == 2:
@@ -606,12 +610,41 @@ def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, r
     if form not in (BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS):
         raise ValueError("form must be BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP or BATCH_CELLS")
     sch.batch_form = int(form)
+    return sch, lad
+
+
+def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None,
+                         form: int = 0):
+    """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
+    rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr).
+    form: BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP or BATCH_CELLS."""
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
+    n = th.shape[0]
+    sch, _lad = _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form)
     res = (lbm_throat_result * n)()
     rows = (lbm_increment * (n * sch.n_incr))()
     _check(load().lbm_run_throat_batch(th.ctypes.data_as(_DP), n, ctypes.byref(params), ctypes.byref(sch), res, rows,
                                        stream if stream is not None else _torch_stream()), "lbm_run_throat_batch")
     I = sch.n_incr
     return [r.as_dict() for r in res], [[rows[t * I + i].as_dict() for i in range(I)] for t in range(n)]
+
+
+def lbm_run_throat_batch_refined(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float,
+                                 n_fine: int, stream=None, form: int = 0):
+    """lbm_run_throat_batch plus the entry pressures refined to 1 / n_fine of a
+    ladder step; returns (results, rows, p_ce_fine array)."""
+    th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
+    n = th.shape[0]
+    sch, _lad = _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form)
+    res = (lbm_throat_result * n)()
+    rows = (lbm_increment * (n * sch.n_incr))()
+    fine = np.empty(n)
+    _check(load().lbm_run_throat_batch_refined(th.ctypes.data_as(_DP), n, ctypes.byref(params), ctypes.byref(sch),
+                                               int(n_fine), res, rows, fine.ctypes.data_as(_DP),
+                                               stream if stream is not None else _torch_stream()),
+           "lbm_run_throat_batch_refined")
+    I = sch.n_incr
+    return [r.as_dict() for r in res], [[rows[t * I + i].as_dict() for i in range(I)] for t in range(n)], fine
 
 
 def lbm_destroy(h):

@@ -897,6 +897,7 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
         out->ms_per_step = best;
         out->n_candidates = (int)cand.size();
         out->prefetch = best_t.kind == LBM_KERNEL_PUSH ? best_t.push_pf : 0;
+        out->shape = best_t.kind == LBM_KERNEL_PUSH ? best_t.push_shape : -1;
     }
     return LBM_OK;
 }

@@ -163,6 +163,8 @@ constexpr int PUSH_MAX_PREFETCH = 4;
 int push_shape_count();
 int push_shape_rows(int shape);
 int push_shape_stages(int shape);
+int push_shape_ctas(int shape);
+bool push_shape_resident(int shape);
 bool push_step_applicable(const Geom& g);
 int push_default_lz(const Geom& g, int shape);
 cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtensorMap (&maps)[2]);

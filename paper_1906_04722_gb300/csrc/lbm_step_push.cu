@@ -122,7 +122,11 @@ constexpr size_t push_smem_bytes() {
     return (size_t)NS * stage_bytes<BY>() + sizeof(float2) * 4 * BY * PX + sizeof(uint64_t) * NS;
 }
 
-template <int BY, int NS, int MINB, bool TAU1>
+// RR: each interior thread keeps its cell's 19 pairs in registers from the
+// density pass to its collision a plane later, so that a stage is free for the
+// next load as soon as every thread has summed its densities (all NS stages in
+// flight instead of NS - 2; populations read from shared memory once).
+template <int BY, int NS, int MINB, bool TAU1, bool RR>
 __global__ void __launch_bounds__(PX * BY, MINB)
     sc_step_push_kernel(const __grid_constant__ CUtensorMap tm, float2* __restrict__ fout,
                         const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
@@ -191,7 +195,8 @@ __global__ void __launch_bounds__(PX * BY, MINB)
     // the two densities of this thread's box cell on plane p (geometry word wp)
     // into the ring: 0 where a component is not fluid, whatever the slots hold
     // (a buffer's grain slots may hold another layout's values)
-    auto publish = [&](int p, uint32_t wp) {
+    // (RR: the interior threads keep the pairs in `keep`)
+    auto publish = [&](int p, uint32_t wp, float (&keep)[2][Q]) {
         float2 r = make_float2(0.f, 0.f);
         const uint32_t c = (wp >> CLS_SHIFT) & CLS_MASK;
         if (c != CLS_SOLID && c != CLS_OUTSIDE) {
@@ -202,6 +207,10 @@ __global__ void __launch_bounds__(PX * BY, MINB)
                 const float2 v = st[k * NT];
                 a[k & 3] += v.x;
                 b[k & 3] += v.y;
+                if constexpr (RR) {
+                    keep[0][k] = v.x;
+                    keep[1][k] = v.y;
+                }
             }
             r.x = (a[0] + a[1]) + (a[2] + a[3]);
             if (c != CLS_MEMBRANE) r.y = (b[0] + b[1]) + (b[2] + b[3]);
@@ -215,9 +224,10 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     __syncthreads();
+    int next = z0 - 1 + min(NS, z1 - z0 + 2);  // the first plane not yet issued (thread 0)
     if (tid == 0) {
-        for (int p = z0 - 1; p <= z1 && p < z0 - 1 + NS; ++p) issue(p);
-        for (int p = z0 - 1 + NS; p < z0 - 1 + NS + pf; ++p) prefetch(p);
+        for (int p = z0 - 1; p < next; ++p) issue(p);
+        for (int p = next; p < next + pf; ++p) prefetch(p);
     }
 
     // geometry words of planes z0 - 1 .. z0 + 1, then one plane further per
@@ -235,31 +245,36 @@ __global__ void __launch_bounds__(PX * BY, MINB)
     uint32_t a_0, nwb_0;
     extra(z0, w_0, a_0, nwb_0);
 
+    float fc[2][Q], fn[2][Q];  // RR: pairs of the plane to collide and of the next plane
     bool ok = p_mbar_wait_bounded(bar + slot(z0 - 1), parity(z0 - 1));
-    if (ok) publish(z0 - 1, w_m);
+    if (ok) publish(z0 - 1, w_m, fn);
     ok = ok && p_mbar_wait_bounded(bar + slot(z0), parity(z0));
-    if (ok) publish(z0, w_0);
+    if (ok) publish(z0, w_0, fc);
     // a failed wait here is reported by the first iteration's barrier below
     for (int z = z0; z < z1; ++z) {
         const uint32_t w = w_0, a = a_0, nwb = nwb_0;
         const uint32_t w_2 = word(z + 2);  // for the next iteration's publish
         extra(z + 1, w_1, a_0, nwb_0);     // for the next iteration's collision
         const bool okz = ok && p_mbar_wait_bounded(bar + slot(z + 1), parity(z + 1));
-        if (okz) publish(z + 1, w_1);
+        if (okz) publish(z + 1, w_1, fn);
         if (__syncthreads_or(!okz)) {
             if (tid == 0) {
                 atomicOr(err, 1);
                 // bounded waits for every copy still in flight
-                for (int p = max(z0 - 1, z - 1); p <= z1 && p < z - 1 + NS; ++p)
-                    p_mbar_wait_bounded(bar + slot(p), parity(p));
+                for (int p = max(z0 - 1, z - 1); p < next; ++p) p_mbar_wait_bounded(bar + slot(p), parity(p));
             }
             __syncthreads();
             return;
         }
-        if (tid == 0 && z + NS - 1 <= z1) {
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            issue(z + NS - 1);  // into the stage of plane z - 1, read by everyone before the barrier
-            if (pf > 0) prefetch(z + NS - 1 + pf);
+        if (tid == 0) {
+            // stages read by everyone before the barrier: RR frees the stages of
+            // planes up to z + 1, the other form those up to z - 1
+            const int last = RR ? z + 1 + NS : z + NS - 1;
+            if (next <= z1 && next <= last) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            for (; next <= z1 && next <= last; ++next) {
+                issue(next);
+                if (pf > 0) prefetch(next + pf);
+            }
         }
         w_0 = w_1;
         w_1 = w_2;
@@ -267,12 +282,17 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE) {
             const float2* st = stages + (size_t)slot(z) * (Q * NT) + tid;
             float f[2][Q];
-#pragma unroll
             const bool has_nw = cls != CLS_MEMBRANE;
+#pragma unroll
             for (int k = 0; k < Q; ++k) {
-                const float2 v = st[k * NT];
-                f[0][k] = v.x;
-                f[1][k] = has_nw ? v.y : 0.f;
+                if constexpr (RR) {
+                    f[0][k] = fc[0][k];
+                    f[1][k] = has_nw ? fc[1][k] : 0.f;
+                } else {
+                    const float2 v = st[k * NT];
+                    f[0][k] = v.x;
+                    f[1][k] = has_nw ? v.y : 0.f;
+                }
             }
             float o[2][Q];
             collide_core<TAU1>(
@@ -308,6 +328,13 @@ __global__ void __launch_bounds__(PX * BY, MINB)
                 fout[cell] = make_float2(o[0][0], o[1][0]);
 #pragma unroll
                 for (int k = 1; k < Q; ++k) fout[dst(k, pw)] = make_float2(o[0][k], o[1][k]);
+            }
+        }
+        if constexpr (RR) {
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                fc[0][k] = fn[0][k];
+                fc[1][k] = fn[1][k];
             }
         }
     }
@@ -465,7 +492,7 @@ PushEncodeFn push_encode_fn() {
     return fn;
 }
 
-template <int BY, int NS, int MINB, bool TAU1>
+template <int BY, int NS, int MINB, bool TAU1, bool RR>
 cudaError_t configure_push() {
     static unsigned long long configured = 0;  // one bit per device: the attribute is per device
     int dev = 0;
@@ -473,7 +500,7 @@ cudaError_t configure_push() {
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured & bit)) {
-        e = cudaFuncSetAttribute(sc_step_push_kernel<BY, NS, MINB, TAU1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sc_step_push_kernel<BY, NS, MINB, TAU1, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)push_smem_bytes<BY, NS>());
         if (e != cudaSuccess) return e;
         configured |= bit;
@@ -481,13 +508,13 @@ cudaError_t configure_push() {
     return cudaSuccess;
 }
 
-template <int BY, int NS, int MINB, bool TAU1>
+template <int BY, int NS, int MINB, bool TAU1, bool RR>
 cudaError_t launch_push_shape(const CUtensorMap& tm, float2* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
                               const uint32_t* adh, const Geom& g, const Phys& p, int lz, int pf, int* err,
                               cudaStream_t s) {
     constexpr int TY = BY - 2;
     const dim3 grid((g.nx + PXI - 1) / PXI, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
-    sc_step_push_kernel<BY, NS, MINB, TAU1><<<grid, dim3(PX, BY), push_smem_bytes<BY, NS>(), s>>>(
+    sc_step_push_kernel<BY, NS, MINB, TAU1, RR><<<grid, dim3(PX, BY), push_smem_bytes<BY, NS>(), s>>>(
         tm, fout, nbr, nbr_nw, adh, g, p, lz, pf, err);
     return cudaGetLastError();
 }
@@ -495,13 +522,35 @@ cudaError_t launch_push_shape(const CUtensorMap& tm, float2* fout, const uint32_
 // tau = 1 in both components selects the compile-time tau = 1 collision
 bool tau_one(const Phys& p) { return p.tau[0] == 1.0f && p.tau[1] == 1.0f; }
 
+// Shapes of the push kernel by index: box rows BY, plane stages NS, CTAs per SM
+// (MINB, which also caps the registers a thread), register-resident pairs (RR).
+struct PushShapeInfo {
+    int by, ns, minb;
+    bool rr;
+};
+constexpr PushShapeInfo kPushShapes[] = {
+    {8, 4, 1, false}, {6, 3, 2, false}, {10, 3, 1, false}, {7, 3, 2, false}, {10, 4, 1, false}, {12, 3, 1, false},
+    {6, 3, 2, true},  {10, 4, 1, true}, {12, 3, 1, true},  {5, 4, 2, true},  {8, 4, 1, true},  {7, 3, 2, true},
+};
+constexpr int N_PUSH_SHAPES = (int)(sizeof(kPushShapes) / sizeof(kPushShapes[0]));
+
+template <int I>
+cudaError_t configure_shape() {
+    constexpr PushShapeInfo S = kPushShapes[I];
+    cudaError_t e = configure_push<S.by, S.ns, S.minb, false, S.rr>();
+    return e == cudaSuccess ? configure_push<S.by, S.ns, S.minb, true, S.rr>() : e;
+}
+
+template <int I>
+cudaError_t launch_shape(bool t1, const CUtensorMap& tm, float2* fo, const uint32_t* nbr, const uint32_t* nbr_nw,
+                         const uint32_t* adh, const Geom& g, const Phys& p, int lz, int pf, int* err, cudaStream_t s) {
+    constexpr PushShapeInfo S = kPushShapes[I];
+    return t1 ? launch_push_shape<S.by, S.ns, S.minb, true, S.rr>(tm, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
+              : launch_push_shape<S.by, S.ns, S.minb, false, S.rr>(tm, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+}
+
 }  // namespace
 
-// Shapes of the push kernel: (rows BY, stages NS, CTAs per SM) by index.
-//   0: 8 rows, 4 stages, 1 CTA    1: 6 rows, 3 stages, 2 CTAs    2: 10 rows, 3 stages, 1 CTA
-//   3: 7 rows, 3 stages, 2 CTAs (at most 144 registers a thread)
-//   4: 10 rows, 4 stages, 1 CTA   5: 12 rows, 3 stages, 1 CTA
-constexpr int N_PUSH_SHAPES = 6;
 int push_shape_count() { return N_PUSH_SHAPES; }
 
 bool push_step_applicable(const Geom& g) { return !g.px && !g.py && g.nx % 2 == 0; }
@@ -524,15 +573,13 @@ cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtens
     return cudaSuccess;
 }
 
-int push_shape_rows(int shape) {
-    static const int rows[N_PUSH_SHAPES] = {8, 6, 10, 7, 10, 12};
-    return (shape >= 0 && shape < N_PUSH_SHAPES) ? rows[shape] : 0;
-}
+int push_shape_rows(int shape) { return (shape >= 0 && shape < N_PUSH_SHAPES) ? kPushShapes[shape].by : 0; }
 
-int push_shape_stages(int shape) {
-    static const int stages[N_PUSH_SHAPES] = {4, 3, 3, 3, 4, 3};
-    return (shape >= 0 && shape < N_PUSH_SHAPES) ? stages[shape] : 0;
-}
+int push_shape_stages(int shape) { return (shape >= 0 && shape < N_PUSH_SHAPES) ? kPushShapes[shape].ns : 0; }
+
+int push_shape_ctas(int shape) { return (shape >= 0 && shape < N_PUSH_SHAPES) ? kPushShapes[shape].minb : 0; }
+
+bool push_shape_resident(int shape) { return shape >= 0 && shape < N_PUSH_SHAPES && kPushShapes[shape].rr; }
 
 int push_default_lz(const Geom& g, int shape) {
     // Short z segments keep neighbouring tiles on the same planes, so that the
@@ -551,14 +598,20 @@ int push_default_lz(const Geom& g, int shape) {
 }
 
 cudaError_t prepare_step_push(int shape) {
-    cudaError_t e = cudaSuccess;
+    static_assert(N_PUSH_SHAPES == 12, "one case per shape below");
     switch (shape) {
-        case 0: e = configure_push<8, 4, 1, false>(); if (e == cudaSuccess) e = configure_push<8, 4, 1, true>(); return e;
-        case 1: e = configure_push<6, 3, 2, false>(); if (e == cudaSuccess) e = configure_push<6, 3, 2, true>(); return e;
-        case 2: e = configure_push<10, 3, 1, false>(); if (e == cudaSuccess) e = configure_push<10, 3, 1, true>(); return e;
-        case 3: e = configure_push<7, 3, 2, false>(); if (e == cudaSuccess) e = configure_push<7, 3, 2, true>(); return e;
-        case 4: e = configure_push<10, 4, 1, false>(); if (e == cudaSuccess) e = configure_push<10, 4, 1, true>(); return e;
-        case 5: e = configure_push<12, 3, 1, false>(); if (e == cudaSuccess) e = configure_push<12, 3, 1, true>(); return e;
+        case 0: return configure_shape<0>();
+        case 1: return configure_shape<1>();
+        case 2: return configure_shape<2>();
+        case 3: return configure_shape<3>();
+        case 4: return configure_shape<4>();
+        case 5: return configure_shape<5>();
+        case 6: return configure_shape<6>();
+        case 7: return configure_shape<7>();
+        case 8: return configure_shape<8>();
+        case 9: return configure_shape<9>();
+        case 10: return configure_shape<10>();
+        case 11: return configure_shape<11>();
     }
     return cudaErrorInvalidValue;
 }
@@ -570,24 +623,18 @@ cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, c
     float2* fo = reinterpret_cast<float2*>(fout);
     const bool t1 = tau_one(p);
     switch (shape) {
-        case 0:
-            return t1 ? launch_push_shape<8, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
-                      : launch_push_shape<8, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 1:
-            return t1 ? launch_push_shape<6, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
-                      : launch_push_shape<6, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 2:
-            return t1 ? launch_push_shape<10, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
-                      : launch_push_shape<10, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 3:
-            return t1 ? launch_push_shape<7, 3, 2, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
-                      : launch_push_shape<7, 3, 2, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 4:
-            return t1 ? launch_push_shape<10, 4, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
-                      : launch_push_shape<10, 4, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 5:
-            return t1 ? launch_push_shape<12, 3, 1, true>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
-                      : launch_push_shape<12, 3, 1, false>(tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 0: return launch_shape<0>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 1: return launch_shape<1>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 2: return launch_shape<2>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 3: return launch_shape<3>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 4: return launch_shape<4>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 5: return launch_shape<5>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 6: return launch_shape<6>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 7: return launch_shape<7>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 8: return launch_shape<8>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 9: return launch_shape<9>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 10: return launch_shape<10>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 11: return launch_shape<11>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
     }
     return cudaErrorInvalidValue;
 }

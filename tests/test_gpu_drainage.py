@@ -225,3 +225,37 @@ def test_batch_matches_oracle(lbm, orc):
         else:
             assert math.isinf(res[t]["p_ce"])
     assert invaded >= 3, "the ladder must invade most of the test throats"
+
+
+def test_batch_refined_entry_pressure(lbm):
+    """lbm_run_throat_batch_refined: the coarse results are the plain batch's bit
+    for bit; each refined p_c^e is the p_c^e of the same throat run on its fine
+    ladder (the coarse levels up to k - 1, n_fine sub-steps to level k, padded)
+    by the plain batch, and lies at or below the coarse one; n_fine = 1 keeps
+    the coarse values."""
+    spheres = W.sample_spheres(128, seed=4)
+    throats = W.delaunay_throats(spheres, 60, seed=21)[[49, 45, 47, 1]]
+    ladder = [2.0 + 0.06 * i for i in range(12)]
+    n_steps, n_fine = 100, 4
+    res, rows = lbm.lbm_run_throat_batch(throats, _params(lbm), ladder, n_steps, W.RHO_MAJOR)
+    res2, rows2, fine = lbm.lbm_run_throat_batch_refined(throats, _params(lbm), ladder, n_steps, W.RHO_MAJOR, n_fine)
+    _rows_equal(res, rows, res2, rows2, np.tile(ladder, (len(throats), 1)))
+    ks = [r["invaded_at"] for r in res]
+    assert sum(k >= 1 for k in ks) >= 3
+    K = max(ks) + n_fine
+    lad = np.empty((len(throats), K))
+    for t, k in enumerate(ks):
+        kk = max(k, 1)
+        lad[t, :kk] = ladder[:kk]
+        a, b = ladder[kk - 1], ladder[kk]
+        lad[t, kk:kk + n_fine] = [a + (b - a) * j / n_fine for j in range(1, n_fine + 1)]
+        lad[t, kk + n_fine:] = b
+    ref, _ = lbm.lbm_run_throat_batch(throats, _params(lbm), lad, n_steps, W.RHO_MAJOR)
+    for t, k in enumerate(ks):
+        if k >= 1 and ref[t]["invaded_at"] >= 0:
+            assert fine[t] == ref[t]["p_ce"], t
+            assert fine[t] <= res[t]["p_ce"] + PC_FLOOR, t
+        else:
+            assert fine[t] == res[t]["p_ce"] or (math.isinf(fine[t]) and math.isinf(res[t]["p_ce"]))
+    _, _, same = lbm.lbm_run_throat_batch_refined(throats, _params(lbm), ladder, n_steps, W.RHO_MAJOR, 1)
+    assert np.array_equal(same, np.array([r["p_ce"] for r in res]))

@@ -224,7 +224,7 @@ def test_staged2_periodic_xy(lbm, orc):
     assert _rel_err(dom.density(), orc.density(cfg, mask, f), mask, orc) <= RTOL_RHO
 
 
-@pytest.mark.parametrize("kernel", ["staged", "tma", "split", "staged2", "push"])
+@pytest.mark.parametrize("kernel", ["staged", "tma", "split", "staged2", "push", "push_resident"])
 def test_unequal_tau_and_body_force_every_kernel(lbm, orc, kernel):
     """tau = (0.8, 1.2) with a body force (weakly damped, the most rounding
     sensitive case of the suite) for every FP32 kernel."""
@@ -242,6 +242,8 @@ def test_unequal_tau_and_body_force_every_kernel(lbm, orc, kernel):
         dom.set_step_kernel(lbm.KERNEL_STAGED2, 8)
     elif kernel == "push":
         dom.set_push_shape(1, 9)
+    elif kernel == "push_resident":
+        dom.set_push_shape(9, 7)
     dom.set_densities(rho0)
     dom.step(80)
     mask = orc.voxelise(shape, spheres)
@@ -292,7 +294,8 @@ def _push_run(lbm, flags, rho0, steps, shape, lz, prefetch=0):
 
 
 @pytest.mark.parametrize("shape,lz,prefetch", [(0, 13, 0), (1, 7, 2), (1, 45, 4), (2, 16, 1), (3, 11, 2), (4, 9, 3),
-                                               (5, 20, 0), (0, 5, 2)])
+                                               (5, 20, 0), (0, 5, 2), (6, 13, 2), (7, 9, 0), (8, 20, 1), (9, 11, 3),
+                                               (10, 7, 2), (11, 45, 0), (9, 1, 2), (6, 2, 0)])
 @pytest.mark.parametrize("periodic_z", [0, 1])
 def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, prefetch, periodic_z):
     """The push kernel reads each cell's own populations and streams at the
@@ -300,7 +303,8 @@ def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, prefetch, period
     share the collision, so after 60 steps the states (read back in the pull
     layout) are the same bit for bit -- every shape, ragged x, y and z tiles,
     reservoirs and a membrane (closed z) or a wrapped z axis, with and without
-    the L2 prefetch (a hint that changes nothing)."""
+    the L2 prefetch (a hint that changes nothing), with the pairs re-read from
+    shared memory or held in registers, down to one- and two-plane segments."""
     flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
     a = _push_run(lbm, flags, rho0, 60, shape, lz, prefetch).state()[0]
     b = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED).state()[0]
