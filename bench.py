@@ -68,7 +68,9 @@ def parse():
     ap.add_argument("--pore-network", action="store_true",
                     help="drainage of the sample by the pore network (throat entry pressures from the batched "
                          "LBM and the incircle estimate) next to the full LBM drainage, one JSON line")
-    ap.add_argument("--pn-steps", type=int, default=5000, help="full-LBM steps per increment for --pore-network")
+    ap.add_argument("--pn-steps", default="5000",
+                    help="full-LBM steps per increment for --pore-network (a comma list runs the full LBM at each; "
+                         "the network is compared with the last)")
     ap.add_argument("--throat-convergence", action="store_true",
                     help="p_c^e of 64 throats against the steps per pressure increment (100 .. 4000), one JSON line")
     ap.add_argument("--surrogate-config5", action="store_true",
@@ -650,16 +652,21 @@ def run_pore_network(args):
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
                              rho_minor=W.RHO_MINOR, reservoirs=True, membrane_layers=3)
     t_all = time.perf_counter()
-    dom = lbm.Domain(params, spheres, box)
-    mask = dom.mask()
-    dom.autotune(trial_steps=10)
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(20)]
     probe = (box[0] // 2, box[1] // 2, box[2] - 6)
-    t0 = time.perf_counter()
-    full = dom.drainage(ladder, args.pn_steps, W.RHO_MAJOR, probe)
-    torch.cuda.synchronize()
-    t_full = time.perf_counter() - t0
-    dom.close()
+    steps_list = [int(x) for x in str(args.pn_steps).split(",")]
+    fulls = {}
+    for ns in steps_list:
+        dom = lbm.Domain(params, spheres, box)
+        mask = dom.mask()
+        dom.autotune(trial_steps=10)
+        t0 = time.perf_counter()
+        fulls[ns] = dom.drainage(ladder, ns, W.RHO_MAJOR, probe)
+        torch.cuda.synchronize()
+        fulls[ns]["seconds"] = time.perf_counter() - t0
+        dom.close()
+    full = fulls[steps_list[-1]]
+    t_full = sum(f["seconds"] for f in fulls.values())
 
     t0 = time.perf_counter()
     tets = lbm.lbm_regular_triangulation(spheres)
@@ -703,9 +710,12 @@ def run_pore_network(args):
              "S_w_network_lbm_pce": float(sw_lbm[i]), "S_w_network_incircle": float(sw_inc[i]),
              "S_w_network_msp": float(sw_msp[i])}
             for i in range(len(levels))]
+    if len(steps_list) > 1:
+        for i, r in enumerate(rows):
+            r["S_w_full_lbm_by_steps"] = {str(ns): float(fulls[ns]["rows"][i]["S_w"]) for ns in steps_list}
     fin = np.isfinite(pce_lbm)
     print(json.dumps({
-        "workload": f"sample{args.size}: full LBM drainage 20 x {args.pn_steps} steps vs pore-network drainage "
+        "workload": f"sample{args.size}: full LBM drainage 20 x {steps_list[-1]} steps vs pore-network drainage "
                     f"on its regular triangulation ({len(tets)} pores, {int(inner.sum())} interior throats); "
                     f"throat ladders 32 x {args.throat_steps} steps"
                     + (f", p_c^e refined to 1/{args.refine} of a ladder step" if args.refine > 1 else ""),
