@@ -85,7 +85,7 @@ def parse():
                          "(lbm_run_throat_batch_refined) for the labels and the judge; 1 = the ladder's own")
     ap.add_argument("--shape", default="",
                     help="fixed step kernel shape instead of tuning: tma:LZ, split, staged:BY:LZ:LEAD, "
-                         "staged2:BY:LZ:2 or push:SHAPE:LZ[:PREFETCH] (SHAPE an lbm_set_push_shape index)")
+                         "staged2:BY:LZ:2 or push:SHAPE:LZ[:PREFETCH[:ORDER]] (SHAPE an lbm_set_push_shape index)")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--throat-batch", choices=["cells", "tiles", "persistent"], default="",
@@ -454,7 +454,8 @@ def run_ours(args, rank, world, local):
         if f[0] == "push":  # push:shape:lz[:prefetch planes]
             sh = int(f[1])
             tuned = {"kind": "push", "shape": sh, "by": lbm.PUSH_SHAPE_TABLE[sh][0], "lz": int(f[2]),
-                     "lead": lbm.PUSH_SHAPE_TABLE[sh][1], "prefetch": int(f[3]) if len(f) > 3 else 0}
+                     "lead": lbm.PUSH_SHAPE_TABLE[sh][1], "prefetch": int(f[3]) if len(f) > 3 else 0,
+                     "order": int(f[4]) if len(f) > 4 else 0}
         else:
             tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
                      {"kind": f[0], "by": int(f[1]), "lz": int(f[2]), "lead": int(f[3])})
@@ -467,6 +468,7 @@ def run_ours(args, rank, world, local):
         if tuned["kind"] == "push":
             d.set_push_shape(tuned["shape"], tuned["lz"])
             d.set_push_prefetch(tuned.get("prefetch", 0))
+            d.set_push_order(tuned.get("order", 0))
         elif tuned["kind"] == "tma":
             d.set_step_kernel(lbm.KERNEL_TMA, tuned["lz"])
         elif tuned["kind"] == "split":

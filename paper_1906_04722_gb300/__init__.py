@@ -90,13 +90,13 @@ class lbm_throat_surrogate_config(ctypes.Structure):
 class lbm_tune_result(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("by", ctypes.c_int), ("lz", ctypes.c_int), ("lead", ctypes.c_int),
                 ("ms_per_step", ctypes.c_double), ("n_candidates", ctypes.c_int), ("prefetch", ctypes.c_int),
-                ("shape", ctypes.c_int)]
+                ("shape", ctypes.c_int), ("order", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"kind": {0: "staged", 1: "tma", 2: "split", 3: "staged2", 4: "push"}.get(self.kind, "?"),
                 "by": self.by, "lz": self.lz, "lead": self.lead,
                 "ms_per_step": self.ms_per_step, "n_candidates": self.n_candidates, "prefetch": self.prefetch,
-                "shape": self.shape}
+                "shape": self.shape, "order": self.order}
 
 
 class lbm_surrogate_config(ctypes.Structure):
@@ -132,6 +132,7 @@ SIGNATURES = {
     "lbm_set_tile": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "lbm_set_push_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "lbm_set_push_prefetch": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "lbm_set_push_order": (ctypes.c_int, [_VP, ctypes.c_int]),
     "lbm_get_tile": (ctypes.c_int, [_VP, _IP, _IP, _IP]),
     "lbm_set_step_kernel": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "lbm_get_step_kernel": (ctypes.c_int, [_VP, _IP, _IP]),
@@ -394,6 +395,10 @@ def lbm_set_push_shape(h, shape: int, lz: int = 0):
 
 def lbm_set_push_prefetch(h, planes: int):
     _check(load().lbm_set_push_prefetch(h, int(planes)), "lbm_set_push_prefetch")
+
+
+def lbm_set_push_order(h, order: int):
+    _check(load().lbm_set_push_order(h, int(order)), "lbm_set_push_order")
 
 
 def lbm_get_step_kernel(h):
@@ -718,6 +723,9 @@ class Domain:
 
     def set_push_prefetch(self, planes):
         lbm_set_push_prefetch(self.h, planes)
+
+    def set_push_order(self, order):
+        lbm_set_push_order(self.h, order)
 
     def autotune(self, trial_steps=20):
         return lbm_autotune(self.h, trial_steps)

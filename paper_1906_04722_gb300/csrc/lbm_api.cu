@@ -100,7 +100,7 @@ void drop_graphs(lbm_domain* d) {
 cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH)
         return launch_step_push(d->tile.push_shape, d->push_maps[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh,
-                                d->geom, d->phys, d->tile.push_lz, d->tile.push_pf, d->d_err, s);
+                                d->geom, d->phys, d->tile.push_lz, d->tile.push_pf, d->tile.push_order, d->d_err, s);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA)
         return launch_step_tma(d->tma, cur, d->f[cur], d->f[cur ^ 1], d->d_nbr_nw, d->d_adh, d->geom, d->phys,
                                d->tile.tma_lz, d->d_err, s);
@@ -351,6 +351,7 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     d->tile.push_shape = 1;  // 6 rows, 3 stages, two CTAs per SM
     d->tile.push_lz = push_default_lz(g, 1);
     d->tile.push_pf = 0;
+    d->tile.push_order = 0;
     d->layout = 0;
     d->push_maps_rows = 0;
 
@@ -767,6 +768,17 @@ int lbm_set_push_prefetch(lbm_domain* d, int planes) {
     return LBM_OK;
 }
 
+int lbm_set_push_order(lbm_domain* d, int order) {
+    if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
+    if (order < 0 || order > 1) {
+        set_error("push segment order must be 0 or 1");
+        return LBM_ERR_ARG;
+    }
+    d->tile.push_order = order;
+    drop_graphs(d);
+    return LBM_OK;
+}
+
 int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead) {
     if (!d || !by || !lz || !lead) { set_error("NULL argument"); return LBM_ERR_ARG; }
     *by = d->tile.by;
@@ -802,14 +814,16 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     if (fp32 && push_step_applicable(g))
         for (int sh = 0; sh < push_shape_count(); ++sh)
             for (int lz : {16, 32, 48, 64})
-                for (int pf : {0, 2}) {
-                    StepTile t = orig;
-                    t.kind = LBM_KERNEL_PUSH;
-                    t.push_shape = sh;
-                    t.push_lz = lz > g.nz ? g.nz : lz;
-                    t.push_pf = pf;
-                    cand.push_back(t);
-                }
+                for (int pf : {0, 2})
+                    for (int order : {0, 1}) {
+                        StepTile t = orig;
+                        t.kind = LBM_KERNEL_PUSH;
+                        t.push_shape = sh;
+                        t.push_lz = lz > g.nz ? g.nz : lz;
+                        t.push_pf = pf;
+                        t.push_order = order;
+                        cand.push_back(t);
+                    }
     if (fp32 && d->tma_ok)
         for (int lz : {8, 12, 16, 24, 32, 48}) add(LBM_KERNEL_TMA, orig.by, lz, orig.lead);
     if (fp32) add(LBM_KERNEL_SPLIT, orig.by, orig.lz, orig.lead);
@@ -898,6 +912,7 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
         out->n_candidates = (int)cand.size();
         out->prefetch = best_t.kind == LBM_KERNEL_PUSH ? best_t.push_pf : 0;
         out->shape = best_t.kind == LBM_KERNEL_PUSH ? best_t.push_shape : -1;
+        out->order = best_t.kind == LBM_KERNEL_PUSH ? best_t.push_order : 0;
     }
     return LBM_OK;
 }

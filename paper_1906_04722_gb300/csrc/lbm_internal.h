@@ -95,6 +95,7 @@ struct StepTile {
     int push_shape;  // shape index of the push kernel (push_shape_rows / _stages)
     int push_lz;     // z-segment length of the push kernel
     int push_pf;     // planes the push kernel prefetches into L2 beyond its loads (0 .. PUSH_MAX_PREFETCH)
+    int push_order;  // 0: segments march +z in x-y-z launch order; 1: a column's segments together, alternating
 };
 
 // Tensor maps of the TMA step kernel (lbm_step_tma.cu): the two population
@@ -171,7 +172,7 @@ cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtens
 cudaError_t prepare_step_push(int shape);
 cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, const uint32_t* nbr,
                              const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p, int lz,
-                             int pf, int* err, cudaStream_t s);
+                             int pf, int order, int* err, cudaStream_t s);
 cudaError_t launch_pull_to_push(const float* fin, float* F, const uint32_t* nbr, const uint32_t* nbr_nw,
                                 const Geom& g, cudaStream_t s);
 cudaError_t launch_push_to_pull(const float* F, float* fout, const uint32_t* nbr, const uint32_t* nbr_nw,

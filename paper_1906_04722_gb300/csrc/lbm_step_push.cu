@@ -130,7 +130,7 @@ template <int BY, int NS, int MINB, bool TAU1, bool RR>
 __global__ void __launch_bounds__(PX * BY, MINB)
     sc_step_push_kernel(const __grid_constant__ CUtensorMap tm, float2* __restrict__ fout,
                         const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
-                        const uint32_t* __restrict__ adh, Geom g, Phys P, int lz, int pf,
+                        const uint32_t* __restrict__ adh, Geom g, Phys P, int lz, int pf, int order,
                         int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (*reinterpret_cast<volatile int*>(err) != 0) return;  // an earlier launch gave up
@@ -141,21 +141,34 @@ __global__ void __launch_bounds__(PX * BY, MINB)
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * stage_bytes<BY>() + sizeof(float2) * 4 * NT);
     const int lane = threadIdx.x, row = threadIdx.y;
     const int tid = row * PX + lane;
-    const int xb = blockIdx.x * PXI - 2;  // box column of lane 0
-    const int yb = blockIdx.y * TY - 1;   // box row of row 0
+    // order 0: the grid is (x tiles, y tiles, z segments) and every segment
+    // marches towards +z.  Order 1: the grid is (z segments, x tiles, y tiles),
+    // so that all segments of a tile column run together, and even segments
+    // march towards -z: two neighbouring segments start (or end) at the plane
+    // they share at the same time, and the second reads its halo planes from L2.
+    const int tile_x = order ? blockIdx.y : blockIdx.x, tile_y = order ? blockIdx.z : blockIdx.y;
+    const int seg = order ? blockIdx.x : blockIdx.z;
+    const int xb = tile_x * PXI - 2;  // box column of lane 0
+    const int yb = tile_y * TY - 1;   // box row of row 0
     const int gx = xb + lane, gy = yb + row;
-    const int z0 = blockIdx.z * lz;
+    const int z0 = seg * lz;
     const int z1 = min(z0 + lz, g.nz);
+    const int n = z1 - z0;  // planes collided
+    const int dir = (order && !(seg & 1)) ? -1 : 1;
+    const int start = dir > 0 ? z0 - 1 : z1;  // plane of sequence index 0: the halo before the first
+    // the segment's planes in marching order: j = 0 the halo plane before the
+    // first collided plane, j = 1 .. n the collided planes, j = n + 1 the halo after
+    auto plane = [&](int j) { return start + dir * j; };
     const bool interior = lane >= 2 && lane < 2 + PXI && row >= 1 && row <= TY && gx < g.nx && gy < g.ny;
     const int col = gy * g.nx + gx;  // valid for interior threads
 
-    auto slot = [&](int p) { return (p - z0 + 1) % NS; };
-    auto parity = [&](int p) { return (uint32_t)(((p - z0 + 1) / NS) & 1); };
-    // plane p of every pair array into its stage; a plane beyond a closed z
+    auto slot = [&](int j) { return j % NS; };
+    auto parity = [&](int j) { return (uint32_t)((j / NS) & 1); };
+    // plane j of every pair array into its stage; a plane beyond a closed z
     // face is not loaded (its densities are zero) and only completes the phase
-    auto issue = [&](int p) {
-        uint64_t* b = bar + slot(p);
-        int zc = p;
+    auto issue = [&](int j) {
+        uint64_t* b = bar + slot(j);
+        int zc = plane(j);
         if (zc < 0 || zc >= g.nz) {
             if (!g.pz) {
                 p_mbar_arrive(b);
@@ -164,43 +177,43 @@ __global__ void __launch_bounds__(PX * BY, MINB)
             zc = zc < 0 ? zc + g.nz : zc - g.nz;
         }
         p_mbar_arrive_expect_tx(b, stage_bytes<BY>());
-        p_tma_load_4d(stages + (size_t)slot(p) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
+        p_tma_load_4d(stages + (size_t)slot(j) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
     };
     // plane p into L2 ahead of its load (pf planes beyond the loads in flight);
     // the box is moved inside the tensor where it sticks out, so that every
     // coordinate is in range (the hint then covers a few other columns)
     const int pfx = max(0, min(2 * xb, 2 * g.nx - 2 * PX));
     const int pfy = max(0, min(yb, g.ny - BY));
-    auto prefetch = [&](int p) {
-        if (p > z1) return;
-        int zc = p;
+    auto prefetch = [&](int j) {
+        if (j > n + 1) return;
+        int zc = plane(j);
         if (zc < 0 || zc >= g.nz) {
             if (!g.pz) return;
             zc = zc < 0 ? zc + g.nz : zc - g.nz;
         }
         p_tma_prefetch_4d(&tm, pfx, pfy, zc, 0);
     };
-    // geometry word of this thread's box cell on plane p (class CLS_OUTSIDE
-    // beyond the box or a closed z face)
+    // geometry word of this thread's box cell on plane j (class CLS_OUTSIDE
+    // beyond the box, the segment or a closed z face)
     const bool in_xy = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny;
-    auto word = [&](int p) -> uint32_t {
-        if (!in_xy || p > z1) return CLS_OUTSIDE << CLS_SHIFT;
-        int zc = p;
+    auto word = [&](int j) -> uint32_t {
+        if (!in_xy || j > n + 1) return CLS_OUTSIDE << CLS_SHIFT;
+        int zc = plane(j);
         if (zc < 0 || zc >= g.nz) {
             if (!g.pz) return CLS_OUTSIDE << CLS_SHIFT;
             zc = zc < 0 ? zc + g.nz : zc - g.nz;
         }
         return __ldg(nbr + (size_t)zc * g.nxy + col);
     };
-    // the two densities of this thread's box cell on plane p (geometry word wp)
+    // the two densities of this thread's box cell on plane j (geometry word wp)
     // into the ring: 0 where a component is not fluid, whatever the slots hold
     // (a buffer's grain slots may hold another layout's values)
     // (RR: the interior threads keep the pairs in `keep`)
-    auto publish = [&](int p, uint32_t wp, float (&keep)[2][Q]) {
+    auto publish = [&](int j, uint32_t wp, float (&keep)[2][Q]) {
         float2 r = make_float2(0.f, 0.f);
         const uint32_t c = (wp >> CLS_SHIFT) & CLS_MASK;
         if (c != CLS_SOLID && c != CLS_OUTSIDE) {
-            const float2* st = stages + (size_t)slot(p) * (Q * NT) + tid;
+            const float2* st = stages + (size_t)slot(j) * (Q * NT) + tid;
             float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
@@ -215,7 +228,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
             r.x = (a[0] + a[1]) + (a[2] + a[3]);
             if (c != CLS_MEMBRANE) r.y = (b[0] + b[1]) + (b[2] + b[3]);
         }
-        ring[(p & 3) * NT + tid] = r;
+        ring[(plane(j) & 3) * NT + tid] = r;
     };
 
     if (tid == 0) {
@@ -224,54 +237,56 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     __syncthreads();
-    int next = z0 - 1 + min(NS, z1 - z0 + 2);  // the first plane not yet issued (thread 0)
+    int next = min(NS, n + 2);  // the first sequence index not yet issued (thread 0)
     if (tid == 0) {
-        for (int p = z0 - 1; p < next; ++p) issue(p);
-        for (int p = next; p < next + pf; ++p) prefetch(p);
+        for (int j = 0; j < next; ++j) issue(j);
+        for (int j = next; j < next + pf; ++j) prefetch(j);
     }
 
-    // geometry words of planes z0 - 1 .. z0 + 1, then one plane further per
+    // geometry words of sequence planes 0 .. 2, then one plane further per
     // iteration; the adhesion and non-wetting bounce words of an interior cell a
     // plane ahead of its collision
-    const uint32_t w_m = word(z0 - 1);
-    uint32_t w_0 = word(z0), w_1 = word(z0 + 1);
-    auto extra = [&](int p, uint32_t wp, uint32_t& ap, uint32_t& np) {
+    const uint32_t w_m = word(0);
+    uint32_t w_0 = word(1), w_1 = word(2);
+    auto extra = [&](int j, uint32_t wp, uint32_t& ap, uint32_t& np) {
         ap = 0u;
         np = 0u;
-        if (!interior || p >= z1) return;
+        if (!interior || j < 1 || j > n) return;
+        const int p = plane(j);
         if (wp & BIT_ADH) ap = __ldg(adh + (size_t)p * g.nxy + col);
         if (wp & BIT_NW_DIFF) np = __ldg(nbr_nw + (size_t)p * g.nxy + col);
     };
     uint32_t a_0, nwb_0;
-    extra(z0, w_0, a_0, nwb_0);
+    extra(1, w_0, a_0, nwb_0);
 
     float fc[2][Q], fn[2][Q];  // RR: pairs of the plane to collide and of the next plane
-    bool ok = p_mbar_wait_bounded(bar + slot(z0 - 1), parity(z0 - 1));
-    if (ok) publish(z0 - 1, w_m, fn);
-    ok = ok && p_mbar_wait_bounded(bar + slot(z0), parity(z0));
-    if (ok) publish(z0, w_0, fc);
+    bool ok = p_mbar_wait_bounded(bar + slot(0), parity(0));
+    if (ok) publish(0, w_m, fn);
+    ok = ok && p_mbar_wait_bounded(bar + slot(1), parity(1));
+    if (ok) publish(1, w_0, fc);
     // a failed wait here is reported by the first iteration's barrier below
-    for (int z = z0; z < z1; ++z) {
+    for (int j = 1; j <= n; ++j) {
+        const int z = plane(j);
         const uint32_t w = w_0, a = a_0, nwb = nwb_0;
-        const uint32_t w_2 = word(z + 2);  // for the next iteration's publish
-        extra(z + 1, w_1, a_0, nwb_0);     // for the next iteration's collision
-        const bool okz = ok && p_mbar_wait_bounded(bar + slot(z + 1), parity(z + 1));
-        if (okz) publish(z + 1, w_1, fn);
+        const uint32_t w_2 = word(j + 2);  // for the next iteration's publish
+        extra(j + 1, w_1, a_0, nwb_0);     // for the next iteration's collision
+        const bool okz = ok && p_mbar_wait_bounded(bar + slot(j + 1), parity(j + 1));
+        if (okz) publish(j + 1, w_1, fn);
         if (__syncthreads_or(!okz)) {
             if (tid == 0) {
                 atomicOr(err, 1);
                 // bounded waits for every copy still in flight
-                for (int p = max(z0 - 1, z - 1); p < next; ++p) p_mbar_wait_bounded(bar + slot(p), parity(p));
+                for (int q = max(0, j - 1); q < next; ++q) p_mbar_wait_bounded(bar + slot(q), parity(q));
             }
             __syncthreads();
             return;
         }
         if (tid == 0) {
             // stages read by everyone before the barrier: RR frees the stages of
-            // planes up to z + 1, the other form those up to z - 1
-            const int last = RR ? z + 1 + NS : z + NS - 1;
-            if (next <= z1 && next <= last) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            for (; next <= z1 && next <= last; ++next) {
+            // sequence planes up to j + 1, the other form those up to j - 1
+            const int last = RR ? j + 1 + NS : j + NS - 1;
+            if (next <= n + 1 && next <= last) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            for (; next <= n + 1 && next <= last; ++next) {
                 issue(next);
                 if (pf > 0) prefetch(next + pf);
             }
@@ -280,7 +295,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         w_1 = w_2;
         const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
         if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE) {
-            const float2* st = stages + (size_t)slot(z) * (Q * NT) + tid;
+            const float2* st = stages + (size_t)slot(j) * (Q * NT) + tid;
             float f[2][Q];
             const bool has_nw = cls != CLS_MEMBRANE;
 #pragma unroll
@@ -510,12 +525,13 @@ cudaError_t configure_push() {
 
 template <int BY, int NS, int MINB, bool TAU1, bool RR>
 cudaError_t launch_push_shape(const CUtensorMap& tm, float2* fout, const uint32_t* nbr, const uint32_t* nbr_nw,
-                              const uint32_t* adh, const Geom& g, const Phys& p, int lz, int pf, int* err,
+                              const uint32_t* adh, const Geom& g, const Phys& p, int lz, int pf, int order, int* err,
                               cudaStream_t s) {
     constexpr int TY = BY - 2;
-    const dim3 grid((g.nx + PXI - 1) / PXI, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
+    const unsigned tx = (g.nx + PXI - 1) / PXI, ty = (g.ny + TY - 1) / TY, sz = (g.nz + lz - 1) / lz;
+    const dim3 grid = order ? dim3(sz, tx, ty) : dim3(tx, ty, sz);
     sc_step_push_kernel<BY, NS, MINB, TAU1, RR><<<grid, dim3(PX, BY), push_smem_bytes<BY, NS>(), s>>>(
-        tm, fout, nbr, nbr_nw, adh, g, p, lz, pf, err);
+        tm, fout, nbr, nbr_nw, adh, g, p, lz, pf, order, err);
     return cudaGetLastError();
 }
 
@@ -543,10 +559,12 @@ cudaError_t configure_shape() {
 
 template <int I>
 cudaError_t launch_shape(bool t1, const CUtensorMap& tm, float2* fo, const uint32_t* nbr, const uint32_t* nbr_nw,
-                         const uint32_t* adh, const Geom& g, const Phys& p, int lz, int pf, int* err, cudaStream_t s) {
+                         const uint32_t* adh, const Geom& g, const Phys& p, int lz, int pf, int order, int* err,
+                         cudaStream_t s) {
     constexpr PushShapeInfo S = kPushShapes[I];
-    return t1 ? launch_push_shape<S.by, S.ns, S.minb, true, S.rr>(tm, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s)
-              : launch_push_shape<S.by, S.ns, S.minb, false, S.rr>(tm, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+    return t1 ? launch_push_shape<S.by, S.ns, S.minb, true, S.rr>(tm, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s)
+              : launch_push_shape<S.by, S.ns, S.minb, false, S.rr>(tm, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err,
+                                                                   s);
 }
 
 }  // namespace
@@ -618,23 +636,23 @@ cudaError_t prepare_step_push(int shape) {
 
 cudaError_t launch_step_push(int shape, const CUtensorMap& tm_in, float* fout, const uint32_t* nbr,
                              const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g, const Phys& p, int lz,
-                             int pf, int* err, cudaStream_t s) {
-    if (lz < 1 || pf < 0 || pf > PUSH_MAX_PREFETCH) return cudaErrorInvalidValue;
+                             int pf, int order, int* err, cudaStream_t s) {
+    if (lz < 1 || pf < 0 || pf > PUSH_MAX_PREFETCH || order < 0 || order > 1) return cudaErrorInvalidValue;
     float2* fo = reinterpret_cast<float2*>(fout);
     const bool t1 = tau_one(p);
     switch (shape) {
-        case 0: return launch_shape<0>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 1: return launch_shape<1>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 2: return launch_shape<2>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 3: return launch_shape<3>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 4: return launch_shape<4>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 5: return launch_shape<5>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 6: return launch_shape<6>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 7: return launch_shape<7>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 8: return launch_shape<8>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 9: return launch_shape<9>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 10: return launch_shape<10>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
-        case 11: return launch_shape<11>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, err, s);
+        case 0: return launch_shape<0>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 1: return launch_shape<1>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 2: return launch_shape<2>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 3: return launch_shape<3>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 4: return launch_shape<4>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 5: return launch_shape<5>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 6: return launch_shape<6>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 7: return launch_shape<7>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 8: return launch_shape<8>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 9: return launch_shape<9>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 10: return launch_shape<10>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
+        case 11: return launch_shape<11>(t1, tm_in, fo, nbr, nbr_nw, adh, g, p, lz, pf, order, err, s);
     }
     return cudaErrorInvalidValue;
 }

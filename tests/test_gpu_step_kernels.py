@@ -280,11 +280,12 @@ def test_bounded_wait_gives_up_and_reports(lbm):
 
 
 # ------------------------------------------------------- paired push kernel
-def _push_run(lbm, flags, rho0, steps, shape, lz, prefetch=0):
+def _push_run(lbm, flags, rho0, steps, shape, lz, prefetch=0, order=0):
     nz, ny, nx = SHAPE
     dom = lbm.Domain(_params(lbm, **flags), SPHERES, (nx, ny, nz))
     dom.set_push_shape(shape, lz)
     dom.set_push_prefetch(prefetch)
+    dom.set_push_order(order)
     assert dom.step_kernel() == (lbm.KERNEL_PUSH, lz)
     dom.set_densities(rho0)
     if not flags.get("periodic"):
@@ -293,20 +294,22 @@ def _push_run(lbm, flags, rho0, steps, shape, lz, prefetch=0):
     return dom
 
 
-@pytest.mark.parametrize("shape,lz,prefetch", [(0, 13, 0), (1, 7, 2), (1, 45, 4), (2, 16, 1), (3, 11, 2), (4, 9, 3),
-                                               (5, 20, 0), (0, 5, 2), (6, 13, 2), (7, 9, 0), (8, 20, 1), (9, 11, 3),
-                                               (10, 7, 2), (11, 45, 0), (9, 1, 2), (6, 2, 0)])
+@pytest.mark.parametrize("shape,lz,prefetch,order", [
+    (0, 13, 0, 0), (1, 7, 2, 1), (1, 45, 4, 0), (2, 16, 1, 1), (3, 11, 2, 0), (4, 9, 3, 1), (5, 20, 0, 0), (0, 5, 2, 1),
+    (6, 13, 2, 0), (7, 9, 0, 1), (8, 20, 1, 0), (9, 11, 3, 1), (10, 7, 2, 0), (11, 45, 0, 1), (9, 1, 2, 1),
+    (6, 2, 0, 1), (3, 4, 2, 1), (11, 6, 0, 1)])
 @pytest.mark.parametrize("periodic_z", [0, 1])
-def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, prefetch, periodic_z):
+def test_push_kernel_equals_staged_bitwise(lbm, orc, shape, lz, prefetch, order, periodic_z):
     """The push kernel reads each cell's own populations and streams at the
     store, the staged kernel pulls; both sum the densities in the same order and
     share the collision, so after 60 steps the states (read back in the pull
     layout) are the same bit for bit -- every shape, ragged x, y and z tiles,
     reservoirs and a membrane (closed z) or a wrapped z axis, with and without
     the L2 prefetch (a hint that changes nothing), with the pairs re-read from
-    shared memory or held in registers, down to one- and two-plane segments."""
+    shared memory or held in registers, down to one- and two-plane segments,
+    every segment marching +z or alternate segments marching -z."""
     flags, mask, cfg, rho0 = _case(lbm, orc, periodic_z)
-    a = _push_run(lbm, flags, rho0, 60, shape, lz, prefetch).state()[0]
+    a = _push_run(lbm, flags, rho0, 60, shape, lz, prefetch, order).state()[0]
     b = _gpu_run(lbm, flags, rho0, 60, lbm.KERNEL_STAGED).state()[0]
     assert np.array_equal(a, b)
 
@@ -366,5 +369,8 @@ def test_push_kernel_applicability(lbm):
     for bad in (-1, 5):
         with pytest.raises(lbm.LbmError):
             d3.set_push_prefetch(bad)
+    for bad in (-1, 2):
+        with pytest.raises(lbm.LbmError):
+            d3.set_push_order(bad)
     d3.set_step_kernel(lbm.KERNEL_PUSH, 9)
     assert d3.step_kernel() == (lbm.KERNEL_PUSH, 9)
