@@ -257,14 +257,28 @@ __device__ __forceinline__ CellAt decode_cell(int2 it, const Geom& g) {
 constexpr int CELL_THREADS = 256;
 constexpr int NB_DIRS = Q - 3;  // directions 3..18 leave the x row; 1 and 2 are +x and -x
 
+// Push-table entries: NB = int holds the item itself (-1: none), NB = int16_t
+// its offset from the item that reads it (INT16_MIN: none), half the bytes;
+// the host picks int16_t when every throat's items lie within 32767 of their
+// neighbours (items follow memory order inside a throat, so a neighbour is at
+// most nx ny + nx + 1 items away).
+__device__ __forceinline__ int nb_encode(int item, int self, int) { return item; }
+__device__ __forceinline__ int16_t nb_encode(int item, int self, int16_t) {
+    return item < 0 ? (int16_t)INT16_MIN : (int16_t)(item - self);
+}
+__device__ __forceinline__ int nb_decode(int v, int) { return v; }
+__device__ __forceinline__ int nb_decode(int16_t v, int self) { return v == INT16_MIN ? -1 : self + v; }
+
 // Compact copies of the geometry words and the push table: nbp[(k - 3) cp + i]
-// is the item of x + e_k, -1 where that cell is grain or beyond the box.
+// is the item of x + e_k (encoded as NB), none where that cell is grain or
+// beyond the box.
+template <class NB>
 __global__ void __launch_bounds__(CELL_THREADS)
     cell_gather_kernel(const ThroatRec* __restrict__ recs, const int2* __restrict__ items, int n_items, int cp,
                        const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw,
                        const uint32_t* __restrict__ adh, const int* __restrict__ box_to_item,
                        uint32_t* __restrict__ wc, uint32_t* __restrict__ wnc, uint32_t* __restrict__ adhc,
-                       int* __restrict__ nbp) {
+                       NB* __restrict__ nbp) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i >= n_items) return;
     const int2 it = items[i];
@@ -280,7 +294,8 @@ __global__ void __launch_bounds__(CELL_THREADS)
     for (int k = 3; k < Q; ++k) {
         const int x = c.x + EX(k), y = c.y + EY(k), z = c.z + EZ(k);
         const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
-        nbp[(size_t)(k - 3) * cp + i] = in ? box_to_item[c_off + (long long)z * g.nxy + y * g.nx + x] : -1;
+        nbp[(size_t)(k - 3) * cp + i] =
+            nb_encode(in ? box_to_item[c_off + (long long)z * g.nxy + y * g.nx + x] : -1, i, NB());
     }
 }
 
@@ -332,11 +347,11 @@ __global__ void __launch_bounds__(CELL_THREADS)
 // alike, separate stores where a membrane makes them differ.  The bounce-back
 // choice selects an address rather than a branch: one store instruction per
 // value for the whole warp, whichever way each lane goes.
-template <bool TAU1>
+template <bool TAU1, class NB>
 __global__ void __launch_bounds__(CELL_THREADS, 2)
     cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float2* __restrict__ fin,
                      float2* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
-                     const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const int* __restrict__ nbp,
+                     const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp,
                      Phys P, const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i >= n_items) return;
@@ -350,11 +365,12 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
         f[0][k] = v.x;
         f[1][k] = has_nw ? v.y : 0.f;
     }
-    const uint32_t wn = has_nw ? __ldg(wnc + i) : 0u;
+    const uint32_t wn = (w & BIT_NW_DIFF) ? __ldg(wnc + i) : w;  // read only next to a membrane
     const uint32_t a = (w & BIT_ADH) ? __ldg(adhc + i) : 0u;
     int dst[Q];  // item of x + e_k
 #pragma unroll
-    for (int k = 1; k < Q; ++k) dst[k] = k == 1 ? i + 1 : k == 2 ? i - 1 : __ldg(nbp + (size_t)(k - 3) * cp + i);
+    for (int k = 1; k < Q; ++k)
+        dst[k] = k == 1 ? i + 1 : k == 2 ? i - 1 : nb_decode(__ldg(nbp + (size_t)(k - 3) * cp + i), i);
     auto rho_at = [&](int k) {
         if (k == 0) return __ldg(rho2 + i);
         const bool wall = (w >> OPP(k)) & 1u;
@@ -362,7 +378,8 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
         return wall ? make_float2(0.f, 0.f) : v;
     };
     Phys Pt = P;
-    Pt.bc = bc_all + 4 * ((size_t)__ldg(&items[i].x) * ladder_stride + *incr_now);
+    if (cls == CLS_INLET || cls == CLS_OUTLET)  // the reservoir pair of the throat's current increment
+        Pt.bc = bc_all + 4 * ((size_t)__ldg(&items[i].x) * ladder_stride + *incr_now);
     float o[2][Q];
     collide_core<TAU1>(f, w, a, Pt, rho_at, [&](int s, int k, float v) { o[s][k] = v; });
     auto addr = [&](int k, uint32_t bits) {
@@ -637,7 +654,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         int4* d_items = nullptr;
         int2* d_cells = nullptr;
         float2* d_rho2 = nullptr;
-        int *d_map = nullptr, *d_nbp = nullptr;
+        int* d_map = nullptr;
+        void* d_nbp = nullptr;
         uint32_t* d_wc = nullptr;
         cudaGraphExec_t exec2[2] = {nullptr, nullptr};
         double* d_rin = nullptr;
@@ -773,7 +791,11 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             BATCH_CUDA(cudaMalloc(&d_map, sizeof(int) * (size_t)std::max<long long>(1, c_tot)));
             BATCH_CUDA(cudaMalloc(&d_rho2, sizeof(float2) * (size_t)std::max(cp, 32)));
             BATCH_CUDA(cudaMalloc(&d_wc, sizeof(uint32_t) * 3 * (size_t)std::max(cp, 32)));
-            BATCH_CUDA(cudaMalloc(&d_nbp, sizeof(int) * (size_t)NB_DIRS * std::max(cp, 32)));
+            // 16-bit push-table offsets where every throat's neighbours lie within reach
+            long long reach = 0;
+            for (const ThroatRec& r : recs) reach = std::max(reach, (long long)r.g.nxy + r.g.nx + 1);
+            const bool nb16 = reach <= 32767;
+            BATCH_CUDA(cudaMalloc(&d_nbp, (nb16 ? sizeof(int16_t) : sizeof(int)) * (size_t)NB_DIRS * std::max(cp, 32)));
             BATCH_CUDA(cudaMalloc(&a0, sizeof(float) * fc_floats));
             BATCH_CUDA(cudaMalloc(&a1, sizeof(float) * fc_floats));
             BATCH_CUDA(cudaMalloc(&d_incr, sizeof(int) * 2));
@@ -787,8 +809,14 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             if (n_cells) {
                 BATCH_CUDA(cudaMemcpyAsync(d_cells, cells.data(), sizeof(int2) * cells.size(), cudaMemcpyHostToDevice,
                                            stream));
-                cell_gather_kernel<<<blocks, CELL_THREADS, 0, stream>>>(d_recs, d_cells, n_cells, cp, d_nbr, d_nbr_nw,
-                                                                       d_adh, d_map, d_wc, d_wnc, d_adhc, d_nbp);
+                if (nb16)
+                    cell_gather_kernel<int16_t><<<blocks, CELL_THREADS, 0, stream>>>(
+                        d_recs, d_cells, n_cells, cp, d_nbr, d_nbr_nw, d_adh, d_map, d_wc, d_wnc, d_adhc,
+                        static_cast<int16_t*>(d_nbp));
+                else
+                    cell_gather_kernel<int><<<blocks, CELL_THREADS, 0, stream>>>(d_recs, d_cells, n_cells, cp, d_nbr,
+                                                                                d_nbr_nw, d_adh, d_map, d_wc, d_wnc,
+                                                                                d_adhc, static_cast<int*>(d_nbp));
                 BATCH_CUDA(cudaGetLastError());
                 cell_init_kernel<<<blocks, CELL_THREADS, 0, stream>>>(d_wc, n_cells, cp, reinterpret_cast<float2*>(a0),
                                                                      (float)params->rho_major,
@@ -807,14 +835,22 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                     cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
                     cerr = cudaGetLastError();
                     if (cerr != cudaSuccess) break;
-                    if (P.tau[0] == 1.0f && P.tau[1] == 1.0f)
-                        cell_step_kernel<true><<<blocks, CELL_THREADS, 0, cap>>>(
-                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, d_nbp, P, d_bc,
-                            sched->per_throat ? I : 0, d_incr);
+                    const bool t1 = P.tau[0] == 1.0f && P.tau[1] == 1.0f;
+                    const int ls = sched->per_throat ? I : 0;
+                    const int16_t* nb16p = static_cast<const int16_t*>(d_nbp);
+                    const int* nb32p = static_cast<const int*>(d_nbp);
+                    if (t1 && nb16)
+                        cell_step_kernel<true, int16_t><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
+                    else if (t1)
+                        cell_step_kernel<true, int><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
+                    else if (nb16)
+                        cell_step_kernel<false, int16_t><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
                     else
-                        cell_step_kernel<false><<<blocks, CELL_THREADS, 0, cap>>>(
-                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, d_nbp, P, d_bc,
-                            sched->per_throat ? I : 0, d_incr);
+                        cell_step_kernel<false, int><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
                     cerr = cudaGetLastError();
                 }
                 if (cerr == cudaSuccess) {
