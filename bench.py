@@ -62,8 +62,8 @@ def parse():
     ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=0,
                     help="population storage: 0 FP32 (the benchmark), 1 FP16 / 2 BF16 deviations")
     ap.add_argument("--drainage", action="store_true",
-                    help="instead of the benchmark: the full drainage of the sample (20 increments x 5000 steps), "
-                         "one JSON line with the p_c - S_w curve")
+                    help="instead of the benchmark: the full drainage of the sample (20 increments x --pn-steps "
+                         "steps), one JSON line with the p_c - S_w curve")
     ap.add_argument("--no-tune", action="store_true", help="time the default kernel instead of the autotuned one")
     ap.add_argument("--pore-network", action="store_true",
                     help="drainage of the sample by the pore network (throat entry pressures from the batched "
@@ -592,7 +592,8 @@ def run_ours(args, rank, world, local):
 
 def run_drainage(args):
     """The fully resolved drainage of the sample: the non-wetting reservoir
-    density raised by 0.02 per increment (20 increments), 5000 steps each, the
+    density raised by 0.02 per increment (20 increments), --pn-steps steps each
+    (a comma list runs the ladder once per entry, from the same start), the
     observables of lbm_measure after every increment (Sec. 2.2.2, Sec. 3.1)."""
     import torch
     import paper_1906_04722_gb300 as lbm
@@ -601,21 +602,25 @@ def run_drainage(args):
     spheres, box = sample_geometry(args.size)
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
                              rho_minor=W.RHO_MINOR, reservoirs=True, membrane_layers=3)
-    dom = lbm.Domain(params, spheres, box)
-    tuned = dom.autotune(trial_steps=10)
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(20)]
     # invasion probe: the centre of the last fluid layer before the membrane
     probe = (box[0] // 2, box[1] // 2, box[2] - 6)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    out = dom.drainage(ladder, 5000, W.RHO_MAJOR, probe)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    rows = [{k: r[k] for k in ("rho_in_nw", "p_c", "p_c_res", "S_w", "n_interface", "phi_probe")} for r in out["rows"]]
-    print(json.dumps({"workload": f"sample{args.size} drainage, 20 increments x 5000 steps", "step_kernel": tuned,
-                      "seconds": dt, "steps_per_s": 20 * 5000 / dt, "invaded_at": out["invaded_at"],
-                      "p_ce": out["p_ce"], "rows": rows}))
-    dom.close()
+    runs = {}
+    for ns in [int(x) for x in str(args.pn_steps).split(",")]:
+        dom = lbm.Domain(params, spheres, box)
+        tuned = dom.autotune(trial_steps=10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = dom.drainage(ladder, ns, W.RHO_MAJOR, probe)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        dom.close()
+        rows = [{k: r[k] for k in ("rho_in_nw", "p_c", "p_c_res", "S_w", "n_interface", "phi_probe")}
+                for r in out["rows"]]
+        runs[str(ns)] = {"step_kernel": tuned, "seconds": dt, "steps_per_s": 20 * ns / dt,
+                         "invaded_at": out["invaded_at"], "p_ce": out["p_ce"], "rows": rows}
+    print(json.dumps({"workload": f"sample{args.size} drainage, 20 increments of +0.02, steps per increment: "
+                                  f"{args.pn_steps}", "runs": runs}))
     return 0
 
 
