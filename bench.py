@@ -88,7 +88,7 @@ def parse():
                          "staged2:BY:LZ:2 or push:SHAPE:LZ[:PREFETCH[:ORDER]] (SHAPE an lbm_set_push_shape index)")
     ap.add_argument("--throat-steps", type=int, default=100,
                     help="time steps per pressure increment of the throat ladder (32 increments)")
-    ap.add_argument("--throat-batch", choices=["cells", "tiles", "persistent"], default="",
+    ap.add_argument("--throat-batch", choices=["cells", "tiles", "persistent", "march"], default="",
                     help="instead of the benchmark: one batch of the 1024 held-out throats in the given form "
                          "(32 increments), and the same batch with no time steps (the set-up cost)")
     ap.add_argument("--throat-count", type=int, default=1024,
@@ -339,7 +339,8 @@ def throat_bench(lbm, W, n_steps, rank, world, sync, tmax, gather=None):
     # the same batch in the other two forms, for context
     out["other_forms"] = {}
     agree = True
-    for form, name in ((lbm.BATCH_PER_STEP, "tiles_per_step"), (lbm.BATCH_PERSISTENT, "persistent")):
+    for form, name in ((lbm.BATCH_MARCH, "march"), (lbm.BATCH_PER_STEP, "tiles_per_step"),
+                       (lbm.BATCH_PERSISTENT, "persistent")):
         sync()
         t0 = time.perf_counter()
         res_f, _ = lbm.lbm_run_throat_batch(tri, params, ladder, n_steps, W.RHO_MAJOR, form=form)
@@ -887,7 +888,8 @@ def run_throat_batch(args):
     import paper_1906_04722_gb300 as lbm
     import workloads as W
 
-    form = {"cells": lbm.BATCH_CELLS, "tiles": lbm.BATCH_PER_STEP, "persistent": lbm.BATCH_PERSISTENT}[args.throat_batch]
+    form = {"cells": lbm.BATCH_CELLS, "tiles": lbm.BATCH_PER_STEP, "persistent": lbm.BATCH_PERSISTENT,
+            "march": lbm.BATCH_MARCH}[args.throat_batch]
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
                              rho_minor=W.RHO_MINOR)
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]

@@ -183,12 +183,16 @@ typedef struct {
  * compactly after streaming; two launches per time step over that cell list,
  * one thread per cell (a density pass, then the collision, which pushes each
  * value to the cell it streams to), so that the grain inside the throat boxes
- * (most of a box) costs neither lanes, traffic nor memory.  All forms give
- * bit-identical rows.  AUTO is CELLS. */
+ * (most of a box) costs neither lanes, traffic nor memory.  MARCH: the same
+ * cell list in one launch per time step, a CTA per chunk of up to 16 planes of
+ * a throat, which computes the densities of a plane and steps the plane below
+ * it right after (a plane's pairs are read a second time from cache, not from
+ * DRAM).  All forms give bit-identical rows.  AUTO is CELLS. */
 #define LBM_BATCH_AUTO 0
 #define LBM_BATCH_PERSISTENT 1
 #define LBM_BATCH_PER_STEP 2
 #define LBM_BATCH_CELLS 3
+#define LBM_BATCH_MARCH 4
 
 /* Per-throat outcome of a batch. */
 typedef struct {

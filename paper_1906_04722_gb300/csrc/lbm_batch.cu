@@ -321,13 +321,10 @@ __global__ void __launch_bounds__(CELL_THREADS)
     for (int k = 0; k < Q; ++k) fc[(size_t)k * cp + i] = make_float2(v[0][k], v[1][k]);
 }
 
-// (rho_w, rho_nw) of every item (Eq. 2), in four interleaved partial sums as the
+// (rho_w, rho_nw) of item i (Eq. 2), in four interleaved partial sums as the
 // staged kernel sums its density ring; 0 for the non-wetting fluid on a membrane.
-__global__ void __launch_bounds__(CELL_THREADS)
-    cell_density_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, const float2* __restrict__ fc,
-                        float2* __restrict__ rho2) {
-    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
-    if (i >= n_items) return;
+__device__ __forceinline__ void cell_density_item(int i, const uint32_t* __restrict__ wc, int cp,
+                                                  const float2* __restrict__ fc, float2* __restrict__ rho2) {
     const uint32_t cls = (__ldg(wc + i) >> CLS_SHIFT) & CLS_MASK;
     float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -340,6 +337,14 @@ __global__ void __launch_bounds__(CELL_THREADS)
     rho2[i] = make_float2((a[0] + a[1]) + (a[2] + a[3]), rn);
 }
 
+// The densities of every item.
+__global__ void __launch_bounds__(CELL_THREADS)
+    cell_density_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, const float2* __restrict__ fc,
+                        float2* __restrict__ rho2) {
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i < n_items) cell_density_item(i, wc, cp, fc, rho2);
+}
+
 // One time step of every item: own population pairs, neighbour densities of the
 // density pass (0 where x + e_k is not fluid for the wetting component, i.e.
 // grain or beyond the box), collide_core (the compile-time tau = 1 form when
@@ -348,13 +353,13 @@ __global__ void __launch_bounds__(CELL_THREADS)
 // choice selects an address rather than a branch: one store instruction per
 // value for the whole warp, whichever way each lane goes.
 template <bool TAU1, class NB>
-__global__ void __launch_bounds__(CELL_THREADS, 2)
-    cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float2* __restrict__ fin,
-                     float2* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
-                     const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp,
-                     Phys P, const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
-    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
-    if (i >= n_items) return;
+__device__ __forceinline__ void cell_step_item(int i, const int2* __restrict__ items, int cp,
+                                               const float2* __restrict__ fin, float2* __restrict__ fout,
+                                               const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
+                                               const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc,
+                                               const NB* __restrict__ nbp, const Phys& P,
+                                               const float* __restrict__ bc_all, int ladder_stride,
+                                               const int* __restrict__ incr_now) {
     const uint32_t w = __ldg(wc + i);
     const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
     const bool has_nw = cls != CLS_MEMBRANE;
@@ -402,6 +407,53 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
 #pragma unroll
         for (int k = 1; k < Q; ++k) fout[addr(k, w)] = make_float2(o[0][k], o[1][k]);
     }
+}
+
+template <bool TAU1, class NB>
+__global__ void __launch_bounds__(CELL_THREADS, 2)
+    cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float2* __restrict__ fin,
+                     float2* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
+                     const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp,
+                     Phys P, const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i < n_items)
+        cell_step_item<TAU1, NB>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all, ladder_stride,
+                                 incr_now);
+}
+
+// One time step of the cell list in one launch, a CTA per chunk of a throat's
+// planes.  Chunk (b, nz, z0, z1): plane_item[b + z] is the first item of plane
+// z of its throat (items follow memory order inside a throat), plane_item[b + nz]
+// its end.  The CTA computes the densities of planes z0 - 1 .. z1 (those in the
+// box) plane by plane and steps each plane of [z0, z1) right after the density
+// of the plane above it: density(z), barrier, step(z - 1).  A plane's pairs are
+// read for its density and again for its step one plane later, from cache
+// rather than DRAM.  Chunks of one throat compute the densities of their shared
+// boundary planes twice, with the same values.
+constexpr int MARCH_THREADS = 128;
+template <bool TAU1, class NB>
+__global__ void __launch_bounds__(MARCH_THREADS, 4)
+    cell_march_kernel(const int4* __restrict__ chunks, const int* __restrict__ plane_item,
+                      const int2* __restrict__ items, int cp, const float2* __restrict__ fin, float2* __restrict__ fout,
+                      float2* __restrict__ rho2, const uint32_t* __restrict__ wc, const uint32_t* __restrict__ wnc,
+                      const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp, Phys P,
+                      const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
+    const int4 ch = chunks[blockIdx.x];
+    const int* pl = plane_item + ch.x;
+    const int nz = ch.y, z0 = ch.z, z1 = ch.w;
+    auto step_plane = [&](int z) {
+        for (int i = __ldg(pl + z) + (int)threadIdx.x; i < __ldg(pl + z + 1); i += MARCH_THREADS)
+            cell_step_item<TAU1, NB>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all, ladder_stride,
+                                     incr_now);
+    };
+    const int zs = max(z0 - 1, 0), ze = min(z1, nz - 1);
+    for (int z = zs; z <= ze; ++z) {
+        for (int i = __ldg(pl + z) + (int)threadIdx.x; i < __ldg(pl + z + 1); i += MARCH_THREADS)
+            cell_density_item(i, wc, cp, fin, rho2);
+        __syncthreads();  // densities of plane z visible to every thread of the CTA
+        if (z - 1 >= z0 && z - 1 < z1) step_plane(z - 1);
+    }
+    if (z1 == nz) step_plane(nz - 1);  // no plane above the top one
 }
 
 // Measurements of throat blockIdx.x from the compact populations, walking its
@@ -547,7 +599,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                                     void* stream_ptr) {
     if (!throats || n < 1 || !params || !sched || !results || !rows || !sched->rho_in_nw || sched->n_incr < 1 ||
         sched->n_steps < 0 || (sched->per_throat != 0 && sched->per_throat != 1) || sched->batch_form < 0 ||
-        sched->batch_form > LBM_BATCH_CELLS) {
+        sched->batch_form > LBM_BATCH_MARCH) {
         set_error("lbm_run_throat_batch: NULL argument or empty batch/schedule");
         return LBM_ERR_ARG;
     }
@@ -560,7 +612,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
     const int I = sched->n_incr;
     try {
         const int form = sched->batch_form == LBM_BATCH_AUTO ? LBM_BATCH_CELLS : sched->batch_form;
-        const bool box_layout = form != LBM_BATCH_CELLS;  // the cell-list form keeps compact arenas only
+        const bool cell_list = form == LBM_BATCH_CELLS || form == LBM_BATCH_MARCH;
+        const bool box_layout = !cell_list;  // the cell-list forms keep compact arenas only
         // host geometry: frames and sizes first (validation, on this thread), then
         // masks, probes and per-throat lists on all host cores
         std::vector<ThroatRec> recs((size_t)n);
@@ -656,6 +709,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         float2* d_rho2 = nullptr;
         int* d_map = nullptr;
         void* d_nbp = nullptr;
+        int* d_plane_item = nullptr;
+        int4* d_chunks = nullptr;
         uint32_t* d_wc = nullptr;
         cudaGraphExec_t exec2[2] = {nullptr, nullptr};
         double* d_rin = nullptr;
@@ -673,6 +728,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             cudaFree(d_rho2);
             cudaFree(d_map);
             cudaFree(d_nbp);
+            cudaFree(d_plane_item);
+            cudaFree(d_chunks);
             cudaFree(d_wc);
             if (exec) cudaGraphExecDestroy(exec);
             for (cudaGraphExec_t& e : exec2)
@@ -756,7 +813,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         const int grid = std::max(1, std::min(n, sms * std::max(1, per_sm)));
         BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
 
-        if (form == LBM_BATCH_CELLS) {
+        if (cell_list) {
             // every non-solid cell of every throat (largest throats first,
             // memory order inside a throat), and the box -> item map
             std::vector<long long> item0((size_t)n);
@@ -786,6 +843,33 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             });
             const int n_cells = (int)cells.size();
             const int cp = (n_cells + 31) / 32 * 32;
+            // marching form: the first item of every plane of every throat, and
+            // chunks of at most MARCH_PLANES planes, largest throats first
+            int n_chunks = 0;
+            if (form == LBM_BATCH_MARCH) {
+                constexpr int MARCH_PLANES = 16;
+                std::vector<int> plane_item;
+                std::vector<int4> chunks;
+                for (int t : order) {
+                    const int nz = recs[t].g.nz, base = (int)plane_item.size();
+                    const std::vector<int>& cl = cells_of[t];
+                    size_t j = 0;
+                    for (int z = 0; z <= nz; ++z) {
+                        while (j < cl.size() && (cl[j] >> 20) < z) ++j;
+                        plane_item.push_back((int)(item0[t] + (long long)j));
+                    }
+                    for (int z0 = 0; z0 < nz; z0 += MARCH_PLANES)
+                        chunks.push_back(make_int4(base, nz, z0, std::min(nz, z0 + MARCH_PLANES)));
+                }
+                n_chunks = (int)chunks.size();
+                BATCH_CUDA(cudaMalloc(&d_plane_item, sizeof(int) * std::max<size_t>(1, plane_item.size())));
+                BATCH_CUDA(cudaMalloc(&d_chunks, sizeof(int4) * std::max<size_t>(1, chunks.size())));
+                BATCH_CUDA(cudaMemcpyAsync(d_plane_item, plane_item.data(), sizeof(int) * plane_item.size(),
+                                           cudaMemcpyHostToDevice, stream));
+                if (n_chunks)
+                    BATCH_CUDA(cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(int4) * chunks.size(),
+                                               cudaMemcpyHostToDevice, stream));
+            }
             const size_t fc_floats = (size_t)2 * Q * std::max(cp, 32);
             BATCH_CUDA(cudaMalloc(&d_cells, sizeof(int2) * std::max<size_t>(1, cells.size())));
             BATCH_CUDA(cudaMalloc(&d_map, sizeof(int) * (size_t)std::max<long long>(1, c_tot)));
@@ -832,13 +916,35 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                     const int c = (gi + st) & 1;
                     const float2* fin = reinterpret_cast<const float2*>(c ? a1 : a0);
                     float2* fout = reinterpret_cast<float2*>(c ? a0 : a1);
-                    cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
-                    cerr = cudaGetLastError();
-                    if (cerr != cudaSuccess) break;
                     const bool t1 = P.tau[0] == 1.0f && P.tau[1] == 1.0f;
                     const int ls = sched->per_throat ? I : 0;
                     const int16_t* nb16p = static_cast<const int16_t*>(d_nbp);
                     const int* nb32p = static_cast<const int*>(d_nbp);
+                    if (form == LBM_BATCH_MARCH) {
+                        if (n_chunks) {
+                            if (t1 && nb16)
+                                cell_march_kernel<true, int16_t><<<n_chunks, MARCH_THREADS, 0, cap>>>(
+                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
+                                    nb16p, P, d_bc, ls, d_incr);
+                            else if (t1)
+                                cell_march_kernel<true, int><<<n_chunks, MARCH_THREADS, 0, cap>>>(
+                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
+                                    nb32p, P, d_bc, ls, d_incr);
+                            else if (nb16)
+                                cell_march_kernel<false, int16_t><<<n_chunks, MARCH_THREADS, 0, cap>>>(
+                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
+                                    nb16p, P, d_bc, ls, d_incr);
+                            else
+                                cell_march_kernel<false, int><<<n_chunks, MARCH_THREADS, 0, cap>>>(
+                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
+                                    nb32p, P, d_bc, ls, d_incr);
+                        }
+                        cerr = cudaGetLastError();
+                        continue;
+                    }
+                    cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
+                    cerr = cudaGetLastError();
+                    if (cerr != cudaSuccess) break;
                     if (t1 && nb16)
                         cell_step_kernel<true, int16_t><<<blocks, CELL_THREADS, 0, cap>>>(
                             d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);

@@ -173,12 +173,31 @@ def test_batch_forms_agree(lbm, n_steps):
     throats = W.delaunay_throats(spheres, 9, seed=13)
     ladders = S.pressure_ladder(S.throat_incircle(throats), 4, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
     out = {}
-    for form in (lbm.BATCH_PERSISTENT, lbm.BATCH_PER_STEP, lbm.BATCH_CELLS):
+    for form in (lbm.BATCH_PERSISTENT, lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH):
         out[form] = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, n_steps, W.RHO_MAJOR, form=form)
     ra, rowsa = out[lbm.BATCH_PERSISTENT]
-    for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS):
+    for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH):
         rb, rowsb = out[form]
         _rows_equal(ra, rowsa, rb, rowsb, ladders)
+
+
+def test_batch_forms_agree_with_a_wide_box(lbm):
+    """A throat whose box has more than 32767 cells per plane makes the cell-list
+    forms keep 32-bit push-table entries (16-bit offsets could not reach a z
+    neighbour); with it in the batch, beside small throats, every form still
+    gives the same rows bit for bit."""
+    big = np.array([[0.0, 0.0, 0.0, 120.0], [250.0, 0.0, 0.0, 120.0], [125.0, 216.5, 0.0, 120.0]])  # 13 M cells
+    mask, _ = lbm.lbm_throat_geometry(big)
+    assert mask.shape[1] * mask.shape[2] > 32767
+    small = W.delaunay_throats(W.sample_spheres(128), 3, seed=14)
+    throats = np.concatenate([big[None], small])
+    ladder = [2.0 + 0.05 * i for i in range(2)]
+    out = {form: lbm.lbm_run_throat_batch(throats, _params(lbm), ladder, 6, W.RHO_MAJOR, form=form)
+           for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH)}
+    ra, rowsa = out[lbm.BATCH_PER_STEP]
+    for form in (lbm.BATCH_CELLS, lbm.BATCH_MARCH):
+        rb, rowsb = out[form]
+        _rows_equal(ra, rowsa, rb, rowsb, np.tile(ladder, (len(throats), 1)))
 
 
 def _rows_equal(ra, rowsa, rb, rowsb, ladders):
