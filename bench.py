@@ -843,6 +843,21 @@ def run_surrogate_config5(args):
                 "pce_rel_err_answered_median": float(np.median(err_ans)) if err_ans.size else None,
                 "pce_rel_err_answered_p90": float(np.percentile(err_ans, 90)) if err_ans.size else None,
                 "answered_in_subset": int(ans_ok.sum())})
+    # the same predictions under other spread rules (the LBM's answers reused; the
+    # fallback's cost scales with the throats it takes at its measured rate)
+    sweep = {}
+    for tol in (0.02, 0.03, 0.05, 0.1):
+        fb_t = rel > tol
+        ans_t = ok & ~fb_t[sub]
+        e = np.abs(pce[sub][ans_t] - truth[ans_t]) / np.abs(truth[ans_t])
+        allv = np.where(fb_t[sub], truth, pce[sub])[ok]
+        e_all = np.abs(allv - truth[ok]) / np.abs(truth[ok])
+        rate = n / (t_net + float(fb_t.sum()) / rate_fb) if len(fb) else float("nan")
+        sweep[f"{tol:g}"] = {"fallback_fraction": float(fb_t.mean()), "throats_per_s": rate,
+                             "vs_plain": rate / plain,
+                             "answered_median": float(np.median(e)) if e.size else None,
+                             "all_median": float(np.median(e_all)), "all_p90": float(np.percentile(e_all, 90))}
+    out["spread_rules"] = sweep
     sur.close()
     print(json.dumps(out))
     return 0
