@@ -170,8 +170,9 @@ def kernel_hash(kernel_name="sc_step_kernel"):
 
 
 def read_traffic(kernel_name):
-    """DRAM bytes per launch of the given step kernel from the committed ncu
-    summary, valid only while that kernel's sources are unchanged."""
+    """DRAM bytes per launch of the given step kernel on the 192^3 sample from
+    the committed ncu summary, valid only while that kernel's sources are
+    unchanged (the caller asks only for that workload)."""
     p = os.path.join(ROOT, "profiles", "sc_step_sample192_traffic.json")
     if not os.path.exists(p):
         return None
@@ -571,7 +572,7 @@ def run_ours(args, rank, world, local):
                       "l2": "inputs larger than L2 (2 x 1.08 GB population buffers)",
                       "step_kernel": tuned if tuned is not None else "default"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": read_traffic(kernel_name), "peak_kind": peak_kind,
+                        "frac": achieved / peak, "traffic": read_traffic(kernel_name) if args.size == 192 else None, "peak_kind": peak_kind,
                         "kernel": kernel_name, "algorithmic_bytes_per_launch": bytes_per_step},
            "gpu_launches": args.steps * (2 if kind == lbm.KERNEL_SPLIT and not args.precision else 1),
            "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
