@@ -424,13 +424,12 @@ __global__ void __launch_bounds__(CELL_THREADS, 2)
 // One time step of the cell list in one launch, a CTA per chunk of a throat's
 // planes.  Chunk (b, nz, z0, z1): plane_item[b + z] is the first item of plane
 // z of its throat (items follow memory order inside a throat), plane_item[b + nz]
-// its end.  The CTA walks phases p = z0 - 1, z0, ...: in phase p it computes the
-// densities of plane p (planes z0 - 1 .. z1 that lie in the box) and steps
-// plane p - 2, whose neighbour densities (planes p - 3 .. p - 1) earlier phases
-// wrote; one barrier ends each phase.  A plane's pairs are read for its density
-// and again for its step two phases later, from cache rather than DRAM.  Chunks
-// of one throat compute the densities of their shared boundary planes twice,
-// with the same values.
+// its end.  The CTA computes the densities of planes z0 - 1 .. z1 (those in the
+// box) plane by plane and steps each plane of [z0, z1) right after the density
+// of the plane above it: density(z), barrier, step(z - 1).  A plane's pairs are
+// read for its density and again for its step one plane later, from cache
+// rather than DRAM.  Chunks of one throat compute the densities of their shared
+// boundary planes twice, with the same values.
 constexpr int MARCH_THREADS = 128;
 template <bool TAU1, class NB>
 __global__ void __launch_bounds__(MARCH_THREADS, 4)
@@ -448,13 +447,13 @@ __global__ void __launch_bounds__(MARCH_THREADS, 4)
                                      incr_now);
     };
     const int zs = max(z0 - 1, 0), ze = min(z1, nz - 1);
-    for (int p = zs; p <= z1 + 1; ++p) {
-        if (p <= ze)
-            for (int i = __ldg(pl + p) + (int)threadIdx.x; i < __ldg(pl + p + 1); i += MARCH_THREADS)
-                cell_density_item(i, wc, cp, fin, rho2);
-        if (p - 2 >= z0 && p - 2 < z1) step_plane(p - 2);
-        __syncthreads();  // the densities of plane p visible to every thread of the CTA
+    for (int z = zs; z <= ze; ++z) {
+        for (int i = __ldg(pl + z) + (int)threadIdx.x; i < __ldg(pl + z + 1); i += MARCH_THREADS)
+            cell_density_item(i, wc, cp, fin, rho2);
+        __syncthreads();  // densities of plane z visible to every thread of the CTA
+        if (z - 1 >= z0 && z - 1 < z1) step_plane(z - 1);
     }
+    if (z1 == nz) step_plane(nz - 1);  // no plane above the top one
 }
 
 // Measurements of throat blockIdx.x from the compact populations, walking its
