@@ -33,7 +33,9 @@
 //
 // DRAM sees each population read once (whole boxes: grain columns of a tile
 // ride along) and written once; the box halos, re-read by neighbouring tiles
-// that march in step, are served by L2.
+// that march in step, are served by L2, and the boundary planes of a z
+// segment, re-read by the next segment later, are loaded with an evict-last
+// policy.
 //
 // Waits on the mbarriers are bounded in time: a wait that runs out sets *err,
 // waits (bounded again) for the copies in flight and ends the CTA.
@@ -96,6 +98,21 @@ __device__ __forceinline__ void p_tma_load_4d(void* dst, const CUtensorMap* map,
         "%5}], [%6];\n" ::"r"(p_smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(p_smem_u32(bar))
         : "memory");
+}
+
+// The same load with an L2 eviction policy (from createpolicy) attached.
+__device__ __forceinline__ void p_tma_load_4d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                                   uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+        "{%2, %3, %4, %5}], [%6], %7;\n" ::"r"(p_smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(p_smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t p_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
 }
 
 // A hint: the box at these coordinates into L2, nothing into shared memory and
@@ -177,7 +194,12 @@ __global__ void __launch_bounds__(PX * BY, MINB)
             zc = zc < 0 ? zc + g.nz : zc - g.nz;
         }
         p_mbar_arrive_expect_tx(b, stage_bytes<BY>());
-        p_tma_load_4d(stages + (size_t)slot(j) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
+        // the segment's two boundary planes are also read by the neighbouring
+        // segment, a wave of CTAs later: kept in L2 in preference to the rest
+        if (j == 0 || j == n + 1)
+            p_tma_load_4d_hint(stages + (size_t)slot(j) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b, p_policy_evict_last());
+        else
+            p_tma_load_4d(stages + (size_t)slot(j) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
     };
     // plane p into L2 ahead of its load (pf planes beyond the loads in flight);
     // the box is moved inside the tensor where it sticks out, so that every
