@@ -636,8 +636,9 @@ int lbm_set_push_prefetch(lbm_domain* d, int planes);
  * segments of a tile column launched together, alternate segments marching
  * towards -z, so that two neighbouring segments start (or end) at the plane
  * they share at the same time and its halo planes are read from DRAM once.
- * Results do not depend on it (bit for bit).  New domains use 0; lbm_autotune
- * sets it with the shape it picks.  LBM_ERR_ARG outside 0 .. 1. */
+ * Results do not depend on it (bit for bit).  New domains use 0, and so does
+ * lbm_autotune (order 1 was slower in every shape on the drainage sample).
+ * LBM_ERR_ARG outside 0 .. 1. */
 int lbm_set_push_order(lbm_domain* d, int order);
 
 /* lbm_autotune -- time the step kernels and launch shapes that apply to the
@@ -645,9 +646,9 @@ int lbm_set_push_order(lbm_domain* d, int order);
  *   trial_steps  time steps timed per candidate (>= 1), after one untimed step;
  *   out          optional: the chosen shape and its time per step.
  * Candidates: for FP32 domains the push kernel (where it applies) in every
- * shape with z segments of 16, 32, 48 and 64 planes, each without and with a
- * two-plane L2 prefetch (lbm_set_push_prefetch) and in both segment orders
- * (lbm_set_push_order), the TMA kernel (where it
+ * shape with z segments of 16, 24, 32, 48 and 64 planes, each without and
+ * with a two-plane L2 prefetch (lbm_set_push_prefetch), in segment order 0
+ * (lbm_set_push_order; order 1 is left to the caller), the TMA kernel (where it
  * applies) with z segments of 8 .. 48 planes, the two-launch kernel, the two-threads-per-cell
  * staged kernel (by 6 or 8, z segments of 8 .. 32), and the staged kernel with
  * by in {6, 8, 10}, lead in {0, 1, 2, 3} (0 and 1: the double-pull variant) and
