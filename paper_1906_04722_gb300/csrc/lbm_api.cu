@@ -159,7 +159,7 @@ int pull_view(lbm_domain* d, const float** out) {
 
 // Tensor maps of both buffers for the push kernel's current shape.
 int ensure_push_maps(lbm_domain* d) {
-    const int rows = push_shape_box_rows(d->tile.push_shape);
+    const int rows = push_shape_rows(d->tile.push_shape);
     if (d->push_maps_rows == rows) return LBM_OK;
     cudaError_t e = encode_push_maps(d->geom, d->f[0], d->f[1], rows, d->push_maps);
     if (e != cudaSuccess) {

@@ -164,7 +164,6 @@ constexpr int PUSH_MAX_PREFETCH = 4;
 int push_shape_count();
 int push_shape_rows(int shape);
 int push_shape_stages(int shape);
-int push_shape_box_rows(int shape);  // rows of one tensor-map box of the shape's loads
 int push_shape_ctas(int shape);
 bool push_shape_resident(int shape);
 bool push_step_applicable(const Geom& g);
@@ -240,7 +239,7 @@ struct lbm_domain {
     float2* d_rho2;     // FP32 domains: (rho_w, rho_nw) per cell for the two-launch step
     int layout;         // FP32 state in f[cur]: 0 = pull layout, 1 = paired push layout
     CUtensorMap push_maps[2];  // tensor maps of f[0], f[1] for the push kernel's shape
-    int push_maps_rows;        // box rows the push maps were encoded for (push_shape_box_rows; 0: none)
+    int push_maps_rows;        // box rows the push maps were encoded for (0: none)
 };
 
 constexpr int GRAPH_STEPS = 64;  // steps per captured graph (even: the buffer parity is unchanged)

@@ -153,12 +153,6 @@ __global__ void __launch_bounds__(PX * BY, MINB)
     if (*reinterpret_cast<volatile int*>(err) != 0) return;  // an earlier launch gave up
     constexpr int TY = BY - 2;
     constexpr int NT = PX * BY;
-    // Even box heights load each plane as BY / 2 boxes of two rows, so that the
-    // rows a neighbouring tile also loads (the first two and the last two) can
-    // carry an evict-last policy; a stage then holds the blocks one after the
-    // other, [BY / 2][Q][2][PX], instead of [Q][BY][PX].
-    constexpr bool SPLIT = BY % 2 == 0;
-    constexpr int KSTRIDE = SPLIT ? 2 * PX : NT;  // distance between directions in a stage
     float2* stages = reinterpret_cast<float2*>(smem);  // [NS][Q][BY][PX]
     float2* ring = reinterpret_cast<float2*>(smem + NS * stage_bytes<BY>());  // [4][BY][PX]
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * stage_bytes<BY>() + sizeof(float2) * 4 * NT);
@@ -201,28 +195,12 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         }
         p_mbar_arrive_expect_tx(b, stage_bytes<BY>());
         // the segment's two boundary planes are also read by the neighbouring
-        // segment, a wave of CTAs later, and the shared rows of every plane by
-        // the neighbouring tiles: kept in L2 in preference to the rest
-        float2* dst = stages + (size_t)slot(j) * (Q * NT);
-        const bool edge = j == 0 || j == n + 1;
-        if constexpr (SPLIT) {
-#pragma unroll
-            for (int r = 0; r < BY; r += 2) {
-                float2* blk = dst + (size_t)(r / 2) * (Q * 2 * PX);
-                if (edge || r == 0 || r == BY - 2)
-                    p_tma_load_4d_hint(blk, &tm, 2 * xb, yb + r, zc, 0, b, p_policy_evict_last());
-                else
-                    p_tma_load_4d(blk, &tm, 2 * xb, yb + r, zc, 0, b);
-            }
-        } else {
-            if (edge)
-                p_tma_load_4d_hint(dst, &tm, 2 * xb, yb, zc, 0, b, p_policy_evict_last());
-            else
-                p_tma_load_4d(dst, &tm, 2 * xb, yb, zc, 0, b);
-        }
+        // segment, a wave of CTAs later: kept in L2 in preference to the rest
+        if (j == 0 || j == n + 1)
+            p_tma_load_4d_hint(stages + (size_t)slot(j) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b, p_policy_evict_last());
+        else
+            p_tma_load_4d(stages + (size_t)slot(j) * (Q * NT), &tm, 2 * xb, yb, zc, 0, b);
     };
-    // this thread's cell in a stage: its offset; direction k lies KSTRIDE further
-    const int soff = SPLIT ? (row / 2) * (Q * 2 * PX) + (row % 2) * PX + lane : tid;
     // plane p into L2 ahead of its load (pf planes beyond the loads in flight);
     // the box is moved inside the tensor where it sticks out, so that every
     // coordinate is in range (the hint then covers a few other columns)
@@ -257,11 +235,11 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         float2 r = make_float2(0.f, 0.f);
         const uint32_t c = (wp >> CLS_SHIFT) & CLS_MASK;
         if (c != CLS_SOLID && c != CLS_OUTSIDE) {
-            const float2* st = stages + (size_t)slot(j) * (Q * NT) + soff;
+            const float2* st = stages + (size_t)slot(j) * (Q * NT) + tid;
             float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
-                const float2 v = st[k * KSTRIDE];
+                const float2 v = st[k * NT];
                 a[k & 3] += v.x;
                 b[k & 3] += v.y;
                 if constexpr (RR) {
@@ -339,7 +317,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
         w_1 = w_2;
         const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
         if (interior && cls != CLS_SOLID && cls != CLS_OUTSIDE) {
-            const float2* st = stages + (size_t)slot(j) * (Q * NT) + soff;
+            const float2* st = stages + (size_t)slot(j) * (Q * NT) + tid;
             float f[2][Q];
             const bool has_nw = cls != CLS_MEMBRANE;
 #pragma unroll
@@ -348,7 +326,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
                     f[0][k] = fc[0][k];
                     f[1][k] = has_nw ? fc[1][k] : 0.f;
                 } else {
-                    const float2 v = st[k * KSTRIDE];
+                    const float2 v = st[k * NT];
                     f[0][k] = v.x;
                     f[1][k] = has_nw ? v.y : 0.f;
                 }
@@ -636,11 +614,6 @@ cudaError_t encode_push_maps(const Geom& g, float* f0, float* f1, int by, CUtens
 }
 
 int push_shape_rows(int shape) { return (shape >= 0 && shape < N_PUSH_SHAPES) ? kPushShapes[shape].by : 0; }
-
-int push_shape_box_rows(int shape) {
-    const int by = push_shape_rows(shape);
-    return by % 2 == 0 ? 2 : by;  // even heights load 2-row boxes (see the kernel)
-}
 
 int push_shape_stages(int shape) { return (shape >= 0 && shape < N_PUSH_SHAPES) ? kPushShapes[shape].ns : 0; }
 
