@@ -156,7 +156,8 @@ def read_peaks():
 KERNEL_SOURCES = {
     "sc_step_kernel": ("lbm_step.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
     "sc_step_tma_kernel": ("lbm_step_tma.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
-    "sc_step_push_kernel": ("lbm_step_push.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
+    "sc_step_push_kernel": ("lbm_step_push.cu", "lbm_push_tma.cuh", "lbm_step_core.cuh", "lbm_device.cuh",
+                            "lbm_internal.h"),
 }
 
 

@@ -593,6 +593,14 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  *                      lbm_get_density_at read the paired layout directly (the
  *                      same bits), lbm_get_state converts a copy into the other
  *                      buffer; callers see the pull layout only.
+ *                      On a 16-bit domain the same kind is the 16-bit push
+ *                      kernel: each pair word of the pull form is stored at
+ *                      the cell that reads it, encoded against the same
+ *                      densities; one box load of the words and one of the
+ *                      density pairs per plane (boxes without periodic x or y
+ *                      and with nx % 4 == 0).  Its results equal the staged
+ *                      16-bit kernel's bit for bit; the read-outs convert a
+ *                      copy into the pull layout.
  * New domains use LBM_KERNEL_STAGED (lbm_autotune times every kind that applies
  * on the domain).  All give the same results up to rounding (not bit for bit:
  * the TMA kernel folds omega w_k into its equilibrium constants).  LBM_ERR_ARG
@@ -617,6 +625,12 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
  *          8: 12 rows, 3 stages, one CTA; 9: 5 rows, 4 stages, two CTAs;
  *          10: 8 rows, 4 stages, one CTA; 11: 7 rows, 3 stages, two CTAs.
  *          A CTA of 32 x rows threads advances 28 x (rows - 2) columns.
+ *          On a 16-bit domain (params.precision 1 or 2) the shapes of the
+ *          16-bit push kernel: 0: 8 rows, 4 stages; 1: 6 rows, 4 stages;
+ *          2: 7 rows, 4 stages; 3: 10 rows, 3 stages; two CTAs per SM each.
+ *          It needs nx % 4 == 0 (besides no periodic x or y), and its results
+ *          equal the staged 16-bit kernel's bit for bit; prefetch and segment
+ *          order do not apply to it.
  *   lz     planes per CTA z segment (lz <= 0: a default for the box).
  * Results do not depend on the shape (bit for bit); with tau = 1 in both
  * components a compile-time tau = 1 form of the collision runs (the same bits).
@@ -652,7 +666,9 @@ int lbm_set_push_order(lbm_domain* d, int order);
  * applies) with z segments of 8 .. 48 planes, the two-launch kernel, the two-threads-per-cell
  * staged kernel (by 6 or 8, z segments of 8 .. 32), and the staged kernel with
  * by in {6, 8, 10}, lead in {0, 1, 2, 3} (0 and 1: the double-pull variant) and
- * z segments of 8 .. 32 planes; for 16-bit storage by in {6, 8, 10} with lead 2.
+ * z segments of 8 .. 32 planes; for 16-bit storage the staged kernel with by in
+ * {6, 8, 10} and lead 2 and (where it applies) the 16-bit push kernel in every
+ * shape with z segments of 16, 24, 32 and 48 planes.
  * Timing uses CUDA events on the domain's stream.  The
  * populations, the step counter and (16-bit) the density fields are saved
  * before and restored after, bit for bit: a tuned domain continues exactly where

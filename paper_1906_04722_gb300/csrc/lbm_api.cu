@@ -98,6 +98,10 @@ void drop_graphs(lbm_domain* d) {
 
 // One step from buffer `cur` to buffer cur ^ 1 on stream s.
 cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
+    if (d->params.precision != 0 && d->tile.kind == LBM_KERNEL_PUSH)
+        return launch_step16_push(d->params.precision, d->tile.push_shape, d->push16_w[cur], d->push16_r[cur],
+                                  reinterpret_cast<uint32_t*>(d->f[cur ^ 1]), d->R[cur ^ 1], d->d_nbr, d->d_nbr_nw,
+                                  d->d_adh, d->geom, d->phys, d->tile.push_lz, d->d_err, s);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH)
         return launch_step_push(d->tile.push_shape, d->push_maps[cur], d->f[cur ^ 1], d->d_nbr, d->d_nbr_nw, d->d_adh,
                                 d->geom, d->phys, d->tile.push_lz, d->tile.push_pf, d->tile.push_order, d->d_err, s);
@@ -117,6 +121,8 @@ cudaError_t launch_one(lbm_domain* d, int cur, cudaStream_t s) {
 }
 
 cudaError_t prepare_one(lbm_domain* d) {
+    if (d->params.precision != 0 && d->tile.kind == LBM_KERNEL_PUSH)
+        return prepare_step16_push(d->params.precision, d->tile.push_shape);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH) return prepare_step_push(d->tile.push_shape);
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA) return prepare_step_tma();
     if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_SPLIT) return cudaSuccess;
@@ -124,16 +130,27 @@ cudaError_t prepare_one(lbm_domain* d) {
     return d->params.precision == 0 ? prepare_step(d->tile) : prepare_step16(d->params.precision, d->tile);
 }
 
-// The layout the current kernel kind steps on: the push kernel keeps the FP32
-// state in the paired push layout, every other kernel in the pull layout.
-int wanted_layout(const lbm_domain* d) {
-    return (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH) ? 1 : 0;
-}
+// The layout the current kernel kind steps on: the push kernels keep the state
+// in the push layout (FP32: paired; 16-bit: the pull words, each at its reader),
+// every other kernel in the pull layout.
+int wanted_layout(const lbm_domain* d) { return d->tile.kind == LBM_KERNEL_PUSH ? 1 : 0; }
 
 // Converts the state into the given layout (into the other buffer, which then
 // becomes the current one).  The step counter is unchanged.
 int set_layout(lbm_domain* d, int layout) {
-    if (d->params.precision != 0 || d->layout == layout) return LBM_OK;
+    if (d->layout == layout) return LBM_OK;
+    if (d->params.precision != 0) {
+        const uint32_t* in = reinterpret_cast<const uint32_t*>(d->f[d->cur]);
+        uint32_t* out = reinterpret_cast<uint32_t*>(d->f[d->cur ^ 1]);
+        if (layout == 1) LBM_CUDA(launch_pull16_to_push16(in, out, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        else LBM_CUDA(launch_push16_to_pull16(in, out, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+        // the density pairs go with the words
+        LBM_CUDA(cudaMemcpyAsync(d->R[d->cur ^ 1], d->R[d->cur], sizeof(float2) * (size_t)d->geom.plane,
+                                 cudaMemcpyDeviceToDevice, d->stream));
+        d->cur ^= 1;
+        d->layout = layout;
+        return LBM_OK;
+    }
     if (layout == 1)
         LBM_CUDA(launch_pull_to_push(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
     else
@@ -154,6 +171,38 @@ int pull_view(lbm_domain* d, const float** out) {
     }
     LBM_CUDA(launch_push_to_pull(d->f[d->cur], d->f[d->cur ^ 1], d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
     *out = d->f[d->cur ^ 1];
+    return LBM_OK;
+}
+
+// The current 16-bit words in the pull layout, for the read-out kernels: f[cur]
+// itself, or (push layout) their conversion into the other buffer, which the
+// next step overwrites anyway.  The density pairs are R[cur] either way.
+int pull16_view(lbm_domain* d, const uint32_t** out) {
+    const uint32_t* in = reinterpret_cast<const uint32_t*>(d->f[d->cur]);
+    if (d->layout == 0) {
+        *out = in;
+        return LBM_OK;
+    }
+    uint32_t* o = reinterpret_cast<uint32_t*>(d->f[d->cur ^ 1]);
+    LBM_CUDA(launch_push16_to_pull16(in, o, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
+    *out = o;
+    return LBM_OK;
+}
+
+// Tensor maps of the 16-bit words and density pairs of both buffers for the
+// 16-bit push kernel's current shape.
+int ensure_push16_maps(lbm_domain* d) {
+    const int rows = push16_shape_rows(d->tile.push_shape);
+    if (d->push16_maps_rows == rows) return LBM_OK;
+    cudaError_t e = encode_push16_maps(d->geom, reinterpret_cast<uint32_t*>(d->f[0]),
+                                       reinterpret_cast<uint32_t*>(d->f[1]), d->R[0], d->R[1], rows, d->push16_w,
+                                       d->push16_r);
+    if (e != cudaSuccess) {
+        d->push16_maps_rows = 0;
+        set_error(std::string("tensor maps of the 16-bit push kernel: ") + cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    d->push16_maps_rows = rows;
     return LBM_OK;
 }
 
@@ -205,9 +254,9 @@ int capture_graph(lbm_domain* d, int parity) {
 int run_steps(lbm_domain* d, int n) {
     if (n <= 0) return LBM_OK;
     if (int rc = set_layout(d, wanted_layout(d))) return rc;
-    if (d->params.precision == 0 && d->tile.kind == LBM_KERNEL_PUSH) {
-        if (int rc = ensure_push_maps(d)) return rc;
-        d->tma_pending = true;  // the push kernel reports a wait that ran out through d_err
+    if (d->tile.kind == LBM_KERNEL_PUSH) {
+        if (int rc = d->params.precision == 0 ? ensure_push_maps(d) : ensure_push16_maps(d)) return rc;
+        d->tma_pending = true;  // the push kernels report a wait that ran out through d_err
     }
     const bool tma = d->params.precision == 0 && d->tile.kind == LBM_KERNEL_TMA;
     if (tma && !d->ghosts_ok) {
@@ -348,12 +397,14 @@ int create_common(const lbm_params* params, const uint8_t* mask_host, const int 
     g.pz = params->periodic[2] ? 1 : 0;
     fill_pull_offsets(g);
     d->tile = default_tile(g);
-    d->tile.push_shape = 1;  // 6 rows, 3 stages, two CTAs per SM
-    d->tile.push_lz = push_default_lz(g, 1);
+    // FP32: shape 1 (6 rows, 3 stages, two CTAs per SM); 16-bit: shape 0 (8 rows, 4 stages)
+    d->tile.push_shape = params->precision == 0 ? 1 : 0;
+    d->tile.push_lz = params->precision == 0 ? push_default_lz(g, 1) : push16_default_lz(g, 0);
     d->tile.push_pf = 0;
     d->tile.push_order = 0;
     d->layout = 0;
     d->push_maps_rows = 0;
+    d->push16_maps_rows = 0;
 
     auto fail = [&](int rc) { free_domain(d); return rc; };
 #define LBM_CUDA_D(call)                                                                  \
@@ -517,9 +568,12 @@ int lbm_get_density_at(lbm_domain* d, int x, int y, int z, double rho_out[2]) {
     } else if (d->params.precision == 0) {
         LBM_CUDA(launch_probe(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
     }
-    else
-        LBM_CUDA(launch_probe16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
+    else {
+        const uint32_t* w16 = nullptr;
+        if (int rc = pull16_view(d, &w16)) return rc;
+        LBM_CUDA(launch_probe16(d->params.precision, w16, d->R[d->cur],
                                 d->d_nbr, d->d_nbr_nw, d->geom, x, y, z, d->d_probe, d->stream));
+    }
     LBM_CUDA(cudaMemcpyAsync(d->h_result, d->d_probe, sizeof(float) * 2, cudaMemcpyDeviceToHost, d->stream));
     int rc = wait_domain(d);
     if (rc) return rc;
@@ -581,10 +635,13 @@ int lbm_measure(lbm_domain* d, lbm_measurement* out) {
         LBM_CUDA(launch_measure(d->f[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials,
                                 d->meas_blocks, d->d_result, d->stream));
     }
-    else
-        LBM_CUDA(launch_measure16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]), d->R[d->cur],
+    else {
+        const uint32_t* w16 = nullptr;
+        if (int rc = pull16_view(d, &w16)) return rc;
+        LBM_CUDA(launch_measure16(d->params.precision, w16, d->R[d->cur],
                                   d->d_nbr, d->d_nbr_nw, d->geom, d->params.G, d->d_partials, d->meas_blocks,
                                   d->d_result, d->stream));
+    }
     LBM_CUDA(cudaMemcpyAsync(d->h_result, d->d_result, sizeof(double) * NMEAS, cudaMemcpyDeviceToHost, d->stream));
     int rc = wait_domain(d);
     if (rc) return rc;
@@ -624,9 +681,12 @@ int lbm_get_density(lbm_domain* d, double* rho_out) {
         } else if (d->params.precision == 0) {
             LBM_CUDA(launch_density(d->f[d->cur], d->d_rho, d->d_nbr, d->d_nbr_nw, d->geom, d->stream));
         }
-        else
-            LBM_CUDA(launch_density16(d->params.precision, reinterpret_cast<const uint32_t*>(d->f[d->cur]),
+        else {
+            const uint32_t* w16 = nullptr;
+            if (int rc = pull16_view(d, &w16)) return rc;
+            LBM_CUDA(launch_density16(d->params.precision, w16,
                                       d->R[d->cur], d->d_nbr, d->d_nbr_nw, d->geom, d->d_rho, d->stream));
+        }
         std::vector<float> tmp((size_t)(2 * d->N));
         LBM_CUDA(cudaMemcpyAsync(tmp.data(), d->d_rho, sizeof(float) * 2 * d->N, cudaMemcpyDeviceToHost, d->stream));
         int rc = wait_domain(d);
@@ -704,14 +764,16 @@ int lbm_set_step_kernel(lbm_domain* d, int kind, int lz) {
         return LBM_ERR_ARG;
     }
     if (kind == LBM_KERNEL_PUSH) {
-        if (d->params.precision != 0 || !push_step_applicable(d->geom)) {
-            set_error("the push step kernel needs an FP32 domain without periodic x or y and with an even nx");
+        const bool fp32 = d->params.precision == 0;
+        if (fp32 ? !push_step_applicable(d->geom) : !push16_step_applicable(d->geom)) {
+            set_error(fp32 ? "the push step kernel needs a box without periodic x or y and with an even nx"
+                           : "the 16-bit push step kernel needs a box without periodic x or y and with nx % 4 == 0");
             return LBM_ERR_STATE;
         }
         if (lz > 0) d->tile.push_lz = lz > d->geom.nz ? d->geom.nz : lz;
         d->tile.kind = kind;
         drop_graphs(d);
-        return ensure_push_maps(d);
+        return fp32 ? ensure_push_maps(d) : ensure_push16_maps(d);
     }
     if ((kind == LBM_KERNEL_SPLIT || kind == LBM_KERNEL_STAGED2) && d->params.precision != 0) {
         set_error("the two-launch and two-threads-per-cell step kernels need an FP32 domain");
@@ -745,16 +807,22 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz) {
 
 int lbm_set_push_shape(lbm_domain* d, int shape, int lz) {
     if (!d) { set_error("domain is NULL"); return LBM_ERR_ARG; }
-    if (shape < 0 || shape >= push_shape_count()) { set_error("unknown push kernel shape"); return LBM_ERR_ARG; }
-    if (d->params.precision != 0 || !push_step_applicable(d->geom)) {
-        set_error("the push step kernel needs an FP32 domain without periodic x or y and with an even nx");
+    const bool fp32 = d->params.precision == 0;
+    if (shape < 0 || shape >= (fp32 ? push_shape_count() : push16_shape_count())) {
+        set_error("unknown push kernel shape");
+        return LBM_ERR_ARG;
+    }
+    if (fp32 ? !push_step_applicable(d->geom) : !push16_step_applicable(d->geom)) {
+        set_error(fp32 ? "the push step kernel needs a box without periodic x or y and with an even nx"
+                       : "the 16-bit push step kernel needs a box without periodic x or y and with nx % 4 == 0");
         return LBM_ERR_STATE;
     }
     d->tile.push_shape = shape;
-    d->tile.push_lz = lz > 0 ? (lz > d->geom.nz ? d->geom.nz : lz) : push_default_lz(d->geom, shape);
+    d->tile.push_lz = lz > 0 ? (lz > d->geom.nz ? d->geom.nz : lz)
+                             : (fp32 ? push_default_lz(d->geom, shape) : push16_default_lz(d->geom, shape));
     d->tile.kind = LBM_KERNEL_PUSH;
     drop_graphs(d);
-    return ensure_push_maps(d);
+    return fp32 ? ensure_push_maps(d) : ensure_push16_maps(d);
 }
 
 int lbm_set_push_prefetch(lbm_domain* d, int planes) {
@@ -824,6 +892,17 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
                         t.push_order = order;
                         cand.push_back(t);
                     }
+    if (!fp32 && push16_step_applicable(g))
+        for (int sh = 0; sh < push16_shape_count(); ++sh)
+            for (int lz : {16, 24, 32, 48}) {
+                StepTile t = orig;
+                t.kind = LBM_KERNEL_PUSH;
+                t.push_shape = sh;
+                t.push_lz = lz > g.nz ? g.nz : lz;
+                t.push_pf = 0;
+                t.push_order = 0;
+                cand.push_back(t);
+            }
     if (fp32 && d->tma_ok)
         for (int lz : {8, 12, 16, 24, 32, 48}) add(LBM_KERNEL_TMA, orig.by, lz, orig.lead);
     if (fp32) add(LBM_KERNEL_SPLIT, orig.by, orig.lz, orig.lead);
@@ -903,11 +982,15 @@ int lbm_autotune(lbm_domain* d, int trial_steps, lbm_tune_result* out) {
     if (rc) return rc;
     if (out) {
         out->kind = best_t.kind;
-        out->by = best_t.kind == LBM_KERNEL_PUSH ? push_shape_rows(best_t.push_shape) : best_t.by;
+        out->by = best_t.kind == LBM_KERNEL_PUSH
+                      ? (fp32 ? push_shape_rows(best_t.push_shape) : push16_shape_rows(best_t.push_shape))
+                      : best_t.by;
         out->lz = best_t.kind == LBM_KERNEL_TMA ? best_t.tma_lz
                   : best_t.kind == LBM_KERNEL_PUSH ? best_t.push_lz
                                                    : best_t.lz;
-        out->lead = best_t.kind == LBM_KERNEL_PUSH ? push_shape_stages(best_t.push_shape) : best_t.lead;
+        out->lead = best_t.kind == LBM_KERNEL_PUSH
+                        ? (fp32 ? push_shape_stages(best_t.push_shape) : push16_shape_stages(best_t.push_shape))
+                        : best_t.lead;
         out->ms_per_step = best;
         out->n_candidates = (int)cand.size();
         out->prefetch = best_t.kind == LBM_KERNEL_PUSH ? best_t.push_pf : 0;

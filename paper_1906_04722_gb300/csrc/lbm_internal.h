@@ -161,6 +161,24 @@ cudaError_t launch_step_split(const float* fin, float* fout, float2* rho2, const
 double throat_incircle(const double* s3);
 
 constexpr int PUSH_MAX_PREFETCH = 4;
+
+// The push kernel of 16-bit storage (lbm_step16_push.cu) and the conversions
+// of a 16-bit state between the pull and push layouts (lbm_step16.cu).
+int push16_shape_count();
+int push16_shape_rows(int shape);
+int push16_shape_stages(int shape);
+bool push16_step_applicable(const Geom& g);
+int push16_default_lz(const Geom& g, int shape);
+cudaError_t encode_push16_maps(const Geom& g, uint32_t* w0, uint32_t* w1, float2* r0, float2* r1, int by,
+                               CUtensorMap (&mw)[2], CUtensorMap (&mr)[2]);
+cudaError_t prepare_step16_push(int precision, int shape);
+cudaError_t launch_step16_push(int precision, int shape, const CUtensorMap& tw, const CUtensorMap& tr,
+                               uint32_t* wout, float2* Rout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                               const uint32_t* adh, const Geom& g, const Phys& p, int lz, int* err, cudaStream_t s);
+cudaError_t launch_pull16_to_push16(const uint32_t* win, uint32_t* wout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                    const Geom& g, cudaStream_t s);
+cudaError_t launch_push16_to_pull16(const uint32_t* win, uint32_t* wout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                    const Geom& g, cudaStream_t s);
 int push_shape_count();
 int push_shape_rows(int shape);
 int push_shape_stages(int shape);
@@ -239,6 +257,9 @@ struct lbm_domain {
     float2* d_rho2;     // FP32 domains: (rho_w, rho_nw) per cell for the two-launch step
     int layout;         // FP32 state in f[cur]: 0 = pull layout, 1 = paired push layout
     CUtensorMap push_maps[2];  // tensor maps of f[0], f[1] for the push kernel's shape
+    CUtensorMap push16_w[2];   // 16-bit storage: tensor maps of the words of f[0], f[1]
+    CUtensorMap push16_r[2];   // and of the density pairs R[0], R[1]
+    int push16_maps_rows;      // box rows the 16-bit push maps were encoded for (0: none)
     int push_maps_rows;        // box rows the push maps were encoded for (0: none)
 };
 

@@ -23,46 +23,12 @@
 #include <algorithm>
 #include <cstring>
 
+#include "lbm_pair16.cuh"
 #include "lbm_step_core.cuh"
 
 namespace lbmk {
 
 namespace {
-
-template <class H2>
-struct Pair;
-
-template <>
-struct Pair<__half2> {
-    static __device__ __forceinline__ float2 unpack(uint32_t u) {
-        __half2 h;
-        memcpy(&h, &u, 4);
-        return __half22float2(h);
-    }
-    static __device__ __forceinline__ uint32_t pack(float a, float b) {
-        const __half2 h = __floats2half2_rn(a, b);
-        uint32_t u;
-        memcpy(&u, &h, 4);
-        return u;
-    }
-    static __device__ __forceinline__ float round1(float v) { return __half2float(__float2half_rn(v)); }
-};
-
-template <>
-struct Pair<__nv_bfloat162> {
-    static __device__ __forceinline__ float2 unpack(uint32_t u) {
-        __nv_bfloat162 h;
-        memcpy(&h, &u, 4);
-        return __bfloat1622float2(h);
-    }
-    static __device__ __forceinline__ uint32_t pack(float a, float b) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        uint32_t u;
-        memcpy(&u, &h, 4);
-        return u;
-    }
-    static __device__ __forceinline__ float round1(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-};
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -363,6 +329,76 @@ __global__ void probe16_kernel(const uint32_t* __restrict__ win, const float2* _
     out[1] = rn;
 }
 
+// Pull layout -> push layout of a 16-bit state: W[k][D] = the word D pulls in
+// direction k, each half from its own component's source (D - e_k where that is
+// fluid for the component, else D's own slot kbar); 0 where D is grain and in the
+// non-wetting half of a membrane cell.  The deviations stay as they are: in
+// both layouts a value is held against the density of the cell that reads it.
+__global__ void pull16_to_push16_kernel(const uint32_t* __restrict__ win, uint32_t* __restrict__ wout,
+                                        const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw, Geom g) {
+    const long long N = (long long)g.nxy * g.nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)c;
+        const int x = ci % g.nx, y = (ci / g.nx) % g.ny, z = ci / g.nxy;
+        const uint32_t w = nbr[ci];
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        if (cls == CLS_SOLID) {
+            for (int k = 0; k < Q; ++k) wout[(size_t)k * g.plane + ci] = 0u;
+            continue;
+        }
+        const bool has_nw = cls != CLS_MEMBRANE;
+        const uint32_t wn = !has_nw ? w : ((w & BIT_NW_DIFF) ? nbr_nw[ci] : w);
+        const Column col = make_column(x, y, g);
+        const bool seam = seam_of(g, col, z);
+        int zo[3];
+        zo[0] = nb1(z - 1, g.nz, g.pz) * g.nxy;
+        zo[1] = z * g.nxy;
+        zo[2] = nb1(z + 1, g.nz, g.pz) * g.nxy;
+        for (int k = 0; k < Q; ++k) {
+            const uint32_t a = win[src_index(g, col, z, zo, seam, ci, w, k)];
+            const uint32_t b = has_nw ? win[src_index(g, col, z, zo, seam, ci, wn, k)] : 0u;
+            wout[(size_t)k * g.plane + ci] = (a & 0xffffu) | (b & 0xffff0000u);
+        }
+    }
+}
+
+// Push layout -> pull layout of a 16-bit state: half s of slot k of cell y holds
+// what y + e_k pulls from y, half s of W[k][y + e_k], where y + e_k is fluid for
+// component s; otherwise what y pulls from itself in direction kbar, half s of
+// W[kbar][y].  0 where the component is not fluid.
+__global__ void push16_to_pull16_kernel(const uint32_t* __restrict__ win, uint32_t* __restrict__ wout,
+                                        const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ nbr_nw, Geom g) {
+    const long long N = (long long)g.nxy * g.nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)c;
+        const int x = ci % g.nx, y = (ci / g.nx) % g.ny, z = ci / g.nxy;
+        const uint32_t w = nbr[ci];
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        uint32_t out[Q];
+        for (int k = 0; k < Q; ++k) out[k] = 0u;
+        for (int s = 0; s < 2; ++s) {
+            if (cls == CLS_SOLID || (s == 1 && cls == CLS_MEMBRANE)) continue;
+            const uint32_t bits = s == 0 ? w : ((w & BIT_NW_DIFF) ? nbr_nw[ci] : w);
+            for (int k = 0; k < Q; ++k) {
+                // bit kbar of the pull bits: y + e_k is not fluid for component s
+                size_t src;
+                if (k == 0 || ((bits >> OPP(k)) & 1u)) {
+                    src = (size_t)OPP(k) * g.plane + ci;  // OPP(0) = 0: the rest slot
+                } else {
+                    bool ok = true;
+                    const int tx = wrap1(x + EX(k), g.nx, g.px, ok);
+                    const int ty = wrap1(y + EY(k), g.ny, g.py, ok);
+                    const int tz = wrap1(z + EZ(k), g.nz, g.pz, ok);
+                    src = (size_t)k * g.plane + (size_t)tz * g.nxy + (size_t)ty * g.nx + tx;
+                }
+                const uint32_t half = s == 0 ? (win[src] & 0xffffu) : (win[src] & 0xffff0000u);
+                out[k] |= half;
+            }
+        }
+        for (int k = 0; k < Q; ++k) wout[(size_t)k * g.plane + ci] = out[k];
+    }
+}
+
 // Start of a 16-bit state: every deviation 0 and R = rho0, so the first pull
 // yields w_k rho0(x) exactly (the rest equilibrium of the given densities).
 __global__ void init16_kernel(const float* __restrict__ rho0, float2* __restrict__ R, Geom g) {
@@ -455,6 +491,18 @@ cudaError_t launch_probe16(int precision, const uint32_t* w, const float2* R, co
                            const uint32_t* nbr_nw, const Geom& g, int x, int y, int z, float* out, cudaStream_t s) {
     if (precision == 1) probe16_kernel<__half2><<<1, 1, 0, s>>>(w, R, nbr, nbr_nw, g, x, y, z, out);
     else probe16_kernel<__nv_bfloat162><<<1, 1, 0, s>>>(w, R, nbr, nbr_nw, g, x, y, z, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pull16_to_push16(const uint32_t* win, uint32_t* wout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                    const Geom& g, cudaStream_t s) {
+    pull16_to_push16_kernel<<<grid_cells((long long)g.nxy * g.nz), 256, 0, s>>>(win, wout, nbr, nbr_nw, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push16_to_pull16(const uint32_t* win, uint32_t* wout, const uint32_t* nbr, const uint32_t* nbr_nw,
+                                    const Geom& g, cudaStream_t s) {
+    push16_to_pull16_kernel<<<grid_cells((long long)g.nxy * g.nz), 256, 0, s>>>(win, wout, nbr, nbr_nw, g);
     return cudaGetLastError();
 }
 
