@@ -45,6 +45,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+POP_STORAGE = {0: "FP32 populations", 1: "FP16 population deviations", 2: "BF16 population deviations"}
 METRIC = "D3Q19 2-comp Shan-Chen MLUPS & % HBM peak; pore throats/s vs plain"
 FALLBACK_HBM_GBS = 6800.0
 E2E_SUBSTEPS = 100
@@ -449,6 +450,9 @@ def run_ours(args, rank, world, local):
         # 16-bit storage: 19 pair words read + written and the density pair read
         # + written per non-solid cell
         bytes_per_step = n_upd * (19 * 4 * 2 + 8 + 8)
+    # one population buffer: 19 slots of (w, nw) pairs of 4-byte floats or of a
+    # 4-byte word of two 16-bit deviations per cell
+    pop_buffer_gb = 19 * (8 if args.precision == 0 else 4) * box[0] * box[1] * box[2] / 1e9
     dom.set_pressure_bc(2.1, W.RHO_MAJOR)
     # the library's autotuner picks the step kernel and its launch shape on this
     # domain (state restored afterwards); untimed
@@ -485,9 +489,13 @@ def run_ours(args, rank, world, local):
     apply_tuned(dom)
 
     kind, _ = dom.step_kernel()
-    if args.precision:
+    h2 = "half2" if args.precision == 1 else "bfloat162"
+    if args.precision and kind == lbm.KERNEL_PUSH:
+        rows, stages, ctas = lbm.PUSH16_SHAPE_TABLE[tuned["shape"]][:3]
+        kernel_name = "sc_step16_push_kernel<%s,%d,%d,%d>" % (h2, rows, stages, ctas)
+    elif args.precision:
         by, _, lead = lbm.lbm_get_tile(dom.h)
-        kernel_name = "sc_step16_kernel<%s,%d,%d>" % ("half2" if args.precision == 1 else "bfloat162", by, lead)
+        kernel_name = "sc_step16_kernel<%s,%d,%d>" % (h2, by, lead)
     elif kind == lbm.KERNEL_PUSH:
         rows, stages, ctas, resident = lbm.PUSH_SHAPE_TABLE[tuned["shape"]]
         kernel_name = "sc_step_push_kernel<%d,%d,%d,%s,%s>" % (
@@ -567,10 +575,10 @@ def run_ours(args, rank, world, local):
            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "f16 deviations, f32 math", 2: "bf16 deviations, f32 math"}[args.precision],
            "data": "synthetic",
            "config": {"workload": f"sample{args.size}: {args.size}^3, {len(spheres)} RSA spheres r~U[10,14], "
-                                  "reservoirs + 3 membrane layers, FP32 populations, one fused step per launch",
+                                  f"reservoirs + 3 membrane layers, {POP_STORAGE[args.precision]}, one fused step per launch",
                       "fluid_cells": n_upd, "global_batch": world, "seq_len": 0,
                       "parallelism": "replicas" if world > 1 else "single GPU",
-                      "l2": "inputs larger than L2 (2 x 1.08 GB population buffers)",
+                      "l2": "inputs larger than L2 (2 x %.2f GB population buffers)" % pop_buffer_gb,
                       "step_kernel": tuned if tuned is not None else "default"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": read_traffic(kernel_name) if args.size == 192 else None, "peak_kind": peak_kind,

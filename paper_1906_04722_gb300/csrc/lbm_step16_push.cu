@@ -60,7 +60,17 @@ constexpr size_t push16_smem_bytes() {
            sizeof(uint64_t) * NS;
 }
 
-template <class H2, int BY, int NS, int MINB>
+// one cell's 19 pair words and its R pair
+struct CellWords {
+    uint32_t w[Q];
+    float2 R;
+};
+
+// RR: each interior thread keeps its cell's words in registers from the density
+// pass to its collision, so a stage is free once its plane's densities are in
+// the ring and all NS stages are in flight; otherwise the collision reads the
+// words from the stage again and NS - 2 stages load ahead.
+template <class H2, int BY, int NS, int MINB, bool RR>
 __global__ void __launch_bounds__(P16X * BY, MINB)
     sc_step16_push_kernel(const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap tr,
                           uint32_t* __restrict__ wout, float2* __restrict__ Rout, const uint32_t* __restrict__ nbr,
@@ -127,27 +137,34 @@ __global__ void __launch_bounds__(P16X * BY, MINB)
         }
         return __ldg(nbr + (size_t)zc * g.nxy + col);
     };
-    // the populations of this thread's box cell on plane j from its own words and
-    // R pair (the pull kernel's reconstruction; 0 for the non-wetting fluid on a
-    // membrane, whatever that half of the words holds)
-    auto reconstruct = [&](int j, bool has_nw, float (&f)[2][Q]) {
+    // the pair words and the R pair of this thread's box cell on plane j
+    auto fetch = [&](int j, CellWords& c) {
         const uint32_t* ws = reinterpret_cast<const uint32_t*>(stw + (size_t)slot(j) * WP) + sc;
-        const float2 R = reinterpret_cast<const float2*>(str + (size_t)slot(j) * RP)[sc];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) c.w[k] = ws[k * (BY * P16BX)];
+        c.R = reinterpret_cast<const float2*>(str + (size_t)slot(j) * RP)[sc];
+    };
+    // the populations of a cell from its words and R pair (the pull kernel's
+    // reconstruction; 0 for the non-wetting fluid on a membrane, whatever that
+    // half of the words holds)
+    auto reconstruct = [&](const CellWords& c, bool has_nw, float (&f)[2][Q]) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            const float2 h = Pair<H2>::unpack(ws[k * (BY * P16BX)]);
-            f[0][k] = h.x + WK(k) * R.x;
-            f[1][k] = has_nw ? h.y + WK(k) * R.y : 0.f;
+            const float2 h = Pair<H2>::unpack(c.w[k]);
+            f[0][k] = h.x + WK(k) * c.R.x;
+            f[1][k] = has_nw ? h.y + WK(k) * c.R.y : 0.f;
         }
     };
     // densities of the box cell on plane j into the ring (0 where not fluid; a
     // buffer's grain slots may hold anything), and into R out for the interior
-    auto publish = [&](int j, uint32_t wp) {
+    // (RR: the words stay in `keep` for the collision)
+    auto publish = [&](int j, uint32_t wp, CellWords& keep) {
         const uint32_t c = (wp >> CLS_SHIFT) & CLS_MASK;
         float rw = 0.f, rn = 0.f;
         if (c != CLS_SOLID && c != CLS_OUTSIDE) {
             float f[2][Q];
-            reconstruct(j, c != CLS_MEMBRANE, f);
+            fetch(j, keep);
+            reconstruct(keep, c != CLS_MEMBRANE, f);
             float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < Q; ++k) {
@@ -183,10 +200,11 @@ __global__ void __launch_bounds__(P16X * BY, MINB)
     uint32_t w_0 = word(1), w_1 = word(2);
     uint32_t a_0, nwb_0;
     extra(1, w_0, a_0, nwb_0);
+    CellWords cur, nxt;  // RR: words of the plane to collide and of the next plane
     bool ok = p_mbar_wait_bounded(bar + slot(0), parity(0));
-    if (ok) publish(0, w_m);
+    if (ok) publish(0, w_m, nxt);
     ok = ok && p_mbar_wait_bounded(bar + slot(1), parity(1));
-    if (ok) publish(1, w_0);
+    if (ok) publish(1, w_0, cur);
     // a failed wait here is reported by the first iteration's barrier below
     for (int j = 1; j <= n; ++j) {
         const int z = plane(j);
@@ -194,29 +212,40 @@ __global__ void __launch_bounds__(P16X * BY, MINB)
         const uint32_t w_2 = word(j + 2);  // for the next iteration's publish
         extra(j + 1, w_1, a_0, nwb_0);     // for the next iteration's collision
         const bool okz = ok && p_mbar_wait_bounded(bar + slot(j + 1), parity(j + 1));
-        if (okz) publish(j + 1, w_1);
+        if (okz) publish(j + 1, w_1, nxt);
         if (__syncthreads_or(!okz)) {
             if (tid == 0) {
                 atomicOr(err, 1);
-                for (int q = max(0, j - 1); q < next; ++q) p_mbar_wait_bounded(bar + slot(q), parity(q));
+                for (int q = max(0, next - NS); q < next; ++q) p_mbar_wait_bounded(bar + slot(q), parity(q));
             }
             __syncthreads();
             return;
         }
         if (tid == 0) {
-            // the stage of sequence plane j - 1 was read by everyone before the barrier
-            const int last = j + NS - 1;
+            // stages read by everyone before the barrier: RR frees the stages of
+            // sequence planes up to j + 1, the other form those up to j - 1
+            const int last = RR ? j + 1 + NS : j + NS - 1;
             if (next <= n + 1 && next <= last) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             for (; next <= n + 1 && next <= last; ++next) issue(next);
         }
         w_0 = w_1;
         w_1 = w_2;
         const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
-        if (!interior || cls == CLS_SOLID || cls == CLS_OUTSIDE) continue;
+        if (!interior || cls == CLS_SOLID || cls == CLS_OUTSIDE) {
+            if constexpr (RR) cur = nxt;
+            continue;
+        }
         const bool has_nw = cls != CLS_MEMBRANE;
         const uint32_t wn = has_nw && (w & BIT_NW_DIFF) ? nwb : w;
         float f[2][Q];
-        reconstruct(j, has_nw, f);
+        if constexpr (RR) {
+            reconstruct(cur, has_nw, f);
+            cur = nxt;
+        } else {
+            CellWords c;
+            fetch(j, c);
+            reconstruct(c, has_nw, f);
+        }
         float out[2][Q];
         collide_generic<BY>(f, ring, w, a, z, row, lane, P, [&](int s, int k, float v) { out[s][k] = v; });
         if (!has_nw) {
@@ -263,7 +292,7 @@ __global__ void __launch_bounds__(P16X * BY, MINB)
     }
 }
 
-template <class H2, int BY, int NS, int MINB>
+template <class H2, int BY, int NS, int MINB, bool RR>
 cudaError_t configure_push16() {
     static unsigned long long configured = 0;  // one bit per device: the attribute is per device
     int dev = 0;
@@ -271,7 +300,7 @@ cudaError_t configure_push16() {
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(configured & bit)) {
-        e = cudaFuncSetAttribute(sc_step16_push_kernel<H2, BY, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sc_step16_push_kernel<H2, BY, NS, MINB, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)push16_smem_bytes<BY, NS>());
         if (e != cudaSuccess) return e;
         configured |= bit;
@@ -279,29 +308,33 @@ cudaError_t configure_push16() {
     return cudaSuccess;
 }
 
-template <class H2, int BY, int NS, int MINB>
+template <class H2, int BY, int NS, int MINB, bool RR>
 cudaError_t launch_push16_shape(const CUtensorMap& tw, const CUtensorMap& tr, uint32_t* wout, float2* Rout,
                                 const uint32_t* nbr, const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g,
                                 const Phys& p, int lz, int* err, cudaStream_t s) {
     constexpr int TY = BY - 2;
     const dim3 grid((g.nx + P16XI - 1) / P16XI, (g.ny + TY - 1) / TY, (g.nz + lz - 1) / lz);
-    sc_step16_push_kernel<H2, BY, NS, MINB><<<grid, dim3(P16X, BY), push16_smem_bytes<BY, NS>(), s>>>(
+    sc_step16_push_kernel<H2, BY, NS, MINB, RR><<<grid, dim3(P16X, BY), push16_smem_bytes<BY, NS>(), s>>>(
         tw, tr, wout, Rout, nbr, nbr_nw, adh, g, p, lz, err);
     return cudaGetLastError();
 }
 
 // Shapes by index: box rows BY, plane stages NS, CTAs per SM (which also caps a
-// thread's registers).
+// thread's registers), register-resident words (RR).
 struct Push16ShapeInfo {
     int by, ns, minb;
+    bool rr;
 };
-constexpr Push16ShapeInfo kPush16Shapes[] = {{8, 4, 2}, {6, 4, 2}, {7, 4, 2}, {10, 3, 2}};
+constexpr Push16ShapeInfo kPush16Shapes[] = {{8, 4, 2, false}, {6, 4, 2, false}, {7, 4, 2, false},
+                                             {10, 3, 2, false}, {6, 4, 2, true},  {8, 4, 2, true},
+                                             {7, 4, 2, true},   {6, 3, 3, true},  {5, 4, 3, true},
+                                             {10, 4, 1, true},  {12, 3, 1, true}, {8, 3, 2, true}};
 constexpr int N_PUSH16_SHAPES = (int)(sizeof(kPush16Shapes) / sizeof(kPush16Shapes[0]));
 
 template <int I, class H2>
 cudaError_t configure16_shape() {
     constexpr Push16ShapeInfo S = kPush16Shapes[I];
-    return configure_push16<H2, S.by, S.ns, S.minb>();
+    return configure_push16<H2, S.by, S.ns, S.minb, S.rr>();
 }
 
 template <int I, class H2>
@@ -309,7 +342,7 @@ cudaError_t launch16_shape(const CUtensorMap& tw, const CUtensorMap& tr, uint32_
                            const uint32_t* nbr, const uint32_t* nbr_nw, const uint32_t* adh, const Geom& g,
                            const Phys& p, int lz, int* err, cudaStream_t s) {
     constexpr Push16ShapeInfo S = kPush16Shapes[I];
-    return launch_push16_shape<H2, S.by, S.ns, S.minb>(tw, tr, wout, Rout, nbr, nbr_nw, adh, g, p, lz, err, s);
+    return launch_push16_shape<H2, S.by, S.ns, S.minb, S.rr>(tw, tr, wout, Rout, nbr, nbr_nw, adh, g, p, lz, err, s);
 }
 
 using Encode16Fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -387,22 +420,26 @@ int push16_default_lz(const Geom& g, int shape) {
 }
 
 cudaError_t prepare_step16_push(int precision, int shape) {
-    static_assert(N_PUSH16_SHAPES == 4, "one case per shape below");
-    if (precision == 1) {
-        switch (shape) {
-            case 0: return configure16_shape<0, __half2>();
-            case 1: return configure16_shape<1, __half2>();
-            case 2: return configure16_shape<2, __half2>();
-            case 3: return configure16_shape<3, __half2>();
-        }
-    } else if (precision == 2) {
-        switch (shape) {
-            case 0: return configure16_shape<0, __nv_bfloat162>();
-            case 1: return configure16_shape<1, __nv_bfloat162>();
-            case 2: return configure16_shape<2, __nv_bfloat162>();
-            case 3: return configure16_shape<3, __nv_bfloat162>();
-        }
+    static_assert(N_PUSH16_SHAPES == 12, "one case per shape below");
+#define LBM_C16(I)                                                                                               \
+    case I:                                                                                                      \
+        return precision == 1 ? configure16_shape<I, __half2>() : configure16_shape<I, __nv_bfloat162>();
+    if (precision != 1 && precision != 2) return cudaErrorInvalidValue;
+    switch (shape) {
+        LBM_C16(0)
+        LBM_C16(1)
+        LBM_C16(2)
+        LBM_C16(3)
+        LBM_C16(4)
+        LBM_C16(5)
+        LBM_C16(6)
+        LBM_C16(7)
+        LBM_C16(8)
+        LBM_C16(9)
+        LBM_C16(10)
+        LBM_C16(11)
     }
+#undef LBM_C16
     return cudaErrorInvalidValue;
 }
 
@@ -421,6 +458,14 @@ cudaError_t launch_step16_push(int precision, int shape, const CUtensorMap& tw, 
         LBM_P16(1)
         LBM_P16(2)
         LBM_P16(3)
+        LBM_P16(4)
+        LBM_P16(5)
+        LBM_P16(6)
+        LBM_P16(7)
+        LBM_P16(8)
+        LBM_P16(9)
+        LBM_P16(10)
+        LBM_P16(11)
     }
 #undef LBM_P16
     return cudaErrorInvalidValue;

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(PX * BY, MINB)
             if (tid == 0) {
                 atomicOr(err, 1);
                 // bounded waits for every copy still in flight
-                for (int q = max(0, j - 1); q < next; ++q) p_mbar_wait_bounded(bar + slot(q), parity(q));
+                for (int q = max(0, next - NS); q < next; ++q) p_mbar_wait_bounded(bar + slot(q), parity(q));
             }
             __syncthreads();
             return;

@@ -56,7 +56,8 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("shape,lz", [(0, 13), (1, 7), (2, 45), (3, 16), (0, 1), (1, 2)])
+@pytest.mark.parametrize("shape,lz", [(0, 13), (1, 7), (2, 45), (3, 16), (0, 1), (1, 2), (4, 13), (5, 7), (6, 45),
+                                      (7, 16), (8, 1), (9, 2), (10, 13), (11, 5)])
 @pytest.mark.parametrize("periodic_z", [0, 1])
 def test_push16_equals_staged16_bitwise(lbm, precision, shape, lz, periodic_z):
     a = _domain(lbm, precision, periodic_z)
