@@ -628,12 +628,14 @@ int lbm_get_step_kernel(const lbm_domain* d, int* kind, int* lz);
  *          On a 16-bit domain (params.precision 1 or 2) the shapes of the
  *          16-bit push kernel: 0: 8 rows, 4 stages; 1: 6 rows, 4 stages;
  *          2: 7 rows, 4 stages; 3: 10 rows, 3 stages; two CTAs per SM each;
- *          4 .. 11 keep each cell's pair words in registers from the density
- *          pass to the collision: 4: 6 rows, 4 stages, two CTAs; 5: 8 rows,
- *          4 stages, two CTAs; 6: 7 rows, 4 stages, two CTAs; 7: 6 rows,
- *          3 stages, three CTAs; 8: 5 rows, 4 stages, three CTAs; 9: 10 rows,
- *          4 stages, one CTA; 10: 12 rows, 3 stages, one CTA; 11: 8 rows,
- *          3 stages, two CTAs.  It needs nx % 4 == 0 (besides no periodic x or y), and its results
+ *          6: 9 rows, 3 stages, two CTAs; 7: 7 rows, 3 stages, three CTAs;
+ *          8: 6 rows, 3 stages, three CTAs; 9: 11 rows, 3 stages, two CTAs;
+ *          4, 5, 10 and 11 keep each cell's pair words in registers from the
+ *          density pass to the collision: 4: 6 rows, 4 stages, two CTAs;
+ *          5: 8 rows, 4 stages, two CTAs; 10: 12 rows, 3 stages, one CTA;
+ *          11: 8 rows, 3 stages, two CTAs.  With tau = 1 in both components a
+ *          compile-time tau = 1 form of the collision runs (the same bits).
+ *          It needs nx % 4 == 0 (besides no periodic x or y), and its results
  *          equal the staged 16-bit kernel's bit for bit; prefetch and segment
  *          order do not apply to it.
  *   lz     planes per CTA z segment (lz <= 0: a default for the box).

@@ -381,7 +381,7 @@ PUSH_SHAPE_TABLE = [(8, 4, 1, False), (6, 3, 2, False), (10, 3, 1, False), (7, 3
 PUSH_SHAPES = len(PUSH_SHAPE_TABLE)
 # lbm_set_push_shape index on a 16-bit domain -> (box rows, plane stages, CTAs per SM, words held in registers)
 PUSH16_SHAPE_TABLE = [(8, 4, 2, False), (6, 4, 2, False), (7, 4, 2, False), (10, 3, 2, False), (6, 4, 2, True),
-                      (8, 4, 2, True), (7, 4, 2, True), (6, 3, 3, True), (5, 4, 3, True), (10, 4, 1, True),
+                      (8, 4, 2, True), (9, 3, 2, False), (7, 3, 3, False), (6, 3, 3, False), (11, 3, 2, False),
                       (12, 3, 1, True), (8, 3, 2, True)]
 BATCH_AUTO = 0
 BATCH_PERSISTENT = 1
