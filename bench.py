@@ -159,11 +159,15 @@ KERNEL_SOURCES = {
     "sc_step_tma_kernel": ("lbm_step_tma.cu", "lbm_step_core.cuh", "lbm_device.cuh", "lbm_internal.h"),
     "sc_step_push_kernel": ("lbm_step_push.cu", "lbm_push_tma.cuh", "lbm_step_core.cuh", "lbm_device.cuh",
                             "lbm_internal.h"),
+    "sc_step16_push_kernel": ("lbm_step16_push.cuh", "lbm_step16_push.cu", "lbm_step16_push_bf16.cu",
+                              "lbm_pair16.cuh", "lbm_push_tma.cuh", "lbm_step_core.cuh", "lbm_device.cuh",
+                              "lbm_internal.h"),
 }
 
 
 def kernel_hash(kernel_name="sc_step_kernel"):
-    key = next((k for k in ("sc_step_tma_kernel", "sc_step_push_kernel") if kernel_name.startswith(k)),
+    key = next((k for k in ("sc_step_tma_kernel", "sc_step_push_kernel", "sc_step16_push_kernel")
+                if kernel_name.startswith(k)),
                "sc_step_kernel")
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[key]:
@@ -460,8 +464,9 @@ def run_ours(args, rank, world, local):
         f = args.shape.split(":")
         if f[0] == "push":  # push:shape:lz[:prefetch planes]
             sh = int(f[1])
-            tuned = {"kind": "push", "shape": sh, "by": lbm.PUSH_SHAPE_TABLE[sh][0], "lz": int(f[2]),
-                     "lead": lbm.PUSH_SHAPE_TABLE[sh][1], "prefetch": int(f[3]) if len(f) > 3 else 0,
+            table = lbm.PUSH16_SHAPE_TABLE if args.precision else lbm.PUSH_SHAPE_TABLE
+            tuned = {"kind": "push", "shape": sh, "by": table[sh][0], "lz": int(f[2]),
+                     "lead": table[sh][1], "prefetch": int(f[3]) if len(f) > 3 else 0,
                      "order": int(f[4]) if len(f) > 4 else 0}
         else:
             tuned = ({"kind": "tma", "lz": int(f[1])} if f[0] == "tma" else {"kind": "split"} if f[0] == "split" else
