@@ -96,19 +96,25 @@ def test_16bit_mass_conservation(lbm, precision):
         assert abs(m1[s] - m0[s]) <= 1e-4 * m0[s], (s, m0[s], m1[s])
 
 
+@pytest.mark.parametrize("kernel", ["push", "staged"])
 @pytest.mark.parametrize("precision,bound", [(1, 2e-3), (2, 2e-2)])
-def test_16bit_sample192_sampled_cells(lbm, orc, precision, bound):
-    """The 192^3 drainage sample with 16-bit storage in the launch shape the
-    autotuner picks for it (32 x 8 threads, 32-plane z segments): two steps from
-    a seeded noisy state, sampled cells against the oracle run on crops that
-    hold their whole dependency cone (2 cells per step)."""
+def test_16bit_sample192_sampled_cells(lbm, orc, precision, bound, kernel):
+    """The 192^3 drainage sample with 16-bit storage in the launch shapes the
+    autotuner picks for it: the push kernel's 10-row shape with 24-plane z
+    segments, and the staged kernel with 32 x 8 threads and 32-plane segments.
+    Two steps from a seeded noisy state, sampled cells against the oracle run on
+    crops that hold their whole dependency cone (2 cells per step)."""
     shape = (192, 192, 192)
     spheres = W.sample192_spheres()
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR, rho_minor=W.RHO_MINOR,
                              reservoirs=True, membrane_layers=3, precision=precision)
     dom = lbm.Domain(params, spheres, (192, 192, 192))
-    dom.set_tile(8, 32, 2)
-    assert dom.tile() == (8, 32, 2)
+    if kernel == "push":
+        dom.set_push_shape(3, 24)
+        assert dom.step_kernel() == (lbm.KERNEL_PUSH, 24)
+    else:
+        dom.set_tile(8, 32, 2)
+        assert dom.tile() == (8, 32, 2)
     mask = orc.voxelise(shape, spheres, reservoirs=True, membrane_layers=3)
     assert np.array_equal(dom.mask(), mask)
     rho0 = W.initial_densities(shape, noise=2e-2, seed=8)
@@ -135,5 +141,6 @@ def test_16bit_sample192_sampled_cells(lbm, orc, precision, bound):
             if s == 1 and mask[z, y, x] & orc.M_MEMBRANE:
                 continue
             worst = max(worst, abs(rho_g[s, z, y, x] - ro[s]) / max(abs(ro[s]), W.RHO_MINOR))
-    print(json.dumps({"precision": {1: "fp16", 2: "bf16"}[precision], "sample192_max_rel_density_err_2_steps": worst}))
+    print(json.dumps({"precision": {1: "fp16", 2: "bf16"}[precision], "kernel": kernel,
+                      "sample192_max_rel_density_err_2_steps": worst}))
     assert worst <= bound, worst
