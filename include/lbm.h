@@ -172,6 +172,10 @@ typedef struct {
                                  for all throats                                      */
     int batch_form;           /* lbm_run_throat_batch: LBM_BATCH_AUTO, _PERSISTENT or
                                  _PER_STEP (below)                                    */
+    int march_threads;        /* LBM_BATCH_MARCH: threads per CTA, 128, 256, 384 or
+                                 512 (0: the default, LBM_MARCH_THREADS)               */
+    int march_planes;         /* LBM_BATCH_MARCH: planes per chunk, 1 .. 64 (0: the
+                                 default, LBM_MARCH_PLANES)                            */
 } lbm_schedule;
 
 /* Forms of lbm_run_throat_batch.  PERSISTENT: one launch per increment, a CTA
@@ -184,8 +188,8 @@ typedef struct {
  * one thread per cell (a density pass, then the collision, which pushes each
  * value to the cell it streams to), so that the grain inside the throat boxes
  * (most of a box) costs neither lanes, traffic nor memory.  MARCH: the same
- * cell list in one launch per time step, a CTA per chunk of up to 16 planes of
- * a throat, which computes the densities of a plane and steps the plane below
+ * cell list in one launch per time step, a CTA per chunk of up to
+ * march_planes planes of a throat, which computes the densities of a plane and steps the plane below
  * it right after (a plane's pairs are read a second time from cache, not from
  * DRAM).  All forms give bit-identical rows.  AUTO is CELLS. */
 #define LBM_BATCH_AUTO 0
@@ -193,6 +197,10 @@ typedef struct {
 #define LBM_BATCH_PER_STEP 2
 #define LBM_BATCH_CELLS 3
 #define LBM_BATCH_MARCH 4
+/* Defaults of the marching form's launch shape (lbm_schedule.march_threads,
+ * .march_planes). */
+#define LBM_MARCH_THREADS 128
+#define LBM_MARCH_PLANES 16
 
 /* Per-throat outcome of a batch. */
 typedef struct {

@@ -433,9 +433,9 @@ __global__ void __launch_bounds__(CELL_THREADS, 3)
 // read for its density and again for its step one plane later, from cache
 // rather than DRAM.  Chunks of one throat compute the densities of their shared
 // boundary planes twice, with the same values.
-constexpr int MARCH_THREADS = 128;
-template <bool TAU1, class NB>
-__global__ void __launch_bounds__(MARCH_THREADS, 4)
+// MT threads a CTA, MINB CTAs an SM (which caps a thread's registers).
+template <int MT, int MINB, bool TAU1, class NB>
+__global__ void __launch_bounds__(MT, MINB)
     cell_march_kernel(const int4* __restrict__ chunks, const int* __restrict__ plane_item,
                       const int2* __restrict__ items, int cp, const float2* __restrict__ fin, float2* __restrict__ fout,
                       float2* __restrict__ rho2, const uint32_t* __restrict__ wc, const uint32_t* __restrict__ wnc,
@@ -445,18 +445,64 @@ __global__ void __launch_bounds__(MARCH_THREADS, 4)
     const int* pl = plane_item + ch.x;
     const int nz = ch.y, z0 = ch.z, z1 = ch.w;
     auto step_plane = [&](int z) {
-        for (int i = __ldg(pl + z) + (int)threadIdx.x; i < __ldg(pl + z + 1); i += MARCH_THREADS)
+#pragma unroll 1
+        for (int i = __ldg(pl + z) + (int)threadIdx.x; i < __ldg(pl + z + 1); i += MT)
             cell_step_item<TAU1, NB>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all, ladder_stride,
                                      incr_now);
     };
     const int zs = max(z0 - 1, 0), ze = min(z1, nz - 1);
     for (int z = zs; z <= ze; ++z) {
-        for (int i = __ldg(pl + z) + (int)threadIdx.x; i < __ldg(pl + z + 1); i += MARCH_THREADS)
+#pragma unroll 1
+        for (int i = __ldg(pl + z) + (int)threadIdx.x; i < __ldg(pl + z + 1); i += MT)
             cell_density_item(i, wc, cp, fin, rho2);
         __syncthreads();  // densities of plane z visible to every thread of the CTA
         if (z - 1 >= z0 && z - 1 < z1) step_plane(z - 1);
     }
     if (z1 == nz) step_plane(nz - 1);  // no plane above the top one
+}
+
+// One marching step with MT threads a CTA over n_chunks chunks.
+template <int MT, int MINB>
+cudaError_t launch_march_mt(bool t1, bool nb16, int n_chunks, cudaStream_t s, const int4* chunks,
+                            const int* plane_item, const int2* items, int cp, const float2* fin, float2* fout,
+                            float2* rho2, const uint32_t* wc, const uint32_t* wnc, const uint32_t* adhc,
+                            const void* nbp, const Phys& P, const float* bc, int ls, const int* incr) {
+    const int16_t* n16 = static_cast<const int16_t*>(nbp);
+    const int* n32 = static_cast<const int*>(nbp);
+    if (t1 && nb16)
+        cell_march_kernel<MT, MINB, true, int16_t><<<n_chunks, MT, 0, s>>>(chunks, plane_item, items, cp, fin, fout,
+                                                                         rho2, wc, wnc, adhc, n16, P, bc, ls, incr);
+    else if (t1)
+        cell_march_kernel<MT, MINB, true, int><<<n_chunks, MT, 0, s>>>(chunks, plane_item, items, cp, fin, fout, rho2,
+                                                                     wc, wnc, adhc, n32, P, bc, ls, incr);
+    else if (nb16)
+        cell_march_kernel<MT, MINB, false, int16_t><<<n_chunks, MT, 0, s>>>(chunks, plane_item, items, cp, fin, fout,
+                                                                          rho2, wc, wnc, adhc, n16, P, bc, ls, incr);
+    else
+        cell_march_kernel<MT, MINB, false, int><<<n_chunks, MT, 0, s>>>(chunks, plane_item, items, cp, fin, fout,
+                                                                      rho2, wc, wnc, adhc, n32, P, bc, ls, incr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march(int mt, bool t1, bool nb16, int n_chunks, cudaStream_t s, const int4* chunks,
+                         const int* plane_item, const int2* items, int cp, const float2* fin, float2* fout,
+                         float2* rho2, const uint32_t* wc, const uint32_t* wnc, const uint32_t* adhc, const void* nbp,
+                         const Phys& P, const float* bc, int ls, const int* incr) {
+    switch (mt) {
+        case 128:
+            return launch_march_mt<128, 4>(t1, nb16, n_chunks, s, chunks, plane_item, items, cp, fin, fout, rho2, wc,
+                                           wnc, adhc, nbp, P, bc, ls, incr);
+        case 256:
+            return launch_march_mt<256, 2>(t1, nb16, n_chunks, s, chunks, plane_item, items, cp, fin, fout, rho2, wc,
+                                           wnc, adhc, nbp, P, bc, ls, incr);
+        case 384:
+            return launch_march_mt<384, 1>(t1, nb16, n_chunks, s, chunks, plane_item, items, cp, fin, fout, rho2, wc,
+                                           wnc, adhc, nbp, P, bc, ls, incr);
+        case 512:
+            return launch_march_mt<512, 1>(t1, nb16, n_chunks, s, chunks, plane_item, items, cp, fin, fout, rho2, wc,
+                                           wnc, adhc, nbp, P, bc, ls, incr);
+    }
+    return cudaErrorInvalidValue;
 }
 
 // Measurements of throat blockIdx.x from the compact populations, walking its
@@ -611,6 +657,13 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             set_error("lbm_run_throat_batch: tau must be > 0.5");
             return LBM_ERR_ARG;
         }
+    const int march_threads = sched->march_threads ? sched->march_threads : LBM_MARCH_THREADS;
+    const int march_planes = sched->march_planes ? sched->march_planes : LBM_MARCH_PLANES;
+    if ((march_threads != 128 && march_threads != 256 && march_threads != 384 && march_threads != 512) ||
+        march_planes < 1 || march_planes > 64) {
+        set_error("lbm_run_throat_batch: march_threads must be 0, 128, 256, 384 or 512 and march_planes 0 .. 64");
+        return LBM_ERR_ARG;
+    }
     cudaStream_t stream = (cudaStream_t)stream_ptr;
     const int I = sched->n_incr;
     try {
@@ -847,10 +900,9 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             const int n_cells = (int)cells.size();
             const int cp = (n_cells + 31) / 32 * 32;
             // marching form: the first item of every plane of every throat, and
-            // chunks of at most MARCH_PLANES planes, largest throats first
+            // chunks of at most march_planes planes, largest throats first
             int n_chunks = 0;
             if (form == LBM_BATCH_MARCH) {
-                constexpr int MARCH_PLANES = 16;
                 std::vector<int> plane_item;
                 std::vector<int4> chunks;
                 for (int t : order) {
@@ -861,8 +913,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                         while (j < cl.size() && (cl[j] >> 20) < z) ++j;
                         plane_item.push_back((int)(item0[t] + (long long)j));
                     }
-                    for (int z0 = 0; z0 < nz; z0 += MARCH_PLANES)
-                        chunks.push_back(make_int4(base, nz, z0, std::min(nz, z0 + MARCH_PLANES)));
+                    for (int z0 = 0; z0 < nz; z0 += march_planes)
+                        chunks.push_back(make_int4(base, nz, z0, std::min(nz, z0 + march_planes)));
                 }
                 n_chunks = (int)chunks.size();
                 BATCH_CUDA(cudaMalloc(&d_plane_item, sizeof(int) * std::max<size_t>(1, plane_item.size())));
@@ -924,25 +976,12 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                     const int16_t* nb16p = static_cast<const int16_t*>(d_nbp);
                     const int* nb32p = static_cast<const int*>(d_nbp);
                     if (form == LBM_BATCH_MARCH) {
-                        if (n_chunks) {
-                            if (t1 && nb16)
-                                cell_march_kernel<true, int16_t><<<n_chunks, MARCH_THREADS, 0, cap>>>(
-                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                    nb16p, P, d_bc, ls, d_incr);
-                            else if (t1)
-                                cell_march_kernel<true, int><<<n_chunks, MARCH_THREADS, 0, cap>>>(
-                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                    nb32p, P, d_bc, ls, d_incr);
-                            else if (nb16)
-                                cell_march_kernel<false, int16_t><<<n_chunks, MARCH_THREADS, 0, cap>>>(
-                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                    nb16p, P, d_bc, ls, d_incr);
-                            else
-                                cell_march_kernel<false, int><<<n_chunks, MARCH_THREADS, 0, cap>>>(
-                                    d_chunks, d_plane_item, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                    nb32p, P, d_bc, ls, d_incr);
-                        }
-                        cerr = cudaGetLastError();
+                        if (n_chunks)
+                            cerr = launch_march(march_threads, t1, nb16, n_chunks, cap, d_chunks, d_plane_item,
+                                                d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, d_nbp, P, d_bc,
+                                                ls, d_incr);
+                        else
+                            cerr = cudaGetLastError();
                         continue;
                     }
                     cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
