@@ -172,8 +172,9 @@ typedef struct {
                                  for all throats                                      */
     int batch_form;           /* lbm_run_throat_batch: LBM_BATCH_AUTO, _PERSISTENT or
                                  _PER_STEP (below)                                    */
-    int march_threads;        /* LBM_BATCH_MARCH: threads per CTA, 128, 256, 384 or
-                                 512 (0: the default, LBM_MARCH_THREADS)               */
+    int march_threads;        /* LBM_BATCH_MARCH: threads per CTA, 128 (four CTAs an
+                                 SM), 256 (two), 384 or 512 (one); 0: the default,
+                                 LBM_MARCH_THREADS                                     */
     int march_planes;         /* LBM_BATCH_MARCH: planes per chunk, 1 .. 64 (0: the
                                  default, LBM_MARCH_PLANES)                            */
 } lbm_schedule;
@@ -199,7 +200,7 @@ typedef struct {
 #define LBM_BATCH_MARCH 4
 /* Defaults of the marching form's launch shape (lbm_schedule.march_threads,
  * .march_planes). */
-#define LBM_MARCH_THREADS 128
+#define LBM_MARCH_THREADS 256
 #define LBM_MARCH_PLANES 16
 
 /* Per-throat outcome of a batch. */

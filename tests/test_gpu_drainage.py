@@ -181,6 +181,27 @@ def test_batch_forms_agree(lbm, n_steps):
         _rows_equal(ra, rowsa, rb, rowsb, ladders)
 
 
+@pytest.mark.parametrize("march", [(128, 1), (256, 3), (384, 64), (512, 7)])
+def test_march_shapes_agree(lbm, march):
+    """The marching form in every CTA size, with chunks of 1 to 64 planes (chunk
+    boundaries inside and outside the throat boxes), gives the cell-list form's
+    rows bit for bit."""
+    from paper_1906_04722_gb300 import surrogate as S
+    throats = W.delaunay_throats(W.sample_spheres(128), 6, seed=15)
+    ladders = S.pressure_ladder(S.throat_incircle(throats), 3, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
+    ra, rowsa = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, 7, W.RHO_MAJOR, form=lbm.BATCH_CELLS)
+    rb, rowsb = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, 7, W.RHO_MAJOR, form=lbm.BATCH_MARCH,
+                                         march=march)
+    _rows_equal(ra, rowsa, rb, rowsb, ladders)
+
+
+def test_march_shape_validation(lbm):
+    throats = W.delaunay_throats(W.sample_spheres(128), 1, seed=15)
+    for march in ((100, 16), (256, 65), (256, -1)):
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_run_throat_batch(throats, _params(lbm), [2.0], 1, W.RHO_MAJOR, form=lbm.BATCH_MARCH, march=march)
+
+
 def test_batch_forms_agree_with_a_wide_box(lbm):
     """A throat whose box has more than 32767 cells per plane makes the cell-list
     forms keep 32-bit push-table entries (16-bit offsets could not reach a z
