@@ -508,26 +508,22 @@ cudaError_t launch_march(int mt, bool t1, bool nb16, int n_chunks, cudaStream_t 
 }
 
 // Wave form: the cell list in one launch per time step, whose CTAs take work
-// units off a ticket counter in the order the host laid out.  A throat's planes
-// are cut into groups of whole planes holding about WAVE_GROUP_ITEMS items; a
-// unit is one group: (first item, end item, global group index, bits), bit 0
-// the kind (0: the densities of the group's items, 1: their step), bit 1: the
-// group below belongs to the same throat, bit 2: the group above does.  A
-// density unit publishes a flag for its group (the launch's epoch, so flags
-// never need clearing); a step unit waits, bounded, for the flags of its group
-// and of the groups on either side, whose density units the host placed
-// WAVE_LAG groups ahead of it.  A CTA holds two tickets, the unit it works on
-// and the next (fetched while it works), always in increasing order.  No wait
-// can block for ever: the unfinished unit with the smallest ticket is always
-// one a CTA works on, and if it is a step unit, every density unit it waits for
-// holds a smaller ticket and is finished.  A group's pairs are read from DRAM by
-// its density unit and again from L2 by its step unit a few units later.  A
-// wait that runs out (2 s) sets err, the other waits then give up at once, and
-// the host reports LBM_ERR_TIMEOUT.
-constexpr int WAVE_THREADS = 256;
-constexpr int WAVE_MINB = 2;  // 128 registers: the unit loop around the step needs them
-constexpr int WAVE_LAG = 2;
-constexpr int WAVE_GROUP_ITEMS = 1024;
+// units off a ticket counter in the order the host laid out.  A unit is one
+// plane of one throat: (first item, end item, global plane index, bits), bit 0
+// the kind (0: the densities of the plane's items, 1: their step), bit 1: the
+// plane below belongs to the same throat, bit 2: the plane above does.  A
+// density unit publishes a flag for its plane (the launch's epoch, so flags
+// never need clearing); a step unit waits, bounded, for the flags of its plane
+// and its neighbours, whose density units the host placed WAVE_LAG planes ahead
+// of it.  No wait can block for ever: a unit waits only on density units, which
+// hold smaller tickets, were taken by CTAs already running and never wait
+// themselves.  A plane's pairs are read from DRAM by its density unit and again
+// from L2 by its step unit a few planes later, since all CTAs work within a
+// window of a few hundred planes.  A wait that runs out (2 s) sets err, the
+// other waits then give up at once, and the host reports LBM_ERR_TIMEOUT.
+constexpr int WAVE_THREADS = 128;
+constexpr int WAVE_MINB = 4;  // 128 registers: the unit loop around the step needs them
+constexpr int WAVE_LAG = 4;
 constexpr long long WAVE_WAIT_NS = 2000000000LL;
 
 struct WaveState {
@@ -569,15 +565,13 @@ __global__ void __launch_bounds__(WAVE_THREADS, WAVE_MINB)
                      float2* __restrict__ rho2, const uint32_t* __restrict__ wc, const uint32_t* __restrict__ wnc,
                      const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp, Phys P,
                      const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
-    __shared__ int s_next;
+    __shared__ int s_u, s_ok;
     const int epoch = *reinterpret_cast<volatile int*>(&ws->epoch) + 1;
-    if (threadIdx.x == 0) s_next = atomicAdd(&ws->ticket, 1);
     for (;;) {
+        if (threadIdx.x == 0) s_u = atomicAdd(&ws->ticket, 1);
         __syncthreads();
-        const int u = s_next;
-        __syncthreads();  // every thread has read s_next before thread 0 writes it again
+        const int u = s_u;
         if (u >= n_units) break;  // the same for every thread of the CTA
-        if (threadIdx.x == 0) s_next = atomicAdd(&ws->ticket, 1);  // the next unit, while this one runs
         const int4 U = __ldg(units + u);
         if (!(U.w & 1)) {
 #pragma unroll 1
@@ -586,20 +580,22 @@ __global__ void __launch_bounds__(WAVE_THREADS, WAVE_MINB)
             __syncthreads();
             if (threadIdx.x == 0) wave_st_release(flags + U.z, epoch);
         } else {
-            // threads 0, 1, 2 wait for the groups below, at and above this one
-            bool ok = true;
-            const int t = (int)threadIdx.x;
-            if (t < 3 && (t == 1 || (t == 0 && (U.w & 2)) || (t == 2 && (U.w & 4)))) {
-                ok = wave_wait(flags + U.z - 1 + t, epoch, &ws->err);
+            if (threadIdx.x == 0) {
+                const bool ok = wave_wait(flags + U.z, epoch, &ws->err) &&
+                                (!(U.w & 2) || wave_wait(flags + U.z - 1, epoch, &ws->err)) &&
+                                (!(U.w & 4) || wave_wait(flags + U.z + 1, epoch, &ws->err));
                 if (!ok) atomicExch(&ws->err, 1);
+                s_ok = ok;
             }
-            if (__syncthreads_and(ok)) {
+            __syncthreads();
+            if (s_ok) {
 #pragma unroll 1
-                for (int i = U.x + t; i < U.y; i += WAVE_THREADS)
+                for (int i = U.x + (int)threadIdx.x; i < U.y; i += WAVE_THREADS)
                     cell_step_item<TAU1, NB, true>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all,
                                                    ladder_stride, incr_now);
             }
         }
+        __syncthreads();  // s_u and s_ok are written again next round
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -1038,14 +1034,13 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                     BATCH_CUDA(cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(int4) * chunks.size(),
                                                cudaMemcpyHostToDevice, stream));
             }
-            // wave form: per throat, groups of whole planes with about
-            // WAVE_GROUP_ITEMS items, the density unit of group q and the step
-            // unit of group q - WAVE_LAG in turn (every group keeps its density
-            // unit, which may only raise the flag)
+            // wave form: per throat, the density unit of plane q and the step
+            // unit of plane q - WAVE_LAG in turn (empty planes keep their
+            // density unit, which only raises the flag)
             int n_units = 0, wave_grid = 0;
             if (form == LBM_BATCH_WAVE) {
                 std::vector<int4> units;
-                int n_planes = 0;  // groups, globally numbered
+                int n_planes = 0;
                 for (int t : order) {
                     const int nz = recs[t].g.nz;
                     const std::vector<int>& cl = cells_of[t];
@@ -1055,21 +1050,14 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                         while (j < cl.size() && (cl[j] >> 20) < z) ++j;
                         first[(size_t)z] = (int)(item0[t] + (long long)j);
                     }
-                    std::vector<int> gb{0};  // first plane of each group, then nz
-                    for (int z = 1; z < nz; ++z)
-                        if (first[(size_t)z] - first[(size_t)gb.back()] >= WAVE_GROUP_ITEMS) gb.push_back(z);
-                    gb.push_back(nz);
-                    const int ng = (int)gb.size() - 1;
-                    auto lo = [&](int k) { return first[(size_t)gb[(size_t)k]]; };
-                    auto hi = [&](int k) { return first[(size_t)gb[(size_t)k + 1]]; };
-                    for (int q = 0; q < ng + WAVE_LAG; ++q) {
-                        if (q < ng) units.push_back(make_int4(lo(q), hi(q), n_planes + q, 0));
-                        const int k = q - WAVE_LAG;
-                        if (k >= 0 && k < ng && hi(k) > lo(k))
-                            units.push_back(make_int4(lo(k), hi(k), n_planes + k,
-                                                      1 | (k > 0 ? 2 : 0) | (k + 1 < ng ? 4 : 0)));
+                    for (int q = 0; q < nz + WAVE_LAG; ++q) {
+                        if (q < nz) units.push_back(make_int4(first[(size_t)q], first[(size_t)q + 1], n_planes + q, 0));
+                        const int z = q - WAVE_LAG;
+                        if (z >= 0 && z < nz && first[(size_t)z + 1] > first[(size_t)z])
+                            units.push_back(make_int4(first[(size_t)z], first[(size_t)z + 1], n_planes + z,
+                                                      1 | (z > 0 ? 2 : 0) | (z + 1 < nz ? 4 : 0)));
                     }
-                    n_planes += ng;
+                    n_planes += nz;
                 }
                 // every step unit after the density units it waits for
                 std::vector<char> seen((size_t)std::max(1, n_planes), 0);
