@@ -91,7 +91,7 @@ def parse():
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--throat-batch", default="",
                     help="instead of the benchmark: one batch of the 1024 held-out throats in the given form "
-                         "(cells, tiles, persistent, wave, march or march:THREADS:PLANES; 32 increments), and the same "
+                         "(cells, tiles, persistent, march or march:THREADS:PLANES; 32 increments), and the same "
                          "batch with no time steps (the set-up cost)")
     ap.add_argument("--throat-count", type=int, default=1024,
                     help="with --throat-batch: every (1024 // count)-th throat of the packing (profiling captures)")
@@ -921,7 +921,7 @@ def run_throat_batch(args):
 
     name, *shape = args.throat_batch.split(":")
     form = {"cells": lbm.BATCH_CELLS, "tiles": lbm.BATCH_PER_STEP, "persistent": lbm.BATCH_PERSISTENT,
-            "march": lbm.BATCH_MARCH, "wave": lbm.BATCH_WAVE}[name]
+            "march": lbm.BATCH_MARCH}[name]
     march = (int(shape[0]), int(shape[1])) if shape else (0, 0)  # march:THREADS:PLANES
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
                              rho_minor=W.RHO_MINOR)

@@ -192,18 +192,12 @@ typedef struct {
  * cell list in one launch per time step, a CTA per chunk of up to
  * march_planes planes of a throat, which computes the densities of a plane and steps the plane below
  * it right after (a plane's pairs are read a second time from cache, not from
- * DRAM).  WAVE: the same cell list in one launch per time step, whose CTAs take
- * (throat, plane) work units off a ticket counter: the densities of a plane,
- * and a few planes later the step of the plane below once the densities it
- * needs are published (bounded waits on per-plane flags; LBM_ERR_TIMEOUT if
- * one runs out), so that the step reads the pairs from L2.  All forms give
- * bit-identical rows.  AUTO is CELLS. */
+ * DRAM).  All forms give bit-identical rows.  AUTO is CELLS. */
 #define LBM_BATCH_AUTO 0
 #define LBM_BATCH_PERSISTENT 1
 #define LBM_BATCH_PER_STEP 2
 #define LBM_BATCH_CELLS 3
 #define LBM_BATCH_MARCH 4
-#define LBM_BATCH_WAVE 5
 /* Defaults of the marching form's launch shape (lbm_schedule.march_threads,
  * .march_planes). */
 #define LBM_MARCH_THREADS 256

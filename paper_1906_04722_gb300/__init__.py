@@ -389,7 +389,6 @@ BATCH_PERSISTENT = 1
 BATCH_PER_STEP = 2
 BATCH_CELLS = 3
 BATCH_MARCH = 4
-BATCH_WAVE = 5
 
 
 def lbm_set_step_kernel(h, kind: int, lz: int = 0):
@@ -619,9 +618,8 @@ def _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march=(0, 0)):
     sch.n_steps = int(n_steps)
     sch.rho_in_nw = lad.ctypes.data_as(_DP)
     sch.rho_out_w = float(rho_out_w)
-    if form not in (BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS, BATCH_MARCH, BATCH_WAVE):
-        raise ValueError("form must be BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS, BATCH_MARCH or "
-                         "BATCH_WAVE")
+    if form not in (BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS, BATCH_MARCH):
+        raise ValueError("form must be BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS or BATCH_MARCH")
     sch.batch_form = int(form)
     sch.march_threads, sch.march_planes = int(march[0]), int(march[1])
     return sch, lad
@@ -631,7 +629,7 @@ def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, r
                          form: int = 0, march=(0, 0)):
     """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
     rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr).
-    form: BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS, BATCH_MARCH or BATCH_WAVE.
+    form: BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS or BATCH_MARCH.
     march: (threads per CTA, planes per chunk) of BATCH_MARCH, 0 for the defaults."""
     th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
     n = th.shape[0]

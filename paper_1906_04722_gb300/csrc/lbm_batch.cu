@@ -351,9 +351,8 @@ __global__ void __launch_bounds__(CELL_THREADS)
 // TAU1), push: one 8-byte store per direction where both components stream
 // alike, separate stores where a membrane makes them differ.  The bounce-back
 // choice selects an address rather than a branch: one store instruction per
-// value for the whole warp, whichever way each lane goes.  CG: the densities are
-// read through L2 only (ld.global.cg), for a launch that writes them while it runs.
-template <bool TAU1, class NB, bool CG = false>
+// value for the whole warp, whichever way each lane goes.
+template <bool TAU1, class NB>
 __device__ __forceinline__ void cell_step_item(int i, const int2* __restrict__ items, int cp,
                                                const float2* __restrict__ fin, float2* __restrict__ fout,
                                                const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
@@ -377,11 +376,10 @@ __device__ __forceinline__ void cell_step_item(int i, const int2* __restrict__ i
 #pragma unroll
     for (int k = 1; k < Q; ++k)
         dst[k] = k == 1 ? i + 1 : k == 2 ? i - 1 : nb_decode(__ldg(nbp + (size_t)(k - 3) * cp + i), i);
-    auto rho_load = [&](int j) { return CG ? __ldcg(rho2 + j) : __ldg(rho2 + j); };
     auto rho_at = [&](int k) {
-        if (k == 0) return rho_load(i);
+        if (k == 0) return __ldg(rho2 + i);
         const bool wall = (w >> OPP(k)) & 1u;
-        const float2 v = rho_load(wall ? i : dst[k]);
+        const float2 v = __ldg(rho2 + (wall ? i : dst[k]));
         return wall ? make_float2(0.f, 0.f) : v;
     };
     Phys Pt = P;
@@ -505,107 +503,6 @@ cudaError_t launch_march(int mt, bool t1, bool nb16, int n_chunks, cudaStream_t 
                                            wnc, adhc, nbp, P, bc, ls, incr);
     }
     return cudaErrorInvalidValue;
-}
-
-// Wave form: the cell list in one launch per time step, whose CTAs take work
-// units off a ticket counter in the order the host laid out.  A unit is one
-// plane of one throat: (first item, end item, global plane index, bits), bit 0
-// the kind (0: the densities of the plane's items, 1: their step), bit 1: the
-// plane below belongs to the same throat, bit 2: the plane above does.  A
-// density unit publishes a flag for its plane (the launch's epoch, so flags
-// never need clearing); a step unit waits, bounded, for the flags of its plane
-// and its neighbours, whose density units the host placed WAVE_LAG planes ahead
-// of it.  No wait can block for ever: a unit waits only on density units, which
-// hold smaller tickets, were taken by CTAs already running and never wait
-// themselves.  A plane's pairs are read from DRAM by its density unit and again
-// from L2 by its step unit a few planes later, since all CTAs work within a
-// window of a few hundred planes.  A wait that runs out (2 s) sets err, the
-// other waits then give up at once, and the host reports LBM_ERR_TIMEOUT.
-constexpr int WAVE_THREADS = 128;
-constexpr int WAVE_MINB = 4;  // 128 registers: the unit loop around the step needs them
-constexpr int WAVE_LAG = 4;
-constexpr long long WAVE_WAIT_NS = 2000000000LL;
-
-struct WaveState {
-    int ticket;  // next unit to hand out
-    int done;    // CTAs finished in this launch
-    int epoch;   // launches finished
-    int err;     // a wait ran out
-};
-
-__device__ __forceinline__ int wave_ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void wave_st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long wave_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// flag >= epoch within WAVE_WAIT_NS, unless another wait already ran out
-__device__ bool wave_wait(const int* flag, int epoch, const int* err) {
-    if (wave_ld_acquire(flag) >= epoch) return true;
-    const unsigned long long t0 = wave_ns();
-    for (;;) {
-        __nanosleep(64);
-        if (wave_ld_acquire(flag) >= epoch) return true;
-        if (*reinterpret_cast<const volatile int*>(err)) return false;
-        if ((long long)(wave_ns() - t0) > WAVE_WAIT_NS) return false;
-    }
-}
-
-template <bool TAU1, class NB>
-__global__ void __launch_bounds__(WAVE_THREADS, WAVE_MINB)
-    cell_wave_kernel(const int4* __restrict__ units, int n_units, int* __restrict__ flags, WaveState* ws,
-                     const int2* __restrict__ items, int cp, const float2* __restrict__ fin, float2* __restrict__ fout,
-                     float2* __restrict__ rho2, const uint32_t* __restrict__ wc, const uint32_t* __restrict__ wnc,
-                     const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp, Phys P,
-                     const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
-    __shared__ int s_u, s_ok;
-    const int epoch = *reinterpret_cast<volatile int*>(&ws->epoch) + 1;
-    for (;;) {
-        if (threadIdx.x == 0) s_u = atomicAdd(&ws->ticket, 1);
-        __syncthreads();
-        const int u = s_u;
-        if (u >= n_units) break;  // the same for every thread of the CTA
-        const int4 U = __ldg(units + u);
-        if (!(U.w & 1)) {
-#pragma unroll 1
-            for (int i = U.x + (int)threadIdx.x; i < U.y; i += WAVE_THREADS) cell_density_item(i, wc, cp, fin, rho2);
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) wave_st_release(flags + U.z, epoch);
-        } else {
-            if (threadIdx.x == 0) {
-                const bool ok = wave_wait(flags + U.z, epoch, &ws->err) &&
-                                (!(U.w & 2) || wave_wait(flags + U.z - 1, epoch, &ws->err)) &&
-                                (!(U.w & 4) || wave_wait(flags + U.z + 1, epoch, &ws->err));
-                if (!ok) atomicExch(&ws->err, 1);
-                s_ok = ok;
-            }
-            __syncthreads();
-            if (s_ok) {
-#pragma unroll 1
-                for (int i = U.x + (int)threadIdx.x; i < U.y; i += WAVE_THREADS)
-                    cell_step_item<TAU1, NB, true>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all,
-                                                   ladder_stride, incr_now);
-            }
-        }
-        __syncthreads();  // s_u and s_ok are written again next round
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&ws->done, 1) == (int)gridDim.x - 1) {  // the last CTA: ready the next launch
-            ws->ticket = 0;
-            ws->done = 0;
-            __threadfence();
-            atomicAdd(&ws->epoch, 1);
-        }
-    }
 }
 
 // Measurements of throat blockIdx.x from the compact populations, walking its
@@ -751,7 +648,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                                     void* stream_ptr) {
     if (!throats || n < 1 || !params || !sched || !results || !rows || !sched->rho_in_nw || sched->n_incr < 1 ||
         sched->n_steps < 0 || (sched->per_throat != 0 && sched->per_throat != 1) || sched->batch_form < 0 ||
-        sched->batch_form > LBM_BATCH_WAVE) {
+        sched->batch_form > LBM_BATCH_MARCH) {
         set_error("lbm_run_throat_batch: NULL argument or empty batch/schedule");
         return LBM_ERR_ARG;
     }
@@ -771,7 +668,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
     const int I = sched->n_incr;
     try {
         const int form = sched->batch_form == LBM_BATCH_AUTO ? LBM_BATCH_CELLS : sched->batch_form;
-        const bool cell_list = form == LBM_BATCH_CELLS || form == LBM_BATCH_MARCH || form == LBM_BATCH_WAVE;
+        const bool cell_list = form == LBM_BATCH_CELLS || form == LBM_BATCH_MARCH;
         const bool box_layout = !cell_list;  // the cell-list forms keep compact arenas only
         // host geometry: frames and sizes first (validation, on this thread), then
         // masks, probes and per-throat lists on all host cores
@@ -870,9 +767,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         void* d_nbp = nullptr;
         int* d_plane_item = nullptr;
         int4* d_chunks = nullptr;
-        int4* d_units = nullptr;
-        int* d_flags = nullptr;
-        WaveState* d_wave = nullptr;
         uint32_t* d_wc = nullptr;
         cudaGraphExec_t exec2[2] = {nullptr, nullptr};
         double* d_rin = nullptr;
@@ -892,9 +786,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             cudaFree(d_nbp);
             cudaFree(d_plane_item);
             cudaFree(d_chunks);
-            cudaFree(d_units);
-            cudaFree(d_flags);
-            cudaFree(d_wave);
             cudaFree(d_wc);
             if (exec) cudaGraphExecDestroy(exec);
             for (cudaGraphExec_t& e : exec2)
@@ -1034,57 +925,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                     BATCH_CUDA(cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(int4) * chunks.size(),
                                                cudaMemcpyHostToDevice, stream));
             }
-            // wave form: per throat, the density unit of plane q and the step
-            // unit of plane q - WAVE_LAG in turn (empty planes keep their
-            // density unit, which only raises the flag)
-            int n_units = 0, wave_grid = 0;
-            if (form == LBM_BATCH_WAVE) {
-                std::vector<int4> units;
-                int n_planes = 0;
-                for (int t : order) {
-                    const int nz = recs[t].g.nz;
-                    const std::vector<int>& cl = cells_of[t];
-                    std::vector<int> first((size_t)nz + 1);
-                    size_t j = 0;
-                    for (int z = 0; z <= nz; ++z) {
-                        while (j < cl.size() && (cl[j] >> 20) < z) ++j;
-                        first[(size_t)z] = (int)(item0[t] + (long long)j);
-                    }
-                    for (int q = 0; q < nz + WAVE_LAG; ++q) {
-                        if (q < nz) units.push_back(make_int4(first[(size_t)q], first[(size_t)q + 1], n_planes + q, 0));
-                        const int z = q - WAVE_LAG;
-                        if (z >= 0 && z < nz && first[(size_t)z + 1] > first[(size_t)z])
-                            units.push_back(make_int4(first[(size_t)z], first[(size_t)z + 1], n_planes + z,
-                                                      1 | (z > 0 ? 2 : 0) | (z + 1 < nz ? 4 : 0)));
-                    }
-                    n_planes += nz;
-                }
-                // every step unit after the density units it waits for
-                std::vector<char> seen((size_t)std::max(1, n_planes), 0);
-                for (const int4& u : units) {
-                    if (!(u.w & 1)) {
-                        seen[(size_t)u.z] = 1;
-                    } else if (!seen[(size_t)u.z] || ((u.w & 2) && !seen[(size_t)u.z - 1]) ||
-                               ((u.w & 4) && !seen[(size_t)u.z + 1])) {
-                        cleanup();
-                        set_error("lbm_run_throat_batch: wave units out of order");
-                        return LBM_ERR_STATE;
-                    }
-                }
-                n_units = (int)units.size();
-                BATCH_CUDA(cudaMalloc(&d_units, sizeof(int4) * std::max<size_t>(1, units.size())));
-                BATCH_CUDA(cudaMalloc(&d_flags, sizeof(int) * (size_t)std::max(1, n_planes)));
-                BATCH_CUDA(cudaMalloc(&d_wave, sizeof(WaveState)));
-                BATCH_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int) * (size_t)std::max(1, n_planes), stream));
-                BATCH_CUDA(cudaMemsetAsync(d_wave, 0, sizeof(WaveState), stream));
-                if (n_units)
-                    BATCH_CUDA(cudaMemcpyAsync(d_units, units.data(), sizeof(int4) * units.size(),
-                                               cudaMemcpyHostToDevice, stream));
-                int per_sm = 0;
-                BATCH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_wave_kernel<true, int16_t>,
-                                                                         WAVE_THREADS, 0));
-                wave_grid = std::max(1, std::min(n_units, std::max(1, per_sm) * device_sm_count()));
-            }
             const size_t fc_floats = (size_t)2 * Q * std::max(cp, 32);
             BATCH_CUDA(cudaMalloc(&d_cells, sizeof(int2) * std::max<size_t>(1, cells.size())));
             BATCH_CUDA(cudaMalloc(&d_map, sizeof(int) * (size_t)std::max<long long>(1, c_tot)));
@@ -1135,26 +975,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                     const int ls = sched->per_throat ? I : 0;
                     const int16_t* nb16p = static_cast<const int16_t*>(d_nbp);
                     const int* nb32p = static_cast<const int*>(d_nbp);
-                    if (form == LBM_BATCH_WAVE) {
-                        if (t1 && nb16)
-                            cell_wave_kernel<true, int16_t><<<wave_grid, WAVE_THREADS, 0, cap>>>(
-                                d_units, n_units, d_flags, d_wave, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                nb16p, P, d_bc, ls, d_incr);
-                        else if (t1)
-                            cell_wave_kernel<true, int><<<wave_grid, WAVE_THREADS, 0, cap>>>(
-                                d_units, n_units, d_flags, d_wave, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                nb32p, P, d_bc, ls, d_incr);
-                        else if (nb16)
-                            cell_wave_kernel<false, int16_t><<<wave_grid, WAVE_THREADS, 0, cap>>>(
-                                d_units, n_units, d_flags, d_wave, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                nb16p, P, d_bc, ls, d_incr);
-                        else
-                            cell_wave_kernel<false, int><<<wave_grid, WAVE_THREADS, 0, cap>>>(
-                                d_units, n_units, d_flags, d_wave, d_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc,
-                                nb32p, P, d_bc, ls, d_incr);
-                        cerr = cudaGetLastError();
-                        continue;
-                    }
                     if (form == LBM_BATCH_MARCH) {
                         if (n_chunks)
                             cerr = launch_march(march_threads, t1, nb16, n_chunks, cap, d_chunks, d_plane_item,
@@ -1293,15 +1113,8 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         }
         BATCH_CUDA(cudaMemcpyAsync(rows, d_rows, sizeof(lbm_increment) * (size_t)n * I, cudaMemcpyDeviceToHost,
                                    stream));
-        WaveState wave_end{};
-        if (d_wave)
-            BATCH_CUDA(cudaMemcpyAsync(&wave_end, d_wave, sizeof(WaveState), cudaMemcpyDeviceToHost, stream));
         BATCH_CUDA(cudaStreamSynchronize(stream));
         cleanup();
-        if (wave_end.err) {
-            set_error("lbm_run_throat_batch: a wave step unit waited more than 2 s for a density unit");
-            return LBM_ERR_TIMEOUT;
-        }
 #undef BATCH_CUDA
         // invasion and p_c^e per throat (the rule of lbm_run_drainage)
         for (int t = 0; t < n; ++t) {

@@ -173,10 +173,10 @@ def test_batch_forms_agree(lbm, n_steps):
     throats = W.delaunay_throats(spheres, 9, seed=13)
     ladders = S.pressure_ladder(S.throat_incircle(throats), 4, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
     out = {}
-    for form in (lbm.BATCH_PERSISTENT, lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH, lbm.BATCH_WAVE):
+    for form in (lbm.BATCH_PERSISTENT, lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH):
         out[form] = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, n_steps, W.RHO_MAJOR, form=form)
     ra, rowsa = out[lbm.BATCH_PERSISTENT]
-    for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH, lbm.BATCH_WAVE):
+    for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH):
         rb, rowsb = out[form]
         _rows_equal(ra, rowsa, rb, rowsb, ladders)
 
@@ -192,21 +192,6 @@ def test_march_shapes_agree(lbm, march):
     ra, rowsa = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, 7, W.RHO_MAJOR, form=lbm.BATCH_CELLS)
     rb, rowsb = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, 7, W.RHO_MAJOR, form=lbm.BATCH_MARCH,
                                          march=march)
-    _rows_equal(ra, rowsa, rb, rowsb, ladders)
-
-
-@pytest.mark.parametrize("n_steps", [1, 5])
-def test_wave_unequal_tau_and_body_force(lbm, n_steps):
-    """The wave form against the cell-list form with unequal relaxation times (the
-    general collision) and a body force, over increments of one and five steps
-    (the arenas swap between increments at an odd count)."""
-    from paper_1906_04722_gb300 import surrogate as S
-    throats = W.delaunay_throats(W.sample_spheres(128), 5, seed=16)
-    ladders = S.pressure_ladder(S.throat_incircle(throats), 3, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
-    params = lbm.make_params(tau=(0.8, 1.2), G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
-                             rho_minor=W.RHO_MINOR, body_force=(0.0, 0.0, 1e-5))
-    ra, rowsa = lbm.lbm_run_throat_batch(throats, params, ladders, n_steps, W.RHO_MAJOR, form=lbm.BATCH_CELLS)
-    rb, rowsb = lbm.lbm_run_throat_batch(throats, params, ladders, n_steps, W.RHO_MAJOR, form=lbm.BATCH_WAVE)
     _rows_equal(ra, rowsa, rb, rowsb, ladders)
 
 
@@ -229,9 +214,9 @@ def test_batch_forms_agree_with_a_wide_box(lbm):
     throats = np.concatenate([big[None], small])
     ladder = [2.0 + 0.05 * i for i in range(2)]
     out = {form: lbm.lbm_run_throat_batch(throats, _params(lbm), ladder, 6, W.RHO_MAJOR, form=form)
-           for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH, lbm.BATCH_WAVE)}
+           for form in (lbm.BATCH_PER_STEP, lbm.BATCH_CELLS, lbm.BATCH_MARCH)}
     ra, rowsa = out[lbm.BATCH_PER_STEP]
-    for form in (lbm.BATCH_CELLS, lbm.BATCH_MARCH, lbm.BATCH_WAVE):
+    for form in (lbm.BATCH_CELLS, lbm.BATCH_MARCH):
         rb, rowsb = out[form]
         _rows_equal(ra, rowsa, rb, rowsb, np.tile(ladder, (len(throats), 1)))
 
