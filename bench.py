@@ -91,7 +91,7 @@ def parse():
                     help="time steps per pressure increment of the throat ladder (32 increments)")
     ap.add_argument("--throat-batch", default="",
                     help="instead of the benchmark: one batch of the 1024 held-out throats in the given form "
-                         "(cells, cells:CHUNK_ITEMS, tiles, persistent, march or march:THREADS:PLANES; 32 increments), and the same "
+                         "(cells, tiles, persistent, march or march:THREADS:PLANES; 32 increments), and the same "
                          "batch with no time steps (the set-up cost)")
     ap.add_argument("--throat-count", type=int, default=1024,
                     help="with --throat-batch: every (1024 // count)-th throat of the packing (profiling captures)")
@@ -922,8 +922,7 @@ def run_throat_batch(args):
     name, *shape = args.throat_batch.split(":")
     form = {"cells": lbm.BATCH_CELLS, "tiles": lbm.BATCH_PER_STEP, "persistent": lbm.BATCH_PERSISTENT,
             "march": lbm.BATCH_MARCH}[name]
-    march = (int(shape[0]), int(shape[1])) if shape and name == "march" else (0, 0)  # march:THREADS:PLANES
-    chunk = int(shape[0]) if shape and name == "cells" else 0  # cells:CHUNK_ITEMS
+    march = (int(shape[0]), int(shape[1])) if shape else (0, 0)  # march:THREADS:PLANES
     params = lbm.make_params(tau=W.TAU, G=W.G_COHESION, G_ads=W.G_ADS, rho_major=W.RHO_MAJOR,
                              rho_minor=W.RHO_MINOR)
     ladder = [W.RHO_MAJOR + 0.02 * i for i in range(32)]
@@ -934,8 +933,7 @@ def run_throat_batch(args):
     for key, steps in (("full", args.throat_steps), ("no_steps", 0)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res, _ = lbm.lbm_run_throat_batch(tri, params, ladder, steps, W.RHO_MAJOR, form=form, march=march,
-                                          chunk_items=chunk)
+        res, _ = lbm.lbm_run_throat_batch(tri, params, ladder, steps, W.RHO_MAJOR, form=form, march=march)
         torch.cuda.synchronize()
         out[key + "_s"] = time.perf_counter() - t0
     out["throats_per_s"] = len(tri) / out["full_s"]

@@ -177,11 +177,6 @@ typedef struct {
                                  LBM_MARCH_THREADS                                     */
     int march_planes;         /* LBM_BATCH_MARCH: planes per chunk, 1 .. 64 (0: the
                                  default, LBM_MARCH_PLANES)                            */
-    int cell_chunk_items;     /* LBM_BATCH_CELLS: cut the cell list at throat
-                                 boundaries into chunks of at least this many items
-                                 and run chunk c's step beside chunk c + 1's densities
-                                 (the step then reads the pairs the density launch
-                                 just read from L2); 0: one chunk                      */
 } lbm_schedule;
 
 /* Forms of lbm_run_throat_batch.  PERSISTENT: one launch per increment, a CTA

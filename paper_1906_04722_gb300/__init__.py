@@ -70,7 +70,7 @@ class lbm_schedule(ctypes.Structure):
     _fields_ = [("n_incr", ctypes.c_int), ("n_steps", ctypes.c_int),
                 ("rho_in_nw", ctypes.POINTER(ctypes.c_double)), ("rho_out_w", ctypes.c_double),
                 ("per_throat", ctypes.c_int), ("batch_form", ctypes.c_int), ("march_threads", ctypes.c_int),
-                ("march_planes", ctypes.c_int), ("cell_chunk_items", ctypes.c_int)]
+                ("march_planes", ctypes.c_int)]
 
 
 class lbm_throat_result(ctypes.Structure):
@@ -607,7 +607,7 @@ def lbm_throat_lattice_features(throats) -> np.ndarray:
     return out
 
 
-def _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march=(0, 0), chunk_items=0):
+def _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march=(0, 0)):
     lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
     sch = lbm_schedule()
     if lad.ndim == 2:
@@ -622,20 +622,18 @@ def _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march=(0, 0), chunk_
         raise ValueError("form must be BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS or BATCH_MARCH")
     sch.batch_form = int(form)
     sch.march_threads, sch.march_planes = int(march[0]), int(march[1])
-    sch.cell_chunk_items = int(chunk_items)
     return sch, lad
 
 
 def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None,
-                         form: int = 0, march=(0, 0), chunk_items: int = 0):
+                         form: int = 0, march=(0, 0)):
     """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
     rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr).
     form: BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS or BATCH_MARCH.
-    march: (threads per CTA, planes per chunk) of BATCH_MARCH, 0 for the defaults.
-    chunk_items: BATCH_CELLS in chunks of at least this many items (0: one chunk)."""
+    march: (threads per CTA, planes per chunk) of BATCH_MARCH, 0 for the defaults."""
     th = np.ascontiguousarray(np.asarray(throats, dtype=np.float64).reshape(-1, 3, 4))
     n = th.shape[0]
-    sch, _lad = _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march, chunk_items)
+    sch, _lad = _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march)
     res = (lbm_throat_result * n)()
     rows = (lbm_increment * (n * sch.n_incr))()
     _check(load().lbm_run_throat_batch(th.ctypes.data_as(_DP), n, ctypes.byref(params), ctypes.byref(sch), res, rows,

@@ -337,15 +337,15 @@ __device__ __forceinline__ void cell_density_item(int i, const uint32_t* __restr
     rho2[i] = make_float2((a[0] + a[1]) + (a[2] + a[3]), rn);
 }
 
-// The densities of items i0 .. i1 - 1.
+// The densities of every item.
 __global__ void __launch_bounds__(CELL_THREADS)
-    cell_density_kernel(const uint32_t* __restrict__ wc, int i0, int i1, int cp, const float2* __restrict__ fc,
+    cell_density_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, const float2* __restrict__ fc,
                         float2* __restrict__ rho2) {
-    const int i = i0 + (int)blockIdx.x * CELL_THREADS + (int)threadIdx.x;
-    if (i < i1) cell_density_item(i, wc, cp, fc, rho2);
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i < n_items) cell_density_item(i, wc, cp, fc, rho2);
 }
 
-// One time step of item i: own population pairs, neighbour densities of the
+// One time step of every item: own population pairs, neighbour densities of the
 // density pass (0 where x + e_k is not fluid for the wetting component, i.e.
 // grain or beyond the box), collide_core (the compile-time tau = 1 form when
 // TAU1), push: one 8-byte store per direction where both components stream
@@ -409,17 +409,17 @@ __device__ __forceinline__ void cell_step_item(int i, const int2* __restrict__ i
     }
 }
 
-// The step of items i0 .. i1 - 1, three CTAs of 256 per SM (80 registers a
-// thread): 24 warps hide more of the neighbour-density and push-table latency
-// than 16 (423 against 402 throats/s on the 1024-throat batch)
+// three CTAs of 256 per SM (80 registers a thread): 24 warps hide more of the
+// neighbour-density and push-table latency than 16 (423 against 402 throats/s on
+// the 1024-throat batch)
 template <bool TAU1, class NB>
 __global__ void __launch_bounds__(CELL_THREADS, 3)
-    cell_step_kernel(const int2* __restrict__ items, int i0, int i1, int cp, const float2* __restrict__ fin,
+    cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float2* __restrict__ fin,
                      float2* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
                      const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp,
                      Phys P, const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
-    const int i = i0 + (int)blockIdx.x * CELL_THREADS + (int)threadIdx.x;
-    if (i < i1)
+    const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
+    if (i < n_items)
         cell_step_item<TAU1, NB>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all, ladder_stride,
                                  incr_now);
 }
@@ -657,10 +657,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             set_error("lbm_run_throat_batch: tau must be > 0.5");
             return LBM_ERR_ARG;
         }
-    if (sched->cell_chunk_items < 0) {
-        set_error("lbm_run_throat_batch: cell_chunk_items must be >= 0");
-        return LBM_ERR_ARG;
-    }
     const int march_threads = sched->march_threads ? sched->march_threads : LBM_MARCH_THREADS;
     const int march_planes = sched->march_planes ? sched->march_planes : LBM_MARCH_PLANES;
     if ((march_threads != 128 && march_threads != 256 && march_threads != 384 && march_threads != 512) ||
@@ -776,8 +772,7 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         double* d_rin = nullptr;
         lbm_increment* d_rows = nullptr;
         cudaGraphExec_t exec = nullptr;
-        cudaStream_t cap = nullptr, cap2 = nullptr;
-        std::vector<cudaEvent_t> chunk_ev;  // chunked cell list: [density done, step done] per chunk, fork
+        cudaStream_t cap = nullptr;
         auto cleanup = [&]() {
             cudaFree(a0); cudaFree(a1); cudaFree(d_bc); cudaFree(d_mask); cudaFree(d_nbr); cudaFree(d_nbr_nw);
             cudaFree(d_adh); cudaFree(d_recs); cudaFree(d_order); cudaFree(d_counter); cudaFree(d_rows);
@@ -796,8 +791,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             for (cudaGraphExec_t& e : exec2)
                 if (e) cudaGraphExecDestroy(e);
             if (cap) cudaStreamDestroy(cap);
-            if (cap2) cudaStreamDestroy(cap2);
-            for (cudaEvent_t e : chunk_ev) cudaEventDestroy(e);
         };
 #define BATCH_CUDA(call)                               \
     do {                                               \
@@ -890,19 +883,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                 set_error("lbm_run_throat_batch: too many cells for the cell-list form");
                 return LBM_ERR_ARG;
             }
-            // chunks of the cell list at throat boundaries (the throats in item order)
-            std::vector<int> chunk_at{0};
-            {
-                long long acc = 0;
-                for (int t : order) {
-                    acc += (long long)cells_of[t].size();
-                    if (sched->cell_chunk_items > 0 && acc - chunk_at.back() >= sched->cell_chunk_items &&
-                        acc < n_items)
-                        chunk_at.push_back((int)acc);
-                }
-                chunk_at.push_back((int)std::min<long long>(n_items, INT_MAX));
-            }
-            const int n_cchunks = (int)chunk_at.size() - 1;
             std::vector<int2> cells((size_t)n_items);
             std::vector<int> box_to_item((size_t)c_tot);
             host_parallel_for(n, [&](int t) {
@@ -982,11 +962,6 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                                                                      (float)params->rho_minor);
                 BATCH_CUDA(cudaGetLastError());
             }
-            if (n_cchunks > 1) {
-                BATCH_CUDA(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
-                chunk_ev.assign((size_t)2 * n_cchunks, nullptr);
-                for (cudaEvent_t& e : chunk_ev) BATCH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            }
             BATCH_CUDA(cudaStreamSynchronize(stream));  // host lists go out of scope
             const int n_graphs = (sched->n_steps & 1) ? 2 : 1;
             for (int gi = 0; gi < n_graphs; ++gi) {
@@ -1009,52 +984,22 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                             cerr = cudaGetLastError();
                         continue;
                     }
-                    auto density = [&](int i0, int i1, cudaStream_t st) {
-                        cell_density_kernel<<<(unsigned)((i1 - i0 + CELL_THREADS - 1) / CELL_THREADS), CELL_THREADS,
-                                              0, st>>>(d_wc, i0, i1, cp, fin, d_rho2);
-                    };
-                    auto step = [&](int i0, int i1, cudaStream_t st) {
-                        const unsigned nb = (unsigned)((i1 - i0 + CELL_THREADS - 1) / CELL_THREADS);
-                        if (t1 && nb16)
-                            cell_step_kernel<true, int16_t><<<nb, CELL_THREADS, 0, st>>>(
-                                d_cells, i0, i1, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
-                        else if (t1)
-                            cell_step_kernel<true, int><<<nb, CELL_THREADS, 0, st>>>(
-                                d_cells, i0, i1, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
-                        else if (nb16)
-                            cell_step_kernel<false, int16_t><<<nb, CELL_THREADS, 0, st>>>(
-                                d_cells, i0, i1, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
-                        else
-                            cell_step_kernel<false, int><<<nb, CELL_THREADS, 0, st>>>(
-                                d_cells, i0, i1, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
-                    };
-                    if (n_cchunks == 1) {
-                        density(0, n_cells, cap);
-                        step(0, n_cells, cap);
-                        cerr = cudaGetLastError();
-                        continue;
-                    }
-                    // chunk c: its densities on cap, its step on cap2 once they are
-                    // done, beside the densities of chunk c + 1; the densities of
-                    // chunk c wait for the step of chunk c - 2, so that at most two
-                    // chunks' pairs are in flight through L2; cap joins the last
-                    // step before the next time step (throats, and so pushes and
-                    // neighbour densities, never cross a chunk boundary)
-                    cudaEvent_t* ev_d = chunk_ev.data();
-                    cudaEvent_t* ev_s = chunk_ev.data() + n_cchunks;
-                    for (int c = 0; c < n_cchunks && cerr == cudaSuccess; ++c) {
-                        if (c >= 2) cerr = cudaStreamWaitEvent(cap, ev_s[c - 2], 0);
-                        if (cerr != cudaSuccess) break;
-                        density(chunk_at[(size_t)c], chunk_at[(size_t)c + 1], cap);
-                        cerr = cudaGetLastError();
-                        if (cerr == cudaSuccess) cerr = cudaEventRecord(ev_d[c], cap);
-                        if (cerr == cudaSuccess) cerr = cudaStreamWaitEvent(cap2, ev_d[c], 0);
-                        if (cerr != cudaSuccess) break;
-                        step(chunk_at[(size_t)c], chunk_at[(size_t)c + 1], cap2);
-                        cerr = cudaGetLastError();
-                        if (cerr == cudaSuccess) cerr = cudaEventRecord(ev_s[c], cap2);
-                    }
-                    if (cerr == cudaSuccess) cerr = cudaStreamWaitEvent(cap, ev_s[n_cchunks - 1], 0);
+                    cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
+                    cerr = cudaGetLastError();
+                    if (cerr != cudaSuccess) break;
+                    if (t1 && nb16)
+                        cell_step_kernel<true, int16_t><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
+                    else if (t1)
+                        cell_step_kernel<true, int><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
+                    else if (nb16)
+                        cell_step_kernel<false, int16_t><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
+                    else
+                        cell_step_kernel<false, int><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
+                    cerr = cudaGetLastError();
                 }
                 if (cerr == cudaSuccess) {
                     const int c = (gi + sched->n_steps) & 1;

@@ -195,30 +195,11 @@ def test_march_shapes_agree(lbm, march):
     _rows_equal(ra, rowsa, rb, rowsb, ladders)
 
 
-@pytest.mark.parametrize("chunk_items", [1, 3000, 20000])
-def test_cell_chunks_agree(lbm, chunk_items):
-    """The cell list cut into chunks at throat boundaries (every throat its own
-    chunk, a few throats a chunk, two chunks), each chunk's step running beside
-    the next chunk's densities on a second stream, gives the rows of the
-    unchunked list bit for bit, over odd and even step counts."""
-    from paper_1906_04722_gb300 import surrogate as S
-    throats = W.delaunay_throats(W.sample_spheres(128), 8, seed=17)
-    ladders = S.pressure_ladder(S.throat_incircle(throats), 3, 0.4, 1.6, W.RHO_MAJOR, W.RHO_MINOR, W.G_COHESION)
-    for n_steps in (5, 6):
-        ra, rowsa = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, n_steps, W.RHO_MAJOR,
-                                             form=lbm.BATCH_CELLS)
-        rb, rowsb = lbm.lbm_run_throat_batch(throats, _params(lbm), ladders, n_steps, W.RHO_MAJOR,
-                                             form=lbm.BATCH_CELLS, chunk_items=chunk_items)
-        _rows_equal(ra, rowsa, rb, rowsb, ladders)
-
-
 def test_march_shape_validation(lbm):
     throats = W.delaunay_throats(W.sample_spheres(128), 1, seed=15)
     for march in ((100, 16), (256, 65), (256, -1)):
         with pytest.raises(lbm.LbmError):
             lbm.lbm_run_throat_batch(throats, _params(lbm), [2.0], 1, W.RHO_MAJOR, form=lbm.BATCH_MARCH, march=march)
-    with pytest.raises(lbm.LbmError):
-        lbm.lbm_run_throat_batch(throats, _params(lbm), [2.0], 1, W.RHO_MAJOR, chunk_items=-1)
 
 
 def test_batch_forms_agree_with_a_wide_box(lbm):
