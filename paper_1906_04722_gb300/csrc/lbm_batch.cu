@@ -78,24 +78,36 @@ __device__ void measure_cells(const Geom& g, double G, int probe, double rho_in_
     for (int i = 0; i < NMEAS; ++i) acc[i] = 0.0;
     const int N = g.nxy * g.nz;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int c = tid; c < N; c += BATCH_THREADS) {
-        float rwf, rnf;
-        const uint32_t w = state(c, rwf, rnf);
-        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
-        if (cls == CLS_SOLID) continue;
-        const double rw = rwf, rn = rnf;
-        acc[MS_MASS_W] += rw;
-        acc[MS_MASS_NW] += rn;
-        if (!isfinite(rw) || !isfinite(rn)) acc[MS_N_NONFINITE] += 1.0;
-        const double p = (rw + rn) / 3.0 + G * rw * rn / 3.0;  // Eq. 5
-        if (cls == CLS_INLET) { acc[MS_PIN] += p; acc[MS_N_IN] += 1.0; continue; }
-        if (cls == CLS_OUTLET) { acc[MS_POUT] += p; acc[MS_N_OUT] += 1.0; continue; }
-        acc[MS_N_FLUID] += 1.0;
-        if (rw > rn) acc[MS_N_W] += 1.0;
-        const double phi = (rw - rn) / (rw + rn);
-        if (fabs(phi) < 0.5) acc[MS_N_INTERFACE] += 1.0;
-        if (phi > 0.9) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
-        if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
+    // a thread's cells are tid, tid + BATCH_THREADS, ...: read MEAS_AHEAD of them at
+    // a time (their loads in flight together), then add them up in that order
+    constexpr int MEAS_AHEAD = 4;
+    for (int c0 = tid; c0 < N; c0 += MEAS_AHEAD * BATCH_THREADS) {
+        float rwf[MEAS_AHEAD], rnf[MEAS_AHEAD];
+        uint32_t wv[MEAS_AHEAD];
+#pragma unroll
+        for (int u = 0; u < MEAS_AHEAD; ++u) {
+            const int c = c0 + u * BATCH_THREADS;
+            rwf[u] = rnf[u] = 0.f;
+            wv[u] = c < N ? state(c, rwf[u], rnf[u]) : (uint32_t)CLS_SOLID << CLS_SHIFT;
+        }
+#pragma unroll
+        for (int u = 0; u < MEAS_AHEAD; ++u) {
+            const uint32_t cls = (wv[u] >> CLS_SHIFT) & CLS_MASK;
+            if (cls == CLS_SOLID) continue;
+            const double rw = rwf[u], rn = rnf[u];
+            acc[MS_MASS_W] += rw;
+            acc[MS_MASS_NW] += rn;
+            if (!isfinite(rw) || !isfinite(rn)) acc[MS_N_NONFINITE] += 1.0;
+            const double p = (rw + rn) / 3.0 + G * rw * rn / 3.0;  // Eq. 5
+            if (cls == CLS_INLET) { acc[MS_PIN] += p; acc[MS_N_IN] += 1.0; continue; }
+            if (cls == CLS_OUTLET) { acc[MS_POUT] += p; acc[MS_N_OUT] += 1.0; continue; }
+            acc[MS_N_FLUID] += 1.0;
+            if (rw > rn) acc[MS_N_W] += 1.0;
+            const double phi = (rw - rn) / (rw + rn);
+            if (fabs(phi) < 0.5) acc[MS_N_INTERFACE] += 1.0;
+            if (phi > 0.9) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
+            if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
+        }
     }
     double tot[NMEAS];
 #pragma unroll
