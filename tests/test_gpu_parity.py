@@ -210,26 +210,32 @@ def test_checkpoint_resume_bitwise(lbm):
     assert np.array_equal(a, b)
 
 
-def test_sample192_full_size_sampled_cells(lbm, orc):
+@pytest.mark.parametrize("kernel", ["push", "staged"])
+def test_sample192_full_size_sampled_cells(lbm, orc, kernel):
     """The 192^3 drainage sample in the launch configuration the benchmark
-    times: two steps from a seeded noisy state, sampled cells against the
-    oracle run on a crop that holds their whole dependency cone (2 cells per
-    step), plus the bit-exact mask."""
+    times (the push kernel in the shape its autotuner picks: 6 rows, 3 stages,
+    24-plane z segments) and in the staged kernel new domains start with: four
+    steps from a seeded noisy state, sampled cells against the oracle run on a
+    crop that holds their whole dependency cone (2 cells per step), plus the
+    bit-exact mask."""
     shape = (192, 192, 192)
     spheres = W.sample192_spheres()
     flags = dict(reservoirs=True, membrane_layers=3)
     dom = lbm.Domain(_params(lbm, **flags), spheres, (192, 192, 192))
+    if kernel == "push":
+        dom.set_push_shape(6, 24)
+        assert dom.step_kernel() == (lbm.KERNEL_PUSH, 24)
     mask = orc.voxelise(shape, spheres, reservoirs=True, membrane_layers=3)
     assert np.array_equal(dom.mask(), mask)
     rho0 = W.initial_densities(shape, noise=2e-2, seed=8)
     dom.set_densities(rho0)
-    K = 2
+    K = 4
     dom.step(K)
     rho_g = dom.density()
     rng = np.random.default_rng(13)
     R = 2 * K + 2
     fluid = np.argwhere(mask == 0)
-    picks = fluid[rng.choice(len(fluid), 24, replace=False)]
+    picks = fluid[rng.choice(len(fluid), 40, replace=False)]
     edge = np.array([[0, 0, 0], [191, 191, 191], [1, 95, 0], [190, 100, 191]])
     for z, y, x in list(picks) + [tuple(e) for e in edge]:
         zs, ys, xs = [slice(max(0, v - R), min(192, v + R + 1)) for v in (z, y, x)]
