@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(P16X * BY, MINB)
                           const uint32_t* __restrict__ nbr_nw, const uint32_t* __restrict__ adh, Geom g, Phys P,
                           int lz, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (*reinterpret_cast<volatile int*>(err) != 0) return;  // an earlier launch gave up
+    // an earlier launch or CTA gave up: the whole CTA leaves (one decision for all its threads)
+    if (__syncthreads_or(*reinterpret_cast<volatile int*>(err) != 0)) return;
     constexpr int TY = BY - 2;
     constexpr int NT = P16X * BY;
     constexpr uint32_t WP = pad128(words16_bytes<BY>()), RP = pad128(r16_bytes<BY>());

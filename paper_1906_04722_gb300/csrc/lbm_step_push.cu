@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(PX * BY, MINB)
                         const uint32_t* __restrict__ adh, Geom g, Phys P, int lz, int pf, int order,
                         int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (*reinterpret_cast<volatile int*>(err) != 0) return;  // an earlier launch gave up
+    // an earlier launch or CTA gave up: the whole CTA leaves (one decision for all its threads)
+    if (__syncthreads_or(*reinterpret_cast<volatile int*>(err) != 0)) return;
     constexpr int TY = BY - 2;
     constexpr int NT = PX * BY;
     float2* stages = reinterpret_cast<float2*>(smem);  // [NS][Q][BY][PX]

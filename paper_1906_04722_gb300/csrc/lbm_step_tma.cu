@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                        const float* __restrict__ fin, float* __restrict__ fout, const uint32_t* __restrict__ nbr_nw,
                        const uint32_t* __restrict__ adh, Geom g, Phys P, int lz, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
-    // a launch after one that gave up does no work (the host reports the error)
-    if (*reinterpret_cast<volatile int*>(err) != 0) return;
+    // an earlier launch or CTA gave up: the whole CTA leaves (one decision for all its threads)
+    if (__syncthreads_or(*reinterpret_cast<volatile int*>(err) != 0)) return;
     float* pop = reinterpret_cast<float*>(smem + SM_POP);
     uint32_t* words = reinterpret_cast<uint32_t*>(smem + SM_WORDS);
     float* rho = reinterpret_cast<float*>(smem + SM_RHO);
