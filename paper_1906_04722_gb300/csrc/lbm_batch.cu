@@ -421,11 +421,11 @@ __device__ __forceinline__ void cell_step_item(int i, const int2* __restrict__ i
     }
 }
 
-// three CTAs of 256 per SM (80 registers a thread): 24 warps hide more of the
-// neighbour-density and push-table latency than 16 (423 against 402 throats/s on
-// the 1024-throat batch)
+// four CTAs of 256 per SM (64 registers a thread, a few spilled): 32 warps hide
+// more of the neighbour-density and push-table latency than 24 or 16 (427, 424
+// and 402 throats/s on the 1024-throat batch)
 template <bool TAU1, class NB>
-__global__ void __launch_bounds__(CELL_THREADS, 3)
+__global__ void __launch_bounds__(CELL_THREADS, 4)
     cell_step_kernel(const int2* __restrict__ items, int n_items, int cp, const float2* __restrict__ fin,
                      float2* __restrict__ fout, const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
                      const uint32_t* __restrict__ wnc, const uint32_t* __restrict__ adhc, const NB* __restrict__ nbp,
