@@ -67,28 +67,35 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;  // valid in thread 0
 }
 
-// Measurements of one throat box (definitions of lbm_measure), into row.
-// state(c, rw, rn) returns the geometry word of box cell c (class CLS_SOLID for
-// grain) and its densities after streaming, summed in k order.
+// Measurements of a throat box (definitions of lbm_measure).  The box's cells
+// are cut into slices of MEAS_SLICE cells; a slice's sums are the CTA sum
+// (block_sum) of per-thread sums, thread t adding cells t, t + BATCH_THREADS, ...
+// of the slice in that order; a throat's sums are its slices' sums added in
+// slice order.  Every form computes exactly these sums: the box forms slice by
+// slice in one CTA, the cell-list form one CTA per slice.
+constexpr int MEAS_SLICE = 32 * BATCH_THREADS;
+
+// The sums of box cells c0 .. c1 - 1 (valid in thread 0).  state(c, rw, rn)
+// returns the geometry word of box cell c (class CLS_SOLID for grain) and its
+// densities after streaming, summed in k order.
 template <class CellState>
-__device__ void measure_cells(const Geom& g, double G, int probe, double rho_in_nw, double* red, lbm_increment* row,
-                              CellState&& state) {
+__device__ void measure_slice(int c0, int c1, double G, double* red, CellState&& state, double (&tot)[NMEAS]) {
     double acc[NMEAS];
 #pragma unroll
     for (int i = 0; i < NMEAS; ++i) acc[i] = 0.0;
-    const int N = g.nxy * g.nz;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    // a thread's cells are tid, tid + BATCH_THREADS, ...: read MEAS_AHEAD of them at
-    // a time (their loads in flight together), then add them up in that order
+    // a thread's cells are c0 + tid, c0 + tid + BATCH_THREADS, ...: read MEAS_AHEAD
+    // of them at a time (their loads in flight together), then add them up in
+    // that order
     constexpr int MEAS_AHEAD = 4;
-    for (int c0 = tid; c0 < N; c0 += MEAS_AHEAD * BATCH_THREADS) {
+    for (int cb = c0 + tid; cb < c1; cb += MEAS_AHEAD * BATCH_THREADS) {
         float rwf[MEAS_AHEAD], rnf[MEAS_AHEAD];
         uint32_t wv[MEAS_AHEAD];
 #pragma unroll
         for (int u = 0; u < MEAS_AHEAD; ++u) {
-            const int c = c0 + u * BATCH_THREADS;
+            const int c = cb + u * BATCH_THREADS;
             rwf[u] = rnf[u] = 0.f;
-            wv[u] = c < N ? state(c, rwf[u], rnf[u]) : (uint32_t)CLS_SOLID << CLS_SHIFT;
+            wv[u] = c < c1 ? state(c, rwf[u], rnf[u]) : (uint32_t)CLS_SOLID << CLS_SHIFT;
         }
 #pragma unroll
         for (int u = 0; u < MEAS_AHEAD; ++u) {
@@ -109,25 +116,47 @@ __device__ void measure_cells(const Geom& g, double G, int probe, double rho_in_
             if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
         }
     }
-    double tot[NMEAS];
 #pragma unroll
     for (int i = 0; i < NMEAS; ++i) tot[i] = block_sum(acc[i], red);
-    float pr[2] = {0.f, 0.f};
-    if (tid == 0 && probe >= 0) state(probe, pr[0], pr[1]);
+}
+
+// The increment's row from a throat's sums and its probe densities.
+__device__ void measure_row(const double (&tot)[NMEAS], double rho_in_nw, int probe, float pw, float pn,
+                            lbm_increment* row) {
+    lbm_increment r;
+    r.rho_in_nw = rho_in_nw;
+    r.p_w = tot[MS_N_BULK_W] > 0 ? tot[MS_PW] / tot[MS_N_BULK_W] : NAN;
+    r.p_nw = tot[MS_N_BULK_NW] > 0 ? tot[MS_PNW] / tot[MS_N_BULK_NW] : NAN;
+    r.p_c = r.p_nw - r.p_w;
+    const double pin = tot[MS_N_IN] > 0 ? tot[MS_PIN] / tot[MS_N_IN] : NAN;
+    const double pout = tot[MS_N_OUT] > 0 ? tot[MS_POUT] / tot[MS_N_OUT] : NAN;
+    r.p_c_res = pin - pout;
+    r.S_w = tot[MS_N_FLUID] > 0 ? tot[MS_N_W] / tot[MS_N_FLUID] : NAN;
+    const double a = pw, b = pn;
+    r.phi_probe = probe >= 0 && (a + b) != 0.0 ? (a - b) / (a + b) : 0.0;
+    r.n_interface = (long long)tot[MS_N_INTERFACE];
+    *row = r;
+}
+
+// Measurements of one throat box in one CTA, slice by slice, into row.
+template <class CellState>
+__device__ void measure_cells(const Geom& g, double G, int probe, double rho_in_nw, double* red, lbm_increment* row,
+                              CellState&& state) {
+    const int N = g.nxy * g.nz;
+    double tot[NMEAS];
+#pragma unroll
+    for (int i = 0; i < NMEAS; ++i) tot[i] = 0.0;
+    for (int c0 = 0; c0 < N; c0 += MEAS_SLICE) {
+        double part[NMEAS];
+        measure_slice(c0, min(N, c0 + MEAS_SLICE), G, red, state, part);
+#pragma unroll
+        for (int i = 0; i < NMEAS; ++i) tot[i] += part[i];
+    }
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     if (tid == 0) {
-        lbm_increment r;
-        r.rho_in_nw = rho_in_nw;
-        r.p_w = tot[MS_N_BULK_W] > 0 ? tot[MS_PW] / tot[MS_N_BULK_W] : NAN;
-        r.p_nw = tot[MS_N_BULK_NW] > 0 ? tot[MS_PNW] / tot[MS_N_BULK_NW] : NAN;
-        r.p_c = r.p_nw - r.p_w;
-        const double pin = tot[MS_N_IN] > 0 ? tot[MS_PIN] / tot[MS_N_IN] : NAN;
-        const double pout = tot[MS_N_OUT] > 0 ? tot[MS_POUT] / tot[MS_N_OUT] : NAN;
-        r.p_c_res = pin - pout;
-        r.S_w = tot[MS_N_FLUID] > 0 ? tot[MS_N_W] / tot[MS_N_FLUID] : NAN;
-        const double a = pr[0], b = pr[1];
-        r.phi_probe = probe >= 0 && (a + b) != 0.0 ? (a - b) / (a + b) : 0.0;
-        r.n_interface = (long long)tot[MS_N_INTERFACE];
-        *row = r;
+        float pr[2] = {0.f, 0.f};
+        if (probe >= 0) state(probe, pr[0], pr[1]);
+        measure_row(tot, rho_in_nw, probe, pr[0], pr[1], row);
     }
 }
 
@@ -517,36 +546,63 @@ cudaError_t launch_march(int mt, bool t1, bool nb16, int n_chunks, cudaStream_t 
     return cudaErrorInvalidValue;
 }
 
-// Measurements of throat blockIdx.x from the compact populations, walking its
-// box in the order of the box-layout forms (the same sums, the same rounding);
-// the last CTA to finish advances the increment index.
+// Measurements of the cell-list form from the compact populations, one CTA per
+// slice of a throat box: slice (throat, first box cell, end box cell, index of
+// the throat's first slice), walked in the box order of the box-layout forms
+// through the box -> item map (the same sums, the same rounding).  The last CTA
+// of a throat to finish adds its slices' sums in slice order and writes the
+// row; the last CTA of all advances the increment index.
 __global__ void __launch_bounds__(BATCH_THREADS)
-    cell_measure_kernel(const ThroatRec* __restrict__ recs, int n, const int* __restrict__ box_to_item, int cp,
-                        const float2* __restrict__ fc, const uint32_t* __restrict__ wc, double G,
-                        const double* __restrict__ rin_all, int ladder_stride, lbm_increment* __restrict__ rows,
-                        int n_incr, int* incr_now, int* done) {
+    cell_measure_kernel(const ThroatRec* __restrict__ recs, const int4* __restrict__ slices, int n_slices,
+                        const int* __restrict__ box_to_item, int cp, const float2* __restrict__ fc,
+                        const uint32_t* __restrict__ wc, double G, const double* __restrict__ rin_all,
+                        int ladder_stride, lbm_increment* __restrict__ rows, int n_incr, double* partials,
+                        int* throat_done, int* incr_now, int* done) {
     __shared__ double red[32];
-    const int id = blockIdx.x;
+    __shared__ int s_last;
+    const int4 S = slices[blockIdx.x];
+    const int id = S.x;
     const int incr = *incr_now;
     const Geom g = recs[id].g;
     const int* map = box_to_item + recs[id].c_off;
-    measure_cells(g, G, recs[id].probe, rin_all[(size_t)id * ladder_stride + incr], red,
-                  rows + (size_t)id * n_incr + incr, [&](int c, float& rw, float& rn) {
-                      rw = 0.f;
-                      rn = 0.f;
-                      const int j = map[c];
-                      if (j < 0) return (uint32_t)CLS_SOLID << CLS_SHIFT;
-                      const uint32_t w = wc[j];
-                      const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
-                      for (int k = 0; k < Q; ++k) rw += fc[(size_t)k * cp + j].x;
-                      if (cls != CLS_MEMBRANE)
-                          for (int k = 0; k < Q; ++k) rn += fc[(size_t)k * cp + j].y;
-                      return w;
-                  });
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
+    auto state = [&](int c, float& rw, float& rn) {
+        rw = 0.f;
+        rn = 0.f;
+        const int j = map[c];
+        if (j < 0) return (uint32_t)CLS_SOLID << CLS_SHIFT;
+        const uint32_t w = wc[j];
+        const uint32_t cls = (w >> CLS_SHIFT) & CLS_MASK;
+        for (int k = 0; k < Q; ++k) rw += fc[(size_t)k * cp + j].x;
+        if (cls != CLS_MEMBRANE)
+            for (int k = 0; k < Q; ++k) rn += fc[(size_t)k * cp + j].y;
+        return w;
+    };
+    double part[NMEAS];
+    measure_slice(S.y, S.z, G, red, state, part);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int n_sl = (g.nxy * g.nz + MEAS_SLICE - 1) / MEAS_SLICE;
+    if (tid == 0) {
+        for (int i = 0; i < NMEAS; ++i) partials[(size_t)blockIdx.x * NMEAS + i] = part[i];
         __threadfence();
-        if (atomicAdd(done, 1) == n - 1) {  // every CTA has read the index
+        s_last = atomicAdd(throat_done + id, 1) == n_sl - 1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (s_last) {  // every slice of this throat has stored its sums
+            __threadfence();
+            throat_done[id] = 0;
+            double tot[NMEAS];
+            for (int i = 0; i < NMEAS; ++i) tot[i] = 0.0;
+            for (int q = 0; q < n_sl; ++q)
+                for (int i = 0; i < NMEAS; ++i) tot[i] += __ldcg(partials + (size_t)(S.w + q) * NMEAS + i);
+            const int probe = recs[id].probe;
+            float pr[2] = {0.f, 0.f};
+            if (probe >= 0) state(probe, pr[0], pr[1]);
+            measure_row(tot, rin_all[(size_t)id * ladder_stride + incr], probe, pr[0], pr[1],
+                        rows + (size_t)id * n_incr + incr);
+        }
+        __threadfence();
+        if (atomicAdd(done, 1) == n_slices - 1) {  // every CTA has read the index
             *done = 0;
             *incr_now = incr + 1;
         }
@@ -779,6 +835,9 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
         void* d_nbp = nullptr;
         int* d_plane_item = nullptr;
         int4* d_chunks = nullptr;
+        int4* d_slices = nullptr;
+        double* d_partials = nullptr;
+        int* d_throat_done = nullptr;
         uint32_t* d_wc = nullptr;
         cudaGraphExec_t exec2[2] = {nullptr, nullptr};
         double* d_rin = nullptr;
@@ -798,6 +857,9 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
             cudaFree(d_nbp);
             cudaFree(d_plane_item);
             cudaFree(d_chunks);
+            cudaFree(d_slices);
+            cudaFree(d_partials);
+            cudaFree(d_throat_done);
             cudaFree(d_wc);
             if (exec) cudaGraphExecDestroy(exec);
             for (cudaGraphExec_t& e : exec2)
@@ -937,6 +999,21 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                     BATCH_CUDA(cudaMemcpyAsync(d_chunks, chunks.data(), sizeof(int4) * chunks.size(),
                                                cudaMemcpyHostToDevice, stream));
             }
+            // measurement slices of every throat box
+            std::vector<int4> slices;
+            for (int t = 0; t < n; ++t) {
+                const int N = recs[t].g.nxy * recs[t].g.nz, first = (int)slices.size();
+                for (int c0 = 0; c0 < N; c0 += MEAS_SLICE)
+                    slices.push_back(make_int4(t, c0, std::min(N, c0 + MEAS_SLICE), first));
+            }
+            const int n_slices = (int)slices.size();
+            BATCH_CUDA(cudaMalloc(&d_slices, sizeof(int4) * std::max<size_t>(1, slices.size())));
+            BATCH_CUDA(cudaMalloc(&d_partials, sizeof(double) * NMEAS * std::max<size_t>(1, slices.size())));
+            BATCH_CUDA(cudaMalloc(&d_throat_done, sizeof(int) * (size_t)n));
+            BATCH_CUDA(cudaMemsetAsync(d_throat_done, 0, sizeof(int) * (size_t)n, stream));
+            if (n_slices)
+                BATCH_CUDA(cudaMemcpyAsync(d_slices, slices.data(), sizeof(int4) * slices.size(),
+                                           cudaMemcpyHostToDevice, stream));
             const size_t fc_floats = (size_t)2 * Q * std::max(cp, 32);
             BATCH_CUDA(cudaMalloc(&d_cells, sizeof(int2) * std::max<size_t>(1, cells.size())));
             BATCH_CUDA(cudaMalloc(&d_map, sizeof(int) * (size_t)std::max<long long>(1, c_tot)));
@@ -1015,11 +1092,10 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                 }
                 if (cerr == cudaSuccess) {
                     const int c = (gi + sched->n_steps) & 1;
-                    cell_measure_kernel<<<n, dim3(32, BATCH_BY), 0, cap>>>(d_recs, n, d_map, cp,
-                                                                           reinterpret_cast<const float2*>(c ? a1 : a0),
-                                                                           d_wc,
-                                                                           params->G, d_rin, sched->per_throat ? I : 0,
-                                                                           d_rows, I, d_incr, d_incr + 1);
+                    cell_measure_kernel<<<n_slices, dim3(32, BATCH_BY), 0, cap>>>(
+                        d_recs, d_slices, n_slices, d_map, cp, reinterpret_cast<const float2*>(c ? a1 : a0), d_wc,
+                        params->G, d_rin, sched->per_throat ? I : 0, d_rows, I, d_partials, d_throat_done, d_incr,
+                        d_incr + 1);
                     cerr = cudaGetLastError();
                 }
                 cudaGraph_t graph = nullptr;
