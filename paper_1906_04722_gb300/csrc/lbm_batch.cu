@@ -105,15 +105,32 @@ __device__ void measure_slice(int c0, int c1, double G, double* red, CellState&&
             acc[MS_MASS_W] += rw;
             acc[MS_MASS_NW] += rn;
             if (!isfinite(rw) || !isfinite(rn)) acc[MS_N_NONFINITE] += 1.0;
-            const double p = (rw + rn) / 3.0 + G * rw * rn / 3.0;  // Eq. 5
+            const double x = rw - rn, y = rw + rn;
+            const double p = (y + G * rw * rn) * (1.0 / 3.0);  // Eq. 5
             if (cls == CLS_INLET) { acc[MS_PIN] += p; acc[MS_N_IN] += 1.0; continue; }
             if (cls == CLS_OUTLET) { acc[MS_POUT] += p; acc[MS_N_OUT] += 1.0; continue; }
             acc[MS_N_FLUID] += 1.0;
             if (rw > rn) acc[MS_N_W] += 1.0;
-            const double phi = (rw - rn) / (rw + rn);
-            if (fabs(phi) < 0.5) acc[MS_N_INTERFACE] += 1.0;
-            if (phi > 0.9) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
-            if (phi < -0.9) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
+            // phi = x / y against 0.5 and 0.9 without the division: for y > 0,
+            // |phi| < 0.5 is |x| < 0.5 y exactly (the scaling is exact and no
+            // quotient of doubles lies within half an ulp below 0.5); the product
+            // 0.9 y is rounded, so a cell within 1e-12 of that threshold is decided
+            // by the division itself, as is every cell with y <= 0 or not finite
+            bool in_if, bulk_w, bulk_nw;
+            const double t9 = 0.9 * y;
+            if (y > 0.0 && fabs(fabs(x) - t9) > 1e-12 * y) {
+                in_if = fabs(x) < 0.5 * y;
+                bulk_w = x > t9;
+                bulk_nw = x < -t9;
+            } else {
+                const double phi = x / y;
+                in_if = fabs(phi) < 0.5;
+                bulk_w = phi > 0.9;
+                bulk_nw = phi < -0.9;
+            }
+            if (in_if) acc[MS_N_INTERFACE] += 1.0;
+            if (bulk_w) { acc[MS_PW] += p; acc[MS_N_BULK_W] += 1.0; }
+            if (bulk_nw) { acc[MS_PNW] += p; acc[MS_N_BULK_NW] += 1.0; }
         }
     }
 #pragma unroll
