@@ -395,22 +395,10 @@ __device__ __forceinline__ void cell_density_item(int i, const uint32_t* __restr
     rho2[i] = make_float2((a[0] + a[1]) + (a[2] + a[3]), rn);
 }
 
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialization may start while the kernel before it in the stream still runs;
-// griddepcontrol.wait holds it until that kernel has finished and its writes are
-// visible, and griddepcontrol.launch_dependents lets the next kernel start.
-// Without the launch attribute both are no-ops.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// The densities of every item.  It reads the populations the previous step
-// wrote: it waits for that step before anything else, then lets the step that
-// follows start (whose first loads read the same populations).
+// The densities of every item.
 __global__ void __launch_bounds__(CELL_THREADS)
     cell_density_kernel(const uint32_t* __restrict__ wc, int n_items, int cp, const float2* __restrict__ fc,
                         float2* __restrict__ rho2) {
-    grid_dep_wait();
-    grid_dep_release();
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i < n_items) cell_density_item(i, wc, cp, fc, rho2);
 }
@@ -422,7 +410,7 @@ __global__ void __launch_bounds__(CELL_THREADS)
 // alike, separate stores where a membrane makes them differ.  The bounce-back
 // choice selects an address rather than a branch: one store instruction per
 // value for the whole warp, whichever way each lane goes.
-template <bool TAU1, class NB, bool PDL = false>
+template <bool TAU1, class NB>
 __device__ __forceinline__ void cell_step_item(int i, const int2* __restrict__ items, int cp,
                                                const float2* __restrict__ fin, float2* __restrict__ fout,
                                                const float2* __restrict__ rho2, const uint32_t* __restrict__ wc,
@@ -446,10 +434,6 @@ __device__ __forceinline__ void cell_step_item(int i, const int2* __restrict__ i
 #pragma unroll
     for (int k = 1; k < Q; ++k)
         dst[k] = k == 1 ? i + 1 : k == 2 ? i - 1 : nb_decode(__ldg(nbp + (size_t)(k - 3) * cp + i), i);
-    if constexpr (PDL) {  // the densities come from the launch before this one
-        grid_dep_wait();
-        grid_dep_release();
-    }
     auto rho_at = [&](int k) {
         if (k == 0) return __ldg(rho2 + i);
         const bool wall = (w >> OPP(k)) & 1u;
@@ -494,8 +478,8 @@ __global__ void __launch_bounds__(CELL_THREADS, 4)
                      Phys P, const float* __restrict__ bc_all, int ladder_stride, const int* __restrict__ incr_now) {
     const int i = blockIdx.x * CELL_THREADS + threadIdx.x;
     if (i < n_items)
-        cell_step_item<TAU1, NB, true>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all, ladder_stride,
-                                       incr_now);
+        cell_step_item<TAU1, NB>(i, items, cp, fin, fout, rho2, wc, wnc, adhc, nbp, P, bc_all, ladder_stride,
+                                 incr_now);
 }
 
 // One time step of the cell list in one launch, a CTA per chunk of a throat's
@@ -742,23 +726,6 @@ extern "C" int lbm_throat_geometry(const double* spheres3, int dims_out[3], unsi
         if (probe_out) std::memcpy(probe_out, probe, sizeof(probe));
     }
     return LBM_OK;
-}
-
-// A launch that may start while the kernel before it in the stream finishes
-// (programmatic stream serialization; the kernel waits with grid_dep_wait).
-template <class... KArgs, class... Args>
-cudaError_t launch_overlapped(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_params* params,
@@ -1123,33 +1090,22 @@ extern "C" int lbm_run_throat_batch(const double* throats, int n, const lbm_para
                             cerr = cudaGetLastError();
                         continue;
                     }
-                    cerr = launch_overlapped(cell_density_kernel, blocks, CELL_THREADS, cap,
-                                             (const uint32_t*)d_wc, n_cells, cp, fin, d_rho2);
+                    cell_density_kernel<<<blocks, CELL_THREADS, 0, cap>>>(d_wc, n_cells, cp, fin, d_rho2);
+                    cerr = cudaGetLastError();
                     if (cerr != cudaSuccess) break;
                     if (t1 && nb16)
-                        cerr = launch_overlapped(cell_step_kernel<true, int16_t>, blocks, CELL_THREADS, cap,
-                                                 (const int2*)d_cells, n_cells, cp, fin, fout, (const float2*)d_rho2,
-                                                 (const uint32_t*)d_wc, (const uint32_t*)d_wnc,
-                                                 (const uint32_t*)d_adhc, nb16p, P, (const float*)d_bc, ls,
-                                                 (const int*)d_incr);
+                        cell_step_kernel<true, int16_t><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
                     else if (t1)
-                        cerr = launch_overlapped(cell_step_kernel<true, int>, blocks, CELL_THREADS, cap,
-                                                 (const int2*)d_cells, n_cells, cp, fin, fout, (const float2*)d_rho2,
-                                                 (const uint32_t*)d_wc, (const uint32_t*)d_wnc,
-                                                 (const uint32_t*)d_adhc, nb32p, P, (const float*)d_bc, ls,
-                                                 (const int*)d_incr);
+                        cell_step_kernel<true, int><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
                     else if (nb16)
-                        cerr = launch_overlapped(cell_step_kernel<false, int16_t>, blocks, CELL_THREADS, cap,
-                                                 (const int2*)d_cells, n_cells, cp, fin, fout, (const float2*)d_rho2,
-                                                 (const uint32_t*)d_wc, (const uint32_t*)d_wnc,
-                                                 (const uint32_t*)d_adhc, nb16p, P, (const float*)d_bc, ls,
-                                                 (const int*)d_incr);
+                        cell_step_kernel<false, int16_t><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb16p, P, d_bc, ls, d_incr);
                     else
-                        cerr = launch_overlapped(cell_step_kernel<false, int>, blocks, CELL_THREADS, cap,
-                                                 (const int2*)d_cells, n_cells, cp, fin, fout, (const float2*)d_rho2,
-                                                 (const uint32_t*)d_wc, (const uint32_t*)d_wnc,
-                                                 (const uint32_t*)d_adhc, nb32p, P, (const float*)d_bc, ls,
-                                                 (const int*)d_incr);
+                        cell_step_kernel<false, int><<<blocks, CELL_THREADS, 0, cap>>>(
+                            d_cells, n_cells, cp, fin, fout, d_rho2, d_wc, d_wnc, d_adhc, nb32p, P, d_bc, ls, d_incr);
+                    cerr = cudaGetLastError();
                 }
                 if (cerr == cudaSuccess) {
                     const int c = (gi + sched->n_steps) & 1;
