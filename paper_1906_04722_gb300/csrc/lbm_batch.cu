@@ -1,4 +1,4 @@
-// lbm_batch.cu -- many pore throats per call (lbm_run_throat_batch), in three
+// lbm_batch.cu -- many pore throats per call (lbm_run_throat_batch), in four
 // forms that give the same rows bit for bit.
 //
 // The hybrid method runs one small LBM simulation per pore throat (Sec. 2.2.2)
@@ -11,7 +11,10 @@
 // populations of the non-solid cells only, compactly and after streaming, and
 // runs two launches per time step over that list: densities, then the
 // collision, which pushes every value to the cell it streams to.  A measurement
-// launch (a CTA per throat) ends each increment.
+// launch (a CTA per slice of a throat box) ends each increment.
+//
+// March.  The same cell list in one launch per time step: a CTA per chunk of a
+// throat's planes sums the densities of a plane and steps the plane below it.
 //
 // Tiles.  One launch per time step over a work list of (throat, active tile,
 // z segment) items of the box layout, the step_column of the single-domain
