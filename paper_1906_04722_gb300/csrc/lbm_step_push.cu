@@ -6,9 +6,10 @@
 // the other FP32 kernels): float2 F[nz][ny][19][nx], F[z][y][k][x] =
 // (f_k^w, f_k^nw) of cell (x, y, z) at the current time level, i.e. the
 // populations after streaming and before collision.  The 19 slots of a row of
-// cells follow one another, so that a box load reads 19 consecutive row
-// segments per row of cells instead of one segment in each of 19 arrays far
-// apart (DRAM serves the former about 12 % faster on this access pattern).  A cell's own 19 pairs are all it needs for its moments
+// cells follow one another, so that a box load reads 19 row segments within one
+// stretch of memory per row of cells instead of one segment in each of 19
+// arrays far apart (a plain-load streaming probe of this access pattern ran
+// 12 % faster in this layout; the step kernel's TMA loads gained 1.5-2 %).  A cell's own 19 pairs are all it needs for its moments
 // (Eqs. 2-3); streaming with half-way bounce-back (Eq. 1, left-hand side)
 // happens at the store: the post-collision f*_k of cell x goes to slot k of
 // x + e_k, or, when x + e_k is not fluid for the component, to slot kbar of x
