@@ -80,6 +80,12 @@ def test_new_entry_points_reject_bad_arguments_before_device_work(lib):
     rc = L.lbm_run_throat_batch(tri.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1, ctypes.byref(lib.make_params()),
                                 ctypes.byref(sch), res, rows, None)
     assert rc == lib.LBM_ERR_ARG
+    # the marching form's launch shape: 128, 256, 384 or 512 threads, 1 .. 64 planes
+    for march in ((100, 16), (256, 65), (256, -1), (-128, 8)):
+        with pytest.raises(lib.LbmError) as e:
+            lib.lbm_run_throat_batch(tri, lib.make_params(), [2.0], 1, 2.0, form=lib.BATCH_MARCH, march=march)
+        assert e.value.code == lib.LBM_ERR_ARG
+        assert "march" in lib.lbm_last_error()
 
 
 @pytest.mark.parametrize("field,value", [("tau", (0.5, 1.0)), ("precision", 3), ("membrane_layers", -1),
