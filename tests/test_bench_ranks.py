@@ -1,7 +1,10 @@
 """The multi-rank path of bench.py on CPU: two gloo ranks (the replicas a
 torchrun launch starts, one per GPU) agree on the slowest rank's time and
-report the whole job's rate; the reference arm runs on rank 0 only."""
+report the whole job's rate; the reference arm runs on rank 0 only, and its
+JSON line carries the keys the benchmark contract names."""
+import json
 import os
+import subprocess
 import socket
 import sys
 
@@ -65,3 +68,23 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args(), 1, 2) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_has_the_contract_keys():
+    """bench.py --impl reference (the FP64 oracle on the host cores) prints one
+    JSON line with the base keys, impl, cpu_baseline and an e2e object that
+    moves no bytes between host and device."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT, check=True).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
