@@ -9,6 +9,7 @@ missing and cannot be built, loading raises: there is no CPU fallback.
 """
 from __future__ import annotations
 
+import collections.abc
 import ctypes
 import os
 import threading
@@ -607,6 +608,33 @@ def lbm_throat_lattice_features(throats) -> np.ndarray:
     return out
 
 
+class ThroatRows(collections.abc.Sequence):
+    """The rows of a throat batch, throat by throat: item t is the list of that
+    throat's n_incr rows (dicts of lbm_increment's fields).  The rows stay in the
+    library's array until read; each throat's list is built on first access."""
+
+    def __init__(self, arr, n: int, n_incr: int):
+        self._arr, self._n, self._incr = arr, n, n_incr
+        self._built = {}
+
+    def __len__(self):
+        return self._n
+
+    def __getitem__(self, t):
+        if isinstance(t, slice):
+            return [self[i] for i in range(*t.indices(self._n))]
+        t = int(t)
+        if t < 0:
+            t += self._n
+        if not 0 <= t < self._n:
+            raise IndexError("throat index out of range")
+        out = self._built.get(t)
+        if out is None:
+            out = [self._arr[t * self._incr + i].as_dict() for i in range(self._incr)]
+            self._built[t] = out
+        return out
+
+
 def _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march=(0, 0)):
     lad = np.ascontiguousarray(np.asarray(rho_in_nw, dtype=np.float64))
     sch = lbm_schedule()
@@ -627,7 +655,8 @@ def _batch_schedule(n, rho_in_nw, n_steps, rho_out_w, form, march=(0, 0)):
 
 def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float, stream=None,
                          form: int = 0, march=(0, 0)):
-    """Batched per-throat drainage; returns (results: list of dict, rows: list of lists of dict).
+    """Batched per-throat drainage; returns (results: list of dict, rows: ThroatRows, a sequence whose
+    item t is the list of throat t's rows as dicts).
     rho_in_nw: one ladder (n_incr,) for all throats, or one per throat (n, n_incr).
     form: BATCH_AUTO, BATCH_PERSISTENT, BATCH_PER_STEP, BATCH_CELLS or BATCH_MARCH.
     march: (threads per CTA, planes per chunk) of BATCH_MARCH, 0 for the defaults."""
@@ -638,8 +667,7 @@ def lbm_run_throat_batch(throats, params: lbm_params, rho_in_nw, n_steps: int, r
     rows = (lbm_increment * (n * sch.n_incr))()
     _check(load().lbm_run_throat_batch(th.ctypes.data_as(_DP), n, ctypes.byref(params), ctypes.byref(sch), res, rows,
                                        stream if stream is not None else _torch_stream()), "lbm_run_throat_batch")
-    I = sch.n_incr
-    return [r.as_dict() for r in res], [[rows[t * I + i].as_dict() for i in range(I)] for t in range(n)]
+    return [r.as_dict() for r in res], ThroatRows(rows, n, sch.n_incr)
 
 
 def lbm_run_throat_batch_refined(throats, params: lbm_params, rho_in_nw, n_steps: int, rho_out_w: float,
@@ -656,8 +684,7 @@ def lbm_run_throat_batch_refined(throats, params: lbm_params, rho_in_nw, n_steps
                                                int(n_fine), res, rows, fine.ctypes.data_as(_DP),
                                                stream if stream is not None else _torch_stream()),
            "lbm_run_throat_batch_refined")
-    I = sch.n_incr
-    return [r.as_dict() for r in res], [[rows[t * I + i].as_dict() for i in range(I)] for t in range(n)], fine
+    return [r.as_dict() for r in res], ThroatRows(rows, n, sch.n_incr), fine
 
 
 def lbm_destroy(h):

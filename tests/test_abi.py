@@ -124,3 +124,26 @@ def test_null_domain_calls_rejected(lib):
     assert L.lbm_set_pressure_bc(None, 2.0, 2.0) == lib.LBM_ERR_ARG
     assert "NULL" in lib.lbm_last_error()
     L.lbm_destroy(None)  # ignored
+
+
+def test_throat_rows_sequence(lib):
+    """The batch's rows as the binding returns them: throat t's list of rows,
+    built from the library's array on first access, with len, negative indices,
+    slices and iteration of a list of lists."""
+    n, n_incr = 3, 4
+    arr = (lib.lbm_increment * (n * n_incr))()
+    for t in range(n):
+        for i in range(n_incr):
+            arr[t * n_incr + i].S_w = t + 0.1 * i
+            arr[t * n_incr + i].n_interface = 10 * t + i
+    rows = lib.ThroatRows(arr, n, n_incr)
+    assert len(rows) == n
+    assert rows[1][2]["S_w"] == 1.2 and rows[1][2]["n_interface"] == 12
+    assert rows[-1][0] == arr[2 * n_incr].as_dict()
+    assert rows[0:2] == [rows[0], rows[1]]
+    assert rows[1] is rows[1]  # built once
+    flat = []
+    flat += rows
+    assert flat == [[arr[t * n_incr + i].as_dict() for i in range(n_incr)] for t in range(n)]
+    with pytest.raises(IndexError):
+        rows[3]
