@@ -590,8 +590,9 @@ int lbm_get_tile(const lbm_domain* d, int* by, int* lz, int* lead);
  *   LBM_KERNEL_PUSH    the state is kept in a paired push layout (the two
  *                      components of a direction side by side, each cell's
  *                      populations at the current time level at its own
- *                      address; streaming with bounce-back happens at the
- *                      store); one thread per CTA loads each plane of a
+ *                      address, the 19 directions of a row of cells one row
+ *                      after another; streaming with bounce-back happens at
+ *                      the store); one thread per CTA loads each plane of a
  *                      32-column tile, all 19 directions, with one tensor
  *                      memory accelerator copy (FP32; boxes without periodic x
  *                      or y and with an even nx); lz planes per z segment
